@@ -1,0 +1,368 @@
+"""FP64 CPU oracle for the per-pulse beam-scene interaction (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+arm of ``bench.py`` import this package.  It shares no code with the CUDA
+library: its C source (``helios_oracle.c``) is compiled here with gcc and
+loaded through ctypes; the only thing both sides have in common is the seeded
+input module ``scenes``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "helios_oracle.c")
+_HDR = os.path.join(_HERE, "helios_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libhelios_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NO_WINDOW = -(2 ** 31)
+F_EDGE, F_TIE, F_VOX, F_WIN, F_ECHO, F_OBJ = 1, 2, 4, 8, 16, 32
+F_OVERFLOW, F_NOHIT = 256, 512
+F_GEOMETRY = F_EDGE | F_TIE | F_VOX | F_WIN        # waveform may differ
+F_DECISION = F_GEOMETRY | F_ECHO | F_OBJ           # echo lists may differ
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE double, no contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Scanner(C.Structure):
+    _fields_ = [("prf_hz", C.c_double), ("divergence_rad", C.c_double),
+                ("quality", C.c_int32), ("pulse_shape", C.c_int32),
+                ("wavelength_m", C.c_double), ("beam_waist_m", C.c_double), ("focus_m", C.c_double),
+                ("peak_power_w", C.c_double), ("receiver_diam_m", C.c_double),
+                ("eta_sys", C.c_double), ("eta_atm", C.c_double),
+                ("pulse_fwhm_ns", C.c_double), ("pulse_length_ns", C.c_double), ("bin_ns", C.c_double),
+                ("n_bins", C.c_int32), ("max_echoes", C.c_int32),
+                ("echo_threshold_rel", C.c_double), ("range_noise_sigma_m", C.c_double),
+                ("deflector", C.c_int32), ("grid_n_az", C.c_int32), ("grid_n_el", C.c_int32),
+                ("pad0", C.c_int32),
+                ("scan_freq_hz", C.c_double), ("scan_angle_max_rad", C.c_double),
+                ("head_rate_rad_s", C.c_double), ("el_min_rad", C.c_double), ("el_max_rad", C.c_double)]
+
+
+class Leg(C.Structure):
+    _fields_ = [("platform", C.c_int32), ("quality", C.c_int32), ("leg_id", C.c_uint32),
+                ("pad0", C.c_int32), ("start", C.c_double * 3), ("end", C.c_double * 3),
+                ("speed_mps", C.c_double), ("attitude_rpy", C.c_double * 3), ("t0", C.c_double),
+                ("n_pulses", C.c_int64)]
+
+
+class SceneIn(C.Structure):
+    _fields_ = [("n_tri", C.c_int64), ("tri", C.c_void_p), ("refl", C.c_void_p),
+                ("has_grid", C.c_int32), ("pad0", C.c_int32), ("g_origin", C.c_double * 3),
+                ("g_cell", C.c_double), ("g_dims", C.c_int32 * 3), ("pad1", C.c_int32),
+                ("g_density", C.c_void_p), ("g_G", C.c_double), ("g_leaf_refl", C.c_double)]
+
+
+class Out(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("window_bin", "waveform", "echo_count", "echo_bin",
+                                            "echo_amp", "echo_range", "echo_range_clean",
+                                            "echo_object", "subray_hit", "subray_range", "flags")]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = C.CDLL(build())
+            d3 = C.POINTER(C.c_double)
+            l.or_philox4x64_10.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+            l.or_uniform24.argtypes = [C.c_uint64]
+            l.or_uniform24.restype = C.c_double
+            l.or_subray_count.argtypes = [C.c_int]
+            l.or_subray_angles.argtypes = [C.c_int, C.c_double, C.c_int, d3, d3]
+            l.or_onb.argtypes = [d3, d3, d3]
+            l.or_pulse_ray.argtypes = [C.POINTER(Scanner), C.POINTER(Leg), C.c_int64, d3, d3]
+            l.or_subray_dir.argtypes = [C.POINTER(Scanner), C.c_int, C.c_int, d3, d3]
+            for f in ("or_beam_width",):
+                getattr(l, f).argtypes = [C.POINTER(Scanner), C.c_double]
+                getattr(l, f).restype = C.c_double
+            l.or_subray_intensity.argtypes = [C.POINTER(Scanner), C.c_double, C.c_double]
+            l.or_subray_intensity.restype = C.c_double
+            l.or_pulse_shape.argtypes = [C.POINTER(Scanner), C.c_double]
+            l.or_pulse_shape.restype = C.c_double
+            l.or_triangle_power.argtypes = [C.POINTER(Scanner)] + [C.c_double] * 4
+            l.or_triangle_power.restype = C.c_double
+            l.or_scene_build.argtypes = [C.POINTER(SceneIn)]
+            l.or_scene_build.restype = C.c_void_p
+            l.or_scene_free.argtypes = [C.c_void_p]
+            l.or_scene_bvh_nodes.argtypes = [C.c_void_p]
+            l.or_scene_bvh_nodes.restype = C.c_int64
+            l.or_intersect.argtypes = [C.c_void_p, d3, d3, d3, d3, C.POINTER(C.c_uint32)]
+            l.or_intersect.restype = C.c_int64
+            l.or_intersect_brute.argtypes = [C.c_void_p, d3, d3, d3, d3]
+            l.or_intersect_brute.restype = C.c_int64
+            l.or_march.argtypes = [C.c_void_p, d3, d3, C.c_double, C.c_int64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]
+            l.or_march.restype = C.c_int64
+            l.or_trace_returns.argtypes = [C.c_void_p, C.POINTER(Scanner), d3, d3, C.c_double,
+                                           C.c_int, C.c_uint64, C.c_uint32, C.c_int64, C.c_int,
+                                           C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.POINTER(C.c_uint32)]
+            l.or_trace_returns.restype = C.c_int64
+            l.or_scan.argtypes = [C.c_void_p, C.POINTER(Scanner), C.POINTER(Leg), C.c_void_p,
+                                  C.c_int64, C.c_int, C.c_uint64, C.c_void_p, C.POINTER(Out), C.c_int]
+            l.or_adjoint.argtypes = [C.c_void_p, C.POINTER(Scanner), C.POINTER(Leg), C.c_void_p,
+                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+            _lib = l
+    return _lib
+
+
+def _d3(x):
+    return (C.c_double * 3)(*[float(v) for v in x])
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def scanner_struct(sc) -> Scanner:
+    s = Scanner()
+    s.prf_hz = sc.prf_hz
+    s.divergence_rad = sc.divergence_rad
+    s.quality = sc.beam_sample_quality
+    s.pulse_shape = sc.pulse_shape
+    s.wavelength_m = sc.wavelength_m
+    s.beam_waist_m = sc.beam_waist_m
+    s.focus_m = sc.focus_m
+    s.peak_power_w = sc.peak_power_w
+    s.receiver_diam_m = sc.receiver_diam_m
+    s.eta_sys = sc.eta_sys
+    s.eta_atm = sc.eta_atm
+    s.pulse_fwhm_ns = sc.pulse_fwhm_ns
+    s.pulse_length_ns = sc.pulse_length_ns
+    s.bin_ns = sc.bin_ns
+    s.n_bins = sc.n_bins
+    s.max_echoes = sc.max_echoes
+    s.echo_threshold_rel = sc.echo_threshold_rel
+    s.range_noise_sigma_m = sc.range_noise_sigma_m
+    s.deflector = sc.deflector
+    s.grid_n_az = sc.grid_n_az
+    s.grid_n_el = sc.grid_n_el
+    s.scan_freq_hz = sc.scan_freq_hz
+    s.scan_angle_max_rad = sc.scan_angle_max_rad
+    s.head_rate_rad_s = sc.head_rate_rad_s
+    s.el_min_rad = sc.el_min_rad
+    s.el_max_rad = sc.el_max_rad
+    return s
+
+
+def leg_struct(lg) -> Leg:
+    l = Leg()
+    l.platform = lg.platform
+    l.quality = lg.beam_sample_quality
+    l.leg_id = lg.leg_id
+    l.start = _d3(lg.start)
+    l.end = _d3(lg.end)
+    l.speed_mps = lg.speed_mps
+    l.attitude_rpy = _d3(lg.attitude_rpy)
+    l.t0 = lg.t0
+    l.n_pulses = lg.n_pulses
+    return l
+
+
+class OracleScene:
+    """A scene (triangles of all meshes concatenated, at most one voxel grid) in FP64."""
+
+    def __init__(self, scene):
+        tris, refl = [], []
+        for m in scene.meshes:
+            tris.append(m.verts[m.faces.astype(np.int64)].reshape(-1, 9))
+            refl.append(m.reflectance)
+        self.tri = np.ascontiguousarray(np.concatenate(tris, 0) if tris else np.zeros((0, 9)),
+                                        dtype=np.float32)
+        self.refl = np.ascontiguousarray(np.concatenate(refl, 0) if refl else np.zeros(0),
+                                         dtype=np.float32)
+        self.n_tri = self.tri.shape[0]
+        self.mesh_offsets = np.cumsum([0] + [m.faces.shape[0] for m in scene.meshes])
+        si = SceneIn()
+        si.n_tri = self.n_tri
+        si.tri = _ptr(self.tri)
+        si.refl = _ptr(self.refl)
+        if len(scene.grids) > 1:
+            raise ValueError("the oracle handles at most one voxel grid per scene")
+        self.grid = scene.grids[0] if scene.grids else None
+        if self.grid is not None:
+            g = self.grid
+            self.density = np.ascontiguousarray(g.density, dtype=np.float32)
+            si.has_grid = 1
+            # the GPU receives FP32 origin/cell: use the same real numbers
+            si.g_origin = _d3(np.float32(g.origin).astype(np.float64))
+            si.g_cell = float(np.float32(g.cell))
+            si.g_dims = (C.c_int32 * 3)(*[int(x) for x in g.dims])
+            si.g_density = _ptr(self.density)
+            si.g_G = float(np.float32(g.G))
+            si.g_leaf_refl = float(np.float32(g.leaf_reflectance))
+            self.n_vox = int(np.prod(g.dims))
+        else:
+            self.density = None
+            self.n_vox = 0
+        self._si = si
+        self.handle = lib().or_scene_build(C.byref(si))
+
+    def set_density(self, density):
+        """Point the grid at another density array (same shape) without rebuilding."""
+        self.density = np.ascontiguousarray(density, dtype=np.float32)
+        self._si.g_density = _ptr(self.density)
+        lib().or_scene_free(self.handle)
+        self.handle = lib().or_scene_build(C.byref(self._si))
+
+    def close(self):
+        if self.handle:
+            lib().or_scene_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def intersect(self, o, d):
+        t, c = C.c_double(), C.c_double()
+        f = C.c_uint32(0)
+        i = lib().or_intersect(self.handle, _d3(o), _d3(d), C.byref(t), C.byref(c), C.byref(f))
+        return int(i), t.value, c.value, int(f.value)
+
+    def intersect_brute(self, o, d):
+        t, c = C.c_double(), C.c_double()
+        i = lib().or_intersect_brute(self.handle, _d3(o), _d3(d), C.byref(t), C.byref(c))
+        return int(i), t.value, c.value
+
+    def march(self, o, d, t_hi=math.inf, cap=100000):
+        vid = np.zeros(cap, np.int64)
+        ti = np.zeros(cap)
+        to = np.zeros(cap)
+        n = lib().or_march(self.handle, _d3(o), _d3(d), t_hi, cap, _ptr(vid), _ptr(ti), _ptr(to))
+        n = min(n, cap)
+        return vid[:n], ti[:n], to[:n]
+
+
+def trace_returns(oscene, scanner, o, ds, alpha=0.0, mode=0, seed=0, leg_id=0, pulse=0, s=0,
+                  cap=100000):
+    """Returns (R, P, id, flags) of one subray, in summation order."""
+    R = np.zeros(cap)
+    P = np.zeros(cap)
+    ids = np.zeros(cap, np.int64)
+    f = C.c_uint32(0)
+    sc = scanner_struct(scanner)
+    n = lib().or_trace_returns(oscene.handle, C.byref(sc), _d3(o), _d3(ds), float(alpha), int(mode),
+                               int(seed) & (2 ** 64 - 1), int(leg_id), int(pulse), int(s), cap,
+                               _ptr(R), _ptr(P), _ptr(ids), C.byref(f))
+    n = min(n, cap)
+    return R[:n], P[:n], ids[:n], int(f.value)
+
+
+def subray_count(q: int) -> int:
+    return int(lib().or_subray_count(q))
+
+
+def subray_angles(q, theta_r, s):
+    a, p = C.c_double(), C.c_double()
+    lib().or_subray_angles(q, theta_r, s, C.byref(a), C.byref(p))
+    return a.value, p.value
+
+
+def philox4x64_10(ctr, key):
+    c = (C.c_uint64 * 4)(*[int(x) & (2 ** 64 - 1) for x in ctr])
+    k = (C.c_uint64 * 2)(*[int(x) & (2 ** 64 - 1) for x in key])
+    o = (C.c_uint64 * 4)()
+    lib().or_philox4x64_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def onb(n):
+    u, v = (C.c_double * 3)(), (C.c_double * 3)()
+    lib().or_onb(_d3(n), u, v)
+    return np.array(u[:]), np.array(v[:])
+
+
+def pulse_ray(scanner, leg, k):
+    o, d = (C.c_double * 3)(), (C.c_double * 3)()
+    s, l = scanner_struct(scanner), leg_struct(leg)
+    lib().or_pulse_ray(C.byref(s), C.byref(l), int(k), o, d)
+    return np.array(o[:]), np.array(d[:])
+
+
+def subray_dir(scanner, q, s, d):
+    out = (C.c_double * 3)()
+    sc = scanner_struct(scanner)
+    lib().or_subray_dir(C.byref(sc), q, s, _d3(d), out)
+    return np.array(out[:])
+
+
+def beam_width(scanner, R):
+    return lib().or_beam_width(C.byref(scanner_struct(scanner)), R)
+
+
+def subray_intensity(scanner, R, alpha):
+    return lib().or_subray_intensity(C.byref(scanner_struct(scanner)), R, alpha)
+
+
+def pulse_shape(scanner, t_ns):
+    return lib().or_pulse_shape(C.byref(scanner_struct(scanner)), t_ns)
+
+
+def triangle_power(scanner, Is, R, refl, cos_inc):
+    return lib().or_triangle_power(C.byref(scanner_struct(scanner)), Is, R, refl, cos_inc)
+
+
+def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_window=None,
+         threads=0):
+    """Simulate the given pulse indices of one leg; returns a dict of numpy arrays."""
+    if pulses is None:
+        pulses = np.arange(leg.n_pulses, dtype=np.int64)
+    pulses = np.ascontiguousarray(pulses, dtype=np.int64)
+    n = pulses.shape[0]
+    q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else scanner.beam_sample_quality
+    S = subray_count(q)
+    nb, K = scanner.n_bins, scanner.max_echoes
+    r = dict(window_bin=np.zeros(n, np.int32), waveform=np.zeros((n, nb)),
+             echo_count=np.zeros(n, np.int32), echo_bin=np.zeros((n, K), np.int32),
+             echo_amp=np.zeros((n, K)), echo_range=np.zeros((n, K)),
+             echo_range_clean=np.zeros((n, K)), echo_object=np.zeros((n, K), np.int32),
+             subray_hit=np.zeros((n, S), np.int32), subray_range=np.zeros((n, S)),
+             flags=np.zeros(n, np.uint32))
+    out = Out(**{k: _ptr(v) for k, v in r.items()})
+    fw = None
+    if fixed_window is not None:
+        fw = np.ascontiguousarray(fixed_window, dtype=np.int32)
+    s, l = scanner_struct(scanner), leg_struct(leg)
+    lib().or_scan(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), n, int(mode),
+                  int(seed) & (2 ** 64 - 1), _ptr(fw), C.byref(out), int(threads))
+    r["pulses"] = pulses
+    r["S"] = S
+    return r
+
+
+def adjoint(oscene: OracleScene, scanner, leg, pulses, g, window, threads=0):
+    """dL/d(reflectance) [n_tri] and dL/d(density) [n_vox] for dL/dW = g (expected mode)."""
+    pulses = np.ascontiguousarray(pulses, dtype=np.int64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    window = np.ascontiguousarray(window, dtype=np.int32)
+    d_refl = np.zeros(oscene.n_tri)
+    d_dens = np.zeros(max(oscene.n_vox, 1))
+    s, l = scanner_struct(scanner), leg_struct(leg)
+    lib().or_adjoint(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), pulses.shape[0],
+                     _ptr(g), _ptr(window), _ptr(d_refl), _ptr(d_dens), int(threads))
+    return d_refl, d_dens[:oscene.n_vox]

@@ -1,0 +1,134 @@
+/* helios_oracle.h - FP64 CPU oracle of the per-pulse beam-scene interaction.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference the
+ * CUDA path is checked against.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline / reference arm of bench.py may load it.  It shares no source,
+ * header, table or helper with the CUDA library (include/helios.h and
+ * paper_2101_09154_gb300/csrc never include this file, and this file never
+ * includes theirs).
+ *
+ * Every quantity is computed in IEEE double precision.  Inputs arrive as the
+ * same FP32 arrays the GPU receives and are promoted on entry.
+ */
+#ifndef HELIOS_ORACLE_H
+#define HELIOS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double prf_hz;
+    double divergence_rad;       /* full angle at the 1/e^2 points (Sec. 3.4, Fig. subrays) */
+    int32_t quality;             /* beamSampleQuality q: number of subray rings */
+    int32_t pulse_shape;         /* 0 Gaussian (FWHM), 1 Eq. beam_time (t/tau)^2 e^{-t/tau} */
+    double wavelength_m, beam_waist_m, focus_m;
+    double peak_power_w, receiver_diam_m, eta_sys, eta_atm;
+    double pulse_fwhm_ns, pulse_length_ns, bin_ns;
+    int32_t n_bins, max_echoes;
+    double echo_threshold_rel, range_noise_sigma_m;
+    int32_t deflector, grid_n_az, grid_n_el, pad0;
+    double scan_freq_hz, scan_angle_max_rad, head_rate_rad_s, el_min_rad, el_max_rad;
+} or_scanner;
+
+typedef struct {
+    int32_t platform;            /* 0 static, 1 linear path */
+    int32_t quality;             /* -1: the scanner's */
+    uint32_t leg_id;
+    int32_t pad0;
+    double start[3], end[3];
+    double speed_mps;
+    double attitude_rpy[3];
+    double t0;
+    int64_t n_pulses;
+} or_leg;
+
+typedef struct {
+    int64_t n_tri;
+    const float* tri;            /* [n_tri][3][3] vertex coordinates */
+    const float* refl;           /* [n_tri] Lambertian reflectance */
+    int32_t has_grid, pad0;
+    double g_origin[3];
+    double g_cell;
+    int32_t g_dims[3], pad1;     /* nx, ny, nz */
+    const float* g_density;      /* [nz][ny][nx] plant area density */
+    double g_G;                  /* sigma = G * density */
+    double g_leaf_refl;
+} or_scene_in;
+
+typedef struct or_scene or_scene;
+
+typedef struct {
+    int32_t* window_bin;         /* [n]        first bin index m of the window, OR_NO_WINDOW: no return */
+    double* waveform;            /* [n][n_bins] */
+    int32_t* echo_count;         /* [n] */
+    int32_t* echo_bin;           /* [n][K]     bin within the window */
+    double* echo_amp;            /* [n][K] */
+    double* echo_range;          /* [n][K]     with range noise */
+    double* echo_range_clean;    /* [n][K]     without noise */
+    int32_t* echo_object;        /* [n][K]     primitive id (tri, or n_tri + voxel) */
+    int32_t* subray_hit;         /* [n][S]     event primitive, -1 none */
+    double* subray_range;        /* [n][S] */
+    uint32_t* flags;             /* [n]        OR_F_* */
+} or_out;
+
+#define OR_NO_WINDOW   INT32_MIN
+
+/* parity flags: conditions under which an FP32 result may legitimately differ */
+#define OR_F_EDGE      (1u << 0)  /* a candidate triangle within eps of an edge */
+#define OR_F_TIE       (1u << 1)  /* two hits within eps in t */
+#define OR_F_VOX       (1u << 2)  /* a transmission decision within eps */
+#define OR_F_WIN       (1u << 3)  /* window start within eps of a bin boundary */
+#define OR_F_ECHO      (1u << 4)  /* a local-max / threshold decision within tolerance */
+#define OR_F_OBJ       (1u << 5)  /* echo object argmax near-tie */
+#define OR_F_OVERFLOW  (1u << 8)  /* more echoes than max_echoes */
+#define OR_F_NOHIT     (1u << 9)  /* no subray returned */
+
+void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+double or_uniform24(uint64_t w);
+int or_subray_count(int q);
+int or_subray_angles(int q, double theta_r, int s, double* alpha, double* phi);
+void or_onb(const double n[3], double u[3], double v[3]);
+void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, double o[3], double d[3]);
+void or_subray_dir(const or_scanner* sn, int q, int s, const double d[3], double ds[3]);
+double or_beam_width(const or_scanner* sn, double R);
+double or_subray_intensity(const or_scanner* sn, double R, double alpha);
+double or_pulse_shape(const or_scanner* sn, double t_ns);
+double or_triangle_power(const or_scanner* sn, double Is, double R, double refl, double cos_inc);
+
+or_scene* or_scene_build(const or_scene_in* in);
+void or_scene_free(or_scene* sc);
+int64_t or_scene_bvh_nodes(const or_scene* sc);
+
+/* closest hit; returns id (-1 none), t, |cos incidence|, parity flags */
+int64_t or_intersect(const or_scene* sc, const double o[3], const double d[3],
+                     double* t, double* cos_inc, uint32_t* flags);
+int64_t or_intersect_brute(const or_scene* sc, const double o[3], const double d[3],
+                           double* t, double* cos_inc);
+/* voxels crossed with positive length before t_hi: ids, t_in, t_out; returns count */
+int64_t or_march(const or_scene* sc, const double o[3], const double d[3], double t_hi,
+                 int64_t cap, int64_t* vid, double* t_in, double* t_out);
+
+/* the returns (range, power, primitive) of one subray from origin o along unit ds */
+int64_t or_trace_returns(const or_scene* sc, const or_scanner* sn, const double o[3],
+                         const double ds[3], double alpha, int mode, uint64_t seed, uint32_t leg_id,
+                         int64_t pulse, int s, int64_t cap, double* R, double* P, int64_t* id,
+                         uint32_t* flags);
+
+/* mode 0 stochastic, 1 expected.  fixed_window (nullable) holds the window
+ * start per pulse.  n_threads <= 0: all online cores. */
+int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
+            const int64_t* pulses, int64_t n, int mode, uint64_t seed,
+            const int32_t* fixed_window, const or_out* out, int n_threads);
+
+/* adjoint of the expected-mode waveform: g = dL/dW [n][n_bins], window held
+ * fixed.  Accumulates into d_refl [n_tri] and d_density [nz*ny*nx]. */
+int or_adjoint(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
+               const int64_t* pulses, int64_t n, const double* g, const int32_t* window,
+               double* d_refl, double* d_density, int n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

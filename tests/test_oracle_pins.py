@@ -1,0 +1,539 @@
+"""Pins for the FP64 oracle: facts fixed by the paper or by mathematics,
+independent of the oracle's own code (CPU only).
+
+Each test names the passage or the closed form it relies on.  A plausible
+mistake in the oracle (a dropped term, a wrong sign, a swapped axis, an
+off-by-one ring) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C_LIGHT = 299792458.0
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+# --------------------------------------------------------------------------
+# counter-based generator
+# --------------------------------------------------------------------------
+
+def test_philox_matches_numpy_independent_implementation():
+    """Philox4x64-10 (Salmon et al. 2011) against numpy's own implementation.
+
+    numpy's bit generator increments its 256-bit counter before each block,
+    so a generator started at ``ctr - 1`` emits block ``ctr`` first.
+    """
+    rng = np.random.default_rng(1234)
+    for _ in range(200):
+        ctr = [int(x) for x in rng.integers(0, 2 ** 63, size=4, dtype=np.int64)]
+        ctr[0] = max(ctr[0], 1)
+        key = [int(x) for x in rng.integers(0, 2 ** 63, size=2, dtype=np.int64)]
+        mine = oracle.philox4x64_10(ctr, key)
+        prev = [ctr[0] - 1] + ctr[1:]
+        ref = [int(x) for x in np.random.Philox(counter=prev, key=key).random_raw(4)]
+        assert mine == ref
+
+
+def test_uniform24_open_interval_and_fp32_exact():
+    lib = oracle.lib()
+    for w in [0, 1, 2 ** 40 - 1, 2 ** 40, 2 ** 64 - 1, 0x8000000000000000]:
+        u = lib.or_uniform24(w)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u          # identical in FP32 and FP64
+
+
+# --------------------------------------------------------------------------
+# subrays (Sec. 3.4)
+# --------------------------------------------------------------------------
+
+def test_subray_counts_match_paper_caption():
+    for q, count in _golden("subray_counts.txt"):
+        assert oracle.subray_count(int(q)) == int(count)
+
+
+def test_subray_counts_small_q():
+    # centre + 6 + 12 (+ 18) subrays: the 19-subray beam with rings at half and
+    # full divergence radius, and the q = 3 beam of the paper's timing runs
+    assert [oracle.subray_count(q) for q in range(4)] == [1, 7, 19, 37]
+
+
+def test_subray_ring_geometry():
+    sc = scenes.Scanner(divergence_rad=0.3e-3)
+    rng = np.random.default_rng(5)
+    for q in (1, 2, 3, 5):
+        S = oracle.subray_count(q)
+        for _ in range(5):
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            u, v = oracle.onb(d)
+            ring_of = []
+            for s in range(S):
+                alpha, phi = oracle.subray_angles(q, 0.15e-3, s)
+                ds = oracle.subray_dir(sc, q, s, d)
+                assert abs(np.linalg.norm(ds) - 1.0) < 1e-14
+                # angular offset from the pulse axis equals the ring angle
+                ang = math.atan2(np.linalg.norm(np.cross(d, ds)), float(np.dot(d, ds)))
+                assert abs(ang - alpha) < 1e-12
+                if s > 0:
+                    # azimuth in the (u, v) frame equals phi
+                    az = math.atan2(float(np.dot(ds, v)), float(np.dot(ds, u))) % (2 * math.pi)
+                    assert abs((az - phi + math.pi) % (2 * math.pi) - math.pi) < 1e-6
+                ring_of.append(round(alpha / 0.15e-3 * q))
+            # ring i holds floor(2 pi i) subrays, outermost at the full radius
+            counts = np.bincount(ring_of)
+            assert counts[0] == 1
+            for i in range(1, q + 1):
+                assert counts[i] == math.floor(2 * math.pi * i)
+
+
+@pytest.mark.parametrize("n", [(0, 0, 1), (0, 0, -1), (1, 0, 0), (1, 0, -0.0), (0.6, 0.0, 0.8),
+                               (-0.3, 0.9, -0.3162277660168379)])
+def test_onb_is_right_handed_orthonormal(n):
+    n = np.array(n, float)
+    n /= np.linalg.norm(n)
+    u, v = oracle.onb(n)
+    M = np.stack([u, v, n])
+    assert np.allclose(M @ M.T, np.eye(3), atol=1e-15)
+    assert np.allclose(np.cross(u, v), n, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# pulses: platform (Sec. 3.2) and deflectors (Sec. 3.3)
+# --------------------------------------------------------------------------
+
+def test_tls_grid_directions():
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=8, grid_n_el=5,
+                        el_min_rad=-0.5, el_max_rad=0.7)
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(1.0, 2.0, 3.0), n_pulses=40)
+    for i in range(8):
+        for j in range(5):
+            o, d = oracle.pulse_ray(sc, leg, i * 5 + j)
+            az = 2 * math.pi * i / 8
+            el = -0.5 + 1.2 * j / 4
+            assert np.allclose(o, [1, 2, 3])
+            assert np.allclose(d, [math.cos(el) * math.cos(az), math.cos(el) * math.sin(az),
+                                   math.sin(el)], atol=1e-15)
+
+
+def test_linear_platform_position_heading_and_mirror():
+    f = 50.0
+    amax = math.radians(20)
+    sc = scenes.Scanner(prf_hz=1000.0, deflector=scenes.DEFL_OSCILLATING, scan_freq_hz=f,
+                        scan_angle_max_rad=amax)
+    # flight along +y: heading 90 deg, the platform's left (+y) maps to world -x
+    leg = scenes.Leg(platform=scenes.PLATFORM_LINEAR, start=(0, 0, 100), end=(0, 100, 100),
+                     speed_mps=10.0, n_pulses=100000)
+    o, d = oracle.pulse_ray(sc, leg, 0)
+    assert np.allclose(o, [0, 0, 100]) and np.allclose(d, [0, 0, -1], atol=1e-15)
+    k = 5  # t = 5 ms = 1/(4 f): swing at +amax
+    o, d = oracle.pulse_ray(sc, leg, k)
+    assert np.allclose(o, [0, 10.0 * k / 1000.0, 100])
+    assert np.allclose(d, [-math.sin(amax), 0, -math.cos(amax)], atol=1e-12)
+    # past the end of the leg the platform waits at the waypoint
+    o, _ = oracle.pulse_ray(sc, leg, 20000)
+    assert np.allclose(o, [0, 100, 100])
+
+
+def _scan_angles(deflector, n=20000):
+    sc = scenes.Scanner(prf_hz=n * 10.0, deflector=deflector, scan_freq_hz=10.0,
+                        scan_angle_max_rad=math.radians(30))
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(0, 0, 0))
+    th = []
+    for k in range(n):
+        _, d = oracle.pulse_ray(sc, leg, k)
+        th.append(math.atan2(d[1], -d[2]))
+    return np.array(th)
+
+
+def test_swinging_mirror_denser_at_extrema_polygon_even():
+    """Sec. 3.3: a swinging mirror yields higher point density at the extrema,
+    a polygon mirror even density along parallel lines."""
+    h, _ = np.histogram(_scan_angles(scenes.DEFL_OSCILLATING), bins=10)
+    assert h[0] > 2 * h[5] and h[-1] > 2 * h[4]
+    h, _ = np.histogram(_scan_angles(scenes.DEFL_POLYGON), bins=10)
+    assert h.max() - h.min() <= 0.02 * h.mean() + 2
+
+
+# --------------------------------------------------------------------------
+# beam and radar equation (Eq. beamdiv, Eq. beamdiv_w, Eq. ladlut_intensity)
+# --------------------------------------------------------------------------
+
+def test_gaussian_beam_width_textbook():
+    sc = scenes.Scanner(divergence_rad=0.3e-3, wavelength_m=1064e-9, focus_m=7.0)
+    w0 = 1064e-9 / (math.pi * 0.15e-3)
+    assert abs(w0 - 2.2578e-3) < 1e-6
+    zr = math.pi * w0 ** 2 / 1064e-9
+    assert abs(zr - 15.05) < 0.01
+    assert abs(oracle.beam_width(sc, 7.0) - w0) < 1e-15             # waist at the focus
+    assert abs(oracle.beam_width(sc, 7.0 + zr) / w0 - math.sqrt(2)) < 1e-12  # Rayleigh range
+    R = 1e6
+    assert abs(oracle.beam_width(sc, R) / ((R - 7.0) * 0.15e-3) - 1) < 1e-9   # far-field cone
+
+
+def test_subray_intensity_one_over_e2_at_divergence_radius():
+    sc = scenes.Scanner(divergence_rad=0.3e-3, peak_power_w=2.0)
+    assert oracle.subray_intensity(sc, 500.0, 0.0) == 2.0
+    # far field: the ring at theta_r = divergence/2 sits on the 1/e^2 contour
+    assert abs(oracle.subray_intensity(sc, 1e5, 0.15e-3) / 2.0 - math.exp(-2)) < 1e-6
+
+
+def test_radar_equation_with_lambertian_cross_section():
+    """Eq. ladlut_intensity, P = lambda sigma P0 alpha^2 / (4 pi d^4 beta^2), with the
+    extended Lambertian cross-section sigma = pi rho d^2 beta^2 cos(theta): beta cancels."""
+    sc = scenes.Scanner(receiver_diam_m=0.12, eta_sys=0.8, eta_atm=0.95)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        I, R, rho, c = rng.uniform(0.1, 3), rng.uniform(1, 800), rng.uniform(0, 1), rng.uniform(0, 1)
+        for beta in (1e-4, 3e-4, 2e-3):
+            sigma = math.pi * rho * R ** 2 * beta ** 2 * c
+            expect = (0.8 * 0.95) * sigma * I * 0.12 ** 2 / (4 * math.pi * R ** 4 * beta ** 2)
+            got = oracle.triangle_power(sc, I, R, rho, c)
+            assert abs(got - expect) <= 1e-12 * expect
+
+
+def test_pulse_shapes():
+    g = scenes.Scanner(pulse_shape=scenes.PULSE_GAUSSIAN, pulse_fwhm_ns=4.0)
+    assert oracle.pulse_shape(g, 0.0) == 1.0
+    assert abs(oracle.pulse_shape(g, 2.0) - 0.5) < 1e-15
+    assert abs(oracle.pulse_shape(g, -2.0) - 0.5) < 1e-15
+    # Eq. beam_time with tau = pulse length / 1.75: peak 4/e^2 at t = 2 tau, area 2 tau
+    c = scenes.Scanner(pulse_shape=scenes.PULSE_CARLSSON, pulse_length_ns=3.5)
+    tau = 2.0
+    assert abs(oracle.pulse_shape(c, 2 * tau) - 4 * math.exp(-2)) < 1e-15
+    ts = np.linspace(0, 80, 80001)
+    vals = np.array([oracle.pulse_shape(c, t) for t in ts])
+    assert abs(ts[np.argmax(vals)] - 2 * tau) < 1e-3
+    assert abs(np.trapezoid(vals, ts) - 2 * tau) < 1e-6
+    assert oracle.pulse_shape(c, -0.1) == 0.0
+
+
+# --------------------------------------------------------------------------
+# intersection (Sec. 5.1)
+# --------------------------------------------------------------------------
+
+def test_bvh_matches_brute_force_on_random_soups():
+    rng = np.random.default_rng(11)
+    for seed in range(40):
+        n = int(rng.integers(1, 400))
+        osc = oracle.OracleScene(scenes.triangle_soup(seed, n))
+        for _ in range(50):
+            o = rng.uniform(-15, 15, 3)
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            i, t, c, f = osc.intersect(o, d)
+            j, t2, c2 = osc.intersect_brute(o, d)
+            if f:
+                continue
+            assert i == j
+            if i >= 0:
+                assert t == t2 and c == c2
+        osc.close()
+
+
+def test_plane_range_and_incidence_closed_form():
+    D = 37.5
+    osc = oracle.OracleScene(scenes.flat_target(D, 0.0, half=1000.0))
+    o = np.array([0.3, -0.1, 0.0])          # off the plate's shared diagonal
+    for phi in np.radians([0, 5, 17, 33, 60]):
+        d = np.array([0.0, math.sin(phi), -math.cos(phi)])
+        i, t, c, f = osc.intersect(o, d)
+        assert i >= 0 and f == 0
+        assert abs(t - D / math.cos(phi)) < 1e-12 * t
+        assert abs(c - math.cos(phi)) < 1e-14
+    for tilt in np.radians([10, 25, 50]):
+        osc = oracle.OracleScene(scenes.flat_target(D, tilt, half=16.0))
+        i, t, c, f = osc.intersect(o, [0.0, 0.0, -1.0])
+        # plane through (0, 0, -D) with normal (0, -sin, cos): z = -D + y tan(tilt);
+        # the corners are FP32, which moves the plane by at most ~ulp(40 m)
+        assert f == 0
+        assert abs(t - (D - o[1] * math.tan(tilt))) < 1e-5
+        assert abs(c - math.cos(tilt)) < 1e-6
+
+
+def test_edge_flag_on_shared_edge():
+    # the diagonal of the 2-triangle plate is shared: a ray through it is flagged
+    osc = oracle.OracleScene(scenes.flat_target(10.0, 0.0, half=5.0))
+    d = np.array([0.3, 0.3, -10.0])
+    d /= np.linalg.norm(d)
+    _, _, _, f = osc.intersect([0, 0, 0], d)
+    assert f & oracle.F_EDGE
+    d = np.array([0.3, -0.1, -10.0])
+    d /= np.linalg.norm(d)
+    _, _, _, f = osc.intersect([0, 0, 0], d)
+    assert f == 0
+
+
+# --------------------------------------------------------------------------
+# voxels (Sec. 3.5.4, Sec. 5.2)
+# --------------------------------------------------------------------------
+
+def _grid_scene(dens, origin=(-1.0, -1.0, -1.0), cell=0.5, ground_z=None, G=0.5, refl=0.3):
+    nz, ny, nx = dens.shape
+    grid = scenes.VoxelGrid(origin=origin, cell=cell, dims=(nx, ny, nz),
+                            density=np.ascontiguousarray(dens, np.float32), G=G,
+                            leaf_reflectance=0.5)
+    meshes = []
+    if ground_z is not None:
+        gv = np.array([[-500, -500, ground_z], [500, -500, ground_z], [500, 500, ground_z],
+                       [-500, 500, ground_z]], float)
+        meshes.append(scenes.Mesh(gv.astype(np.float32), np.array([[0, 1, 2], [0, 2, 3]], np.int32),
+                                  np.full(2, refl, np.float32)))
+    return scenes.Scene(meshes=meshes, grids=[grid])
+
+
+def test_march_matches_per_voxel_slab_brute_force():
+    rng = np.random.default_rng(2)
+    dims = (5, 4, 3)
+    dens = np.ones(dims[::-1], np.float32)
+    osc = oracle.OracleScene(_grid_scene(dens, origin=(-1.0, -1.0, -1.0), cell=0.5))
+    lo = np.array([-1.0, -1.0, -1.0])
+    for _ in range(300):
+        o = rng.uniform(-4, 4, 3)
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        vid, ti, to = osc.march(o, d)
+        # brute force: every voxel box, exact slab interval, positive length, t >= 0
+        ref = []
+        for z in range(3):
+            for y in range(4):
+                for x in range(5):
+                    a = lo + 0.5 * np.array([x, y, z])
+                    b = a + 0.5
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        t1 = (a - o) / d
+                        t2 = (b - o) / d
+                    tin = max(0.0, np.max(np.minimum(t1, t2)))
+                    tout = np.min(np.maximum(t1, t2))
+                    if tout - tin > 1e-9:
+                        ref.append((tin, (z * 4 + y) * 5 + x, tout))
+        ref.sort()
+        got = [(a, int(v), b) for a, v, b in zip(ti, vid, to) if b - a > 1e-9]
+        assert [r[1] for r in ref] == [g[1] for g in got]
+        for r, g in zip(ref, got):
+            assert abs(r[0] - g[0]) < 1e-12 and abs(r[2] - g[2]) < 1e-12
+
+
+def _f32(x):
+    """The real number an FP32 input actually holds."""
+    return float(np.float32(x))
+
+
+def _voxel_power_unit(sc, R, alpha=0.0):
+    Is = oracle.subray_intensity(sc, R, alpha)
+    return oracle.triangle_power(sc, Is, R, 0.5, 1.0)
+
+
+def test_expected_mode_transmittance_is_exp_minus_sigma_path():
+    """Eq. intersection_dist in expectation: a slab of density d, thickness L,
+    projection factor G transmits exp(-G d L) to the target behind it."""
+    sc = scenes.Scanner()
+    dens = np.full((4, 40, 40), 1.3, np.float32)   # 4 layers of 0.5 m, 20 x 20 m wide
+    osc = oracle.OracleScene(_grid_scene(dens, origin=(-10.0, -10.0, 0.0), cell=0.5, ground_z=-2.0))
+    bare = oracle.OracleScene(_grid_scene(np.zeros_like(dens), origin=(-10.0, -10.0, 0.0), cell=0.5,
+                                          ground_z=-2.0))
+    for phi in np.radians([0.0, 10.0, 20.0]):
+        d = np.array([0.0, math.sin(phi), -math.cos(phi)])
+        o = np.array([0.0, -12.0 * math.tan(phi), 10.0])
+        R, P, ids, _ = oracle.trace_returns(osc, sc, o, d, mode=1)
+        R0, P0, ids0, _ = oracle.trace_returns(bare, sc, o, d, mode=1)
+        assert ids[-1] == ids0[-1] >= 0 and len(P0) == 1
+        # path inside the slab: 2 m thick along z
+        L = 2.0 / math.cos(phi)
+        assert abs(P[-1] / P0[0] - math.exp(-0.5 * _f32(1.3) * L)) < 1e-12
+        # voxel weights + transmitted weight = 1 (nothing is created or lost)
+        w = [p / _voxel_power_unit(sc, r) for r, p in zip(R[:-1], P[:-1])]
+        assert abs(sum(w) + P[-1] / P0[0] - 1.0) < 1e-12
+
+
+def test_expected_mode_transmittance_multiplies_across_layers():
+    sc = scenes.Scanner()
+    dens = np.zeros((3, 1, 1), np.float32)
+    dens[0], dens[1], dens[2] = 0.7, 0.0, 2.1        # layers 1 m each (bottom to top)
+    osc = oracle.OracleScene(_grid_scene(dens, origin=(-0.5, -0.5, 0.0), cell=1.0, ground_z=-1.0))
+    bare = oracle.OracleScene(_grid_scene(np.zeros_like(dens), origin=(-0.5, -0.5, 0.0), cell=1.0,
+                                          ground_z=-1.0))
+    d = np.array([0.0, 0.0, -1.0])
+    R, P, ids, _ = oracle.trace_returns(osc, sc, [0, 0, 5.0], d, mode=1)
+    R0, P0, _, _ = oracle.trace_returns(bare, sc, [0, 0, 5.0], d, mode=1)
+    assert len(P) == 3   # two non-empty voxels + ground
+    assert abs(P[-1] / P0[0] - math.exp(-0.5 * _f32(2.1)) * math.exp(-0.5 * _f32(0.7))) < 1e-13
+    # each voxel returns at its segment midpoint
+    assert abs(R[0] - 2.5) < 1e-12 and abs(R[1] - 4.5) < 1e-12
+
+
+def test_stochastic_transmission_frequency_binomial():
+    """Eq. intersection_dist: the probability to cross the slab is exp(-G d L)."""
+    sc = scenes.Scanner()
+    dens = np.full((2, 1, 1), 0.8, np.float32)
+    osc = oracle.OracleScene(_grid_scene(dens, origin=(-0.5, -0.5, 0.0), cell=1.0, ground_z=-1.0))
+    n = 20000
+    hits_ground = 0
+    depths = []
+    for k in range(n):
+        R, P, ids, f = oracle.trace_returns(osc, sc, [0, 0, 5.0], [0, 0, -1.0], mode=0, seed=77,
+                                            leg_id=3, pulse=k, s=0)
+        assert len(R) == 1
+        if ids[0] < osc.n_tri:
+            hits_ground += 1
+        else:
+            depths.append(R[0] - 3.0)
+    p = math.exp(-0.5 * _f32(0.8) * 2.0)
+    sd = math.sqrt(n * p * (1 - p))
+    assert abs(hits_ground - n * p) < 5 * sd
+    # stop depth inside the slab is exponential with rate sigma, truncated at 2 m
+    sig = 0.5 * _f32(0.8)
+    mean_trunc = 1 / sig - 2.0 * math.exp(-2 * sig) / (1 - math.exp(-2 * sig))
+    depths = np.array(depths)
+    assert abs(depths.mean() - mean_trunc) < 5 * depths.std() / math.sqrt(len(depths))
+
+
+# --------------------------------------------------------------------------
+# waveform and echoes (Sec. 3.4, Sec. 3.7)
+# --------------------------------------------------------------------------
+
+def _nadir_leg(n=1, el_lo=-math.pi / 2, el_hi=-math.pi / 2):
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=1, grid_n_el=n,
+                        el_min_rad=el_lo, el_max_rad=el_hi, n_bins=200, beam_sample_quality=0)
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(0, 0, 0), n_pulses=n)
+    return sc, leg
+
+
+def test_single_flat_target_waveform_area_and_echo():
+    D = 23.456
+    sc, leg = _nadir_leg()
+    osc = oracle.OracleScene(scenes.flat_target(D, 0.0, half=100.0))
+    r = oracle.scan(osc, sc, leg, mode=0, seed=1)
+    assert r["echo_count"][0] == 1
+    P = oracle.triangle_power(sc, sc.peak_power_w, D, 0.5, 1.0)
+    W = r["waveform"][0]
+    m = r["window_bin"][0]
+    tau = 2 * D / C_LIGHT * 1e9
+    sig = 4.0 / (2 * math.sqrt(2 * math.log(2)))
+    # the bin sum is the Gaussian's integral from the window start t0, plus the
+    # Euler-Maclaurin endpoint terms at t0 (the window clips the leading tail)
+    dt = sc.bin_ns
+    t0 = m * dt
+    x0 = t0 - tau
+    f0 = P * math.exp(-x0 * x0 / (2 * sig * sig))
+    df0 = -f0 * x0 / (sig * sig)
+    integral = P * sig * math.sqrt(2 * math.pi) * 0.5 * math.erfc(x0 / (sig * math.sqrt(2)))
+    expect = integral + 0.5 * dt * f0 - dt * dt / 12.0 * df0
+    assert abs(W.sum() * dt - expect) < 1e-7 * expect
+    # the echo sits on the bin nearest to the delay: within half a bin in range
+    b = r["echo_bin"][0, 0]
+    assert abs((m + b) * sc.bin_ns - tau) <= 0.5 * sc.bin_ns + 1e-12
+    assert abs(r["echo_range_clean"][0, 0] - D) <= C_LIGHT * sc.bin_ns * 1e-9 / 4 + 1e-9
+    assert r["echo_object"][0, 0] in (0, 1)
+
+
+def test_two_targets_in_one_footprint_give_two_echoes():
+    """Sec. 3.4: parts of the footprint on different targets give separate echoes."""
+    D1, D2 = 20.0, 26.0
+    sc, leg = _nadir_leg()
+    sc.beam_sample_quality = 2
+    sc.divergence_rad = 0.3e-3
+    near = np.array([[-5, 0.0005, -D1], [5, 0.0005, -D1], [5, 5, -D1], [-5, 5, -D1]], np.float32)
+    far = np.array([[-50, -50, -D2], [50, -50, -D2], [50, 50, -D2], [-50, 50, -D2]], np.float32)
+    F = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    scene = scenes.Scene(meshes=[scenes.Mesh(near, F, np.full(2, 0.5, np.float32)),
+                                 scenes.Mesh(far, F, np.full(2, 0.5, np.float32))])
+    osc = oracle.OracleScene(scene)
+    r = oracle.scan(osc, sc, leg, mode=0, seed=1)
+    assert r["echo_count"][0] == 2
+    got = sorted(r["echo_range_clean"][0, :2])
+    half_bin = C_LIGHT * sc.bin_ns * 1e-9 / 4
+    assert abs(got[0] - D1) < half_bin + 1e-6 and abs(got[1] - D2) < half_bin + 2e-6
+    hits = r["subray_hit"][0]
+    assert set(hits[hits >= 0] // 2) == {0, 1}   # both plates are hit by some subrays
+
+
+def test_range_noise_is_normal_with_scanner_sigma():
+    """Sec. 3.7: each range gets a N(0, sigma) error; Box-Muller on Philox draws."""
+    n = 4000
+    sc, leg = _nadir_leg(n, -math.radians(89.0), -math.radians(88.0))
+    osc = oracle.OracleScene(scenes.flat_target(30.0, 0.0, half=100.0))
+    r = oracle.scan(osc, sc, leg, mode=0, seed=9)
+    assert (r["echo_count"] == 1).all()
+    e = r["echo_range"][:, 0] - r["echo_range_clean"][:, 0]
+    assert abs(e.mean()) < 5 * 0.01 / math.sqrt(n)
+    assert abs(e.std() / 0.01 - 1) < 0.06
+    assert abs(np.mean(e ** 4) / np.mean(e ** 2) ** 2 - 3) < 0.3   # Gaussian kurtosis
+
+
+def test_scan_is_deterministic_and_thread_independent():
+    w = scenes.tls_tiny(n_az=30, n_el=30)
+    osc = oracle.OracleScene(w.scenes[0])
+    a = oracle.scan(osc, w.scanners[0], w.legs[0], threads=1, seed=5)
+    b = oracle.scan(osc, w.scanners[0], w.legs[0], threads=7, seed=5)
+    for k in ("waveform", "echo_range", "subray_hit", "flags", "window_bin"):
+        assert np.array_equal(a[k], b[k])
+
+
+# --------------------------------------------------------------------------
+# adjoint (expected mode): analytic gradient vs central differences in FP64
+# --------------------------------------------------------------------------
+
+def test_adjoint_matches_central_differences():
+    w = scenes.uls_voxels(seed=4, n=24, n_pulses=4000, n_bins=256, agl=8.0, speed=1.0, prf=2000.0)
+    w.scanners[0].beam_sample_quality = 1
+    scene = w.scenes[0]
+    sc, leg = w.scanners[0], w.legs[0]
+    pulses = np.arange(0, 4000, 250, dtype=np.int64)
+    osc = oracle.OracleScene(scene)
+    base = scene.grids[0].density.copy()
+    ref_d = scenes.perturbed_density(base, seed=1)
+    osc.set_density(ref_d)
+    W_ref = oracle.scan(osc, sc, leg, pulses, mode=1)["waveform"]
+    osc.set_density(base)
+    fwd = oracle.scan(osc, sc, leg, pulses, mode=1)
+    win = fwd["window_bin"]
+    assert (win != oracle.NO_WINDOW).all()
+    g = 2.0 * (fwd["waveform"] - W_ref)
+    d_refl, d_dens = oracle.adjoint(osc, sc, leg, pulses, g, win)
+
+    def loss(dens=None, refl=None):
+        if refl is not None:
+            scene.meshes[0].reflectance[:] = refl
+            o2 = oracle.OracleScene(scene)
+        else:
+            o2 = osc
+            o2.set_density(dens)
+        W = oracle.scan(o2, sc, leg, pulses, mode=1, fixed_window=win)["waveform"]
+        return float(((W - W_ref) ** 2).sum())
+
+    touched = np.nonzero(d_dens)[0]
+    assert len(touched) > 20
+    rng = np.random.default_rng(2)
+    for v in rng.choice(touched, 12, replace=False):
+        x = float(base.ravel()[v])
+        h = 1e-4 * max(abs(x), 1e-2)
+        dp = base.copy().ravel(); dp[v] = np.float32(x + h)
+        dm = base.copy().ravel(); dm[v] = np.float32(x - h)
+        hh = (float(dp[v]) - float(dm[v])) / 2
+        fd = (loss(dens=dp.reshape(base.shape)) - loss(dens=dm.reshape(base.shape))) / (2 * hh)
+        assert abs(fd - d_dens[v]) <= 1e-5 * abs(d_dens[v]) + 1e-9 * np.abs(d_dens).max()
+    osc.set_density(base)
+    refl0 = scene.meshes[0].reflectance.copy()
+    for t in range(2):
+        h = 1e-3
+        rp = refl0.copy(); rp[t] += np.float32(h)
+        rm = refl0.copy(); rm[t] -= np.float32(h)
+        hh = (float(rp[t]) - float(rm[t])) / 2
+        fd = (loss(refl=rp) - loss(refl=rm)) / (2 * hh)
+        assert abs(fd - d_refl[t]) <= 1e-6 * abs(d_refl[t]) + 1e-12
+    scene.meshes[0].reflectance[:] = refl0
