@@ -1,0 +1,409 @@
+// bvh.cu - on-device LBVH build for the scene's triangles.
+//
+// Sec. 5.1 of the paper uses a recursive kD-tree built on the CPU.  Here the
+// acceleration structure is built on the GPU in a handful of data-parallel
+// passes (Karras, "Maximizing parallelism in the construction of BVHs,
+// octrees, and k-d trees", HPG 2012):
+//   gather   faces -> triangle records, centroid bounds
+//   morton   63-bit Morton code of each centroid (21 bits per axis)
+//   sort     LSD radix sort, 8-bit digits, stable warp-level ranking
+//   karras   binary radix tree over the sorted codes (index breaks ties)
+//   refit    bottom-up boxes; a node is finished by the second child to
+//            arrive (atomic counter), so no thread ever waits on another
+// Temporary buffers are stream-ordered allocations on the build stream.
+#include "hg_device.cuh"
+#include "hg_host.h"
+
+#include <algorithm>
+
+namespace hg {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kTile = kSortThreads * kSortItems;
+
+struct MeshTable {
+    const float* verts[kMaxMesh];
+    const int32_t* faces[kMaxMesh];
+    int64_t n_verts[kMaxMesh];
+    int32_t first[kMaxMesh + 1];
+    int32_t n_mesh;
+};
+
+__device__ __forceinline__ int f2ord(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// faces -> unsorted triangle records + centroid bounds (as ordered ints)
+__global__ void k_gather(MeshTable mt, int n, float4* tmp, int* bounds, int* err) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    float c[3] = {0.f, 0.f, 0.f};
+    bool ok = g < n;
+    if (ok) {
+        int m = 0;
+        while (m + 1 < mt.n_mesh && mt.first[m + 1] <= g) ++m;
+        int f = g - mt.first[m];
+        const int32_t* fc = mt.faces[m] + 3 * (size_t)f;
+        int i0 = fc[0], i1 = fc[1], i2 = fc[2];
+        int64_t nv = mt.n_verts[m];
+        if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+            atomicOr(err, 1);
+            i0 = i1 = i2 = 0;
+        }
+        const float* v = mt.verts[m];
+        float4 a = make_float4(v[3 * (size_t)i0], v[3 * (size_t)i0 + 1], v[3 * (size_t)i0 + 2], __int_as_float(g));
+        float4 b = make_float4(v[3 * (size_t)i1], v[3 * (size_t)i1 + 1], v[3 * (size_t)i1 + 2], __int_as_float(m));
+        float4 cc = make_float4(v[3 * (size_t)i2], v[3 * (size_t)i2 + 1], v[3 * (size_t)i2 + 2], __int_as_float(f));
+        tmp[3 * (size_t)g] = a;
+        tmp[3 * (size_t)g + 1] = b;
+        tmp[3 * (size_t)g + 2] = cc;
+        c[0] = (a.x + b.x + cc.x) * (1.0f / 3.0f);
+        c[1] = (a.y + b.y + cc.y) * (1.0f / 3.0f);
+        c[2] = (a.z + b.z + cc.z) * (1.0f / 3.0f);
+    }
+    __shared__ int sb[6];
+    if (threadIdx.x < 6) sb[threadIdx.x] = (threadIdx.x < 3) ? INT_MAX : INT_MIN;
+    __syncthreads();
+    if (ok) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&sb[a], f2ord(c[a]));
+            atomicMax(&sb[3 + a], f2ord(c[a]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) atomicMin(&bounds[threadIdx.x], sb[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicMax(&bounds[threadIdx.x], sb[threadIdx.x]);
+}
+
+__device__ __forceinline__ uint64_t spread21(uint64_t x) {
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton(const float4* tmp, int n, const int* bounds, uint64_t* keys, uint32_t* vals) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    float4 a = tmp[3 * (size_t)g], b = tmp[3 * (size_t)g + 1], c = tmp[3 * (size_t)g + 2];
+    float cen[3] = {(a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                    (a.z + b.z + c.z) * (1.0f / 3.0f)};
+    uint64_t code = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        float lo = ord2f(bounds[ax]), hi = ord2f(bounds[3 + ax]);
+        float ext = hi - lo;
+        float u = ext > 0.0f ? (cen[ax] - lo) / ext : 0.0f;
+        float q = fminf(fmaxf(u * 2097152.0f, 0.0f), 2097151.0f);
+        code |= spread21((uint64_t)q) << (2 - ax);
+    }
+    keys[g] = code;
+    vals[g] = (uint32_t)g;
+}
+
+// ---------------- radix sort ----------------
+__global__ void k_hist(const uint64_t* keys, int n, int shift, uint32_t* hist, int nblk) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kTile;
+    for (int i = threadIdx.x; i < kTile; i += kSortThreads) {
+        int g = base + i;
+        if (g < n) atomicAdd(&h[(keys[g] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                          int n, int shift, const uint32_t* offs, int nblk) {
+    __shared__ uint32_t wc[kSortThreads / 32][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kTile + w * 32 * kSortItems;
+    uint32_t rank[kSortItems];
+    int dig[kSortItems];
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        int g = base + it * 32 + lane;
+        int d = g < n ? (int)((kin[g] >> shift) & 0xff) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = d < 256 ? wc[w][d] : 0u;
+        rank[it] = before + __popc(peers & lt);
+        dig[it] = d;
+        __syncwarp();
+        if (d < 256 && (peers & lt) == 0u) wc[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        int d = threadIdx.x;  // 256 threads == 256 digits
+        uint32_t run = 0;
+        for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+            uint32_t t = wc[ww][d];
+            wc[ww][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        int g = base + it * 32 + lane;
+        if (g < n) {
+            int d = dig[it];
+            uint32_t pos = offs[(size_t)d * nblk + blockIdx.x] + wc[w][d] + rank[it];
+            kout[pos] = kin[g];
+            vout[pos] = vin[g];
+        }
+    }
+}
+
+// exclusive scan, one block of 1024 threads x 2 items per 2048 elements
+__global__ void k_scan_block(const uint32_t* in, uint32_t* out, int n, uint32_t* sums) {
+    __shared__ uint32_t s[2048];
+    int base = blockIdx.x * 2048;
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) s[i] = base + i < n ? in[base + i] : 0u;
+    __syncthreads();
+    // Blelloch up-sweep / down-sweep
+    for (int d = 1; d < 2048; d <<= 1) {
+        int i = (threadIdx.x + 1) * 2 * d - 1;
+        if (i < 2048) s[i] += s[i - d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (sums) sums[blockIdx.x] = s[2047];
+        s[2047] = 0;
+    }
+    __syncthreads();
+    for (int d = 1024; d >= 1; d >>= 1) {
+        int i = (threadIdx.x + 1) * 2 * d - 1;
+        if (i < 2048) {
+            uint32_t t = s[i - d];
+            s[i - d] = s[i];
+            s[i] += t;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        if (base + i < n) out[base + i] = s[i];
+}
+
+__global__ void k_scan_add(uint32_t* data, int n, const uint32_t* sums) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) data[i] += sums[i / 2048];
+}
+
+// ---------------- hierarchy ----------------
+__device__ __forceinline__ int delta(const uint64_t* k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = k[i], b = k[j];
+    if (a == b) return 64 + __clz((unsigned)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+__global__ void k_karras(const uint64_t* k, int n, int* child, int* iparent, int* lparent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(k, n, i, i - d);
+    int lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(k, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? ~gamma : gamma;
+    int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+    if (left < 0) lparent[~left] = i; else iparent[left] = i;
+    if (right < 0) lparent[~right] = i; else iparent[right] = i;
+    if (i == 0) iparent[0] = -1;
+}
+
+__global__ void k_pack(const float4* tmp, const uint32_t* vals, int n, float4* tris, int32_t* inv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    inv[vals[i]] = i;
+    size_t s = 3 * (size_t)vals[i];
+    tris[3 * (size_t)i] = tmp[s];
+    tris[3 * (size_t)i + 1] = tmp[s + 1];
+    tris[3 * (size_t)i + 2] = tmp[s + 2];
+}
+
+__device__ __forceinline__ void tri_box(const float4* tris, int t, float b[6]) {
+    float4 a = tris[3 * (size_t)t], c = tris[3 * (size_t)t + 1], d = tris[3 * (size_t)t + 2];
+    b[0] = fminf(a.x, fminf(c.x, d.x));
+    b[1] = fminf(a.y, fminf(c.y, d.y));
+    b[2] = fminf(a.z, fminf(c.z, d.z));
+    b[3] = fmaxf(a.x, fmaxf(c.x, d.x));
+    b[4] = fmaxf(a.y, fmaxf(c.y, d.y));
+    b[5] = fmaxf(a.z, fmaxf(c.z, d.z));
+}
+
+// widen a box by ~1e-6 relative so FP32 slab tests stay conservative
+__device__ __forceinline__ void widen(float b[6]) {
+    for (int a = 0; a < 3; ++a) {
+        b[a] -= 1e-6f * fmaxf(fabsf(b[a]), 1.0f);
+        b[3 + a] += 1e-6f * fmaxf(fabsf(b[3 + a]), 1.0f);
+    }
+}
+
+__global__ void k_refit(const float4* tris, int n, const int* child, const int* iparent,
+                        const int* lparent, float* ibox, int* counter, float4* nodes) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = lparent[i];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&counter[p], 1) == 0) return;  // first child to arrive: stop
+        __threadfence();
+        int c[2] = {child[2 * p], child[2 * p + 1]};
+        float b[2][6];
+        for (int k = 0; k < 2; ++k) {
+            if (c[k] < 0) tri_box(tris, ~c[k], b[k]);
+            else for (int q = 0; q < 6; ++q) b[k][q] = __ldcg(&ibox[6 * (size_t)c[k] + q]);
+        }
+        float u[6];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = fminf(b[0][a], b[1][a]);
+            u[3 + a] = fmaxf(b[0][3 + a], b[1][3 + a]);
+        }
+        for (int q = 0; q < 6; ++q) __stcg(&ibox[6 * (size_t)p + q], u[q]);
+        // axis of largest centre separation; child0 = the lower one along it
+        float sep[3];
+        for (int a = 0; a < 3; ++a) sep[a] = (b[1][a] + b[1][3 + a]) - (b[0][a] + b[0][3 + a]);
+        int axis = 0;
+        if (fabsf(sep[1]) > fabsf(sep[axis])) axis = 1;
+        if (fabsf(sep[2]) > fabsf(sep[axis])) axis = 2;
+        int k0 = 0, k1 = 1;
+        if (sep[axis] < 0.0f) { k0 = 1; k1 = 0; }
+        widen(b[0]);
+        widen(b[1]);
+        const float* x = b[k0];
+        const float* y = b[k1];
+        float4* nd = nodes + 4 * (size_t)p;
+        nd[0] = make_float4(x[0], x[1], x[2], x[3]);
+        nd[1] = make_float4(x[4], x[5], y[0], y[1]);
+        nd[2] = make_float4(y[2], y[3], y[4], y[5]);
+        nd[3] = make_float4(__int_as_float(c[k0]), __int_as_float(c[k1]), __int_as_float(iparent[p]),
+                            __int_as_float(axis));
+        p = iparent[p];
+    }
+}
+
+int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+struct StreamBufs {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    cudaError_t err = cudaSuccess;
+    void* get(size_t bytes) {
+        void* p = nullptr;
+        if (err != cudaSuccess) return nullptr;
+        err = cudaMallocAsync(&p, bytes > 0 ? bytes : 16, st);
+        if (err == cudaSuccess) ptrs.push_back(p);
+        return p;
+    }
+    ~StreamBufs() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+cudaError_t exclusive_scan(uint32_t* data, int n, StreamBufs& B) {
+    int nb = blocks_for(n, 2048);
+    if (nb <= 1) {
+        k_scan_block<<<1, 1024, 0, B.st>>>(data, data, n, nullptr);
+        return cudaGetLastError();
+    }
+    uint32_t* sums = (uint32_t*)B.get(sizeof(uint32_t) * nb);
+    if (!sums) return B.err;
+    k_scan_block<<<nb, 1024, 0, B.st>>>(data, data, n, sums);
+    cudaError_t e = exclusive_scan(sums, nb, B);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<blocks_for(n, 256), 256, 0, B.st>>>(data, n, sums);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st) {
+    const int n = (int)s->n_tri;
+    MeshTable mt;
+    memset(&mt, 0, sizeof(mt));
+    mt.n_mesh = desc->n_meshes;
+    for (int m = 0; m < desc->n_meshes; ++m) {
+        mt.verts[m] = desc->meshes[m].verts;
+        mt.faces[m] = desc->meshes[m].faces;
+        mt.n_verts[m] = desc->meshes[m].n_verts;
+        mt.first[m] = s->mesh_first[m];
+    }
+    mt.first[desc->n_meshes] = (int32_t)n;
+    if (n == 0) return HELIOS_OK;
+    StreamBufs B;
+    B.st = st;
+    float4* tmp = (float4*)B.get(sizeof(float4) * 3 * (size_t)n);
+    int* bounds = (int*)B.get(sizeof(int) * 8);
+    uint64_t* k0 = (uint64_t*)B.get(sizeof(uint64_t) * n);
+    uint64_t* k1 = (uint64_t*)B.get(sizeof(uint64_t) * n);
+    uint32_t* v0 = (uint32_t*)B.get(sizeof(uint32_t) * n);
+    uint32_t* v1 = (uint32_t*)B.get(sizeof(uint32_t) * n);
+    int nblk = blocks_for(n, kTile);
+    uint32_t* hist = (uint32_t*)B.get(sizeof(uint32_t) * 256 * (size_t)nblk);
+    int* child = (int*)B.get(sizeof(int) * 2 * (size_t)std::max(n - 1, 1));
+    int* ipar = (int*)B.get(sizeof(int) * (size_t)std::max(n - 1, 1));
+    int* lpar = (int*)B.get(sizeof(int) * (size_t)n);
+    float* ibox = (float*)B.get(sizeof(float) * 6 * (size_t)std::max(n - 1, 1));
+    int* cnt = (int*)B.get(sizeof(int) * (size_t)std::max(n - 1, 1));
+    if (B.err != cudaSuccess) return set_error(HELIOS_ERR_OOM, "BVH scratch allocation failed: %s", cudaGetErrorString(B.err));
+    cudaError_t e;
+    int init[8] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN, 0, 0};
+    // bounds[6] is the device error word (bad face index)
+    e = cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_cuda_error("BVH init", e);
+    k_gather<<<blocks_for(n, 256), 256, 0, st>>>(mt, n, tmp, bounds, bounds + 6);
+    k_morton<<<blocks_for(n, 256), 256, 0, st>>>(tmp, n, bounds, k0, v0);
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_hist<<<nblk, kSortThreads, 0, st>>>(k0, n, shift, hist, nblk);
+        e = exclusive_scan(hist, 256 * nblk, B);
+        if (e != cudaSuccess) return set_cuda_error("BVH sort scan", e);
+        k_scatter<<<nblk, kSortThreads, 0, st>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    k_pack<<<blocks_for(n, 256), 256, 0, st>>>(tmp, v0, n, s->tris, s->tri_index);
+    if (n > 1) {
+        e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(n - 1), st);
+        if (e != cudaSuccess) return set_cuda_error("BVH counters", e);
+        k_karras<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, child, ipar, lpar);
+        k_refit<<<blocks_for(n, 256), 256, 0, st>>>(s->tris, n, child, ipar, lpar, ibox, cnt, s->nodes);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error("BVH build kernels", e);
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, bounds + 6, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error("BVH build", e);
+    if (flag) return set_error(HELIOS_ERR_INVALID_ARG, "a face index is outside its mesh's vertex range");
+    return HELIOS_OK;
+}
+
+}  // namespace hg

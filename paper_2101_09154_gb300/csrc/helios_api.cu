@@ -1,0 +1,429 @@
+// helios_api.cu - the extern "C" boundary of libhelios_gb300.so: argument
+// validation, derived instrument constants, scene lifetime and launches.
+#include "hg_host.h"
+
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+namespace hg {
+
+static thread_local std::string g_err;
+
+helios_status set_error(helios_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+helios_status set_cuda_error(const char* what, cudaError_t e) {
+    (void)cudaGetLastError();  // clear a non-sticky error
+    return set_error(e == cudaErrorMemoryAllocation ? HELIOS_ERR_OOM : HELIOS_ERR_CUDA, "%s: %s",
+                     what, cudaGetErrorString(e));
+}
+
+static int32_t subray_count(int32_t q) {
+    if (q < 0) return -1;
+    int32_t s = 1;
+    for (int i = 1; i <= q; ++i) s += (int32_t)std::floor(2.0 * kPi * (double)i);
+    return s;
+}
+
+static helios_status check_scanner(const helios_scanner_desc& s, int idx) {
+    auto bad = [&](const char* what) {
+        return set_error(HELIOS_ERR_INVALID_ARG, "scanner %d: %s", idx, what);
+    };
+    if (!(s.prf_hz > 0.0) || !std::isfinite(s.prf_hz)) return bad("prf_hz must be > 0");
+    if (!(s.divergence_rad > 0.0) || !(s.divergence_rad < 0.5)) return bad("divergence_rad must be in (0, 0.5)");
+    if (s.beam_sample_quality < 0 || s.beam_sample_quality > 9) return bad("beam_sample_quality must be in 0..9");
+    if (!(s.wavelength_m > 0.0)) return bad("wavelength_m must be > 0");
+    if (!(s.bin_ns > 0.0)) return bad("bin_ns must be > 0");
+    if (s.n_bins < 4 || s.n_bins > 4096) return bad("n_bins must be in 4..4096");
+    if (s.max_echoes < 1 || s.max_echoes > 32) return bad("max_echoes must be in 1..32");
+    if (!(s.echo_threshold_rel >= 0.0 && s.echo_threshold_rel <= 1.0)) return bad("echo_threshold_rel must be in [0,1]");
+    if (!(s.range_noise_sigma_m >= 0.0)) return bad("range_noise_sigma_m must be >= 0");
+    if (!(s.peak_power_w >= 0.0) || !(s.receiver_diam_m >= 0.0)) return bad("power parameters must be >= 0");
+    if (s.pulse_shape == HELIOS_PULSE_GAUSSIAN) {
+        if (!(s.pulse_fwhm_ns > 0.0)) return bad("pulse_fwhm_ns must be > 0");
+    } else if (s.pulse_shape == HELIOS_PULSE_CARLSSON) {
+        if (!(s.pulse_length_ns > 0.0)) return bad("pulse_length_ns must be > 0");
+    } else {
+        return bad("unknown pulse_shape");
+    }
+    if (s.deflector < 0 || s.deflector > 3) return bad("unknown deflector");
+    if (s.deflector == HELIOS_DEFL_TLS_GRID && (s.grid_n_az < 1 || s.grid_n_el < 1))
+        return bad("TLS grid needs grid_n_az, grid_n_el >= 1");
+    return HELIOS_OK;
+}
+
+static DevScanner derive_scanner(const helios_scanner_desc& s) {
+    DevScanner d;
+    memset(&d, 0, sizeof(d));
+    d.prf = s.prf_hz;
+    d.bin_ns = s.bin_ns;
+    d.theta_r = 0.5 * s.divergence_rad;
+    d.scan_freq = s.scan_freq_hz;
+    d.amax = s.scan_angle_max_rad;
+    d.head_rate = s.head_rate_rad_s;
+    d.el_min = s.el_min_rad;
+    d.el_max = s.el_max_rad;
+    double w0 = s.beam_waist_m > 0.0 ? s.beam_waist_m : s.wavelength_m / (kPi * d.theta_r);
+    d.w0sq = (float)(w0 * w0);
+    d.zk = (float)(s.wavelength_m / (kPi * w0 * w0));
+    d.focus = (float)s.focus_m;
+    d.pconst = (float)(s.peak_power_w * s.receiver_diam_m * s.receiver_diam_m * s.eta_sys * s.eta_atm / 4.0);
+    // pulse support: where the shape falls below 2^-30 of its peak
+    if (s.pulse_shape == HELIOS_PULSE_GAUSSIAN) {
+        double sig = s.pulse_fwhm_ns / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+        double gk2 = 1.4426950408889634 / (2.0 * sig * sig);
+        d.gk2 = (float)gk2;
+        d.cut_lo = d.cut_hi = (float)std::sqrt(30.0 / gk2);
+        d.n_pre = (int32_t)std::ceil(3.0 * sig / s.bin_ns);
+        d.echo_offset_ns = 0.0;
+    } else {
+        double tau = s.pulse_length_ns / 1.75;
+        d.ctau_inv = (float)(1.0 / tau);
+        double peak = 4.0 * std::exp(-2.0), y = 2.0;
+        while (y * y * std::exp(-y) >= std::ldexp(peak, -30)) y += 0.25;
+        d.cut_lo = 0.0f;
+        d.cut_hi = (float)(y * tau);
+        d.n_pre = 0;
+        d.echo_offset_ns = 2.0 * tau;
+    }
+    d.thr_rel = (float)s.echo_threshold_rel;
+    d.noise_sigma = (float)s.range_noise_sigma_m;
+    d.q_default = s.beam_sample_quality;
+    d.pulse_shape = s.pulse_shape;
+    d.n_bins = s.n_bins;
+    d.max_echoes = s.max_echoes;
+    d.deflector = s.deflector;
+    d.n_az = s.grid_n_az;
+    d.n_el = s.grid_n_el;
+    return d;
+}
+
+static DevScene dev_scene(const helios_scene* s) {
+    DevScene d;
+    memset(&d, 0, sizeof(d));
+    d.nodes = s->nodes;
+    d.tris = s->tris;
+    d.tri_index = s->tri_index;
+    for (int m = 0; m < s->n_mesh; ++m) d.refl[m] = s->refl[m];
+    for (int m = 0; m <= s->n_mesh; ++m) d.mesh_first[m] = s->mesh_first[m];
+    d.n_tri = (int32_t)s->n_tri;
+    d.n_int = (int32_t)s->n_int;
+    d.n_mesh = s->n_mesh;
+    d.has_grid = s->n_grid;
+    if (s->n_grid) {
+        d.density = s->grid.density;
+        for (int a = 0; a < 3; ++a) {
+            d.dims[a] = s->grid.dims[a];
+            d.g0[a] = s->grid.origin[a];
+        }
+        d.G = s->grid.G;
+        d.leaf_refl = s->grid.leaf_reflectance;
+        d.cell = s->grid.cell;
+    }
+    return d;
+}
+
+struct LegPlan {
+    std::vector<DevLeg> legs;
+    int64_t total_pulses = 0, wave = 0, sub = 0, echo = 0;
+};
+
+static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_scanners,
+                               const helios_leg_desc* legs, int32_t n_legs, int32_t n_scenes,
+                               int rays_per_item, LegPlan& P) {
+    if (n_legs < 0 || (n_legs > 0 && !legs)) return set_error(HELIOS_ERR_INVALID_ARG, "legs is NULL");
+    if (n_scanners < 1 || n_scanners > kMaxScanners || !scanners)
+        return set_error(HELIOS_ERR_INVALID_ARG, "n_scanners must be in 1..%d", kMaxScanners);
+    for (int i = 0; i < n_scanners; ++i) {
+        helios_status st = check_scanner(scanners[i], i);
+        if (st != HELIOS_OK) return st;
+    }
+    P.legs.clear();
+    for (int l = 0; l < n_legs; ++l) {
+        const helios_leg_desc& L = legs[l];
+        if (n_scenes >= 0 && (L.scene_index < 0 || L.scene_index >= n_scenes))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: scene_index out of range", l);
+        if (L.scanner_index < 0 || L.scanner_index >= n_scanners)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: scanner_index out of range", l);
+        if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
+        if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: speed_mps must be >= 0", l);
+        const helios_scanner_desc& sc = scanners[L.scanner_index];
+        int q = L.beam_sample_quality >= 0 ? L.beam_sample_quality : sc.beam_sample_quality;
+        if (q > 9) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: beam_sample_quality must be <= 9", l);
+        DevLeg d;
+        memset(&d, 0, sizeof(d));
+        double D[3];
+        double len2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            d.start[a] = L.start[a];
+            D[a] = L.end[a] - L.start[a];
+            len2 += D[a] * D[a];
+            d.rpy[a] = L.attitude_rpy[a];
+        }
+        d.length = std::sqrt(len2);
+        if (L.platform == HELIOS_PLATFORM_LINEAR && d.length > 0.0) {
+            for (int a = 0; a < 3; ++a) d.dir[a] = D[a] / d.length;
+            d.rpy[2] += std::atan2(D[1], D[0]);  // heading towards the next waypoint
+        }
+        d.speed = L.speed_mps;
+        d.t0 = L.t0;
+        d.n_pulses = L.n_pulses;
+        d.scene = L.scene_index;
+        d.scanner = L.scanner_index;
+        d.platform = L.platform;
+        d.q = q;
+        d.S = subray_count(q);
+        int ppi = rays_per_item / d.S;
+        d.pulses_per_item = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        d.leg_id = L.leg_id;
+        d.pulse_off = P.total_pulses;
+        d.wave_off = P.wave;
+        d.sub_off = P.sub;
+        d.echo_off = P.echo;
+        P.total_pulses += L.n_pulses;
+        P.wave += L.n_pulses * sc.n_bins;
+        P.sub += L.n_pulses * d.S;
+        P.echo += L.n_pulses * sc.max_echoes;
+        P.legs.push_back(d);
+    }
+    return HELIOS_OK;
+}
+
+static helios_status check_scenes(helios_scene* const* scenes, int32_t n_scenes) {
+    if (n_scenes < 1 || n_scenes > kMaxScenes || !scenes)
+        return set_error(HELIOS_ERR_INVALID_ARG, "n_scenes must be in 1..%d", kMaxScenes);
+    for (int i = 0; i < n_scenes; ++i)
+        if (!scenes[i]) return set_error(HELIOS_ERR_INVALID_ARG, "scene %d is NULL", i);
+    return HELIOS_OK;
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" {
+
+const char* helios_last_error(void) { return g_err.c_str(); }
+
+const char* helios_version(void) { return "helios_gb300 0.1 sm_103a"; }
+
+int32_t helios_subray_count(int32_t q) { return subray_count(q); }
+
+helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_stream,
+                                 helios_scene** out) {
+    g_err.clear();
+    if (!desc || !out) return set_error(HELIOS_ERR_INVALID_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (desc->n_meshes < 0 || desc->n_meshes > kMaxMesh)
+        return set_error(HELIOS_ERR_UNSUPPORTED, "n_meshes must be in 0..%d", kMaxMesh);
+    if (desc->n_meshes > 0 && !desc->meshes) return set_error(HELIOS_ERR_INVALID_ARG, "meshes is NULL");
+    if (desc->n_grids < 0) return set_error(HELIOS_ERR_INVALID_ARG, "n_grids < 0");
+    if (desc->n_grids > 1) return set_error(HELIOS_ERR_UNSUPPORTED, "at most one voxel grid per scene");
+    if (desc->n_grids == 1 && !desc->grids) return set_error(HELIOS_ERR_INVALID_ARG, "grids is NULL");
+    int64_t n_tri = 0;
+    for (int m = 0; m < desc->n_meshes; ++m) {
+        const helios_mesh_desc& M = desc->meshes[m];
+        if (M.n_faces < 0 || M.n_verts < 0) return set_error(HELIOS_ERR_INVALID_ARG, "mesh %d: negative size", m);
+        if (M.n_faces > 0 && (!M.verts || !M.faces || !M.reflectance || M.n_verts == 0))
+            return set_error(HELIOS_ERR_INVALID_ARG, "mesh %d: NULL array", m);
+        n_tri += M.n_faces;
+    }
+    int64_t n_vox = 0;
+    if (desc->n_grids == 1) {
+        const helios_voxel_desc& g = desc->grids[0];
+        if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1) return set_error(HELIOS_ERR_INVALID_ARG, "grid dims must be >= 1");
+        if (!(g.cell > 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid cell must be > 0");
+        if (!(g.G >= 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid G must be >= 0");
+        if (!g.density) return set_error(HELIOS_ERR_INVALID_ARG, "grid density is NULL");
+        n_vox = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+    }
+    if (n_tri + n_vox >= (int64_t)INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many primitives for 32-bit ids");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    helios_scene* s = new helios_scene();
+    memset(s, 0, sizeof(*s));
+    cudaGetDevice(&s->device);
+    s->n_tri = n_tri;
+    s->n_int = n_tri > 1 ? n_tri - 1 : 0;
+    s->n_mesh = desc->n_meshes;
+    s->n_grid = desc->n_grids;
+    int64_t off = 0;
+    for (int m = 0; m < desc->n_meshes; ++m) {
+        s->mesh_first[m] = (int32_t)off;
+        s->mesh_faces[m] = desc->meshes[m].n_faces;
+        s->refl[m] = desc->meshes[m].reflectance;
+        off += desc->meshes[m].n_faces;
+    }
+    s->mesh_first[desc->n_meshes] = (int32_t)off;
+    if (desc->n_grids == 1) s->grid = desc->grids[0];
+    cudaError_t e = cudaSuccess;
+    if (s->n_int > 0) e = cudaMalloc(&s->nodes, sizeof(float4) * 4 * (size_t)s->n_int);
+    if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tris, sizeof(float4) * 3 * (size_t)n_tri);
+    if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tri_index, sizeof(int32_t) * (size_t)n_tri);
+    if (e != cudaSuccess) {
+        helios_status r = set_cuda_error("scene allocation", e);
+        cudaFree(s->nodes);
+        cudaFree(s->tris);
+        cudaFree(s->tri_index);
+        delete s;
+        return r;
+    }
+    s->bytes = (int64_t)sizeof(float4) * (4 * s->n_int + 3 * n_tri) + (int64_t)sizeof(int32_t) * n_tri;
+    helios_status r = build_bvh(s, desc, st);
+    if (r != HELIOS_OK) {
+        cudaStreamSynchronize(st);
+        cudaFree(s->nodes);
+        cudaFree(s->tris);
+        cudaFree(s->tri_index);
+        delete s;
+        return r;
+    }
+    *out = s;
+    return HELIOS_OK;
+}
+
+helios_status helios_free_scene(helios_scene* scene) {
+    g_err.clear();
+    if (!scene) return HELIOS_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != scene->device) cudaSetDevice(scene->device);
+    cudaFree(scene->nodes);
+    cudaFree(scene->tris);
+    cudaFree(scene->tri_index);
+    if (cur != scene->device) cudaSetDevice(cur);
+    delete scene;
+    return HELIOS_OK;
+}
+
+helios_status helios_scene_get_info(const helios_scene* scene, helios_scene_info* info) {
+    g_err.clear();
+    if (!scene || !info) return set_error(HELIOS_ERR_INVALID_ARG, "scene and info must not be NULL");
+    info->n_triangles = scene->n_tri;
+    info->n_bvh_nodes = scene->n_int;
+    info->device_bytes = scene->bytes;
+    info->n_meshes = scene->n_mesh;
+    info->n_grids = scene->n_grid;
+    return HELIOS_OK;
+}
+
+helios_status helios_output_layout(const helios_scanner_desc* scanners, int32_t n_scanners,
+                                   const helios_leg_desc* legs, int32_t n_legs,
+                                   int64_t* pulse_offset, int64_t* wave_offset,
+                                   int64_t* subray_offset, int64_t* echo_offset,
+                                   helios_layout* totals) {
+    g_err.clear();
+    LegPlan P;
+    helios_status st = plan_legs(scanners, n_scanners, legs, n_legs, -1, 768, P);
+    if (st != HELIOS_OK) return st;
+    for (int l = 0; l < n_legs; ++l) {
+        if (pulse_offset) pulse_offset[l] = P.legs[l].pulse_off;
+        if (wave_offset) wave_offset[l] = P.legs[l].wave_off;
+        if (subray_offset) subray_offset[l] = P.legs[l].sub_off;
+        if (echo_offset) echo_offset[l] = P.legs[l].echo_off;
+    }
+    if (totals) {
+        totals->total_pulses = P.total_pulses;
+        totals->waveform_floats = P.wave;
+        totals->subray_elems = P.sub;
+        totals->echo_elems = P.echo;
+    }
+    return HELIOS_OK;
+}
+
+helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
+                               const helios_scanner_desc* scanners, int32_t n_scanners,
+                               const helios_leg_desc* legs, int32_t n_legs,
+                               const helios_scan_opts* opts, const helios_outputs* out,
+                               void* cuda_stream) {
+    g_err.clear();
+    helios_status st = check_scenes(scenes, n_scenes);
+    if (st != HELIOS_OK) return st;
+    if (!opts || !out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and out must not be NULL");
+    if (opts->mode != HELIOS_MODE_STOCHASTIC && opts->mode != HELIOS_MODE_EXPECTED)
+        return set_error(HELIOS_ERR_INVALID_ARG, "unknown mode");
+    if (!out->waveform || !out->window_bin || !out->echo_count || !out->echo_range)
+        return set_error(HELIOS_ERR_INVALID_ARG, "waveform, window_bin, echo_count, echo_range are required");
+    if (out->subray_range && !out->subray_hit)
+        return set_error(HELIOS_ERR_INVALID_ARG, "subray_range needs subray_hit");
+    int threads = opts->block_threads > 0 ? opts->block_threads : 256;
+    if (threads % 32 != 0 || threads < 64 || threads > 256)
+        return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
+    int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
+    if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
+    LegPlan P;
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, P);
+    if (st != HELIOS_OK) return st;
+    ScanLaunch L;
+    for (int i = 0; i < n_scenes; ++i) L.scenes.push_back(dev_scene(scenes[i]));
+    for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
+    L.legs = P.legs;
+    L.out.waveform = out->waveform;
+    L.out.window_bin = out->window_bin;
+    L.out.echo_count = out->echo_count;
+    L.out.echo_range = out->echo_range;
+    L.out.echo_amp = out->echo_amp;
+    L.out.echo_bin = out->echo_bin;
+    L.out.echo_object = out->echo_object;
+    L.out.pulse_flags = out->pulse_flags;
+    L.out.subray_hit = out->subray_hit;
+    L.out.subray_range = out->subray_range;
+    L.out.status = out->status;
+    L.seed = opts->seed;
+    L.mode = opts->mode;
+    L.persistent = opts->persistent;
+    L.threads = threads;
+    L.blocks_per_sm = opts->blocks_per_sm;
+    if (P.total_pulses == 0) return HELIOS_OK;
+    return launch_scan(L, (cudaStream_t)cuda_stream);
+}
+
+helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
+                                  const helios_scanner_desc* scanners, int32_t n_scanners,
+                                  const helios_leg_desc* legs, int32_t n_legs,
+                                  const helios_scan_opts* opts, const float* d_waveform,
+                                  const int32_t* window_bin, const int32_t* subray_hit,
+                                  const helios_scene_grads* grads, void* cuda_stream) {
+    g_err.clear();
+    helios_status st = check_scenes(scenes, n_scenes);
+    if (st != HELIOS_OK) return st;
+    if (!opts || !d_waveform || !window_bin || !grads)
+        return set_error(HELIOS_ERR_INVALID_ARG, "opts, d_waveform, window_bin, grads must not be NULL");
+    if (opts->mode != HELIOS_MODE_EXPECTED)
+        return set_error(HELIOS_ERR_INVALID_ARG, "the adjoint is defined for mode EXPECTED only");
+    int threads = opts->block_threads > 0 ? opts->block_threads : 256;
+    if (threads % 32 != 0 || threads < 64 || threads > 256)
+        return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
+    LegPlan P;
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, 256, P);
+    if (st != HELIOS_OK) return st;
+    AdjointLaunch L;
+    for (int i = 0; i < n_scenes; ++i) {
+        L.scenes.push_back(dev_scene(scenes[i]));
+        std::vector<float*> dr(kMaxMesh, nullptr);
+        for (int m = 0; m < scenes[i]->n_mesh; ++m)
+            dr[m] = grads[i].d_reflectance ? grads[i].d_reflectance[m] : nullptr;
+        L.d_refl.push_back(dr);
+        L.d_density.push_back(scenes[i]->n_grid && grads[i].d_density ? grads[i].d_density[0] : nullptr);
+    }
+    for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
+    L.legs = P.legs;
+    L.g = d_waveform;
+    L.window = window_bin;
+    L.subray_hit = subray_hit;
+    L.threads = threads;
+    if (P.total_pulses == 0) return HELIOS_OK;
+    return launch_adjoint(L, (cudaStream_t)cuda_stream);
+}
+
+}  // extern "C"

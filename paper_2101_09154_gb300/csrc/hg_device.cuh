@@ -1,0 +1,586 @@
+// hg_device.cuh - device-side data layout and building blocks of the pulse kernels.
+//
+// Everything here runs on sm_103a.  FP32 is used for the BVH traversal, the
+// voxel march and the waveform; FP64 only where the method's tolerances need
+// it (pulse pose, subray direction, final hit range, voxel segment ends).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace hg {
+
+constexpr int kMaxMesh = 16;
+constexpr int kMaxScenes = 16;
+constexpr int kMaxScanners = 4;
+constexpr int kMaxLegs = 96;
+constexpr double kC = 299792458.0;        // speed of light (Sec. 3.4)
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// scene: BVH nodes, packed triangles, per-mesh reflectance, optional grid
+// ---------------------------------------------------------------------------
+// Internal node i occupies nodes[4i .. 4i+3] (64 bytes):
+//   [0] = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
+//   [1] = (c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y)
+//   [2] = (c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z)
+//   [3] = (child0, child1, parent, axis) as int bits
+// child >= 0 is an internal node, child < 0 is the leaf ~tri (a triangle).
+// child0 is the lower child along `axis`, so the near child of a ray with
+// d[axis] >= 0 is child0.  Triangle t occupies tris[3t .. 3t+2]:
+//   (v0, global id), (v1, mesh), (v2, face).
+struct DevScene {
+    const float4* nodes;
+    const float4* tris;
+    const int32_t* tri_index;   // global triangle id -> packed (sorted) position
+    const float* refl[kMaxMesh];
+    const float* density;
+    int32_t mesh_first[kMaxMesh + 1];
+    int32_t n_tri, n_int, n_mesh, has_grid;
+    int32_t dims[3];
+    float G, leaf_refl, cell;
+    float g0[3];
+    int32_t pad;
+};
+
+// Instrument constants derived once per call (host side, FP64).
+struct DevScanner {
+    double prf;
+    double bin_ns;
+    double echo_offset_ns;   // pulse peak delay removed from echo ranges (0: Gaussian)
+    double theta_r;          // half divergence
+    double scan_freq, amax, head_rate, el_min, el_max;
+    float w0sq;              // beam waist squared
+    float zk;                // lambda / (pi w0^2)
+    float focus;
+    float pconst;            // I0 Dr^2 eta_sys eta_atm / 4
+    float gk2;               // Gaussian: log2(e) / (2 sigma^2)   [1/ns^2]
+    float ctau_inv;          // Carlsson: 1/tau                   [1/ns]
+    float cut_lo, cut_hi;    // support of the pulse shape around the delay [ns]
+    float thr_rel, noise_sigma;
+    int32_t q_default, pulse_shape, n_bins, max_echoes;
+    int32_t deflector, n_az, n_el, n_pre;
+};
+
+// One leg, with offsets into the concatenated outputs.
+struct DevLeg {
+    double start[3];
+    double dir[3];           // unit vector start -> end (linear platform)
+    double length, speed, t0;
+    double rpy[3];           // roll, pitch, yaw (heading included)
+    int64_t n_pulses;
+    int64_t pulse_off, wave_off, sub_off, echo_off;
+    int64_t item_begin;      // first work item of this leg
+    int32_t scene, scanner, platform, q;
+    int32_t S, pulses_per_item;
+    uint32_t leg_id;
+    int32_t pad;
+};
+
+struct Outputs {
+    float* waveform;
+    int32_t* window_bin;
+    int32_t* echo_count;
+    float* echo_range;
+    float* echo_amp;
+    int32_t* echo_bin;
+    int32_t* echo_object;
+    uint8_t* pulse_flags;
+    int32_t* subray_hit;
+    float* subray_range;
+    uint32_t* status;
+};
+
+// Per-pulse pose in shared memory: origin, direction, and the two ONB axes.
+struct PulseFrame {
+    double o[3], d[3], u[3], v[3];
+};
+// Per-subray constants: cos(alpha), sin(alpha)cos(phi), sin(alpha)sin(phi), tan(alpha).
+struct SubrayConst {
+    double ca, sacp, sasp;
+    float tan_a;
+    int32_t pad;
+};
+
+constexpr uint32_t kPfEchoOverflow = 0x01u;
+constexpr uint32_t kPfTraversalCap = 0x02u;
+constexpr uint32_t kPfMarchCap = 0x04u;
+constexpr uint32_t kPfNoReturn = 0x08u;
+constexpr uint32_t kStTraversalCap = 0x01u;
+constexpr uint32_t kStMarchCap = 0x02u;
+constexpr uint32_t kStEchoOverflow = 0x04u;
+constexpr int32_t kNoWindow = INT32_MIN;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11).  Counter layout:
+// (pulse, stream<<32 | subray_or_echo, voxel_or_0, leg_id), key (seed, 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                           uint64_t k0, uint64_t k1, uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t h0 = __umul64hi(M0, c0), l0 = M0 * c0;
+        uint64_t h1 = __umul64hi(M1, c2), l1 = M1 * c2;
+        uint64_t y0 = h1 ^ c1 ^ k0, y2 = h0 ^ c3 ^ k1;
+        c0 = y0; c1 = l1; c2 = y2; c3 = l0;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// (top 23 bits + 1/2) * 2^-23: odd multiples of 2^-24, exact in FP32
+__device__ __forceinline__ float uniform23(uint64_t w) {
+    return ((float)(uint32_t)(w >> 41) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// ---------------------------------------------------------------------------
+// pulse pose (Sec. 3.2, 3.3) in FP64
+// ---------------------------------------------------------------------------
+// world = Rz(yaw) Ry(pitch) Rx(roll) platform; rot = (sr, cr, sp, cp, sy, cy)
+__device__ __forceinline__ void rot_rpy(const double rot[6], double x, double y, double z,
+                                        double out[3]) {
+    const double sr = rot[0], cr = rot[1], sp = rot[2], cp = rot[3], sy = rot[4], cy = rot[5];
+    double y1 = y * cr - z * sr, z1 = y * sr + z * cr;
+    double x2 = x * cp + z1 * sp, z2 = -x * sp + z1 * cp;
+    out[0] = x2 * cy - y1 * sy;
+    out[1] = x2 * sy + y1 * cy;
+    out[2] = z2;
+}
+
+__device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& lg,
+                                            const double rot[6], int64_t k, PulseFrame& f) {
+    double elapsed = (double)k / sn.prf;
+    double t = lg.t0 + elapsed;
+    for (int a = 0; a < 3; ++a) f.o[a] = lg.start[a];
+    if (lg.platform == 1 && lg.length > 0.0) {
+        double s = lg.speed * elapsed;
+        if (s > lg.length) s = lg.length;
+        for (int a = 0; a < 3; ++a) f.o[a] = lg.start[a] + s * lg.dir[a];
+    }
+    double x, y, z;
+    switch (sn.deflector) {
+    case 0: {
+        double ph = sn.scan_freq * t;
+        ph -= floor(ph);
+        double th = -sn.amax + 2.0 * sn.amax * ph;
+        double st, ct;
+        sincos(th, &st, &ct);
+        x = 0.0; y = st; z = -ct;
+        break;
+    }
+    case 1: {
+        double th = sn.amax * sin(2.0 * kPi * sn.scan_freq * t);
+        double st, ct;
+        sincos(th, &st, &ct);
+        x = 0.0; y = st; z = -ct;
+        break;
+    }
+    case 2: {
+        int64_t i = k / sn.n_el, j = k % sn.n_el;
+        double az = 2.0 * kPi * (double)i / (double)sn.n_az;
+        double el = sn.el_min;
+        if (sn.n_el > 1) el = sn.el_min + (sn.el_max - sn.el_min) * (double)j / (double)(sn.n_el - 1);
+        double sa, ca, se, ce;
+        sincos(az, &sa, &ca);
+        sincos(el, &se, &ce);
+        x = ce * ca; y = ce * sa; z = se;
+        break;
+    }
+    default: {
+        double az = sn.head_rate * t;
+        double ph = sn.scan_freq * t;
+        ph -= floor(ph);
+        double el = -sn.amax + 2.0 * sn.amax * ph;
+        double sa, ca, se, ce;
+        sincos(az, &sa, &ca);
+        sincos(el, &se, &ce);
+        x = ce * ca; y = ce * sa; z = se;
+        break;
+    }
+    }
+    rot_rpy(rot, x, y, z, f.d);
+    // orthonormal basis around d (Duff et al., JCGT 2017)
+    double sign = copysign(1.0, f.d[2]);
+    double a = -1.0 / (sign + f.d[2]);
+    double b = f.d[0] * f.d[1] * a;
+    f.u[0] = 1.0 + sign * f.d[0] * f.d[0] * a;
+    f.u[1] = sign * b;
+    f.u[2] = -sign * f.d[0];
+    f.v[0] = b;
+    f.v[1] = sign + f.d[1] * f.d[1] * a;
+    f.v[2] = -f.d[1];
+}
+
+// subray s of quality q (Sec. 3.4): ring i at angle (i/q) theta_r, floor(2 pi i) per ring
+__device__ __forceinline__ void subray_const(int q, double theta_r, int s, SubrayConst& c) {
+    double alpha = 0.0, phi = 0.0;
+    if (s > 0) {
+        int idx = s - 1;
+        for (int i = 1; i <= q; ++i) {
+            int n = (int)floor(2.0 * kPi * (double)i);
+            if (idx < n) {
+                alpha = ((double)i / (double)q) * theta_r;
+                phi = 2.0 * kPi * (double)idx / (double)n;
+                break;
+            }
+            idx -= n;
+        }
+    }
+    double sa, ca, sp, cp;
+    sincos(alpha, &sa, &ca);
+    sincos(phi, &sp, &cp);
+    c.ca = ca;
+    c.sacp = sa * cp;
+    c.sasp = sa * sp;
+    c.tan_a = (float)tan(alpha);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 ray for traversal
+// ---------------------------------------------------------------------------
+struct RayF {
+    float ox, oy, oz;
+    float idx, idy, idz;     // 1/d (tiny components replaced by +-1e-20)
+    float oix, oiy, oiz;     // o * (1/d)
+    float sx, sy, sz;        // watertight shear constants
+    int kx, ky, kz;
+};
+
+__device__ __forceinline__ float safe_inv(float d) {
+    return 1.0f / (fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
+}
+
+__device__ __forceinline__ float sel3(int k, float x, float y, float z) {
+    return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ void make_ray(const double o[3], const double d[3], RayF& r) {
+    r.ox = (float)o[0]; r.oy = (float)o[1]; r.oz = (float)o[2];
+    float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+    r.idx = safe_inv(dx); r.idy = safe_inv(dy); r.idz = safe_inv(dz);
+    r.oix = r.ox * r.idx; r.oiy = r.oy * r.idy; r.oiz = r.oz * r.idz;
+    // watertight test setup (Woop, Benthin & Wald, JCGT 2013)
+    float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dkz = sel3(kz, dx, dy, dz);
+    if (dkz < 0.0f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.sx = sel3(kx, dx, dy, dz) / dkz;
+    r.sy = sel3(ky, dx, dy, dz) / dkz;
+    r.sz = 1.0f / dkz;
+}
+
+// slab test of one box against [0, tmax]
+__device__ __forceinline__ bool slab(const RayF& r, float lx, float ly, float lz, float hx,
+                                     float hy, float hz, float tmax) {
+    float tx0 = fmaf(lx, r.idx, -r.oix), tx1 = fmaf(hx, r.idx, -r.oix);
+    float ty0 = fmaf(ly, r.idy, -r.oiy), ty1 = fmaf(hy, r.idy, -r.oiy);
+    float tz0 = fmaf(lz, r.idz, -r.oiz), tz1 = fmaf(hz, r.idz, -r.oiz);
+    float tmn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float tmx = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tmn <= tmx;
+}
+
+// Watertight ray-triangle test; on a hit closer than t_best updates t_best.
+__device__ __forceinline__ bool tri_hit(const RayF& r, float4 a, float4 b, float4 c,
+                                        float& t_best) {
+    float Ax = a.x - r.ox, Ay = a.y - r.oy, Az = a.z - r.oz;
+    float Bx = b.x - r.ox, By = b.y - r.oy, Bz = b.z - r.oz;
+    float Cx = c.x - r.ox, Cy = c.y - r.oy, Cz = c.z - r.oz;
+    float akx = sel3(r.kx, Ax, Ay, Az), aky = sel3(r.ky, Ax, Ay, Az), akz = sel3(r.kz, Ax, Ay, Az);
+    float bkx = sel3(r.kx, Bx, By, Bz), bky = sel3(r.ky, Bx, By, Bz), bkz = sel3(r.kz, Bx, By, Bz);
+    float ckx = sel3(r.kx, Cx, Cy, Cz), cky = sel3(r.ky, Cx, Cy, Cz), ckz = sel3(r.kz, Cx, Cy, Cz);
+    float ax_ = fmaf(-r.sx, akz, akx), ay_ = fmaf(-r.sy, akz, aky);
+    float bx_ = fmaf(-r.sx, bkz, bkx), by_ = fmaf(-r.sy, bkz, bky);
+    float cx_ = fmaf(-r.sx, ckz, ckx), cy_ = fmaf(-r.sy, ckz, cky);
+    float U = cx_ * by_ - cy_ * bx_;
+    float V = ax_ * cy_ - ay_ * cx_;
+    float W = bx_ * ay_ - by_ * ax_;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        // edge case: recompute the edge functions in double precision
+        U = (float)((double)cx_ * (double)by_ - (double)cy_ * (double)bx_);
+        V = (float)((double)ax_ * (double)cy_ - (double)ay_ * (double)cx_);
+        W = (float)((double)bx_ * (double)ay_ - (double)by_ * (double)ax_);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    float det = U + V + W;
+    if (det == 0.0f) return false;
+    float T = U * (r.sz * akz) + V * (r.sz * bkz) + W * (r.sz * ckz);
+    if (det < 0.0f) { det = -det; T = -T; }
+    if (T <= 0.0f || T >= t_best * det) return false;
+    t_best = T / det;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-coherent stackless BVH traversal (closest hit).
+//
+// All 32 lanes call it together; every branch below depends only on warp-
+// uniform values (node index, state, votes), so the warp walks one node
+// sequence and each lane keeps its own closest hit.  Instead of a stack the
+// walk uses parent links: `from` records whether the node is entered from
+// its parent (-1), returned to from its near child (0) or from its far child
+// (1); -2 means "returned from `prev`, find out which child it was".  Each
+// internal node is entered at most three times, which bounds the loop.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool active,
+                                         float& t_best, int& hit, uint32_t& flags) {
+    const unsigned full = 0xffffffffu;
+    if (S.n_tri == 0) return;
+    if (S.n_int == 0) {
+        if (active) {
+            float4 a = __ldg(&S.tris[0]), b = __ldg(&S.tris[1]), c = __ldg(&S.tris[2]);
+            if (tri_hit(r, a, b, c, t_best)) hit = 0;
+        }
+        return;
+    }
+    unsigned am = __ballot_sync(full, active);
+    if (am == 0u) return;
+    int rep = __ffs(am) - 1;
+    // near/far order from one representative ray of the packet
+    bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
+    bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
+    bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
+    const float tscale = 1.0f + 4.0f * 1.1920929e-7f;
+    int cur = 0, from = -1, prev = 0;
+    const int max_steps = 3 * S.n_int + 8;
+    for (int step = 0;; ++step) {
+        if (step >= max_steps) { flags |= kPfTraversalCap; break; }
+        const float4* nd = S.nodes + 4 * (size_t)cur;
+        float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        int parent = __float_as_int(n3.z), axis = __float_as_int(n3.w) & 3;
+        bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
+        int near_c = pos ? c0 : c1, far_c = pos ? c1 : c0;
+        if (from == -2) from = (near_c == prev) ? 0 : 1;
+        if (from == -1 || from == 0) {
+            // visit near (from == -1) then far (from == 0 or after a near leaf)
+            bool descended = false;
+            for (int slot = (from == -1 ? 0 : 1); slot < 2; ++slot) {
+                bool second = (slot == 0) ? !pos : pos;  // which stored child box
+                float lx, ly, lz, hx, hy, hz;
+                if (!second) { lx = n0.x; ly = n0.y; lz = n0.z; hx = n0.w; hy = n1.x; hz = n1.y; }
+                else { lx = n1.z; ly = n1.w; lz = n2.x; hx = n2.y; hy = n2.z; hz = n2.w; }
+                int child = slot == 0 ? near_c : far_c;
+                bool h = active && slab(r, lx, ly, lz, hx, hy, hz, t_best * tscale);
+                if (!__any_sync(full, h)) continue;
+                if (child < 0) {
+                    if (h) {
+                        int t = ~child;
+                        const float4* tp = S.tris + 3 * (size_t)t;
+                        float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+                        if (tri_hit(r, a, b, c, t_best)) hit = t;
+                    }
+                    continue;
+                }
+                cur = child;
+                from = -1;
+                descended = true;
+                break;
+            }
+            if (descended) continue;
+        }
+        if (cur == 0) break;
+        prev = cur;
+        cur = parent;
+        from = -2;
+    }
+}
+
+// FP64 range along unit direction d to the plane of triangle t (the closest
+// hit found in FP32), and |cos| of the incidence angle.
+__device__ __forceinline__ double refine_hit(const DevScene& S, int t, const double o[3],
+                                             const double d[3], float& cos_inc) {
+    const float4* tp = S.tris + 3 * (size_t)t;
+    float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+    double e1x = (double)b.x - a.x, e1y = (double)b.y - a.y, e1z = (double)b.z - a.z;
+    double e2x = (double)c.x - a.x, e2y = (double)c.y - a.y, e2z = (double)c.z - a.z;
+    double nx = e1y * e2z - e1z * e2y;
+    double ny = e1z * e2x - e1x * e2z;
+    double nz = e1x * e2y - e1y * e2x;
+    double wx = (double)a.x - o[0], wy = (double)a.y - o[1], wz = (double)a.z - o[2];
+    double num = nx * wx + ny * wy + nz * wz;
+    double den = nx * d[0] + ny * d[1] + nz * d[2];
+    float fn2 = (float)(nx * nx + ny * ny + nz * nz);
+    cos_inc = fabsf((float)den) * rsqrtf(fn2);
+    if (cos_inc > 1.0f) cos_inc = 1.0f;
+    return num / den;
+}
+
+// ---------------------------------------------------------------------------
+// Voxel march (Amanatides & Woo 1987): FP32 index stepping, FP64 segment ends.
+// ---------------------------------------------------------------------------
+struct March {
+    int ix, iy, iz;
+    int sx, sy, sz;
+    int px, py, pz;           // first plane crossed on each axis
+    float tnx, tny, tnz;      // next crossing per axis, FP32 (ordering only)
+    // crossing of plane p on axis a: t = (f0_a + (p - p_a) c) / d_a, where
+    // f0_a = (g0_a + p_a c) - o_a is formed in FP64 like the plain definition
+    // (g0 + p c - o)/d, so nearly parallel axes never cancel large terms
+    float f0x, f0y, f0z;
+    float ivx, ivy, ivz;
+    double f64x, f64y, f64z;
+    double iv64x, iv64y, iv64z;
+    float cell;
+    double t_enter, t_end;    // FP64
+    int entry_axis;           // axis crossed to enter the current voxel, -1: grid entry
+    int steps_left;
+};
+
+__device__ __forceinline__ float cross32(int p, int p0, int s, float f0, float iv, float c) {
+    return s == 0 ? 3.0e38f : fmaf((float)(p - p0), c, f0) * iv;
+}
+
+// set up the march along o + t d for t in [t_enter, min(t_exit, t_hi)); false: no voxel
+__device__ __forceinline__ bool march_init(const DevScene& S, const double o[3],
+                                           const double d[3], double t_hi, March& m) {
+    double g0[3] = {(double)S.g0[0], (double)S.g0[1], (double)S.g0[2]};
+    double cell = (double)S.cell;
+    double tlo[3], thi[3];
+    double te = 0.0, tx = 1e300;
+    int dims[3] = {S.dims[0], S.dims[1], S.dims[2]};
+    for (int a = 0; a < 3; ++a) {
+        double lo = g0[a], hi = g0[a] + (double)dims[a] * cell;
+        if (d[a] == 0.0) {
+            if (o[a] < lo || o[a] >= hi) return false;
+            tlo[a] = -1e300; thi[a] = 1e300;
+        } else {
+            double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+            tlo[a] = fmin(ta, tb);
+            thi[a] = fmax(ta, tb);
+        }
+        te = fmax(te, tlo[a]);
+        tx = fmin(tx, thi[a]);
+    }
+    double tend = fmin(tx, t_hi);
+    if (!(te < tend)) return false;
+    int idx[3], stp[3], p0[3];
+    double f0[3], iv[3];
+    for (int a = 0; a < 3; ++a) {
+        stp[a] = d[a] > 0.0 ? 1 : (d[a] < 0.0 ? -1 : 0);
+        if (te > 0.0 && tlo[a] == te && d[a] != 0.0) {
+            idx[a] = d[a] > 0.0 ? 0 : dims[a] - 1;
+        } else {
+            double p = o[a] + te * d[a];
+            double f = floor((p - g0[a]) / cell);
+            f = fmin(fmax(f, 0.0), (double)(dims[a] - 1));
+            idx[a] = (int)f;
+        }
+        p0[a] = stp[a] > 0 ? idx[a] + 1 : idx[a];
+        f0[a] = stp[a] != 0 ? fma((double)p0[a], cell, g0[a]) - o[a] : 0.0;
+        iv[a] = stp[a] != 0 ? 1.0 / d[a] : 0.0;
+    }
+    m.ix = idx[0]; m.iy = idx[1]; m.iz = idx[2];
+    m.sx = stp[0]; m.sy = stp[1]; m.sz = stp[2];
+    m.px = p0[0]; m.py = p0[1]; m.pz = p0[2];
+    m.f64x = f0[0]; m.f64y = f0[1]; m.f64z = f0[2];
+    m.iv64x = iv[0]; m.iv64y = iv[1]; m.iv64z = iv[2];
+    m.f0x = (float)f0[0]; m.f0y = (float)f0[1]; m.f0z = (float)f0[2];
+    m.ivx = (float)iv[0]; m.ivy = (float)iv[1]; m.ivz = (float)iv[2];
+    m.cell = S.cell;
+    m.tnx = cross32(m.px, m.px, m.sx, m.f0x, m.ivx, m.cell);
+    m.tny = cross32(m.py, m.py, m.sy, m.f0y, m.ivy, m.cell);
+    m.tnz = cross32(m.pz, m.pz, m.sz, m.f0z, m.ivz, m.cell);
+    m.t_enter = te;
+    m.t_end = tend;
+    m.entry_axis = -1;
+    m.steps_left = dims[0] + dims[1] + dims[2] + 4;
+    return true;
+}
+
+// FP64 crossing time of the entry (or exit) face of the current voxel on axis a
+__device__ __forceinline__ double plane64(const March& m, int a, bool entry) {
+    int i = a == 0 ? m.ix : (a == 1 ? m.iy : m.iz);
+    int s = a == 0 ? m.sx : (a == 1 ? m.sy : m.sz);
+    int p0 = a == 0 ? m.px : (a == 1 ? m.py : m.pz);
+    double f0 = a == 0 ? m.f64x : (a == 1 ? m.f64y : m.f64z);
+    double iv = a == 0 ? m.iv64x : (a == 1 ? m.iv64y : m.iv64z);
+    int plane = entry ? (s > 0 ? i : i + 1) : (s > 0 ? i + 1 : i);
+    return fma((double)(plane - p0), (double)m.cell, f0) * iv;
+}
+
+// Current voxel: linear id and exit axis.  Returns false once outside the grid.
+struct VoxSeg {
+    int64_t vid;
+    int exit_axis;
+    float t_out32;
+};
+
+__device__ __forceinline__ bool march_current(const DevScene& S, const March& m, VoxSeg& v) {
+    if (m.ix < 0 || m.iy < 0 || m.iz < 0 || m.ix >= S.dims[0] || m.iy >= S.dims[1] ||
+        m.iz >= S.dims[2])
+        return false;
+    int a = 0;
+    float tn = m.tnx;
+    if (m.tny < tn) { a = 1; tn = m.tny; }
+    if (m.tnz < tn) { a = 2; tn = m.tnz; }
+    v.vid = ((int64_t)m.iz * S.dims[1] + m.iy) * S.dims[0] + m.ix;
+    v.exit_axis = a;
+    v.t_out32 = tn;
+    return true;
+}
+
+// FP64 segment of the current voxel, clipped to [t_enter, t_end]
+__device__ __forceinline__ void march_segment64(const March& m, const VoxSeg& v, double& t_in,
+                                                double& t_out) {
+    t_in = m.entry_axis < 0 ? m.t_enter : fmax(plane64(m, m.entry_axis, true), m.t_enter);
+    t_out = fmin(plane64(m, v.exit_axis, false), m.t_end);
+}
+
+// advance to the next voxel; false when past t_end or out of steps
+__device__ __forceinline__ bool march_step(March& m, const VoxSeg& v, uint32_t& flags) {
+    if (--m.steps_left <= 0) { flags |= kPfMarchCap; return false; }
+    if ((double)v.t_out32 >= m.t_end) {
+        // FP32 ordering says the segment ends here; confirm in FP64
+        if (plane64(m, v.exit_axis, false) >= m.t_end) return false;
+    }
+    int a = v.exit_axis;
+    if (a == 0) {
+        m.ix += m.sx;
+        m.tnx = cross32(m.sx > 0 ? m.ix + 1 : m.ix, m.px, m.sx, m.f0x, m.ivx, m.cell);
+    } else if (a == 1) {
+        m.iy += m.sy;
+        m.tny = cross32(m.sy > 0 ? m.iy + 1 : m.iy, m.py, m.sy, m.f0y, m.ivy, m.cell);
+    } else {
+        m.iz += m.sz;
+        m.tnz = cross32(m.sz > 0 ? m.iz + 1 : m.iz, m.pz, m.sz, m.f0z, m.ivz, m.cell);
+    }
+    m.entry_axis = a;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// power (Eq. beamdiv, Eq. beamdiv_w, Eq. ladlut_intensity with a Lambertian
+// cross-section): P = I0 exp(-2 r^2/w^2) Dr^2 eta rho cos / (4 R^2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float return_power(const DevScanner& sn, double R64, float tan_a,
+                                              float rho, float cos_inc) {
+    float R = (float)R64;
+    float z = sn.zk * (R - sn.focus);
+    float w2 = sn.w0sq * (1.0f + z * z);
+    float r = R * tan_a;
+    float Is = expf(-2.0f * r * r / w2);
+    return sn.pconst * Is * rho * cos_inc / (R * R);
+}
+
+// pulse shape at time x (ns) relative to the return's delay
+__device__ __forceinline__ float pulse_shape(const DevScanner& sn, float x) {
+    if (sn.pulse_shape == 0) return exp2f(-x * x * sn.gk2);
+    if (x < 0.0f) return 0.0f;
+    float y = x * sn.ctau_inv;
+    return y * y * expf(-y);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace hg

@@ -1,0 +1,65 @@
+// hg_host.h - host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/helios.h"
+#include "hg_device.cuh"
+
+struct helios_scene {
+    int device;
+    int64_t n_tri, n_int;
+    int32_t n_mesh, n_grid;
+    float4* nodes;            // [n_int][4]
+    float4* tris;             // [n_tri][3]
+    int32_t* tri_index;       // [n_tri] global id -> packed position
+    const float* refl[hg::kMaxMesh];
+    int32_t mesh_first[hg::kMaxMesh + 1];
+    int64_t mesh_faces[hg::kMaxMesh];
+    helios_voxel_desc grid;
+    int64_t bytes;
+};
+
+namespace hg {
+
+helios_status set_error(helios_status code, const char* fmt, ...);
+helios_status set_cuda_error(const char* what, cudaError_t e);
+
+struct ScanLaunch {
+    std::vector<DevScene> scenes;
+    std::vector<DevScanner> scanners;
+    std::vector<DevLeg> legs;
+    Outputs out;
+    uint64_t seed;
+    int mode;
+    int persistent;
+    int threads;
+    int blocks_per_sm;
+};
+
+helios_status launch_scan(const ScanLaunch& L, cudaStream_t st);
+size_t scan_params_bytes();
+
+struct AdjointLaunch {
+    std::vector<DevScene> scenes;
+    std::vector<DevScanner> scanners;
+    std::vector<DevLeg> legs;
+    // gradients per scene
+    std::vector<std::vector<float*>> d_refl;
+    std::vector<float*> d_density;
+    const float* g;
+    const int32_t* window;
+    const int32_t* subray_hit;
+    int threads;
+};
+
+helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st);
+
+helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st);
+
+}  // namespace hg

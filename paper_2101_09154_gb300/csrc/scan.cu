@@ -1,0 +1,567 @@
+// scan.cu - the fused per-pulse kernel: pulse pose -> subrays -> BVH traversal and
+// voxel march -> return power -> waveform -> echoes, one work item (a run of
+// consecutive pulses of one leg) per thread-block iteration.
+//
+// Block layout (256 threads, 8 warps):
+//   phase 0  one thread per pulse: FP64 pose + ONB into shared memory
+//   phase 1  ray-major: each warp takes packets of 32 consecutive subrays
+//            (about 1.7 pulses at 19 subrays, so no lane idles), traverses
+//            the BVH warp-coherently and marches the voxels
+//   phase 2  pulse-major: one warp per pulse sums the returns into a
+//            shared-memory waveform (lanes own bins, returns in fixed order:
+//            deterministic, no atomics), finds echoes with ballots, writes
+//            the waveform row with 16-byte streaming stores.
+#include "hg_device.cuh"
+#include "hg_host.h"
+
+#include <cfloat>
+
+namespace hg {
+
+struct RayRes {
+    double R;      // event range (stochastic) / triangle range (expected); +inf: none
+    double R2;     // expected mode: first voxel return range; +inf: none
+    float P;       // return power (expected mode: triangle power at unit weight)
+    int32_t id;    // event primitive / triangle id; -1: none
+};
+
+template <int NL>
+struct ScanParams {
+    DevScene scenes[kMaxScenes];
+    DevScanner scanners[kMaxScanners];
+    DevLeg legs[NL];
+    Outputs out;
+    uint64_t seed;
+    int32_t n_items, n_legs;
+    int32_t s_cap, pc_cap, rays_cap, nb_cap;
+    int32_t* queue;
+};
+
+__device__ __forceinline__ double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// add one return (delay tau relative to the window start, power P) to the
+// warp's waveform; every bin is touched by one lane, returns come in order
+__device__ __forceinline__ void accumulate(float* W, int nb, const DevScanner& sn, float dt,
+                                           float tau, float P, int lane) {
+    int blo = max(0, __float2int_ru((tau - sn.cut_lo) / dt));
+    int bhi = min(nb - 1, __float2int_rd((tau + sn.cut_hi) / dt));
+    for (int b = blo + lane; b <= bhi; b += 32) W[b] += P * pulse_shape(sn, (float)b * dt - tau);
+}
+
+__device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* bid, int nb,
+                                                const DevScanner& sn, float dt, float tau,
+                                                float P, int32_t id, int lane) {
+    int blo = max(0, __float2int_ru((tau - sn.cut_lo) / dt));
+    int bhi = min(nb - 1, __float2int_rd((tau + sn.cut_hi) / dt));
+    for (int b = blo + lane; b <= bhi; b += 32) {
+        float v = P * pulse_shape(sn, (float)b * dt - tau);
+        W[b] += v;
+        if (v > best[b]) { best[b] = v; bid[b] = id; }
+    }
+}
+
+__device__ __forceinline__ float delay_rel(double R, double mdt) {
+    return (float)(2.0 * R / kC * 1e9 - mdt);
+}
+
+template <int MODE, bool GRID, int NL>
+__global__ void __launch_bounds__(256)
+scan_kernel(const __grid_constant__ ScanParams<NL> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PulseFrame* s_pf = reinterpret_cast<PulseFrame*>(smem);
+    SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
+    RayRes* s_rr = reinterpret_cast<RayRes*>(s_sc + P.s_cap);
+    uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_rr + P.rays_cap);
+    // the per-warp waveform rows start 16-byte aligned (float4 reads below)
+    float* s_w = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(s_pflag + P.pc_cap) + 15u) & ~uintptr_t(15));
+    __shared__ int s_item;
+    __shared__ int s_cached_leg;
+    __shared__ double s_rot[6];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
+    if (tid == 0) s_cached_leg = -1;
+    __syncthreads();
+
+    for (int it = 0;; ++it) {
+        int item;
+        if (NL == 1) {
+            item = blockIdx.x + it * gridDim.x;
+        } else {
+            if (tid == 0) s_item = atomicAdd(P.queue, 1);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= P.n_items) break;
+        int li = 0;
+        if (NL > 1) {
+            int lo = 0, hi = P.n_legs - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (P.legs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+            }
+            li = lo;
+        }
+        const DevLeg& lg = P.legs[li];
+        const DevScanner& sn = P.scanners[lg.scanner];
+        const DevScene& sc = P.scenes[lg.scene];
+        const int S = lg.S;
+        const int64_t p0 = (int64_t)(item - lg.item_begin) * lg.pulses_per_item;
+        const int pc = (int)min((int64_t)lg.pulses_per_item, lg.n_pulses - p0);
+        const int nb = sn.n_bins;
+        const int K = sn.max_echoes;
+        const float dt = (float)sn.bin_ns;
+
+        // subray table and platform attitude, recomputed when the leg changes
+        const bool new_leg = li != s_cached_leg;   // uniform: last written before a barrier
+        __syncthreads();
+        if (new_leg) {
+            for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
+            if (tid == 0) {
+                sincos(lg.rpy[0], &s_rot[0], &s_rot[1]);
+                sincos(lg.rpy[1], &s_rot[2], &s_rot[3]);
+                sincos(lg.rpy[2], &s_rot[4], &s_rot[5]);
+                s_cached_leg = li;
+            }
+            __syncthreads();
+        }
+        // ---------------- phase 0: pulse frames ----------------
+        for (int t = tid; t < pc; t += blockDim.x) {
+            PulseFrame f;
+            pulse_frame(sn, lg, s_rot, p0 + t, f);
+            s_pf[t] = f;
+            s_pflag[t] = 0u;
+        }
+        __syncthreads();
+
+        // ---------------- phase 1: subrays, ray-major packets ----------------
+        const int n_rays = pc * S;
+        for (int pk = warp; pk * 32 < n_rays; pk += nwarps) {
+            int r = pk * 32 + lane;
+            bool active = r < n_rays;
+            int pl = active ? r / S : 0;
+            int s = active ? r - pl * S : 0;
+            double o[3], d[3];
+            {
+                const PulseFrame& f = s_pf[pl];
+                const SubrayConst& c = s_sc[s];
+                for (int a = 0; a < 3; ++a) {
+                    o[a] = f.o[a];
+                    d[a] = c.ca * f.d[a] + c.sacp * f.u[a] + c.sasp * f.v[a];
+                }
+            }
+            RayF ray;
+            make_ray(o, d, ray);
+            float tb = 3.0e38f;
+            int hit = -1;
+            uint32_t fl = 0;
+            traverse(sc, ray, active, tb, hit, fl);
+            RayRes rr;
+            rr.R = CUDART_INF;
+            rr.R2 = CUDART_INF;
+            rr.P = 0.0f;
+            rr.id = -1;
+            float tan_a = s_sc[s].tan_a;
+            if (active) {
+                float cosi = 0.0f;
+                double t_tri = CUDART_INF;
+                int gid = -1;
+                float rho = 0.0f;
+                if (hit >= 0) {
+                    t_tri = refine_hit(sc, hit, o, d, cosi);
+                    const float4* tp = sc.tris + 3 * (size_t)hit;
+                    gid = __float_as_int(__ldg(&tp[0].w));
+                    int mesh = __float_as_int(__ldg(&tp[1].w));
+                    int face = __float_as_int(__ldg(&tp[2].w));
+                    rho = __ldg(&sc.refl[mesh][face]);
+                    if (!(t_tri > 0.0)) { t_tri = CUDART_INF; gid = -1; }
+                }
+                bool voxel_event = false;
+                if (GRID && sc.has_grid) {
+                    March m;
+                    if (march_init(sc, o, d, t_tri, m)) {
+                        const int64_t k = p0 + pl;
+                        for (;;) {
+                            VoxSeg v;
+                            if (!march_current(sc, m, v)) break;
+                            float dens = __ldg(&sc.density[v.vid]);
+                            if (dens > 0.0f) {
+                                double t_in, t_out;
+                                march_segment64(m, v, t_in, t_out);
+                                double len = t_out - t_in;
+                                if (len > 0.0) {
+                                    float sigma = sc.G * dens;
+                                    if (MODE == 0) {
+                                        // Eq. intersection_dist: s = -ln(u)/sigma
+                                        uint64_t w[4];
+                                        philox4x64((uint64_t)k, (uint64_t)(uint32_t)s,
+                                                   (uint64_t)v.vid, (uint64_t)lg.leg_id,
+                                                   P.seed, 0ull, w);
+                                        float sdist = -logf(uniform23(w[0])) / sigma;
+                                        if ((double)sdist < len) {
+                                            double R = t_in + (double)sdist;
+                                            rr.R = R;
+                                            rr.id = sc.n_tri + (int32_t)v.vid;
+                                            rr.P = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f);
+                                            voxel_event = true;
+                                            break;
+                                        }
+                                    } else {
+                                        rr.R2 = t_in + 0.5 * len;
+                                        break;
+                                    }
+                                }
+                            }
+                            if (!march_step(m, v, fl)) break;
+                        }
+                    }
+                }
+                if (!voxel_event && gid >= 0) {
+                    rr.R = t_tri;
+                    rr.id = gid;
+                    rr.P = return_power(sn, t_tri, tan_a, rho, cosi);
+                }
+                s_rr[r] = rr;
+                if (fl) atomicOr(&s_pflag[pl], fl);
+                if (P.out.subray_hit) {
+                    int64_t so = lg.sub_off + (p0 + pl) * S + s;
+                    P.out.subray_hit[so] = rr.id;
+                    if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? (float)rr.R : 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---------------- phase 2: waveform + echoes, one warp per pulse ----------------
+        const int nbw = P.nb_cap;
+        float* W = s_w + (size_t)warp * nbw * (MODE == 1 ? 3 : 1);
+        float* best = W + nbw;
+        int32_t* bid = reinterpret_cast<int32_t*>(W + 2 * nbw);
+        for (int pl = warp; pl < pc; pl += nwarps) {
+            const int64_t k = p0 + pl;
+            const int64_t gp = lg.pulse_off + k;
+            const RayRes* rrp = s_rr + (size_t)pl * S;
+            double rmin = CUDART_INF;
+            for (int s = lane; s < S; s += 32) {
+                RayRes rr = rrp[s];
+                if (rr.id >= 0) rmin = fmin(rmin, rr.R);
+                if (MODE == 1) rmin = fmin(rmin, rr.R2);
+            }
+            rmin = warp_min(rmin);
+            uint32_t pflag = s_pflag[pl];
+            float* row = P.out.waveform + lg.wave_off + k * nb;
+            const int64_t eb = lg.echo_off + k * K;
+            if (rmin == CUDART_INF) {
+                for (int b = lane; b < nb; b += 32) __stcs(row + b, 0.0f);
+                for (int e = lane; e < K; e += 32) {
+                    P.out.echo_range[eb + e] = 0.0f;
+                    if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
+                    if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
+                    if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
+                }
+                if (lane == 0) {
+                    P.out.window_bin[gp] = kNoWindow;
+                    P.out.echo_count[gp] = 0;
+                    if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)(pflag | kPfNoReturn);
+                }
+                continue;
+            }
+            double x = 2.0 * rmin / kC * 1e9 / sn.bin_ns;
+            int32_t m = (int32_t)floor(x) - sn.n_pre;
+            double mdt = (double)m * sn.bin_ns;
+            for (int b = lane; b < nb; b += 32) {
+                W[b] = 0.0f;
+                if (MODE == 1) { best[b] = 0.0f; bid[b] = -1; }
+            }
+            __syncwarp();
+            if (MODE == 0) {
+                for (int s = 0; s < S; ++s) {
+                    RayRes rr = rrp[s];
+                    if (rr.id < 0) continue;
+                    accumulate(W, nb, sn, dt, delay_rel(rr.R, mdt), rr.P, lane);
+                }
+            } else {
+                // expected transmittance: every crossed voxel returns
+                // w = T (1 - e^{-sigma l}) at its midpoint, the triangle T.
+                const PulseFrame& f = s_pf[pl];
+                for (int s0 = 0; s0 < S; s0 += 32) {
+                    int s = s0 + lane;
+                    bool lane_on = s < S;
+                    RayRes rr;
+                    rr.id = -1;
+                    rr.R = CUDART_INF;
+                    rr.P = 0.0f;
+                    float T = 1.0f;
+                    float tan_a = 0.0f;
+                    if (lane_on) {
+                        rr = rrp[s];
+                        tan_a = s_sc[s].tan_a;
+                    }
+                    bool on = false;
+                    March mch;
+                    uint32_t fl = 0;
+                    if (GRID && sc.has_grid && lane_on) {
+                        double o[3], d[3];
+                        const SubrayConst& c = s_sc[s];
+                        for (int a = 0; a < 3; ++a) {
+                            o[a] = f.o[a];
+                            d[a] = c.ca * f.d[a] + c.sacp * f.u[a] + c.sasp * f.v[a];
+                        }
+                        double t_hi = rr.id >= 0 ? rr.R : CUDART_INF;
+                        on = march_init(sc, o, d, t_hi, mch);
+                    }
+                    while (__any_sync(full, on)) {
+                        bool has = false;
+                        float tau = 0.0f, pv = 0.0f;
+                        int32_t vid = 0;
+                        while (on) {
+                            VoxSeg v;
+                            if (!march_current(sc, mch, v)) { on = false; break; }
+                            float dens = __ldg(&sc.density[v.vid]);
+                            if (dens > 0.0f) {
+                                double t_in, t_out;
+                                march_segment64(mch, v, t_in, t_out);
+                                double len = t_out - t_in;
+                                if (len > 0.0) {
+                                    float xs = sc.G * dens * (float)len;
+                                    float w = -T * expm1f(-xs);
+                                    T *= expf(-xs);
+                                    double R = t_in + 0.5 * len;
+                                    pv = w * return_power(sn, R, tan_a, sc.leaf_refl, 1.0f);
+                                    tau = delay_rel(R, mdt);
+                                    vid = sc.n_tri + (int32_t)v.vid;
+                                    has = true;
+                                }
+                            }
+                            if (!march_step(mch, v, fl)) on = false;
+                            if (has) break;
+                        }
+                        unsigned hm = __ballot_sync(full, has);
+                        while (hm) {
+                            int src = __ffs(hm) - 1;
+                            hm &= hm - 1;
+                            float tb = __shfl_sync(full, tau, src);
+                            float pb = __shfl_sync(full, pv, src);
+                            int32_t ib = __shfl_sync(full, vid, src);
+                            accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
+                        }
+                    }
+                    if (fl) atomicOr(&s_pflag[pl], fl);
+                    bool has_tri = lane_on && rr.id >= 0;
+                    float ttau = has_tri ? delay_rel(rr.R, mdt) : 0.0f;
+                    float tp = T * rr.P;
+                    unsigned hm = __ballot_sync(full, has_tri);
+                    while (hm) {
+                        int src = __ffs(hm) - 1;
+                        hm &= hm - 1;
+                        float tb = __shfl_sync(full, ttau, src);
+                        float pb = __shfl_sync(full, tp, src);
+                        int32_t ib = __shfl_sync(full, rr.id, src);
+                        accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
+                    }
+                }
+            }
+            __syncwarp();
+            // ---- echoes: 3-bin local maxima at or above thr * max(W) ----
+            float wmax = 0.0f;
+            for (int b = lane; b < nb; b += 32) wmax = fmaxf(wmax, W[b]);
+            wmax = warp_maxf(wmax);
+            const float thr = sn.thr_rel * wmax;
+            int count = 0;
+            for (int base = 0; base < nb; base += 32) {
+                int b = base + lane;
+                float c = b < nb ? W[b] : 0.0f;
+                float l = (b > 0 && b < nb) ? W[b - 1] : 0.0f;
+                float rgt = (b + 1 < nb) ? W[b + 1] : 0.0f;
+                bool ismax = b < nb && c > l && c >= rgt && c >= thr && c > 0.0f;
+                unsigned mk = __ballot_sync(full, ismax);
+                int pos = count + __popc(mk & lanemask_lt());
+                if (ismax && pos < K) {
+                    int32_t obj = -1;
+                    if (MODE == 1) {
+                        obj = bid[b];
+                    } else {
+                        float bv = -1.0f;
+                        float tbin = (float)b * dt;
+                        for (int s = 0; s < S; ++s) {
+                            RayRes rr = rrp[s];
+                            if (rr.id < 0) continue;
+                            float v = rr.P * pulse_shape(sn, tbin - delay_rel(rr.R, mdt));
+                            if (v > bv) { bv = v; obj = rr.id; }
+                        }
+                    }
+                    double Rc = 0.5 * kC * ((double)(m + b) * sn.bin_ns - sn.echo_offset_ns) * 1e-9;
+                    uint64_t w[4];
+                    philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
+                               (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                    float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
+                    float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+                    P.out.echo_range[eb + pos] = (float)(Rc + (double)(sn.noise_sigma * z));
+                    if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
+                    if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
+                    if (P.out.echo_object) P.out.echo_object[eb + pos] = obj;
+                }
+                count += __popc(mk);
+            }
+            // unused echo slots
+            for (int e = count + lane; e < K; e += 32) {
+                P.out.echo_range[eb + e] = 0.0f;
+                if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
+                if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
+                if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
+            }
+            if (lane == 0) {
+                if (count > K) {
+                    pflag |= kPfEchoOverflow;
+                    if (P.out.status) atomicOr(P.out.status, kStEchoOverflow);
+                }
+                if (P.out.status && (pflag & kPfTraversalCap)) atomicOr(P.out.status, kStTraversalCap);
+                if (P.out.status && (pflag & kPfMarchCap)) atomicOr(P.out.status, kStMarchCap);
+                P.out.window_bin[gp] = m;
+                P.out.echo_count[gp] = min(count, K);
+                if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)pflag;
+            }
+            // ---- waveform row: 16-byte streaming stores when aligned ----
+            if (((reinterpret_cast<uintptr_t>(row) & 15u) == 0) && (nb & 3) == 0) {
+                for (int b = lane * 4; b < nb; b += 128)
+                    __stcs(reinterpret_cast<float4*>(row + b), *reinterpret_cast<const float4*>(W + b));
+            } else {
+                for (int b = lane; b < nb; b += 32) __stcs(row + b, W[b]);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+// ---------------------------------------------------------------------------
+template <int MODE, bool GRID, int NL>
+static helios_status launch_one(const ScanParams<NL>& p, int threads, int blocks_per_sm,
+                                size_t smem, cudaStream_t st, int grid_cap) {
+    auto kern = scan_kernel<MODE, GRID, NL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return set_cuda_error("cudaFuncSetAttribute(scan)", e);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return set_cuda_error("occupancy(scan)", e);
+    if (occ < 1) return set_error(HELIOS_ERR_UNSUPPORTED, "scan kernel does not fit on an SM (smem %zu)", smem);
+    int bps = blocks_per_sm > 0 ? min(blocks_per_sm, occ) : occ;
+    int grid = sms * bps;
+    if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+    kern<<<grid, threads, smem, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error("scan kernel launch", e);
+    return HELIOS_OK;
+}
+
+template <int NL>
+static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int threads,
+                              int blocks_per_sm, size_t smem, cudaStream_t st, int grid_cap) {
+    if (mode == 0) {
+        return grid ? launch_one<0, true, NL>(p, threads, blocks_per_sm, smem, st, grid_cap)
+                    : launch_one<0, false, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    }
+    return grid ? launch_one<1, true, NL>(p, threads, blocks_per_sm, smem, st, grid_cap)
+                : launch_one<1, false, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+}
+
+static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads) {
+    size_t b = sizeof(PulseFrame) * pc_cap + sizeof(SubrayConst) * s_cap +
+               sizeof(RayRes) * rays_cap + sizeof(uint32_t) * pc_cap;
+    b = (b + 15) & ~size_t(15);
+    b += (size_t)(threads / 32) * nb_cap * sizeof(float) * (mode == 1 ? 3 : 1);
+    return b;
+}
+
+helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
+    const int threads = L.threads;
+    const int n_legs = (int)L.legs.size();
+    // smem sizing over all legs of the launch
+    int s_cap = 1, pc_cap = 1, rays_cap = 32, nb_cap = 4;
+    for (const DevLeg& lg : L.legs) {
+        s_cap = max(s_cap, lg.S);
+        pc_cap = max(pc_cap, lg.pulses_per_item);
+        rays_cap = max(rays_cap, lg.S * lg.pulses_per_item);
+        nb_cap = max(nb_cap, L.scanners[lg.scanner].n_bins);
+    }
+    nb_cap = (nb_cap + 3) & ~3;
+    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads);
+    if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
+    bool any_grid = false;
+    for (const DevLeg& lg : L.legs) any_grid |= L.scenes[lg.scene].has_grid != 0;
+
+    if (!L.persistent) {
+        for (int l = 0; l < n_legs; ++l) {
+            ScanParams<1> p;
+            memset(&p, 0, sizeof(p));
+            for (size_t i = 0; i < L.scenes.size(); ++i) p.scenes[i] = L.scenes[i];
+            for (size_t i = 0; i < L.scanners.size(); ++i) p.scanners[i] = L.scanners[i];
+            p.legs[0] = L.legs[l];
+            p.legs[0].item_begin = 0;
+            p.out = L.out;
+            p.seed = L.seed;
+            p.n_legs = 1;
+            int64_t items = (L.legs[l].n_pulses + L.legs[l].pulses_per_item - 1) / L.legs[l].pulses_per_item;
+            if (items == 0) continue;
+            p.n_items = (int32_t)items;
+            p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
+            p.queue = nullptr;
+            bool g = L.scenes[L.legs[l].scene].has_grid != 0;
+            helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
+            if (s != HELIOS_OK) return s;
+        }
+        return HELIOS_OK;
+    }
+    // persistent: one launch per group of up to kMaxLegs legs, fed by an atomic queue
+    for (int l0 = 0; l0 < n_legs; l0 += kMaxLegs) {
+        int nl = min(kMaxLegs, n_legs - l0);
+        ScanParams<kMaxLegs>* p = new ScanParams<kMaxLegs>();
+        memset(p, 0, sizeof(*p));
+        for (size_t i = 0; i < L.scenes.size(); ++i) p->scenes[i] = L.scenes[i];
+        for (size_t i = 0; i < L.scanners.size(); ++i) p->scanners[i] = L.scanners[i];
+        int64_t items = 0;
+        for (int l = 0; l < nl; ++l) {
+            p->legs[l] = L.legs[l0 + l];
+            p->legs[l].item_begin = items;
+            items += (L.legs[l0 + l].n_pulses + L.legs[l0 + l].pulses_per_item - 1) /
+                     L.legs[l0 + l].pulses_per_item;
+        }
+        if (items >= INT32_MAX) { delete p; return set_error(HELIOS_ERR_UNSUPPORTED, "too many work items"); }
+        p->out = L.out;
+        p->seed = L.seed;
+        p->n_legs = nl;
+        p->n_items = (int32_t)items;
+        p->s_cap = s_cap; p->pc_cap = pc_cap; p->rays_cap = rays_cap; p->nb_cap = nb_cap;
+        int32_t* q = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int32_t), st);
+        if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(queue)", e); }
+        e = cudaMemsetAsync(q, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) { cudaFreeAsync(q, st); delete p; return set_cuda_error("cudaMemsetAsync(queue)", e); }
+        p->queue = q;
+        helios_status s = dispatch<kMaxLegs>(*p, L.mode, any_grid, threads, L.blocks_per_sm, smem, st, 0);
+        cudaFreeAsync(q, st);
+        delete p;
+        if (s != HELIOS_OK) return s;
+    }
+    return HELIOS_OK;
+}
+
+static_assert(sizeof(ScanParams<kMaxLegs>) <= 32000, "kernel parameters must fit the 32 KB limit");
+
+size_t scan_params_bytes() { return sizeof(ScanParams<kMaxLegs>); }
+
+}  // namespace hg

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every function include/helios.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "helios.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(helios_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_09154_gb300 as hg
+    return hg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("helios_build_scene", "helios_scan_legs", "helios_scan_adjoint",
+                     "helios_free_scene", "helios_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    assert [hg.subray_count(q) for q in range(4)] == [1, 7, 19, 37]
+    assert hg.subray_count(-1) == -1
+    assert lib.helios_version().startswith(b"helios_gb300")
+    w = scenes.batched_legs(n_legs=5, tile=16, block=8, n_terrain=1, n_voxel=1,
+                            min_pulses=100, max_pulses=1000)
+    lay = hg.output_layout(w.scanners, w.legs)
+    S = [hg.subray_count(l.beam_sample_quality) for l in w.legs]
+    n = [l.n_pulses for l in w.legs]
+    assert lay["total_pulses"] == sum(n)
+    assert list(lay["pulse_offset"]) == [sum(n[:i]) for i in range(5)]
+    assert list(lay["subray_offset"]) == [sum(a * b for a, b in zip(n[:i], S[:i])) for i in range(5)]
+    nb = [w.scanners[l.scanner_index].n_bins for l in w.legs]
+    assert list(lay["wave_offset"]) == [sum(a * b for a, b in zip(n[:i], nb[:i])) for i in range(5)]
+
+
+def test_invalid_arguments_return_codes_without_a_gpu(lib):
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    sc = scenes.Scanner(n_bins=2)          # below the 4-bin minimum
+    leg = scenes.Leg(n_pulses=10)
+    with pytest.raises(hg.HeliosError) as e:
+        hg.output_layout([sc], [leg])
+    assert e.value.code == -1 and "n_bins" in str(e.value)
+    sc = scenes.Scanner(beam_sample_quality=12)
+    with pytest.raises(hg.HeliosError):
+        hg.output_layout([sc], [leg])
+    sc = scenes.Scanner()
+    with pytest.raises(hg.HeliosError):
+        hg.output_layout([sc], [scenes.Leg(scanner_index=3, n_pulses=1)])
+    # NULL scene list is rejected before anything touches a device
+    opts = hg.ScanOpts()
+    outs = hg.Outputs()
+    code = lib.helios_scan_legs(None, 0, None, 0, None, 0, ctypes.byref(opts), ctypes.byref(outs), None)
+    assert code == -1
+    assert b"n_scenes" in lib.helios_last_error()

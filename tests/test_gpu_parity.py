@@ -1,0 +1,193 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Every test here needs a GB300; all inputs are seeded synthetic workloads from
+``scenes``.  Tolerances are documented in ``tests/parity.py``.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from parity import compare, leg_view, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_09154_gb300 as m
+    return m
+
+
+def run_both(hg, w, mode=0, seed=0, rows=None, persistent=False, threads=0, **kw):
+    gsc = [hg.Scene(s) for s in w.scenes]
+    out, lay = hg.scan(gsc, w.scanners, w.legs, mode=mode, seed=seed, persistent=persistent, **kw)
+    torch.cuda.synchronize()
+    res = []
+    for l, leg in enumerate(w.legs):
+        sc = w.scanners[leg.scanner_index]
+        q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else sc.beam_sample_quality
+        S = hg.subray_count(q)
+        r = np.arange(leg.n_pulses) if rows is None else rows
+        osc = oracle.OracleScene(w.scenes[leg.scene_index])
+        ref = oracle.scan(osc, sc, leg, r, mode=mode, seed=seed, threads=threads)
+        res.append((leg_view(out, lay, l, sc, S, r), ref))
+    return out, lay, res
+
+
+def test_tls_tiny_full_scan(hg):
+    """98-triangle TLS scene, all 10^4 pulses, 19 subrays, stochastic mode."""
+    w = scenes.tls_tiny()
+    _, _, res = run_both(hg, w, seed=0)
+    stats = compare(*res[0])
+    assert stats["echoes"] > 3000
+
+
+def test_als_terrain_small_ragged(hg):
+    """Terrain + trees; 6001 pulses (not a multiple of the work item) at 512 bins."""
+    w = scenes.als_terrain(seed=5, size=128, n_trees=12, n_pulses=6001, n_bins=512, agl=120.0,
+                           speed=30.0, prf=50_000.0)
+    _, _, res = run_both(hg, w, seed=3)
+    stats = compare(*res[0])
+    assert stats["echoes"] > 3000
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_uls_voxels_small(hg, mode):
+    """Transmissive voxels over a ground plane, stochastic and expected modes."""
+    w = scenes.uls_voxels(seed=6, n=48, n_pulses=3001, n_bins=512, agl=12.0, speed=1.0,
+                          prf=2000.0)
+    _, _, res = run_both(hg, w, mode=mode, seed=11)
+    stats = compare(*res[0], expected_mode=(mode == 1))
+    assert stats["echoes"] > 1000
+
+
+@pytest.mark.parametrize("q", [0, 1, 3])
+def test_subray_qualities_and_carlsson_pulse(hg, q):
+    """S = 1, 7, 37 (more subrays than warp lanes) with the Eq. beam_time pulse."""
+    w = scenes.tls_tiny(n_az=40, n_el=30)
+    w = scenes.with_scanner(w, beam_sample_quality=q, pulse_shape=scenes.PULSE_CARLSSON,
+                            pulse_length_ns=3.5, n_bins=160)
+    _, _, res = run_both(hg, w, seed=2)
+    compare(*res[0])
+
+
+def test_multi_leg_offsets_and_persistent_bitwise(hg):
+    """Legs of uneven length and quality: per-leg parity, and the persistent
+    work-queue launch reproduces the per-leg launches bit for bit."""
+    w = scenes.batched_legs(seed=8, n_legs=6, tile=64, block=24, n_terrain=2, n_voxel=2,
+                            min_pulses=500, max_pulses=4000, n_bins=256)
+    # shrink the voxel legs' altitude so the small blocks are inside the swath
+    out_a, lay, res = run_both(hg, w, seed=4)
+    for g, ref in res:
+        compare(g, ref)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    out_b, _ = hg.scan(gsc, w.scanners, w.legs, seed=4, persistent=True)
+    torch.cuda.synchronize()
+    for k in ("waveform", "window_bin", "echo_count", "echo_range", "echo_bin", "echo_object",
+              "subray_hit", "subray_range"):
+        assert torch.equal(out_a[k], out_b[k]), k
+
+
+def test_deterministic_repeat(hg):
+    w = scenes.als_terrain(seed=5, size=96, n_trees=6, n_pulses=3000, n_bins=256, agl=80.0)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    a, _ = hg.scan(gsc, w.scanners, w.legs, seed=1)
+    b, _ = hg.scan(gsc, w.scanners, w.legs, seed=1)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_edge_cases_empty_leg_sky_one_triangle_grid_only(hg):
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=16, grid_n_el=9,
+                        el_min_rad=-1.2, el_max_rad=1.2, n_bins=128)
+    one = scenes.Scene(meshes=[scenes.Mesh(np.array([[-5, -5, -2], [5, -5, -2], [0, 6, -2]], np.float32),
+                                           np.array([[0, 1, 2]], np.int32), np.array([0.4], np.float32))])
+    dens = np.zeros((6, 6, 6), np.float32)
+    dens[2:4, 2:4, :] = 1.5
+    gridonly = scenes.Scene(grids=[scenes.VoxelGrid(origin=(-3.0, -3.0, -4.0), cell=1.0, dims=(6, 6, 6),
+                                                    density=dens)])
+    legs = [scenes.Leg(scene_index=0, n_pulses=0, leg_id=1),
+            scenes.Leg(scene_index=0, n_pulses=144, leg_id=2),
+            scenes.Leg(scene_index=1, n_pulses=144, leg_id=3, start=(0.2, 0.1, 0.0))]
+    w = scenes.Workload("edge", [one, gridonly], [sc], legs)
+    out, lay, res = run_both(hg, w, seed=5)
+    for g, ref in res[1:]:
+        compare(g, ref, max_flag_frac=0.3)
+    # upward pulses return nothing
+    g, ref = res[1]
+    nohit = (ref["flags"] & oracle.F_NOHIT) != 0
+    assert nohit.any() and (g["window_bin"][nohit] == hg.NO_WINDOW).all()
+    assert (g["pulse_flags"][nohit] & hg.PF_NO_RETURN).all()
+
+
+def test_bad_face_index_is_rejected(hg):
+    bad = scenes.Scene(meshes=[scenes.Mesh(np.zeros((3, 3), np.float32), np.array([[0, 1, 7]], np.int32),
+                                           np.array([0.5], np.float32))])
+    with pytest.raises(hg.HeliosError) as e:
+        hg.Scene(bad)
+    assert e.value.code == -1
+
+
+def test_adjoint_matches_oracle(hg):
+    """Expected-mode adjoint: GPU gradients vs the oracle's analytic gradients
+    (the latter pinned to FP64 central differences on the CPU)."""
+    w = scenes.uls_voxels(seed=4, n=32, n_pulses=1200, n_bins=384, agl=10.0, speed=1.0, prf=1000.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    out, lay = hg.scan([gs], [sc], [leg], mode=1)
+    ref_d = scenes.perturbed_density(w.scenes[0].grids[0].density, seed=1)
+    gref = hg.Scene(scenes.Scene(meshes=w.scenes[0].meshes,
+                                 grids=[scenes.VoxelGrid(**{**w.scenes[0].grids[0].__dict__,
+                                                           "density": ref_d})]))
+    out_ref, _ = hg.scan([gref], [sc], [leg], mode=1)
+    gW = 2.0 * (out["waveform"] - out_ref["waveform"])
+    grads = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"])
+    torch.cuda.synchronize()
+    osc = oracle.OracleScene(w.scenes[0])
+    rows = np.arange(leg.n_pulses)
+    win = to_np(out["window_bin"])
+    d_refl, d_dens = oracle.adjoint(osc, sc, leg, rows, to_np(gW).reshape(-1, sc.n_bins).astype(np.float64),
+                                    win)
+    gd = to_np(grads[0]["density"][0]).ravel()
+    gr = to_np(grads[0]["reflectance"][0])
+    scale = np.abs(d_dens).max()
+    assert scale > 0
+    err = np.abs(gd - d_dens) - (1e-3 * np.abs(d_dens) + 1e-6 * scale)
+    assert (err <= 0).all(), f"density gradient: {int((err > 0).sum())} entries outside tolerance"
+    assert np.allclose(gr, d_refl, rtol=1e-3, atol=1e-6 * np.abs(d_refl).max())
+    # without the checkpoint the adjoint re-traverses and must agree
+    grads2 = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], None)
+    torch.cuda.synchronize()
+    gd2 = to_np(grads2[0]["density"][0]).ravel()
+    assert np.allclose(gd2, gd, rtol=1e-4, atol=1e-7 * scale)
+
+
+def test_autograd_function(hg):
+    w = scenes.uls_voxels(seed=9, n=24, n_pulses=400, n_bins=256, agl=8.0, speed=1.0, prf=800.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    refl = gs.reflectance[0].requires_grad_(True)
+    dens = gs.density[0].requires_grad_(True)
+    W = hg.WaveformFunction.apply(gs, sc, leg, refl, dens)
+    loss = (W ** 2).sum()
+    loss.backward()
+    assert dens.grad is not None and torch.isfinite(dens.grad).all()
+    assert refl.grad is not None and (refl.grad != 0).any()
+
+
+@pytest.mark.slow
+def test_als_full_size_sampled(hg):
+    """The 3M-triangle ALS workload with 4M pulses in the benchmark's launch
+    configuration; every 997th pulse is checked against the oracle."""
+    w = scenes.als_terrain()
+    rows = np.arange(0, w.legs[0].n_pulses, 997)
+    out, lay, res = run_both(hg, w, seed=0, rows=rows, subrays=True)
+    stats = compare(*res[0])
+    assert stats["pulses"] == len(rows)
