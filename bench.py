@@ -1,0 +1,472 @@
+"""Benchmark: simulated pulses per second of the fused GB300 pulse kernel.
+
+Default workload (N=1): seeded ALS over terrain -- 1024^2 fBm DTM at 1 m plus
+300 procedural trees (3.03 M triangles), 4 M pulses, 19 subrays per pulse,
+512-bin full waveform, echoes, range noise.  One step = one helios_scan_legs
+call over the whole leg (pulse pose -> subrays -> BVH -> power -> waveform ->
+echoes).  The scene (BVH 0.35 GB) and the step's outputs (8.7 GB) are both
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the reference arm) on a bounded sample of the same workload instead.
+Multi-GPU (torchrun, --gpus N): the leg does not shard here, so each rank runs
+an independent replica (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="als", choices=["als", "uls", "tls", "batched"])
+    p.add_argument("--no-extras", action="store_true", help="skip adjoint ratio, e2e and CPU baseline")
+    p.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
+    p.add_argument("--small", action="store_true", help="tiny sizes (tests only)")
+    p.add_argument("--pulses", type=int, default=0, help="override the leg's pulse count (profiling)")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks only)
+# --------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+def workload(name, small=False):
+    import scenes
+    if name == "als":
+        if small:
+            return scenes.als_terrain(size=128, n_trees=8, n_pulses=20000, agl=120.0)
+        return scenes.als_terrain()
+    if name == "uls":
+        if small:
+            return scenes.uls_voxels(n=48, n_pulses=20000, agl=12.0, speed=1.0, prf=2000.0)
+        return scenes.uls_voxels()
+    if name == "tls":
+        return scenes.tls_tiny()
+    if small:
+        return scenes.batched_legs(n_legs=8, tile=64, block=24, n_terrain=2, n_voxel=2,
+                                   min_pulses=1000, max_pulses=20000)
+    return scenes.batched_legs()
+
+
+def workload_config(w, name):
+    sc = w.scanners[0]
+    import paper_2101_09154_gb300 as hg
+    S = [hg.subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
+                         else w.scanners[l.scanner_index].beam_sample_quality) for l in w.legs]
+    return {"workload": w.name, "description": w.note, "pulses": w.n_pulses,
+            "subrays_per_pulse": S[0] if len(set(S)) == 1 else "mixed",
+            "triangles": int(sum(s.n_triangles for s in w.scenes)),
+            "voxels": int(sum(int(np.prod(g.dims)) for s in w.scenes for g in s.grids)),
+            "n_bins": sc.n_bins, "legs": len(w.legs),
+            "l2": "inputs larger than L2 (BVH + triangles > 129 MB, outputs > 1 GB); no flush",
+            "precision": "fp32 traversal/waveform, fp64 pose and hit range"}
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("hg_device.cuh", "scan.cu"):
+        with open(os.path.join(ROOT, "paper_2101_09154_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_name, pulses):
+    """DRAM bytes per launch from the committed ncu summary, if it is for this kernel source."""
+    p = os.path.join(ROOT, "profiles", "scan_kernel_als_terrain.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_src = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_pulse:\s*([0-9.eE+]+)", txt)
+    if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1)) * pulses
+
+
+def algorithmic_bytes(w, layout, subray_outputs=False):
+    """Compulsory traffic of one scan launch: every output byte written once,
+    every scene byte (BVH nodes, packed triangles, reflectance, voxels) read once."""
+    P = layout["total_pulses"]
+    out = layout["waveform_floats"] * 4 + P * (4 + 4 + 1) + layout["echo_elems"] * (4 + 4 + 4 + 4)
+    if subray_outputs:
+        out += layout["subray_elems"] * 8
+    scene = 0
+    for s in w.scenes:
+        n = s.n_triangles
+        scene += max(n - 1, 0) * 64 + n * 48 + n * 4
+        scene += sum(int(np.prod(g.dims)) * 4 for g in s.grids)
+    return int(out + scene)
+
+
+# --------------------------------------------------------------------------
+# the GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args, D):
+    import torch
+    import paper_2101_09154_gb300 as hg
+    from paper_2101_09154_gb300 import build as _b
+
+    _b.build()
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device for --impl ours"
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    w = workload(args.workload, args.small)
+    if args.pulses > 0:
+        for l in w.legs:
+            l.n_pulses = args.pulses
+        w.name += f"_first{args.pulses}p"
+    t0 = time.time()
+    gsc = [hg.Scene(s, device=dev) for s in w.scenes]
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    persistent = args.workload == "batched"
+    mode = 0
+    layout = hg.output_layout(w.scanners, w.legs)
+    out = hg.alloc_outputs(layout, dev, subrays=False, status=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        hg.scan(gsc, w.scanners, w.legs, mode=mode, seed=12345, persistent=persistent, out=out,
+                subrays=False)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clk = Clocks(D.local)
+    clk.start()
+    time.sleep(0.3)
+    D.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    clocks = clk.stop()
+    ms = float(np.mean(per))
+    ms_max = D.max(ms)
+    P = w.n_pulses
+    n_launch = len(w.legs) if not persistent else math.ceil(len(w.legs) / 96)
+    S = workload_config(w, args.workload)["subrays_per_pulse"]
+    subrays_total = sum(l.n_pulses * hg.subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
+                                                     else w.scanners[l.scanner_index].beam_sample_quality)
+                        for l in w.legs)
+    value = D.world * P / (ms_max / 1e3)
+    st = int(out["status"].item())
+    res = {"metric": "pulses/s (19 subrays, waveform on)", "value": value, "unit": "pulses/s",
+           "n_gpus": D.world, "steps": args.steps, "warmup": max(args.warmup, 3),
+           "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {**workload_config(w, args.workload), "parallelism": f"replicas x{D.world}",
+                      "bvh_build_s": round(build_s, 3)},
+           "subrays_per_s": D.world * subrays_total / (ms_max / 1e3),
+           "gpu_launches": n_launch * args.steps,
+           "device_status": st,
+           "step_ms_all": [round(x, 4) for x in per]}
+    # roofline of the (single) kernel per step
+    peaks, kind = measured_peaks()
+    alg = algorithmic_bytes(w, layout)
+    achieved = alg / (ms / 1e3) / 1e9
+    traffic = ncu_traffic(args.workload, P) if args.workload == "als" and not args.small else None
+    res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                       "algorithmic_bytes_per_launch": alg, "peak_source": kind,
+                       "kernel": "hg::scan_kernel<0,false,1>"}
+    res["clocks"] = clocks
+    if not args.no_extras:
+        res["e2e"] = e2e(w, gsc, layout, out, args, stream, D)
+        if D.rank == 0 and D.world == 1:
+            res["adjoint"] = adjoint_ratio(args)
+            res["adjoint_forward_ratio"] = res["adjoint"]["adjoint_forward_ratio"]
+    return res, w
+
+
+def e2e(w, gsc, layout, out, args, stream, D):
+    """Same metric through the public API with host buffers: each step uploads
+    the per-step input (the meshes' reflectance) from pinned host memory,
+    scans, and reads the whole result (waveform + echoes + window) back into
+    pinned host memory."""
+    import torch
+    import paper_2101_09154_gb300 as hg
+    host_refl = [[r.cpu().pin_memory() for r in s.reflectance] for s in gsc]
+    keys = ["waveform", "window_bin", "echo_count", "echo_range", "echo_amp", "echo_bin",
+            "echo_object", "pulse_flags"]
+    host_out = {k: torch.empty(out[k].shape, dtype=out[k].dtype, pin_memory=True) for k in keys}
+    h2d = sum(t.numel() * t.element_size() for s in host_refl for t in s)
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    persistent = args.workload == "batched"
+
+    def step():
+        for s, hs in zip(gsc, host_refl):
+            for r, h in zip(s.reflectance, hs):
+                r.copy_(h, non_blocking=True)
+        hg.scan(gsc, w.scanners, w.legs, seed=12345, persistent=persistent, out=out, subrays=False)
+        for k in keys:
+            host_out[k].copy_(out[k], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = max(2, min(args.steps, 5))
+    D.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = D.max(e0.elapsed_time(e1) / n)
+    return {"value": D.world * w.n_pulses / (ms / 1e3), "unit": "pulses/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n}
+
+
+def adjoint_ratio(args):
+    """Expected-mode forward and adjoint on the voxel-canopy workload (1 M pulses,
+    256^3 voxels, 19 subrays, 1024 bins): time of the adjoint / time of the forward."""
+    import torch
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    w = workload("uls", args.small)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    lay = hg.output_layout([sc], [leg])
+    out = hg.alloc_outputs(lay, gs.device, subrays=True)
+    ref_scene = scenes.Scene(meshes=w.scenes[0].meshes,
+                             grids=[scenes.VoxelGrid(**{**w.scenes[0].grids[0].__dict__,
+                                                       "density": scenes.perturbed_density(
+                                                           w.scenes[0].grids[0].density, seed=1)})])
+    gref = hg.Scene(ref_scene)
+    out_ref, _ = hg.scan([gref], [sc], [leg], mode=1, subrays=False)
+    grads = [{"reflectance": [torch.zeros_like(r) for r in gs.reflectance],
+              "density": [torch.zeros_like(d) for d in gs.density]}]
+
+    def fwd():
+        hg.scan([gs], [sc], [leg], mode=1, out=out)
+
+    def bwd(gW):
+        hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"], grads=grads)
+
+    fwd()
+    gW = 2.0 * (out["waveform"] - out_ref["waveform"])
+    bwd(gW)
+    fs = [hg.scan([gs], [sc], [leg], mode=0, out=out) for _ in range(2)]
+    del fs
+    torch.cuda.synchronize()
+
+    def timed(fn, n=5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s = torch.cuda.current_stream()
+        e0.record(s)
+        for _ in range(n):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    f_ms = timed(fwd)
+    b_ms = timed(lambda: bwd(gW))
+    s_ms = timed(lambda: hg.scan([gs], [sc], [leg], mode=0, out=out))
+    return {"workload": w.name, "pulses": leg.n_pulses, "expected_forward_ms": f_ms,
+            "adjoint_ms": b_ms, "adjoint_forward_ratio": b_ms / f_ms,
+            "stochastic_forward_ms": s_ms,
+            "stochastic_pulses_per_s": leg.n_pulses / (s_ms / 1e3),
+            "expected_pulses_per_s": leg.n_pulses / (f_ms / 1e3)}
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores
+# --------------------------------------------------------------------------
+def oracle_rate(w, target_s, pulses_cap=None):
+    """Time the FP64 oracle (as it stands) on an evenly strided pulse sample."""
+    import oracle
+    osc = oracle.OracleScene(w.scenes[w.legs[0].scene_index])
+    sc, leg = w.scanners[w.legs[0].scanner_index], w.legs[0]
+    cores = os.cpu_count() or 1
+    # calibrate on a small sample, then size the timed sample to ~target_s
+    probe = np.arange(0, leg.n_pulses, max(leg.n_pulses // 2000, 1))[:2000]
+    t0 = time.time()
+    oracle.scan(osc, sc, leg, probe, threads=cores)
+    dt = max(time.time() - t0, 1e-3)
+    n = int(min(leg.n_pulses, max(len(probe), target_s * len(probe) / dt)))
+    if pulses_cap:
+        n = min(n, pulses_cap)
+    rows = np.unique(np.linspace(0, leg.n_pulses - 1, n).astype(np.int64))
+    t0 = time.time()
+    oracle.scan(osc, sc, leg, rows, threads=cores)
+    dt = time.time() - t0
+    q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else sc.beam_sample_quality
+    return {"value": len(rows) / dt, "unit": "pulses/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(rows)} evenly spaced pulses of the {leg.n_pulses}-pulse leg "
+                      f"({oracle.subray_count(q)} subrays each), {dt:.1f} s of FP64 CPU work "
+                      f"on {cores} threads"}
+
+
+def run_reference(args, D):
+    if D.rank != 0:
+        return None
+    w = workload(args.workload, args.small)
+    import oracle
+    oracle.build()
+    rates = []
+    per_step_target = max(1.0, args.cpu_sample_s / max(args.steps, 1))
+    info = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_rate(w, per_step_target)
+        if i >= args.warmup:
+            rates.append(r["value"])
+            info = r
+    value = float(np.mean(rates))
+    return {"impl": "reference", "metric": "pulses/s (19 subrays, waveform on)", "value": value,
+            "unit": "pulses/s", "n_gpus": D.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.n_pulses / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, args.workload),
+            "cpu_baseline": {**info, "value": value},
+            "e2e": {"value": value, "unit": "pulses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    args = parse()
+    D = Dist()
+    try:
+        if args.impl == "reference":
+            res = run_reference(args, D)
+            if res is not None:
+                print(json.dumps(res), flush=True)
+            return
+        res, w = run_ours(args, D)
+        if D.rank == 0:
+            if not args.no_extras and D.world == 1:
+                res["cpu_baseline"] = oracle_rate(w, args.cpu_sample_s)
+            print(json.dumps(res), flush=True)
+    finally:
+        D.close()
+
+
+if __name__ == "__main__":
+    main()

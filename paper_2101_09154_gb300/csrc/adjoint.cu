@@ -37,7 +37,7 @@ __device__ __forceinline__ float corr(const float* g, int nb, const DevScanner& 
 
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PulseFrame* s_pf = reinterpret_cast<PulseFrame*>(smem);
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(smem);
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_g = reinterpret_cast<float*>(s_sc + P.s_cap);
     __shared__ double s_rot[6];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
             pulse_frame(sn, lg, s_rot, p0 + t, f);
-            s_pf[t] = f;
+            split_store(f, s_pf[t]);
         }
         __syncthreads();
         for (int pl = warp; pl < pc; pl += nwarps) {
@@ -75,38 +75,44 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
             const float* grow = P.g + lg.wave_off + k * nb;
             for (int b = lane; b < nb; b += 32) g[b] = __ldcs(grow + b);
             __syncwarp();
-            const PulseFrame& f = s_pf[pl];
+            const PulseFF& f = s_pf[pl];
             for (int s0 = 0; s0 < S; s0 += 32) {
                 const int s = s0 + lane;
                 const bool on = s < S;
                 const int ss = on ? s : 0;
-                double o[3], d[3];
                 const SubrayConst& c = s_sc[ss];
+                float dh[3], dl[3];
+                subray_dir_ff(f, c, dh, dl);
+                double o[3], d[3];
                 for (int a = 0; a < 3; ++a) {
-                    o[a] = f.o[a];
-                    d[a] = c.ca * f.d[a] + c.sacp * f.u[a] + c.sasp * f.v[a];
+                    o[a] = ff2d(f.oh[a], f.ol[a]);
+                    d[a] = ff2d(dh[a], dl[a]);
                 }
                 const float tan_a = c.tan_a;
                 // triangle hit: the forward's checkpoint, else a traversal
                 int hit = -1;
+                float t32 = 0.0f;
                 if (P.subray_hit) {
                     if (on) {
                         int32_t gid = P.subray_hit[lg.sub_off + k * S + s];
                         hit = (gid >= 0 && gid < sc.n_tri) ? __ldg(&sc.tri_index[gid]) : -1;
                     }
+                    if (hit >= 0) t32 = plane_t32(sc, hit, f.oh, dh);
                 } else {
                     RayF ray;
-                    make_ray(o, d, ray);
+                    make_ray(f.oh, dh, ray);
                     float tb = 3.0e38f;
                     uint32_t fl = 0;
                     traverse(sc, ray, on, tb, hit, fl);
+                    t32 = tb;
                 }
                 if (!on) continue;
                 double t_tri = CUDART_INF;
                 float cosi = 0.0f, rho = 0.0f;
                 int mesh = 0, face = 0;
                 if (hit >= 0) {
-                    t_tri = refine_hit(sc, hit, o, d, cosi);
+                    float dt32 = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, t32, cosi);
+                    t_tri = (double)t32 + (double)dt32;
                     const float4* tp = sc.tris + 3 * (size_t)hit;
                     mesh = __float_as_int(__ldg(&tp[1].w));
                     face = __float_as_int(__ldg(&tp[2].w));
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float w = -T * expm1f(-xs);
                                 double R = t_in + 0.5 * len;
                                 float A = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, (float)(2.0 * R / kC * 1e9 - mdt));
+                                          corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
                                 total += (double)A * (double)w;
                                 T *= expf(-xs);
                             }
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 float A_tri = 0.0f;
                 if (hit >= 0) {
                     A_tri = return_power(sn, t_tri, tan_a, 1.0f, cosi) *
-                            corr(g, nb, sn, dt, (float)(2.0 * t_tri / kC * 1e9 - mdt));
+                            corr(g, nb, sn, dt, (float)fma(t_tri, kDelayPerMetre, -mdt));
                     total += (double)A_tri * (double)rho * (double)T;
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
                 }
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float w = -Tb * expm1f(-xs);
                                 double R = t_in + 0.5 * len;
                                 float A = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, (float)(2.0 * R / kC * 1e9 - mdt));
+                                          corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;
                                 double dsig = (double)A * Tb * len * a - len * suffix;
@@ -208,7 +214,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         p->s_cap = lg.S;
         p->pc_cap = lg.pulses_per_item;
         p->nb_cap = (L.scanners[lg.scanner].n_bins + 3) & ~3;
-        size_t smem = sizeof(PulseFrame) * p->pc_cap + sizeof(SubrayConst) * p->s_cap +
+        size_t smem = sizeof(PulseFF) * p->pc_cap + sizeof(SubrayConst) * p->s_cap +
                       sizeof(float) * (size_t)(L.threads / 32) * p->nb_cap;
         cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaFuncSetAttribute(adjoint)", e); }

@@ -94,6 +94,7 @@ static DevScanner derive_scanner(const helios_scanner_desc& s) {
         d.n_pre = 0;
         d.echo_offset_ns = 2.0 * tau;
     }
+    d.bins_per_metre = kDelayPerMetre / s.bin_ns;
     d.thr_rel = (float)s.echo_threshold_rel;
     d.noise_sigma = (float)s.range_noise_sigma_m;
     d.q_default = s.beam_sample_quality;

@@ -17,6 +17,7 @@ constexpr int kMaxScanners = 4;
 constexpr int kMaxLegs = 96;
 constexpr double kC = 299792458.0;        // speed of light (Sec. 3.4)
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kDelayPerMetre = 2.0e9 / kC;  // round-trip delay in ns per metre of range
 
 // ---------------------------------------------------------------------------
 // scene: BVH nodes, packed triangles, per-mesh reflectance, optional grid
@@ -59,6 +60,7 @@ struct DevScanner {
     float ctau_inv;          // Carlsson: 1/tau                   [1/ns]
     float cut_lo, cut_hi;    // support of the pulse shape around the delay [ns]
     float thr_rel, noise_sigma;
+    double bins_per_metre;   // 2 / (c * bin) in bins per metre of range
     int32_t q_default, pulse_shape, n_bins, max_echoes;
     int32_t deflector, n_az, n_el, n_pre;
 };
@@ -92,15 +94,21 @@ struct Outputs {
     uint32_t* status;
 };
 
-// Per-pulse pose in shared memory: origin, direction, and the two ONB axes.
+// FP64 pulse pose (origin, unit direction, ONB axes), computed once per pulse.
 struct PulseFrame {
     double o[3], d[3], u[3], v[3];
 };
-// Per-subray constants: cos(alpha), sin(alpha)cos(phi), sin(alpha)sin(phi), tan(alpha).
+// The same pose as kept in shared memory: origin and direction as unevaluated
+// float pairs hi + lo (about 48 significant bits), the ONB axes in FP32 (they
+// only scale the sub-milliradian subray offsets).
+struct PulseFF {
+    float oh[3], ol[3];
+    float dh[3], dl[3];
+    float u[3], v[3];
+};
+// Per-subray constants: 1 - cos(alpha), sin(alpha)cos(phi), sin(alpha)sin(phi), tan(alpha).
 struct SubrayConst {
-    double ca, sacp, sasp;
-    float tan_a;
-    int32_t pad;
+    float eps, sacp, sasp, tan_a;
 };
 
 constexpr uint32_t kPfEchoOverflow = 0x01u;
@@ -232,11 +240,52 @@ __device__ __forceinline__ void subray_const(int q, double theta_r, int s, Subra
     double sa, ca, sp, cp;
     sincos(alpha, &sa, &ca);
     sincos(phi, &sp, &cp);
-    c.ca = ca;
-    c.sacp = sa * cp;
-    c.sasp = sa * sp;
+    // 1 - cos(alpha) without cancellation: 2 sin^2(alpha/2)
+    double sh = sin(0.5 * alpha);
+    c.eps = (float)(2.0 * sh * sh);
+    c.sacp = (float)(sa * cp);
+    c.sasp = (float)(sa * sp);
     c.tan_a = (float)tan(alpha);
 }
+
+// ---------------------------------------------------------------------------
+// float-float helpers (error-free transformations: Knuth TwoSum, FMA TwoProd)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void split_store(const PulseFrame& f, PulseFF& g) {
+    for (int a = 0; a < 3; ++a) {
+        g.oh[a] = (float)f.o[a];
+        g.ol[a] = (float)(f.o[a] - (double)g.oh[a]);
+        g.dh[a] = (float)f.d[a];
+        g.dl[a] = (float)(f.d[a] - (double)g.dh[a]);
+        g.u[a] = (float)f.u[a];
+        g.v[a] = (float)f.v[a];
+    }
+}
+
+// unit subray direction as hi + lo: d_s = (1 - eps) d + sin(a)(cos(p) u + sin(p) v);
+// the correction to d is below 2e-4 in size, so FP32 carries it to ~1e-11.
+__device__ __forceinline__ void subray_dir_ff(const PulseFF& f, const SubrayConst& c,
+                                              float dh[3], float dl[3]) {
+    for (int a = 0; a < 3; ++a) {
+        float corr = fmaf(-c.eps, f.dh[a], fmaf(c.sacp, f.u[a], c.sasp * f.v[a]));
+        float s, e;
+        two_sum(f.dh[a], corr, s, e);
+        dh[a] = s;
+        dl[a] = e + f.dl[a];
+    }
+}
+
+__device__ __forceinline__ double ff2d(float hi, float lo) { return (double)hi + (double)lo; }
 
 // ---------------------------------------------------------------------------
 // FP32 ray for traversal
@@ -257,9 +306,9 @@ __device__ __forceinline__ float sel3(int k, float x, float y, float z) {
     return k == 0 ? x : (k == 1 ? y : z);
 }
 
-__device__ __forceinline__ void make_ray(const double o[3], const double d[3], RayF& r) {
-    r.ox = (float)o[0]; r.oy = (float)o[1]; r.oz = (float)o[2];
-    float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+__device__ __forceinline__ void make_ray(const float o[3], const float d[3], RayF& r) {
+    r.ox = o[0]; r.oy = o[1]; r.oz = o[2];
+    float dx = d[0], dy = d[1], dz = d[2];
     r.idx = safe_inv(dx); r.idy = safe_inv(dy); r.idz = safe_inv(dz);
     r.oix = r.ox * r.idx; r.oiy = r.oy * r.idy; r.oiz = r.oz * r.idz;
     // watertight test setup (Woop, Benthin & Wald, JCGT 2013)
@@ -392,24 +441,48 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
     }
 }
 
-// FP64 range along unit direction d to the plane of triangle t (the closest
-// hit found in FP32), and |cos| of the incidence angle.
-__device__ __forceinline__ double refine_hit(const DevScene& S, int t, const double o[3],
-                                             const double d[3], float& cos_inc) {
+// Range to the plane of triangle t (the closest hit found in FP32 at t32).
+// The ray is re-anchored at o' = o + t32 d, formed exactly as a float pair;
+// the vertices relative to o' are then metre-sized, so the FP32 plane
+// intersection from o' is good to ~1e-7 m.  Returns R = t32 + dt as (t32, dt)
+// and |cos| of the incidence angle.
+__device__ __forceinline__ float refine_hit_ff(const DevScene& S, int t, const float oh[3],
+                                               const float ol[3], const float dh[3],
+                                               const float dl[3], float t32, float& cos_inc) {
     const float4* tp = S.tris + 3 * (size_t)t;
     float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-    double e1x = (double)b.x - a.x, e1y = (double)b.y - a.y, e1z = (double)b.z - a.z;
-    double e2x = (double)c.x - a.x, e2y = (double)c.y - a.y, e2z = (double)c.z - a.z;
-    double nx = e1y * e2z - e1z * e2y;
-    double ny = e1z * e2x - e1x * e2z;
-    double nz = e1x * e2y - e1y * e2x;
-    double wx = (double)a.x - o[0], wy = (double)a.y - o[1], wz = (double)a.z - o[2];
-    double num = nx * wx + ny * wy + nz * wz;
-    double den = nx * d[0] + ny * d[1] + nz * d[2];
-    float fn2 = (float)(nx * nx + ny * ny + nz * nz);
-    cos_inc = fabsf((float)den) * rsqrtf(fn2);
-    if (cos_inc > 1.0f) cos_inc = 1.0f;
+    float oph[3], opl[3];
+    for (int k = 0; k < 3; ++k) {
+        float p, pe, s, se;
+        two_prod(t32, dh[k], p, pe);
+        two_sum(oh[k], p, s, se);
+        oph[k] = s;
+        opl[k] = ol[k] + (pe + se) + t32 * dl[k];
+    }
+    float w0x = (a.x - oph[0]) - opl[0], w0y = (a.y - oph[1]) - opl[1], w0z = (a.z - oph[2]) - opl[2];
+    float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    float nx = e1y * e2z - e1z * e2y;
+    float ny = e1z * e2x - e1x * e2z;
+    float nz = e1x * e2y - e1y * e2x;
+    float num = nx * w0x + ny * w0y + nz * w0z;
+    float den = nx * dh[0] + ny * dh[1] + nz * dh[2];
+    float n2 = nx * nx + ny * ny + nz * nz;
+    cos_inc = fminf(fabsf(den) * rsqrtf(n2), 1.0f);
     return num / den;
+}
+
+// FP32 plane distance along dh from oh to triangle t: an anchor for
+// refine_hit_ff when only the triangle id is known.
+__device__ __forceinline__ float plane_t32(const DevScene& S, int t, const float oh[3],
+                                           const float dh[3]) {
+    const float4* tp = S.tris + 3 * (size_t)t;
+    float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+    float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    return (nx * (a.x - oh[0]) + ny * (a.y - oh[1]) + nz * (a.z - oh[2])) /
+           (nx * dh[0] + ny * dh[1] + nz * dh[2]);
 }
 
 // ---------------------------------------------------------------------------

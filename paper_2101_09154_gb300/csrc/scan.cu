@@ -67,18 +67,20 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
     }
 }
 
+// delay of range R (ns) relative to the window start mdt = m * bin
 __device__ __forceinline__ float delay_rel(double R, double mdt) {
-    return (float)(2.0 * R / kC * 1e9 - mdt);
+    return (float)fma(R, kDelayPerMetre, -mdt);
 }
 
 template <int MODE, bool GRID, int NL>
 __global__ void __launch_bounds__(256)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PulseFrame* s_pf = reinterpret_cast<PulseFrame*>(smem);
+    RayRes* s_rr = reinterpret_cast<RayRes*>(smem);
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_rr + P.rays_cap);
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
-    RayRes* s_rr = reinterpret_cast<RayRes*>(s_sc + P.s_cap);
-    uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_rr + P.rays_cap);
+    float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
+    uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
     // the per-warp waveform rows start 16-byte aligned (float4 reads below)
     float* s_w = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(s_pflag + P.pc_cap) + 15u) & ~uintptr_t(15));
@@ -137,7 +139,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
             pulse_frame(sn, lg, s_rot, p0 + t, f);
-            s_pf[t] = f;
+            split_store(f, s_pf[t]);
             s_pflag[t] = 0u;
         }
         __syncthreads();
@@ -149,17 +151,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             bool active = r < n_rays;
             int pl = active ? r / S : 0;
             int s = active ? r - pl * S : 0;
-            double o[3], d[3];
-            {
-                const PulseFrame& f = s_pf[pl];
-                const SubrayConst& c = s_sc[s];
-                for (int a = 0; a < 3; ++a) {
-                    o[a] = f.o[a];
-                    d[a] = c.ca * f.d[a] + c.sacp * f.u[a] + c.sasp * f.v[a];
-                }
-            }
+            const PulseFF& f = s_pf[pl];
+            float dh[3], dl[3];
+            subray_dir_ff(f, s_sc[s], dh, dl);
             RayF ray;
-            make_ray(o, d, ray);
+            make_ray(f.oh, dh, ray);
             float tb = 3.0e38f;
             int hit = -1;
             uint32_t fl = 0;
@@ -176,7 +172,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 int gid = -1;
                 float rho = 0.0f;
                 if (hit >= 0) {
-                    t_tri = refine_hit(sc, hit, o, d, cosi);
+                    float dt = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
+                    t_tri = (double)tb + (double)dt;
                     const float4* tp = sc.tris + 3 * (size_t)hit;
                     gid = __float_as_int(__ldg(&tp[0].w));
                     int mesh = __float_as_int(__ldg(&tp[1].w));
@@ -186,6 +183,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 }
                 bool voxel_event = false;
                 if (GRID && sc.has_grid) {
+                    double o[3], d[3];
+                    for (int a = 0; a < 3; ++a) {
+                        o[a] = ff2d(f.oh[a], f.ol[a]);
+                        d[a] = ff2d(dh[a], dl[a]);
+                    }
                     March m;
                     if (march_init(sc, o, d, t_tri, m)) {
                         const int64_t k = p0 + pl;
@@ -274,24 +276,31 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 }
                 continue;
             }
-            double x = 2.0 * rmin / kC * 1e9 / sn.bin_ns;
-            int32_t m = (int32_t)floor(x) - sn.n_pre;
+            int32_t m = (int32_t)floor(rmin * sn.bins_per_metre) - sn.n_pre;
             double mdt = (double)m * sn.bin_ns;
+            if (MODE == 0) {
+                // each subray's delay relative to the window, formed once
+                for (int s = lane; s < S; s += 32) {
+                    RayRes rr = rrp[s];
+                    s_tau[(size_t)pl * S + s] = rr.id >= 0 ? delay_rel(rr.R, mdt) : 0.0f;
+                }
+            }
             for (int b = lane; b < nb; b += 32) {
                 W[b] = 0.0f;
                 if (MODE == 1) { best[b] = 0.0f; bid[b] = -1; }
             }
             __syncwarp();
+            const float* taup = s_tau + (size_t)pl * S;
             if (MODE == 0) {
                 for (int s = 0; s < S; ++s) {
                     RayRes rr = rrp[s];
                     if (rr.id < 0) continue;
-                    accumulate(W, nb, sn, dt, delay_rel(rr.R, mdt), rr.P, lane);
+                    accumulate(W, nb, sn, dt, taup[s], rr.P, lane);
                 }
             } else {
                 // expected transmittance: every crossed voxel returns
                 // w = T (1 - e^{-sigma l}) at its midpoint, the triangle T.
-                const PulseFrame& f = s_pf[pl];
+                const PulseFF& f = s_pf[pl];
                 for (int s0 = 0; s0 < S; s0 += 32) {
                     int s = s0 + lane;
                     bool lane_on = s < S;
@@ -310,10 +319,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     uint32_t fl = 0;
                     if (GRID && sc.has_grid && lane_on) {
                         double o[3], d[3];
-                        const SubrayConst& c = s_sc[s];
+                        float dh[3], dl[3];
+                        subray_dir_ff(f, s_sc[s], dh, dl);
                         for (int a = 0; a < 3; ++a) {
-                            o[a] = f.o[a];
-                            d[a] = c.ca * f.d[a] + c.sacp * f.u[a] + c.sasp * f.v[a];
+                            o[a] = ff2d(f.oh[a], f.ol[a]);
+                            d[a] = ff2d(dh[a], dl[a]);
                         }
                         double t_hi = rr.id >= 0 ? rr.R : CUDART_INF;
                         on = march_init(sc, o, d, t_hi, mch);
@@ -394,7 +404,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         for (int s = 0; s < S; ++s) {
                             RayRes rr = rrp[s];
                             if (rr.id < 0) continue;
-                            float v = rr.P * pulse_shape(sn, tbin - delay_rel(rr.R, mdt));
+                            float v = rr.P * pulse_shape(sn, tbin - taup[s]);
                             if (v > bv) { bv = v; obj = rr.id; }
                         }
                     }
@@ -480,8 +490,8 @@ static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int 
 }
 
 static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads) {
-    size_t b = sizeof(PulseFrame) * pc_cap + sizeof(SubrayConst) * s_cap +
-               sizeof(RayRes) * rays_cap + sizeof(uint32_t) * pc_cap;
+    size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
+               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap;
     b = (b + 15) & ~size_t(15);
     b += (size_t)(threads / 32) * nb_cap * sizeof(float) * (mode == 1 ? 3 : 1);
     return b;
