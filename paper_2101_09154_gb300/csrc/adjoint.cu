@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float xs = sc.G * dens * (float)len;
                                 float w = -T * expm1f(-xs);
                                 double R = t_in + 0.5 * len;
-                                float A = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f) *
+                                float A = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f) *
                                           corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
                                 total += (double)A * (double)w;
                                 T *= expf(-xs);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 }
                 float A_tri = 0.0f;
                 if (hit >= 0) {
-                    A_tri = return_power(sn, t_tri, tan_a, 1.0f, cosi) *
+                    A_tri = return_power(sn, (float)t_tri, tan_a, 1.0f, cosi) *
                             corr(g, nb, sn, dt, (float)fma(t_tri, kDelayPerMetre, -mdt));
                     total += (double)A_tri * (double)rho * (double)T;
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float a = expf(-xs);
                                 float w = -Tb * expm1f(-xs);
                                 double R = t_in + 0.5 * len;
-                                float A = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f) *
+                                float A = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f) *
                                           corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;

@@ -95,6 +95,12 @@ static DevScanner derive_scanner(const helios_scanner_desc& s) {
         d.echo_offset_ns = 2.0 * tau;
     }
     d.bins_per_metre = kDelayPerMetre / s.bin_ns;
+    d.inv_bin = (float)(1.0 / s.bin_ns);
+    d.bpm_hi = (float)d.bins_per_metre;
+    d.bpm_lo = (float)(d.bins_per_metre - (double)d.bpm_hi);
+    d.bin_hi = (float)s.bin_ns;
+    d.bin_lo = (float)(s.bin_ns - (double)d.bin_hi);
+    d.echo_offset_f = (float)d.echo_offset_ns;
     d.thr_rel = (float)s.echo_threshold_rel;
     d.noise_sigma = (float)s.range_noise_sigma_m;
     d.q_default = s.beam_sample_quality;

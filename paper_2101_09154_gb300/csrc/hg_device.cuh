@@ -18,6 +18,10 @@ constexpr int kMaxLegs = 96;
 constexpr double kC = 299792458.0;        // speed of light (Sec. 3.4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kDelayPerMetre = 2.0e9 / kC;  // round-trip delay in ns per metre of range
+// the same constant as a float pair, and half the speed of light in m/ns
+constexpr float kDelayHi = (float)kDelayPerMetre;
+constexpr float kDelayLo = (float)(kDelayPerMetre - (double)kDelayHi);
+constexpr float kHalfCns = (float)(0.5e-9 * kC);
 
 // ---------------------------------------------------------------------------
 // scene: BVH nodes, packed triangles, per-mesh reflectance, optional grid
@@ -61,6 +65,10 @@ struct DevScanner {
     float cut_lo, cut_hi;    // support of the pulse shape around the delay [ns]
     float thr_rel, noise_sigma;
     double bins_per_metre;   // 2 / (c * bin) in bins per metre of range
+    float inv_bin;           // 1 / bin_ns
+    float bpm_hi, bpm_lo;    // bins_per_metre as a float pair
+    float bin_hi, bin_lo;    // bin_ns as a float pair
+    float echo_offset_f;     // echo_offset_ns in FP32
     int32_t q_default, pulse_shape, n_bins, max_echoes;
     int32_t deflector, n_az, n_el, n_pre;
 };
@@ -287,6 +295,43 @@ __device__ __forceinline__ void subray_dir_ff(const PulseFF& f, const SubrayCons
 
 __device__ __forceinline__ double ff2d(float hi, float lo) { return (double)hi + (double)lo; }
 
+// normalised float pair (|lo| <= ulp(hi)/2) and its order
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_norm(float hi, float lo) {
+    FF r;
+    two_sum(hi, lo, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ bool ff_less(const FF& a, const FF& b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ FF ff_split(double x) {
+    FF r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+// floor(a * b) for a normalised pair a and a constant pair (bh, bl)
+__device__ __forceinline__ int ff_floor_mul(const FF& a, float bh, float bl) {
+    float p, e;
+    two_prod(a.hi, bh, p, e);
+    e += fmaf(a.hi, bl, a.lo * bh);
+    float s, t;
+    two_sum(p, e, s, t);
+    float f = floorf(s);
+    if (f == s && t < 0.0f) f -= 1.0f;
+    return (int)f;
+}
+// a * (bh + bl) - (ch + cl) to FP32, for a product close to c (Sterbenz)
+__device__ __forceinline__ float ff_mul_sub(const FF& a, float bh, float bl, float ch, float cl) {
+    float p, e;
+    two_prod(a.hi, bh, p, e);
+    e += fmaf(a.hi, bl, a.lo * bh);
+    return (p - ch) + (e - cl);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 ray for traversal
 // ---------------------------------------------------------------------------
@@ -369,14 +414,33 @@ __device__ __forceinline__ bool tri_hit(const RayF& r, float4 a, float4 b, float
 // ---------------------------------------------------------------------------
 // Warp-coherent stackless BVH traversal (closest hit).
 //
-// All 32 lanes call it together; every branch below depends only on warp-
-// uniform values (node index, state, votes), so the warp walks one node
-// sequence and each lane keeps its own closest hit.  Instead of a stack the
-// walk uses parent links: `from` records whether the node is entered from
-// its parent (-1), returned to from its near child (0) or from its far child
-// (1); -2 means "returned from `prev`, find out which child it was".  Each
-// internal node is entered at most three times, which bounds the loop.
+// All 32 lanes call it together; every branch depends only on warp-uniform
+// values (node index, depth, trail, votes), so the warp walks one node
+// sequence while each lane keeps its own closest hit.  There is no stack:
+// the walk goes up through parent links, and a 128-bit trail holds, per
+// depth, whether the far child of the node on the current path was hit by
+// some lane when the node was entered.  On the way up a node whose far child
+// was already culled is passed with a 16-byte link load and no box test
+// (t_best only shrinks, so a culled box stays culled).  A Karras tree over
+// 63-bit codes with index tie-breaks is at most 95 levels deep, so the trail
+// never overflows; the loop is also bounded by 3 x (internal nodes).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void child_box(const float4& n0, const float4& n1, const float4& n2,
+                                          bool second, float b[6]) {
+    if (!second) { b[0] = n0.x; b[1] = n0.y; b[2] = n0.z; b[3] = n0.w; b[4] = n1.x; b[5] = n1.y; }
+    else { b[0] = n1.z; b[1] = n1.w; b[2] = n2.x; b[3] = n2.y; b[4] = n2.z; b[5] = n2.w; }
+}
+
+__device__ __forceinline__ void leaf_test(const DevScene& S, const RayF& r, int child, bool h,
+                                          float& t_best, int& hit) {
+    if (h) {
+        int t = ~child;
+        const float4* tp = S.tris + 3 * (size_t)t;
+        float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+        if (tri_hit(r, a, b, c, t_best)) hit = t;
+    }
+}
+
 __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool active,
                                          float& t_best, int& hit, uint32_t& flags) {
     const unsigned full = 0xffffffffu;
@@ -392,52 +456,68 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
     if (am == 0u) return;
     int rep = __ffs(am) - 1;
     // near/far order from one representative ray of the packet
-    bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
-    bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
-    bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
+    const bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
+    const bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
+    const bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
     const float tscale = 1.0f + 4.0f * 1.1920929e-7f;
-    int cur = 0, from = -1, prev = 0;
+    uint64_t trail0 = 0, trail1 = 0;   // bit d: far child at depth d still pending
+    int cur = 0, depth = 0;
+    bool down = true;
     const int max_steps = 3 * S.n_int + 8;
     for (int step = 0;; ++step) {
         if (step >= max_steps) { flags |= kPfTraversalCap; break; }
         const float4* nd = S.nodes + 4 * (size_t)cur;
-        float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        int parent = __float_as_int(n3.z), axis = __float_as_int(n3.w) & 3;
-        bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
-        int near_c = pos ? c0 : c1, far_c = pos ? c1 : c0;
-        if (from == -2) from = (near_c == prev) ? 0 : 1;
-        if (from == -1 || from == 0) {
-            // visit near (from == -1) then far (from == 0 or after a near leaf)
-            bool descended = false;
-            for (int slot = (from == -1 ? 0 : 1); slot < 2; ++slot) {
-                bool second = (slot == 0) ? !pos : pos;  // which stored child box
-                float lx, ly, lz, hx, hy, hz;
-                if (!second) { lx = n0.x; ly = n0.y; lz = n0.z; hx = n0.w; hy = n1.x; hz = n1.y; }
-                else { lx = n1.z; ly = n1.w; lz = n2.x; hx = n2.y; hy = n2.z; hz = n2.w; }
-                int child = slot == 0 ? near_c : far_c;
-                bool h = active && slab(r, lx, ly, lz, hx, hy, hz, t_best * tscale);
-                if (!__any_sync(full, h)) continue;
-                if (child < 0) {
-                    if (h) {
-                        int t = ~child;
-                        const float4* tp = S.tris + 3 * (size_t)t;
-                        float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-                        if (tri_hit(r, a, b, c, t_best)) hit = t;
-                    }
-                    continue;
-                }
-                cur = child;
-                from = -1;
-                descended = true;
-                break;
+        if (down) {
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            int axis = __float_as_int(n3.w) & 3;
+            bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
+            int cn = pos ? c0 : c1, cf = pos ? c1 : c0;
+            float bn[6], bf[6];
+            child_box(n0, n1, n2, !pos, bn);
+            child_box(n0, n1, n2, pos, bf);
+            float tmax = t_best * tscale;
+            bool hn = active && slab(r, bn[0], bn[1], bn[2], bn[3], bn[4], bn[5], tmax);
+            bool hf = active && slab(r, bf[0], bf[1], bf[2], bf[3], bf[4], bf[5], tmax);
+            bool an = __any_sync(full, hn), af = __any_sync(full, hf);
+            if (an && cn < 0) { leaf_test(S, r, cn, hn, t_best, hit); an = false; }
+            if (af && cf < 0) {
+                // re-check the far leaf against the (possibly) shorter t_best
+                bool h2 = hf && slab(r, bf[0], bf[1], bf[2], bf[3], bf[4], bf[5], t_best * tscale);
+                leaf_test(S, r, cf, h2, t_best, hit);
+                af = false;
             }
-            if (descended) continue;
+            if (an) {
+                if (af) { if (depth < 64) trail0 |= 1ull << depth; else trail1 |= 1ull << (depth - 64); }
+                cur = cn; ++depth;
+                continue;
+            }
+            if (af) { cur = cf; ++depth; continue; }
+            down = false;   // nothing below: leave this node
+            continue;
         }
+        // going up: leave `cur` for its parent
         if (cur == 0) break;
-        prev = cur;
+        int parent = __float_as_int(__ldg(nd + 3).z);
+        --depth;
+        bool pending = depth < 64 ? ((trail0 >> depth) & 1ull) : ((trail1 >> (depth - 64)) & 1ull);
         cur = parent;
-        from = -2;
+        if (!pending) continue;
+        if (depth < 64) trail0 &= ~(1ull << depth); else trail1 &= ~(1ull << (depth - 64));
+        // the far child of `parent` is still pending: re-test it now
+        const float4* pd = S.nodes + 4 * (size_t)parent;
+        float4 n0 = __ldg(pd), n1 = __ldg(pd + 1), n2 = __ldg(pd + 2), n3 = __ldg(pd + 3);
+        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        int axis = __float_as_int(n3.w) & 3;
+        bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
+        int cf = pos ? c1 : c0;
+        float bf[6];
+        child_box(n0, n1, n2, pos, bf);
+        bool hf = active && slab(r, bf[0], bf[1], bf[2], bf[3], bf[4], bf[5], t_best * tscale);
+        if (__any_sync(full, hf)) {
+            // cf is internal: leaves were tested when `parent` was entered
+            cur = cf; ++depth; down = true;
+        }
     }
 }
 
@@ -632,9 +712,8 @@ __device__ __forceinline__ bool march_step(March& m, const VoxSeg& v, uint32_t& 
 // power (Eq. beamdiv, Eq. beamdiv_w, Eq. ladlut_intensity with a Lambertian
 // cross-section): P = I0 exp(-2 r^2/w^2) Dr^2 eta rho cos / (4 R^2)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float return_power(const DevScanner& sn, double R64, float tan_a,
+__device__ __forceinline__ float return_power(const DevScanner& sn, float R, float tan_a,
                                               float rho, float cos_inc) {
-    float R = (float)R64;
     float z = sn.zk * (R - sn.focus);
     float w2 = sn.w0sq * (1.0f + z * z);
     float r = R * tan_a;

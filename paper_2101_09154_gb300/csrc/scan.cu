@@ -19,10 +19,10 @@
 namespace hg {
 
 struct RayRes {
-    double R;      // event range (stochastic) / triangle range (expected); +inf: none
-    double R2;     // expected mode: first voxel return range; +inf: none
-    float P;       // return power (expected mode: triangle power at unit weight)
-    int32_t id;    // event primitive / triangle id; -1: none
+    float Rh, Rl;    // event range (stochastic) / triangle range (expected), hi + lo
+    float R2h, R2l;  // expected mode: first voxel return range; +inf: none
+    float P;         // return power (expected mode: triangle power at unit weight)
+    int32_t id;      // event primitive / triangle id; -1: none
 };
 
 template <int NL>
@@ -50,16 +50,16 @@ __device__ __forceinline__ float warp_maxf(float v) {
 // warp's waveform; every bin is touched by one lane, returns come in order
 __device__ __forceinline__ void accumulate(float* W, int nb, const DevScanner& sn, float dt,
                                            float tau, float P, int lane) {
-    int blo = max(0, __float2int_ru((tau - sn.cut_lo) / dt));
-    int bhi = min(nb - 1, __float2int_rd((tau + sn.cut_hi) / dt));
+    int blo = max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin));
+    int bhi = min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin));
     for (int b = blo + lane; b <= bhi; b += 32) W[b] += P * pulse_shape(sn, (float)b * dt - tau);
 }
 
 __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* bid, int nb,
                                                 const DevScanner& sn, float dt, float tau,
                                                 float P, int32_t id, int lane) {
-    int blo = max(0, __float2int_ru((tau - sn.cut_lo) / dt));
-    int bhi = min(nb - 1, __float2int_rd((tau + sn.cut_hi) / dt));
+    int blo = max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin));
+    int bhi = min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin));
     for (int b = blo + lane; b <= bhi; b += 32) {
         float v = P * pulse_shape(sn, (float)b * dt - tau);
         W[b] += v;
@@ -161,25 +161,28 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             uint32_t fl = 0;
             traverse(sc, ray, active, tb, hit, fl);
             RayRes rr;
-            rr.R = CUDART_INF;
-            rr.R2 = CUDART_INF;
+            rr.Rh = CUDART_INF_F;
+            rr.Rl = 0.0f;
+            rr.R2h = CUDART_INF_F;
+            rr.R2l = 0.0f;
             rr.P = 0.0f;
             rr.id = -1;
             float tan_a = s_sc[s].tan_a;
+            float dt_hit = 0.0f;
             if (active) {
                 float cosi = 0.0f;
                 double t_tri = CUDART_INF;
                 int gid = -1;
                 float rho = 0.0f;
                 if (hit >= 0) {
-                    float dt = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
-                    t_tri = (double)tb + (double)dt;
+                    dt_hit = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
+                    t_tri = GRID ? (double)tb + (double)dt_hit : 0.0;
                     const float4* tp = sc.tris + 3 * (size_t)hit;
                     gid = __float_as_int(__ldg(&tp[0].w));
                     int mesh = __float_as_int(__ldg(&tp[1].w));
                     int face = __float_as_int(__ldg(&tp[2].w));
                     rho = __ldg(&sc.refl[mesh][face]);
-                    if (!(t_tri > 0.0)) { t_tri = CUDART_INF; gid = -1; }
+                    if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
                 }
                 bool voxel_event = false;
                 if (GRID && sc.has_grid) {
@@ -210,14 +213,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         float sdist = -logf(uniform23(w[0])) / sigma;
                                         if ((double)sdist < len) {
                                             double R = t_in + (double)sdist;
-                                            rr.R = R;
+                                            FF Rs = ff_split(R);
+                                            rr.Rh = Rs.hi;
+                                            rr.Rl = Rs.lo;
                                             rr.id = sc.n_tri + (int32_t)v.vid;
-                                            rr.P = return_power(sn, R, tan_a, sc.leaf_refl, 1.0f);
+                                            rr.P = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f);
                                             voxel_event = true;
                                             break;
                                         }
                                     } else {
-                                        rr.R2 = t_in + 0.5 * len;
+                                        FF R2 = ff_split(t_in + 0.5 * len);
+                                        rr.R2h = R2.hi;
+                                        rr.R2l = R2.lo;
                                         break;
                                     }
                                 }
@@ -227,16 +234,17 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     }
                 }
                 if (!voxel_event && gid >= 0) {
-                    rr.R = t_tri;
+                    rr.Rh = tb;
+                    rr.Rl = dt_hit;
                     rr.id = gid;
-                    rr.P = return_power(sn, t_tri, tan_a, rho, cosi);
+                    rr.P = return_power(sn, tb + dt_hit, tan_a, rho, cosi);
                 }
                 s_rr[r] = rr;
                 if (fl) atomicOr(&s_pflag[pl], fl);
                 if (P.out.subray_hit) {
                     int64_t so = lg.sub_off + (p0 + pl) * S + s;
                     P.out.subray_hit[so] = rr.id;
-                    if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? (float)rr.R : 0.0f;
+                    if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? rr.Rh + rr.Rl : 0.0f;
                 }
             }
         }
@@ -251,17 +259,26 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             const int64_t k = p0 + pl;
             const int64_t gp = lg.pulse_off + k;
             const RayRes* rrp = s_rr + (size_t)pl * S;
-            double rmin = CUDART_INF;
+            FF rmin = {CUDART_INF_F, 0.0f};
             for (int s = lane; s < S; s += 32) {
                 RayRes rr = rrp[s];
-                if (rr.id >= 0) rmin = fmin(rmin, rr.R);
-                if (MODE == 1) rmin = fmin(rmin, rr.R2);
+                if (rr.id >= 0) {
+                    FF r = ff_norm(rr.Rh, rr.Rl);
+                    if (ff_less(r, rmin)) rmin = r;
+                }
+                if (MODE == 1) {
+                    FF r = ff_norm(rr.R2h, rr.R2l);
+                    if (ff_less(r, rmin)) rmin = r;
+                }
             }
-            rmin = warp_min(rmin);
+            for (int o = 16; o > 0; o >>= 1) {
+                FF other = {__shfl_xor_sync(full, rmin.hi, o), __shfl_xor_sync(full, rmin.lo, o)};
+                if (ff_less(other, rmin)) rmin = other;
+            }
             uint32_t pflag = s_pflag[pl];
             float* row = P.out.waveform + lg.wave_off + k * nb;
             const int64_t eb = lg.echo_off + k * K;
-            if (rmin == CUDART_INF) {
+            if (rmin.hi == CUDART_INF_F) {
                 for (int b = lane; b < nb; b += 32) __stcs(row + b, 0.0f);
                 for (int e = lane; e < K; e += 32) {
                     P.out.echo_range[eb + e] = 0.0f;
@@ -276,22 +293,74 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 }
                 continue;
             }
-            int32_t m = (int32_t)floor(rmin * sn.bins_per_metre) - sn.n_pre;
-            double mdt = (double)m * sn.bin_ns;
+            int32_t m = ff_floor_mul(rmin, sn.bpm_hi, sn.bpm_lo) - sn.n_pre;
+            // window start time m * bin as a float pair (exact product)
+            float mdt_h, mdt_l;
+            two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
+            mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
+            const double mdt = (double)mdt_h + (double)mdt_l;
+            // bins [wlo, whi] can be non-zero: the union of the returns' supports
+            int wlo = 0, whi = nb - 1;
             if (MODE == 0) {
                 // each subray's delay relative to the window, formed once
+                int lo = nb, hi = -1;
                 for (int s = lane; s < S; s += 32) {
                     RayRes rr = rrp[s];
-                    s_tau[(size_t)pl * S + s] = rr.id >= 0 ? delay_rel(rr.R, mdt) : 0.0f;
+                    float tau = rr.id >= 0 ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
+                    s_tau[(size_t)pl * S + s] = tau;
+                    if (rr.id >= 0) {
+                        lo = min(lo, max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin)));
+                        hi = max(hi, min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin)));
+                    }
                 }
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(full, lo, o));
+                    hi = max(hi, __shfl_xor_sync(full, hi, o));
+                }
+                wlo = lo;
+                whi = hi;
             }
-            for (int b = lane; b < nb; b += 32) {
-                W[b] = 0.0f;
-                if (MODE == 1) { best[b] = 0.0f; bid[b] = -1; }
+            // zero the window's rows in 16-byte groups [zlo, zhi)
+            const int zlo = wlo & ~3, zhi = whi < wlo ? zlo : min(nbw, (whi | 3) + 1);
+            // a compact window (<= 128 bins) is summed in registers, lanes owning bins
+            const bool in_regs = MODE == 0 && whi - wlo < 128;
+            for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
+                *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (MODE == 1) {
+                    *reinterpret_cast<float4*>(best + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    *reinterpret_cast<int4*>(bid + b) = make_int4(-1, -1, -1, -1);
+                }
             }
             __syncwarp();
             const float* taup = s_tau + (size_t)pl * S;
-            if (MODE == 0) {
+            if (MODE == 0 && in_regs) {
+                // every return at every owned bin, in subray order; terms beyond
+                // the pulse support underflow to (near) zero as in the plain sum
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                float tb0 = (float)(wlo + lane) * dt;
+                for (int s = 0; s < S; ++s) {
+                    RayRes rr = rrp[s];
+                    if (rr.id < 0) continue;
+                    float tau = taup[s];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float x = fmaf((float)(32 * j), dt, tb0) - tau;
+                        acc[j] = fmaf(rr.P, pulse_shape(sn, x), acc[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int b = wlo + lane + 32 * j;
+                    if (b <= whi) W[b] = acc[j];
+                }
+                // alignment pads of the 16-byte groups around [wlo, whi]
+                if (lane < 4) {
+                    int b = zlo + lane;
+                    if (b < wlo) W[b] = 0.0f;
+                    b = whi + 1 + lane;
+                    if (b < zhi) W[b] = 0.0f;
+                }
+            } else if (MODE == 0) {
                 for (int s = 0; s < S; ++s) {
                     RayRes rr = rrp[s];
                     if (rr.id < 0) continue;
@@ -306,7 +375,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     bool lane_on = s < S;
                     RayRes rr;
                     rr.id = -1;
-                    rr.R = CUDART_INF;
+                    rr.Rh = CUDART_INF_F;
+                    rr.Rl = 0.0f;
                     rr.P = 0.0f;
                     float T = 1.0f;
                     float tan_a = 0.0f;
@@ -325,7 +395,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             o[a] = ff2d(f.oh[a], f.ol[a]);
                             d[a] = ff2d(dh[a], dl[a]);
                         }
-                        double t_hi = rr.id >= 0 ? rr.R : CUDART_INF;
+                        double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
                         on = march_init(sc, o, d, t_hi, mch);
                     }
                     while (__any_sync(full, on)) {
@@ -345,7 +415,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                     float w = -T * expm1f(-xs);
                                     T *= expf(-xs);
                                     double R = t_in + 0.5 * len;
-                                    pv = w * return_power(sn, R, tan_a, sc.leaf_refl, 1.0f);
+                                    pv = w * return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f);
                                     tau = delay_rel(R, mdt);
                                     vid = sc.n_tri + (int32_t)v.vid;
                                     has = true;
@@ -366,7 +436,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     }
                     if (fl) atomicOr(&s_pflag[pl], fl);
                     bool has_tri = lane_on && rr.id >= 0;
-                    float ttau = has_tri ? delay_rel(rr.R, mdt) : 0.0f;
+                    float ttau = has_tri ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
                     float tp = T * rr.P;
                     unsigned hm = __ballot_sync(full, has_tri);
                     while (hm) {
@@ -382,16 +452,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             __syncwarp();
             // ---- echoes: 3-bin local maxima at or above thr * max(W) ----
             float wmax = 0.0f;
-            for (int b = lane; b < nb; b += 32) wmax = fmaxf(wmax, W[b]);
+            for (int b = wlo + lane; b <= whi; b += 32) wmax = fmaxf(wmax, W[b]);
             wmax = warp_maxf(wmax);
             const float thr = sn.thr_rel * wmax;
             int count = 0;
-            for (int base = 0; base < nb; base += 32) {
+            // outside [wlo, whi] the waveform is exactly zero: no maxima there
+            for (int base = wlo; base <= whi; base += 32) {
                 int b = base + lane;
-                float c = b < nb ? W[b] : 0.0f;
-                float l = (b > 0 && b < nb) ? W[b - 1] : 0.0f;
-                float rgt = (b + 1 < nb) ? W[b + 1] : 0.0f;
-                bool ismax = b < nb && c > l && c >= rgt && c >= thr && c > 0.0f;
+                bool in = b <= whi;
+                float c = in ? W[b] : 0.0f;
+                float l = (in && b > wlo) ? W[b - 1] : 0.0f;
+                float rgt = (b + 1 <= whi) ? W[b + 1] : 0.0f;
+                bool ismax = in && c > l && c >= rgt && c >= thr && c > 0.0f;
                 unsigned mk = __ballot_sync(full, ismax);
                 int pos = count + __popc(mk & lanemask_lt());
                 if (ismax && pos < K) {
@@ -408,13 +480,15 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (v > bv) { bv = v; obj = rr.id; }
                         }
                     }
-                    double Rc = 0.5 * kC * ((double)(m + b) * sn.bin_ns - sn.echo_offset_ns) * 1e-9;
+                    // echo range in FP32: (m + b) bin - offset is exact or within 1 ulp,
+                    // so the range is good to ~4e-5 m at kilometre scale
+                    float Rc = fmaf((float)(m + b), sn.bin_hi, -sn.echo_offset_f) * kHalfCns;
                     uint64_t w[4];
                     philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
                                (uint64_t)lg.leg_id, P.seed, 0ull, w);
                     float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
                     float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-                    P.out.echo_range[eb + pos] = (float)(Rc + (double)(sn.noise_sigma * z));
+                    P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
                     if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
                     if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
                     if (P.out.echo_object) P.out.echo_object[eb + pos] = obj;
@@ -441,10 +515,13 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             }
             // ---- waveform row: 16-byte streaming stores when aligned ----
             if (((reinterpret_cast<uintptr_t>(row) & 15u) == 0) && (nb & 3) == 0) {
-                for (int b = lane * 4; b < nb; b += 128)
-                    __stcs(reinterpret_cast<float4*>(row + b), *reinterpret_cast<const float4*>(W + b));
+                for (int b = lane * 4; b < nb; b += 128) {
+                    float4 v = (b >= zlo && b < zhi) ? *reinterpret_cast<const float4*>(W + b)
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                    __stcs(reinterpret_cast<float4*>(row + b), v);
+                }
             } else {
-                for (int b = lane; b < nb; b += 32) __stcs(row + b, W[b]);
+                for (int b = lane; b < nb; b += 32) __stcs(row + b, (b >= zlo && b < zhi) ? W[b] : 0.0f);
             }
             __syncwarp();
         }
