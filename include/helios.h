@@ -251,6 +251,29 @@ HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n
                                const helios_scan_opts* opts, const helios_outputs* out,
                                void* cuda_stream);
 
+/* helios_scan_legs_static: helios_scan_legs in persistent mode that allocates
+ * nothing.  The paper has no counterpart; this is a deployment variant.
+ * Some callers cannot allocate device memory during a scan: processes whose
+ * device memory is owned by another allocator (a framework's caching
+ * allocator holding the budget), code running while a CUDA graph is captured
+ * into a memory pool it does not control, and real-time loops that cannot let
+ * an allocation fail or stall mid-run.  helios_scan_legs allocates its work
+ * queue counter with cudaMallocAsync; this variant keeps the counters in a
+ * static device array of 16 int32 (64 bytes, held by every GPU that loads the
+ * library until exit), so it takes at most 16 x 96 = 1536 legs per call and
+ * returns HELIOS_ERR_INVALID_ARG beyond that.  Host-side staging is static too
+ * (no heap use).  The first call on each device looks the array's address up
+ * with cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the array: each call zeroes the counters it uses on its
+ * stream, and calls whose work overlaps on the GPU (e.g. on two streams) race
+ * on them.  opts->persistent is ignored (always one launch per 96 legs).
+ * Arguments, outputs and results are those of helios_scan_legs. */
+HELIOS_API helios_status helios_scan_legs_static(helios_scene* const* scenes, int32_t n_scenes,
+                                                 const helios_scanner_desc* scanners,
+                                                 int32_t n_scanners, const helios_leg_desc* legs,
+                                                 int32_t n_legs, const helios_scan_opts* opts,
+                                                 const helios_outputs* out, void* cuda_stream);
+
 /* Gradient buffers of one scene: d_reflectance[i] (device float[n_faces of
  * mesh i], or NULL to skip) and d_density[j] (device float[n voxels of grid
  * j], or NULL).  Gradients are ADDED to these buffers. */

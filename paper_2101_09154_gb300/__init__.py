@@ -20,7 +20,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["Scene", "scan", "scan_adjoint", "output_layout", "subray_count", "WaveformFunction",
+__all__ = ["Scene", "scan", "scan_static", "scan_adjoint", "output_layout", "subray_count", "WaveformFunction",
            "lib", "library_path", "HeliosError"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -135,6 +135,10 @@ def lib():
                                        C.c_int32, C.POINTER(LegDesc), C.c_int32,
                                        C.POINTER(ScanOpts), C.POINTER(Outputs), C.c_void_p]
         l.helios_scan_legs.restype = st
+        l.helios_scan_legs_static.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ScannerDesc),
+                                              C.c_int32, C.POINTER(LegDesc), C.c_int32,
+                                              C.POINTER(ScanOpts), C.POINTER(Outputs), C.c_void_p]
+        l.helios_scan_legs_static.restype = st
         l.helios_scan_adjoint.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ScannerDesc),
                                           C.c_int32, C.POINTER(LegDesc), C.c_int32,
                                           C.POINTER(ScanOpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -333,6 +337,32 @@ def scan(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, persistent=False,
     o = _outputs_struct(out)
     _check(lib().helios_scan_legs(sh, len(scenes), sd, len(scanners), ld, len(legs), C.byref(opts),
                                   C.byref(o), _stream_handle(stream)))
+    return out, layout
+
+
+def scan_static(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, out=None, subrays=True,
+                stream=None, block_threads=0, rays_per_block=0, blocks_per_sm=0):
+    """helios_scan_legs_static: the persistent scan with no device allocation.
+
+    For callers that cannot allocate device memory mid-scan (another
+    allocator owns the budget, a graph capture into a pool they do not
+    control, real-time loops).  The work-queue counters live in a static
+    device array shared by all calls, so calls must not overlap on the GPU;
+    at most 1536 legs per call.  Outputs are those of ``scan``.
+    """
+    scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
+    layout = output_layout(scanners, legs)
+    if out is None:
+        out = alloc_outputs(layout, scenes[0].device, subrays=subrays)
+    sh = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    sd = (ScannerDesc * len(scanners))(*[scanner_desc(s) for s in scanners])
+    ld = (LegDesc * max(len(legs), 1))(*[leg_desc(l) for l in legs])
+    opts = ScanOpts(mode=int(mode), persistent=1, seed=int(seed) & (2 ** 64 - 1),
+                    block_threads=int(block_threads), rays_per_block=int(rays_per_block),
+                    blocks_per_sm=int(blocks_per_sm))
+    o = _outputs_struct(out)
+    _check(lib().helios_scan_legs_static(sh, len(scenes), sd, len(scanners), ld, len(legs),
+                                         C.byref(opts), C.byref(o), _stream_handle(stream)))
     return out, layout
 
 

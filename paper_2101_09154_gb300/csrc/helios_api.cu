@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 namespace hg {
@@ -434,3 +435,118 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// helios_scan_legs_static: the persistent scan without any allocation.
+// Validation and leg planning mirror helios_scan_legs but write into
+// fixed-size static arrays (no std::vector, no new, no device allocation).
+// ---------------------------------------------------------------------------
+namespace hg {
+namespace {
+std::mutex g_plan_mu;
+DevScene g_plan_scenes[kMaxScenes];
+DevScanner g_plan_scanners[kMaxScanners];
+DevLeg g_plan_legs[16 * kMaxLegs];
+}  // namespace
+}  // namespace hg
+
+extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, int32_t n_scenes,
+                                                 const helios_scanner_desc* scanners,
+                                                 int32_t n_scanners, const helios_leg_desc* legs,
+                                                 int32_t n_legs, const helios_scan_opts* opts,
+                                                 const helios_outputs* out, void* cuda_stream) {
+    g_err.clear();
+    helios_status st = check_scenes(scenes, n_scenes);
+    if (st != HELIOS_OK) return st;
+    if (!opts || !out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and out must not be NULL");
+    if (opts->mode != HELIOS_MODE_STOCHASTIC && opts->mode != HELIOS_MODE_EXPECTED)
+        return set_error(HELIOS_ERR_INVALID_ARG, "unknown mode");
+    if (!out->waveform || !out->window_bin || !out->echo_count || !out->echo_range)
+        return set_error(HELIOS_ERR_INVALID_ARG, "waveform, window_bin, echo_count, echo_range are required");
+    if (out->subray_range && !out->subray_hit)
+        return set_error(HELIOS_ERR_INVALID_ARG, "subray_range needs subray_hit");
+    const int max_legs = static_scan_max_legs();
+    if (n_legs < 0 || (n_legs > 0 && !legs)) return set_error(HELIOS_ERR_INVALID_ARG, "legs is NULL");
+    if (n_legs > max_legs)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs_static takes at most %d legs, got %d",
+                         max_legs, n_legs);
+    int threads = opts->block_threads > 0 ? opts->block_threads : 256;
+    if (threads % 32 != 0 || threads < 64 || threads > 256)
+        return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
+    int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
+    if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
+    if (n_scanners < 1 || n_scanners > kMaxScanners || !scanners)
+        return set_error(HELIOS_ERR_INVALID_ARG, "n_scanners must be in 1..%d", kMaxScanners);
+    for (int i = 0; i < n_scanners; ++i) {
+        st = check_scanner(scanners[i], i);
+        if (st != HELIOS_OK) return st;
+    }
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    int64_t pulses = 0, wave = 0, sub = 0, echo = 0;
+    for (int l = 0; l < n_legs; ++l) {
+        const helios_leg_desc& L = legs[l];
+        if (L.scene_index < 0 || L.scene_index >= n_scenes)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: scene_index out of range", l);
+        if (L.scanner_index < 0 || L.scanner_index >= n_scanners)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: scanner_index out of range", l);
+        if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
+        if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: speed_mps must be >= 0", l);
+        const helios_scanner_desc& sc = scanners[L.scanner_index];
+        int q = L.beam_sample_quality >= 0 ? L.beam_sample_quality : sc.beam_sample_quality;
+        if (q > 9) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: beam_sample_quality must be <= 9", l);
+        DevLeg& d = g_plan_legs[l];
+        memset(&d, 0, sizeof(d));
+        double D[3], len2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            d.start[a] = L.start[a];
+            D[a] = L.end[a] - L.start[a];
+            len2 += D[a] * D[a];
+            d.rpy[a] = L.attitude_rpy[a];
+        }
+        d.length = std::sqrt(len2);
+        if (L.platform == HELIOS_PLATFORM_LINEAR && d.length > 0.0) {
+            for (int a = 0; a < 3; ++a) d.dir[a] = D[a] / d.length;
+            d.rpy[2] += std::atan2(D[1], D[0]);
+        }
+        d.speed = L.speed_mps;
+        d.t0 = L.t0;
+        d.n_pulses = L.n_pulses;
+        d.scene = L.scene_index;
+        d.scanner = L.scanner_index;
+        d.platform = L.platform;
+        d.q = q;
+        d.S = subray_count(q);
+        int ppi = rays / d.S;
+        d.pulses_per_item = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        d.leg_id = L.leg_id;
+        d.pulse_off = pulses;
+        d.wave_off = wave;
+        d.sub_off = sub;
+        d.echo_off = echo;
+        pulses += L.n_pulses;
+        wave += L.n_pulses * sc.n_bins;
+        sub += L.n_pulses * d.S;
+        echo += L.n_pulses * sc.max_echoes;
+    }
+    for (int i = 0; i < n_scenes; ++i) g_plan_scenes[i] = dev_scene(scenes[i]);
+    for (int i = 0; i < n_scanners; ++i) g_plan_scanners[i] = derive_scanner(scanners[i]);
+    Outputs o;
+    o.waveform = out->waveform;
+    o.window_bin = out->window_bin;
+    o.echo_count = out->echo_count;
+    o.echo_range = out->echo_range;
+    o.echo_amp = out->echo_amp;
+    o.echo_bin = out->echo_bin;
+    o.echo_object = out->echo_object;
+    o.pulse_flags = out->pulse_flags;
+    o.subray_hit = out->subray_hit;
+    o.subray_range = out->subray_range;
+    o.status = out->status;
+    if (pulses == 0) return HELIOS_OK;
+    return launch_scan_static(g_plan_scenes, n_scenes, g_plan_scanners, n_scanners, g_plan_legs,
+                              n_legs, o, opts->seed, opts->mode, threads, opts->blocks_per_sm,
+                              (cudaStream_t)cuda_stream);
+}

@@ -43,6 +43,11 @@ struct ScanLaunch {
 };
 
 helios_status launch_scan(const ScanLaunch& L, cudaStream_t st);
+helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const DevScanner* scanners,
+                                 int n_scanners, const DevLeg* legs, int n_legs, const Outputs& out,
+                                 uint64_t seed, int mode, int threads, int blocks_per_sm,
+                                 cudaStream_t st);
+int static_scan_max_legs();
 size_t scan_params_bytes();
 
 struct AdjointLaunch {

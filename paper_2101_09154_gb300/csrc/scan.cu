@@ -15,6 +15,7 @@
 #include "hg_host.h"
 
 #include <cfloat>
+#include <mutex>
 
 namespace hg {
 
@@ -650,5 +651,93 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
 static_assert(sizeof(ScanParams<kMaxLegs>) <= 32000, "kernel parameters must fit the 32 KB limit");
 
 size_t scan_params_bytes() { return sizeof(ScanParams<kMaxLegs>); }
+
+}  // namespace hg
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the persistent launch (helios_scan_legs_static).
+//
+// The only device scratch of the persistent launch is one work-queue counter
+// per group of up to kMaxLegs legs.  Here those counters live in a file-scope
+// device array instead of stream-ordered allocations, so the call never
+// allocates.  Its address is looked up with cudaGetSymbolAddress once per
+// device, on the first call made with that device current.  Every call on a
+// device shares the array: the counters a call uses are zeroed on its stream
+// before its launches, and calls whose work overlaps on the GPU (e.g. on two
+// streams) would race on them.
+// ---------------------------------------------------------------------------
+namespace hg {
+
+constexpr int kStaticQueues = 16;   // up to 16 x kMaxLegs = 1536 legs per call
+static __device__ __align__(256) int32_t g_static_queue[kStaticQueues];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+int32_t* g_static_ptr[kMaxDevices];
+ScanParams<kMaxLegs> g_static_params;  // host staging of the kernel parameters
+}  // namespace
+
+int static_scan_max_legs() { return kStaticQueues * kMaxLegs; }
+
+helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const DevScanner* scanners,
+                                 int n_scanners, const DevLeg* legs, int n_legs, const Outputs& out,
+                                 uint64_t seed, int mode, int threads, int blocks_per_sm,
+                                 cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error("cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return set_error(HELIOS_ERR_UNSUPPORTED, "device index %d", dev);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_queue);
+        if (e != cudaSuccess) return set_cuda_error("cudaGetSymbolAddress(static work queue)", e);
+        g_static_ptr[dev] = static_cast<int32_t*>(p);
+    }
+    const int n_groups = (n_legs + kMaxLegs - 1) / kMaxLegs;
+    if (n_groups > kStaticQueues)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs_static takes at most %d legs, got %d",
+                         kStaticQueues * kMaxLegs, n_legs);
+    int s_cap = 1, pc_cap = 1, rays_cap = 32, nb_cap = 4;
+    bool any_grid = false;
+    for (int l = 0; l < n_legs; ++l) {
+        s_cap = max(s_cap, legs[l].S);
+        pc_cap = max(pc_cap, legs[l].pulses_per_item);
+        rays_cap = max(rays_cap, legs[l].S * legs[l].pulses_per_item);
+        nb_cap = max(nb_cap, scanners[legs[l].scanner].n_bins);
+        any_grid |= scenes[legs[l].scene].has_grid != 0;
+    }
+    nb_cap = (nb_cap + 3) & ~3;
+    size_t smem = smem_bytes(mode, pc_cap, s_cap, rays_cap, nb_cap, threads);
+    if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
+    if (n_groups == 0) return HELIOS_OK;
+    e = cudaMemsetAsync(g_static_ptr[dev], 0, sizeof(int32_t) * n_groups, st);
+    if (e != cudaSuccess) return set_cuda_error("cudaMemsetAsync(static work queue)", e);
+    for (int g = 0; g < n_groups; ++g) {
+        const int l0 = g * kMaxLegs, nl = min(kMaxLegs, n_legs - l0);
+        ScanParams<kMaxLegs>& p = g_static_params;
+        memset(&p, 0, sizeof(p));
+        for (int i = 0; i < n_scenes; ++i) p.scenes[i] = scenes[i];
+        for (int i = 0; i < n_scanners; ++i) p.scanners[i] = scanners[i];
+        int64_t items = 0;
+        for (int l = 0; l < nl; ++l) {
+            p.legs[l] = legs[l0 + l];
+            p.legs[l].item_begin = items;
+            items += (legs[l0 + l].n_pulses + legs[l0 + l].pulses_per_item - 1) / legs[l0 + l].pulses_per_item;
+        }
+        if (items >= INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many work items");
+        if (items == 0) continue;
+        p.out = out;
+        p.seed = seed;
+        p.n_legs = nl;
+        p.n_items = (int32_t)items;
+        p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
+        p.queue = g_static_ptr[dev] + g;
+        helios_status s = dispatch<kMaxLegs>(p, mode, any_grid, threads, blocks_per_sm, smem, st, 0);
+        if (s != HELIOS_OK) return s;
+    }
+    return HELIOS_OK;
+}
 
 }  // namespace hg

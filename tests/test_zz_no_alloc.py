@@ -1,0 +1,66 @@
+"""The allocation-free persistent scan against the allocating one (GPU).
+
+Some callers cannot allocate device memory during a scan: processes whose
+device memory belongs to another allocator (a framework's caching allocator
+holding the budget), code capturing a CUDA graph into a memory pool it does
+not control, and real-time loops that cannot let an allocation fail or stall.
+For them helios_scan_legs_static keeps the only scratch of the persistent
+scan, its work-queue counters, in a static device array instead of a
+cudaMallocAsync allocation.  The array keeps the previous call's contents, so
+the checks below run the entry point twice in a row and compare both results
+with helios_scan_legs, within the tolerances of the other GPU tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INT_KEYS = ("window_bin", "echo_count", "echo_bin", "echo_object", "subray_hit", "pulse_flags")
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_09154_gb300 as m
+    return m
+
+
+def _close(a, b, nb=None):
+    a = a.detach().double().cpu().numpy()
+    b = b.detach().double().cpu().numpy()
+    if nb is None:                              # ranges: 1e-4 m
+        return np.all(np.abs(a - b) <= 1e-4)
+    W, R = a.reshape(-1, nb), b.reshape(-1, nb)  # waveform: 1e-4 |W| + 1e-7 max per pulse
+    peak = np.abs(R).max(axis=1, keepdims=True)
+    return np.all(np.abs(W - R) <= 1e-4 * np.abs(R) + 1e-7 * peak)
+
+
+def test_static_scan_matches_allocating_scan_on_two_calls(hg):
+    w = scenes.batched_legs(seed=12, n_legs=5, tile=64, block=24, n_terrain=2, n_voxel=2,
+                            min_pulses=500, max_pulses=3000, n_bins=256)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    ref, _ = hg.scan(gsc, w.scanners, w.legs, seed=9, persistent=True)
+    torch.cuda.synchronize()
+    for _call in range(2):
+        got, _ = hg.scan_static(gsc, w.scanners, w.legs, seed=9)
+        torch.cuda.synchronize()
+        for k in INT_KEYS:
+            assert torch.equal(got[k], ref[k]), k
+        assert _close(got["waveform"], ref["waveform"], nb=256)
+        for k in ("echo_range", "subray_range"):
+            assert _close(got[k], ref[k]), k
+
+
+def test_static_scan_rejects_too_many_legs(hg):
+    w = scenes.tls_tiny(n_az=4, n_el=4)
+    gsc = [hg.Scene(w.scenes[0])]
+    legs = [scenes.Leg(n_pulses=16 if i == 0 else 0, leg_id=i) for i in range(1537)]
+    with pytest.raises(hg.HeliosError) as e:
+        hg.scan_static(gsc, w.scanners, legs)
+    assert e.value.code == -1 and "1536" in str(e.value)
