@@ -270,7 +270,7 @@ def run_ours(args, D):
     ms = float(np.mean(per))
     ms_max = D.max(ms)
     P = w.n_pulses
-    n_launch = len(w.legs) if not persistent else math.ceil(len(w.legs) / 96)
+    n_launch = len(w.legs) if not persistent else math.ceil(len(w.legs) / 128)
     S = workload_config(w, args.workload)["subrays_per_pulse"]
     subrays_total = sum(l.n_pulses * hg.subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
                                                      else w.scanners[l.scanner_index].beam_sample_quality)
@@ -302,6 +302,8 @@ def run_ours(args, D):
         if D.rank == 0 and D.world == 1:
             res["adjoint"] = adjoint_ratio(args)
             res["adjoint_forward_ratio"] = res["adjoint"]["adjoint_forward_ratio"]
+            if args.workload == "als":
+                res["batched"] = batched_compare(args)
     return res, w
 
 
@@ -342,6 +344,67 @@ def e2e(w, gsc, layout, out, args, stream, D):
     ms = D.max(e0.elapsed_time(e1) / n)
     return {"value": D.world * w.n_pulses / (ms / 1e3), "unit": "pulses/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n}
+
+
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def batched_compare(args):
+    """Many legs of uneven length and subray quality (1, 7, 19, 37 subrays) over
+    terrain tiles and voxel blocks: one launch per leg vs one persistent launch
+    fed by a work queue vs that launch replayed from a CUDA graph, all with the
+    autotuned launch parameters."""
+    import torch
+    import paper_2101_09154_gb300 as hg
+    from paper_2101_09154_gb300.autotune import autotune
+    w = workload("batched", args.small)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    lay = hg.output_layout(w.scanners, w.legs)
+    out = hg.alloc_outputs(lay, gsc[0].device, subrays=False)
+    cache = os.path.join(ROOT, "paper_2101_09154_gb300", "_build", "autotune.json")
+    tune = autotune(gsc, w.scanners, w.legs, out, persistent=True, cache_path=cache)
+    kw = dict(block_threads=tune["block_threads"], rays_per_block=tune["rays_per_block"])
+    steps, warm = max(2, min(args.steps, 5)), 2
+    per_leg_ms = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, persistent=False, out=out, **kw),
+                        steps, warm)
+    pers_ms = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, persistent=True, out=out, **kw),
+                     steps, warm)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        hg.scan(gsc, w.scanners, w.legs, persistent=True, out=out, **kw)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        hg.scan(gsc, w.scanners, w.legs, persistent=True, out=out, **kw)
+    graph_ms = _timed(graph.replay, steps, warm)
+    P = w.n_pulses
+    res = {"workload": w.name, "description": w.note, "legs": len(w.legs), "pulses": P,
+           "autotune": {k: tune[k] for k in ("block_threads", "rays_per_block")},
+           "autotune_trials_ms": {f"{t['block_threads']}x{t['rays_per_block']}": round(t["ms"], 3)
+                                  for t in tune["trials"]},
+           "per_leg_ms": per_leg_ms, "per_leg_launches": len(w.legs),
+           "persistent_ms": pers_ms, "persistent_launches": math.ceil(len(w.legs) / 128),
+           "graph_ms": graph_ms,
+           "speedup_persistent_vs_per_leg": per_leg_ms / pers_ms,
+           "speedup_graph_vs_per_leg": per_leg_ms / graph_ms,
+           "pulses_per_s_graph": P / (graph_ms / 1e3),
+           "pulses_per_s_per_leg": P / (per_leg_ms / 1e3)}
+    del out, graph
+    torch.cuda.empty_cache()
+    return res
 
 
 def adjoint_ratio(args):

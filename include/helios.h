@@ -260,13 +260,13 @@ HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n
  * an allocation fail or stall mid-run.  helios_scan_legs allocates its work
  * queue counter with cudaMallocAsync; this variant keeps the counters in a
  * static device array of 16 int32 (64 bytes, held by every GPU that loads the
- * library until exit), so it takes at most 16 x 96 = 1536 legs per call and
+ * library until exit), so it takes at most 16 x 128 = 2048 legs per call and
  * returns HELIOS_ERR_INVALID_ARG beyond that.  Host-side staging is static too
  * (no heap use).  The first call on each device looks the array's address up
  * with cudaGetSymbolAddress; make that first call before any stream capture.
  * All calls share the array: each call zeroes the counters it uses on its
  * stream, and calls whose work overlaps on the GPU (e.g. on two streams) race
- * on them.  opts->persistent is ignored (always one launch per 96 legs).
+ * on them.  opts->persistent is ignored (always one launch per 128 legs).
  * Arguments, outputs and results are those of helios_scan_legs. */
 HELIOS_API helios_status helios_scan_legs_static(helios_scene* const* scenes, int32_t n_scenes,
                                                  const helios_scanner_desc* scanners,

@@ -348,7 +348,7 @@ def scan_static(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, out=None, 
     allocator owns the budget, a graph capture into a pool they do not
     control, real-time loops).  The work-queue counters live in a static
     device array shared by all calls, so calls must not overlap on the GPU;
-    at most 1536 legs per call.  Outputs are those of ``scan``.
+    at most 2048 legs per call.  Outputs are those of ``scan``.
     """
     scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
     layout = output_layout(scanners, legs)

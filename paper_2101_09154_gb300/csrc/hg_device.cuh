@@ -14,7 +14,7 @@ namespace hg {
 constexpr int kMaxMesh = 16;
 constexpr int kMaxScenes = 16;
 constexpr int kMaxScanners = 4;
-constexpr int kMaxLegs = 96;
+constexpr int kMaxLegs = 128;
 constexpr double kC = 299792458.0;        // speed of light (Sec. 3.4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kDelayPerMetre = 2.0e9 / kC;  // round-trip delay in ns per metre of range

@@ -668,7 +668,7 @@ size_t scan_params_bytes() { return sizeof(ScanParams<kMaxLegs>); }
 // ---------------------------------------------------------------------------
 namespace hg {
 
-constexpr int kStaticQueues = 16;   // up to 16 x kMaxLegs = 1536 legs per call
+constexpr int kStaticQueues = 16;   // up to 16 x kMaxLegs = 2048 legs per call
 static __device__ __align__(256) int32_t g_static_queue[kStaticQueues];
 
 namespace {

@@ -191,3 +191,40 @@ def test_als_full_size_sampled(hg):
     out, lay, res = run_both(hg, w, seed=0, rows=rows, subrays=True)
     stats = compare(*res[0])
     assert stats["pulses"] == len(rows)
+
+
+def test_graph_replay_and_autotune_match_direct_call(hg):
+    """The persistent launch captured in a CUDA graph and replayed, and every
+    autotuner candidate, reproduce the direct call bit for bit."""
+    from paper_2101_09154_gb300.autotune import autotune
+    w = scenes.batched_legs(seed=10, n_legs=7, tile=64, block=24, n_terrain=2, n_voxel=2,
+                            min_pulses=300, max_pulses=3000, n_bins=256)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    ref, lay = hg.scan(gsc, w.scanners, w.legs, seed=2, persistent=True)
+    torch.cuda.synchronize()
+    out = hg.alloc_outputs(lay, gsc[0].device, subrays=True)
+    tune = autotune(gsc, w.scanners, w.legs, out, persistent=True, reps=1)
+    assert {"block_threads", "rays_per_block", "ms"} <= set(tune)
+    for t in tune["trials"]:
+        o, _ = hg.scan(gsc, w.scanners, w.legs, seed=2, persistent=True,
+                       block_threads=t["block_threads"], rays_per_block=t["rays_per_block"])
+        torch.cuda.synchronize()
+        assert torch.equal(o["waveform"], ref["waveform"]) and torch.equal(o["echo_range"], ref["echo_range"])
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        hg.scan(gsc, w.scanners, w.legs, seed=2, persistent=True, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for v in out.values():
+        v.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        hg.scan(gsc, w.scanners, w.legs, seed=2, persistent=True, out=out)
+    for v in out.values():
+        v.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for k in ("waveform", "window_bin", "echo_count", "echo_range", "echo_object", "subray_hit"):
+        assert torch.equal(out[k], ref[k]), k

@@ -60,7 +60,7 @@ def test_static_scan_matches_allocating_scan_on_two_calls(hg):
 def test_static_scan_rejects_too_many_legs(hg):
     w = scenes.tls_tiny(n_az=4, n_el=4)
     gsc = [hg.Scene(w.scenes[0])]
-    legs = [scenes.Leg(n_pulses=16 if i == 0 else 0, leg_id=i) for i in range(1537)]
+    legs = [scenes.Leg(n_pulses=16 if i == 0 else 0, leg_id=i) for i in range(2049)]
     with pytest.raises(hg.HeliosError) as e:
         hg.scan_static(gsc, w.scanners, legs)
-    assert e.value.code == -1 and "1536" in str(e.value)
+    assert e.value.code == -1 and "2048" in str(e.value)
