@@ -82,9 +82,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
     uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
+    float* s_noise = reinterpret_cast<float*>(s_pflag + P.pc_cap);   // [pc_cap][2]
     // the per-warp waveform rows start 16-byte aligned (float4 reads below)
     float* s_w = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(s_pflag + P.pc_cap) + 15u) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(s_noise + 2 * P.pc_cap) + 15u) & ~uintptr_t(15));
     __shared__ int s_item;
     __shared__ int s_cached_leg;
     __shared__ double s_rot[6];
@@ -142,6 +143,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             pulse_frame(sn, lg, s_rot, p0 + t, f);
             split_store(f, s_pf[t]);
             s_pflag[t] = 0u;
+        }
+        // range noise of each pulse's first two echoes (Sec. 3.7), drawn here
+        // where every thread helps instead of by one lane per echo later
+        for (int i = tid; i < 2 * pc; i += blockDim.x) {
+            const int e = i & 1;
+            if (e < K) {
+                uint64_t w[4];
+                philox4x64((uint64_t)(p0 + (i >> 1)), (1ull << 32) | (uint64_t)e, 0ull,
+                           (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
+                s_noise[i] = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            }
         }
         __syncthreads();
 
@@ -484,11 +497,16 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     // echo range in FP32: (m + b) bin - offset is exact or within 1 ulp,
                     // so the range is good to ~4e-5 m at kilometre scale
                     float Rc = fmaf((float)(m + b), sn.bin_hi, -sn.echo_offset_f) * kHalfCns;
-                    uint64_t w[4];
-                    philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
-                               (uint64_t)lg.leg_id, P.seed, 0ull, w);
-                    float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
-                    float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+                    float z;
+                    if (pos < 2) {
+                        z = s_noise[2 * pl + pos];
+                    } else {
+                        uint64_t w[4];
+                        philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
+                                   (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                        float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
+                        z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+                    }
                     P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
                     if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
                     if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
@@ -569,7 +587,7 @@ static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int 
 
 static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads) {
     size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
-               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap;
+               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap;
     b = (b + 15) & ~size_t(15);
     b += (size_t)(threads / 32) * nb_cap * sizeof(float) * (mode == 1 ? 3 : 1);
     return b;
