@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
             const int64_t gp = lg.pulse_off + k;
             const int32_t m = P.window[gp];
             if (m == kNoWindow) continue;
-            const double mdt = (double)m * sn.bin_ns;
+            float mdt_h, mdt_l;    // window start m * bin as a float pair
+            two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
+            mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
             const float* grow = P.g + lg.wave_off + k * nb;
             for (int b = lane; b < nb; b += 32) g[b] = __ldcs(grow + b);
             __syncwarp();
@@ -108,10 +110,10 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 }
                 if (!on) continue;
                 double t_tri = CUDART_INF;
-                float cosi = 0.0f, rho = 0.0f;
+                float cosi = 0.0f, rho = 0.0f, dt32 = 0.0f;
                 int mesh = 0, face = 0;
                 if (hit >= 0) {
-                    float dt32 = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, t32, cosi);
+                    dt32 = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, t32, cosi);
                     t_tri = (double)t32 + (double)dt32;
                     const float4* tp = sc.tris + 3 * (size_t)hit;
                     mesh = __float_as_int(__ldg(&tp[1].w));
@@ -131,15 +133,15 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                         if (!march_current(sc, mch, v)) break;
                         float dens = __ldg(&sc.density[v.vid]);
                         if (dens > 0.0f) {
-                            double t_in, t_out;
-                            march_segment64(mch, v, t_in, t_out);
-                            double len = t_out - t_in;
-                            if (len > 0.0) {
-                                float xs = sc.G * dens * (float)len;
+                            FF t_in, t_out;
+                            march_segment_ff(mch, v, t_in, t_out);
+                            float len = ff_diff(t_out, t_in);
+                            if (len > 0.0f) {
+                                float xs = sc.G * dens * len;
                                 float w = -T * expm1f(-xs);
-                                double R = t_in + 0.5 * len;
-                                float A = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
+                                FF R = ff_add_f(t_in, 0.5f * len);
+                                float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
+                                          corr(g, nb, sn, dt, ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                 total += (double)A * (double)w;
                                 T *= expf(-xs);
                             }
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 }
                 float A_tri = 0.0f;
                 if (hit >= 0) {
-                    A_tri = return_power(sn, (float)t_tri, tan_a, 1.0f, cosi) *
-                            corr(g, nb, sn, dt, (float)fma(t_tri, kDelayPerMetre, -mdt));
+                    A_tri = return_power(sn, t32 + dt32, tan_a, 1.0f, cosi) *
+                            corr(g, nb, sn, dt, ff_mul_sub(ff_norm(t32, dt32), kDelayHi, kDelayLo, mdt_h, mdt_l));
                     total += (double)A_tri * (double)rho * (double)T;
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
                 }
@@ -163,16 +165,16 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                         if (!march_current(sc, mch, v)) break;
                         float dens = __ldg(&sc.density[v.vid]);
                         if (dens > 0.0f) {
-                            double t_in, t_out;
-                            march_segment64(mch, v, t_in, t_out);
-                            double len = t_out - t_in;
-                            if (len > 0.0) {
-                                float xs = sc.G * dens * (float)len;
+                            FF t_in, t_out;
+                            march_segment_ff(mch, v, t_in, t_out);
+                            float len = ff_diff(t_out, t_in);
+                            if (len > 0.0f) {
+                                float xs = sc.G * dens * len;
                                 float a = expf(-xs);
                                 float w = -Tb * expm1f(-xs);
-                                double R = t_in + 0.5 * len;
-                                float A = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, (float)fma(R, kDelayPerMetre, -mdt));
+                                FF R = ff_add_f(t_in, 0.5f * len);
+                                float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
+                                          corr(g, nb, sn, dt, ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;
                                 double dsig = (double)A * Tb * len * a - len * suffix;

@@ -573,15 +573,15 @@ struct March {
     int sx, sy, sz;
     int px, py, pz;           // first plane crossed on each axis
     float tnx, tny, tnz;      // next crossing per axis, FP32 (ordering only)
-    // crossing of plane p on axis a: t = (f0_a + (p - p_a) c) / d_a, where
+    // Crossing of plane p on axis a: t = (f0_a + (p - p_a) c) / d_a, where
     // f0_a = (g0_a + p_a c) - o_a is formed in FP64 like the plain definition
-    // (g0 + p c - o)/d, so nearly parallel axes never cancel large terms
-    float f0x, f0y, f0z;
-    float ivx, ivy, ivz;
-    double f64x, f64y, f64z;
-    double iv64x, iv64y, iv64z;
+    // (g0 + p c - o)/d, so nearly parallel axes never cancel large terms.
+    // f0 and 1/d are kept as float pairs: segment ends are float-float
+    // (~1e-13 relative), with no FP64 instruction per voxel.
+    float f0hx, f0hy, f0hz, f0lx, f0ly, f0lz;
+    float ivhx, ivhy, ivhz, ivlx, ivly, ivlz;
     float cell;
-    double t_enter, t_end;    // FP64
+    FF t_enter, t_end;
     int entry_axis;           // axis crossed to enter the current voxel, -1: grid entry
     int steps_left;
 };
@@ -614,7 +614,7 @@ __device__ __forceinline__ bool march_init(const DevScene& S, const double o[3],
     double tend = fmin(tx, t_hi);
     if (!(te < tend)) return false;
     int idx[3], stp[3], p0[3];
-    double f0[3], iv[3];
+    FF f0[3], iv[3];
     for (int a = 0; a < 3; ++a) {
         stp[a] = d[a] > 0.0 ? 1 : (d[a] < 0.0 ? -1 : 0);
         if (te > 0.0 && tlo[a] == te && d[a] != 0.0) {
@@ -626,36 +626,47 @@ __device__ __forceinline__ bool march_init(const DevScene& S, const double o[3],
             idx[a] = (int)f;
         }
         p0[a] = stp[a] > 0 ? idx[a] + 1 : idx[a];
-        f0[a] = stp[a] != 0 ? fma((double)p0[a], cell, g0[a]) - o[a] : 0.0;
-        iv[a] = stp[a] != 0 ? 1.0 / d[a] : 0.0;
+        f0[a] = ff_split(stp[a] != 0 ? fma((double)p0[a], cell, g0[a]) - o[a] : 0.0);
+        iv[a] = ff_split(stp[a] != 0 ? 1.0 / d[a] : 0.0);
     }
     m.ix = idx[0]; m.iy = idx[1]; m.iz = idx[2];
     m.sx = stp[0]; m.sy = stp[1]; m.sz = stp[2];
     m.px = p0[0]; m.py = p0[1]; m.pz = p0[2];
-    m.f64x = f0[0]; m.f64y = f0[1]; m.f64z = f0[2];
-    m.iv64x = iv[0]; m.iv64y = iv[1]; m.iv64z = iv[2];
-    m.f0x = (float)f0[0]; m.f0y = (float)f0[1]; m.f0z = (float)f0[2];
-    m.ivx = (float)iv[0]; m.ivy = (float)iv[1]; m.ivz = (float)iv[2];
+    m.f0hx = f0[0].hi; m.f0hy = f0[1].hi; m.f0hz = f0[2].hi;
+    m.f0lx = f0[0].lo; m.f0ly = f0[1].lo; m.f0lz = f0[2].lo;
+    m.ivhx = iv[0].hi; m.ivhy = iv[1].hi; m.ivhz = iv[2].hi;
+    m.ivlx = iv[0].lo; m.ivly = iv[1].lo; m.ivlz = iv[2].lo;
     m.cell = S.cell;
-    m.tnx = cross32(m.px, m.px, m.sx, m.f0x, m.ivx, m.cell);
-    m.tny = cross32(m.py, m.py, m.sy, m.f0y, m.ivy, m.cell);
-    m.tnz = cross32(m.pz, m.pz, m.sz, m.f0z, m.ivz, m.cell);
-    m.t_enter = te;
-    m.t_end = tend;
+    m.tnx = cross32(m.px, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
+    m.tny = cross32(m.py, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
+    m.tnz = cross32(m.pz, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
+    m.t_enter = ff_split(te);
+    m.t_end = ff_split(tend);
     m.entry_axis = -1;
     m.steps_left = dims[0] + dims[1] + dims[2] + 4;
     return true;
 }
 
-// FP64 crossing time of the entry (or exit) face of the current voxel on axis a
-__device__ __forceinline__ double plane64(const March& m, int a, bool entry) {
+// float-float crossing time of the entry (or exit) face of the current voxel on axis a
+__device__ __forceinline__ FF plane_ff(const March& m, int a, bool entry) {
     int i = a == 0 ? m.ix : (a == 1 ? m.iy : m.iz);
     int s = a == 0 ? m.sx : (a == 1 ? m.sy : m.sz);
     int p0 = a == 0 ? m.px : (a == 1 ? m.py : m.pz);
-    double f0 = a == 0 ? m.f64x : (a == 1 ? m.f64y : m.f64z);
-    double iv = a == 0 ? m.iv64x : (a == 1 ? m.iv64y : m.iv64z);
+    float f0h = a == 0 ? m.f0hx : (a == 1 ? m.f0hy : m.f0hz);
+    float f0l = a == 0 ? m.f0lx : (a == 1 ? m.f0ly : m.f0lz);
+    float ivh = a == 0 ? m.ivhx : (a == 1 ? m.ivhy : m.ivhz);
+    float ivl = a == 0 ? m.ivlx : (a == 1 ? m.ivly : m.ivlz);
     int plane = entry ? (s > 0 ? i : i + 1) : (s > 0 ? i + 1 : i);
-    return fma((double)(plane - p0), (double)m.cell, f0) * iv;
+    float ph, pl;                       // (plane - p0) * cell, exactly
+    two_prod((float)(plane - p0), m.cell, ph, pl);
+    float sh, sl;                       // f0 + (ph + pl)
+    two_sum(f0h, ph, sh, sl);
+    sl += f0l + pl;
+    FF n = ff_norm(sh, sl);
+    float th, tl;                       // (f0 + ...) * (1/d)
+    two_prod(n.hi, ivh, th, tl);
+    tl = fmaf(n.hi, ivl, fmaf(n.lo, ivh, tl));
+    return ff_norm(th, tl);
 }
 
 // Current voxel: linear id and exit axis.  Returns false once outside the grid.
@@ -679,30 +690,45 @@ __device__ __forceinline__ bool march_current(const DevScene& S, const March& m,
     return true;
 }
 
-// FP64 segment of the current voxel, clipped to [t_enter, t_end]
-__device__ __forceinline__ void march_segment64(const March& m, const VoxSeg& v, double& t_in,
-                                                double& t_out) {
-    t_in = m.entry_axis < 0 ? m.t_enter : fmax(plane64(m, m.entry_axis, true), m.t_enter);
-    t_out = fmin(plane64(m, v.exit_axis, false), m.t_end);
+// float-float segment of the current voxel, clipped to [t_enter, t_end]
+__device__ __forceinline__ void march_segment_ff(const March& m, const VoxSeg& v, FF& t_in,
+                                                 FF& t_out) {
+    t_in = m.t_enter;
+    if (m.entry_axis >= 0) {
+        FF p = plane_ff(m, m.entry_axis, true);
+        if (ff_less(t_in, p)) t_in = p;
+    }
+    t_out = plane_ff(m, v.exit_axis, false);
+    if (ff_less(m.t_end, t_out)) t_out = m.t_end;
+}
+
+// b - a for close float pairs (the hi difference is exact)
+__device__ __forceinline__ float ff_diff(const FF& b, const FF& a) {
+    return (b.hi - a.hi) + (b.lo - a.lo);
+}
+__device__ __forceinline__ FF ff_add_f(const FF& a, float x) {
+    float s, e;
+    two_sum(a.hi, x, s, e);
+    return ff_norm(s, e + a.lo);
 }
 
 // advance to the next voxel; false when past t_end or out of steps
 __device__ __forceinline__ bool march_step(March& m, const VoxSeg& v, uint32_t& flags) {
     if (--m.steps_left <= 0) { flags |= kPfMarchCap; return false; }
-    if ((double)v.t_out32 >= m.t_end) {
-        // FP32 ordering says the segment ends here; confirm in FP64
-        if (plane64(m, v.exit_axis, false) >= m.t_end) return false;
+    if (v.t_out32 >= m.t_end.hi) {
+        // FP32 ordering says the segment ends here; confirm in float-float
+        if (!ff_less(plane_ff(m, v.exit_axis, false), m.t_end)) return false;
     }
     int a = v.exit_axis;
     if (a == 0) {
         m.ix += m.sx;
-        m.tnx = cross32(m.sx > 0 ? m.ix + 1 : m.ix, m.px, m.sx, m.f0x, m.ivx, m.cell);
+        m.tnx = cross32(m.sx > 0 ? m.ix + 1 : m.ix, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
     } else if (a == 1) {
         m.iy += m.sy;
-        m.tny = cross32(m.sy > 0 ? m.iy + 1 : m.iy, m.py, m.sy, m.f0y, m.ivy, m.cell);
+        m.tny = cross32(m.sy > 0 ? m.iy + 1 : m.iy, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
     } else {
         m.iz += m.sz;
-        m.tnz = cross32(m.sz > 0 ? m.iz + 1 : m.iz, m.pz, m.sz, m.f0z, m.ivz, m.cell);
+        m.tnz = cross32(m.sz > 0 ? m.iz + 1 : m.iz, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
     }
     m.entry_axis = a;
     return true;

@@ -68,11 +68,6 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
     }
 }
 
-// delay of range R (ns) relative to the window start mdt = m * bin
-__device__ __forceinline__ float delay_rel(double R, double mdt) {
-    return (float)fma(R, kDelayPerMetre, -mdt);
-}
-
 template <int MODE, bool GRID, int NL>
 __global__ void __launch_bounds__(256)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
@@ -213,10 +208,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (!march_current(sc, m, v)) break;
                             float dens = __ldg(&sc.density[v.vid]);
                             if (dens > 0.0f) {
-                                double t_in, t_out;
-                                march_segment64(m, v, t_in, t_out);
-                                double len = t_out - t_in;
-                                if (len > 0.0) {
+                                FF t_in, t_out;
+                                march_segment_ff(m, v, t_in, t_out);
+                                float len = ff_diff(t_out, t_in);
+                                if (len > 0.0f) {
                                     float sigma = sc.G * dens;
                                     if (MODE == 0) {
                                         // Eq. intersection_dist: s = -ln(u)/sigma
@@ -225,18 +220,17 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                                    (uint64_t)v.vid, (uint64_t)lg.leg_id,
                                                    P.seed, 0ull, w);
                                         float sdist = -logf(uniform23(w[0])) / sigma;
-                                        if ((double)sdist < len) {
-                                            double R = t_in + (double)sdist;
-                                            FF Rs = ff_split(R);
-                                            rr.Rh = Rs.hi;
-                                            rr.Rl = Rs.lo;
+                                        if (sdist < len) {
+                                            FF R = ff_add_f(t_in, sdist);
+                                            rr.Rh = R.hi;
+                                            rr.Rl = R.lo;
                                             rr.id = sc.n_tri + (int32_t)v.vid;
-                                            rr.P = return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f);
+                                            rr.P = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
                                             voxel_event = true;
                                             break;
                                         }
                                     } else {
-                                        FF R2 = ff_split(t_in + 0.5 * len);
+                                        FF R2 = ff_add_f(t_in, 0.5f * len);
                                         rr.R2h = R2.hi;
                                         rr.R2l = R2.lo;
                                         break;
@@ -312,7 +306,6 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             float mdt_h, mdt_l;
             two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
             mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
-            const double mdt = (double)mdt_h + (double)mdt_l;
             // bins [wlo, whi] can be non-zero: the union of the returns' supports
             int wlo = 0, whi = nb - 1;
             if (MODE == 0) {
@@ -421,16 +414,16 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (!march_current(sc, mch, v)) { on = false; break; }
                             float dens = __ldg(&sc.density[v.vid]);
                             if (dens > 0.0f) {
-                                double t_in, t_out;
-                                march_segment64(mch, v, t_in, t_out);
-                                double len = t_out - t_in;
-                                if (len > 0.0) {
-                                    float xs = sc.G * dens * (float)len;
+                                FF t_in, t_out;
+                                march_segment_ff(mch, v, t_in, t_out);
+                                float len = ff_diff(t_out, t_in);
+                                if (len > 0.0f) {
+                                    float xs = sc.G * dens * len;
                                     float w = -T * expm1f(-xs);
                                     T *= expf(-xs);
-                                    double R = t_in + 0.5 * len;
-                                    pv = w * return_power(sn, (float)R, tan_a, sc.leaf_refl, 1.0f);
-                                    tau = delay_rel(R, mdt);
+                                    FF R = ff_add_f(t_in, 0.5f * len);
+                                    pv = w * return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
+                                    tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                                     vid = sc.n_tri + (int32_t)v.vid;
                                     has = true;
                                 }
