@@ -82,6 +82,7 @@ static DevScanner derive_scanner(const helios_scanner_desc& s) {
         double sig = s.pulse_fwhm_ns / (2.0 * std::sqrt(2.0 * std::log(2.0)));
         double gk2 = 1.4426950408889634 / (2.0 * sig * sig);
         d.gk2 = (float)gk2;
+        d.inv_s2 = (float)(1.0 / (sig * sig));
         d.cut_lo = d.cut_hi = (float)std::sqrt(30.0 / gk2);
         d.n_pre = (int32_t)std::ceil(3.0 * sig / s.bin_ns);
         d.echo_offset_ns = 0.0;

@@ -69,6 +69,7 @@ struct DevScanner {
     float bpm_hi, bpm_lo;    // bins_per_metre as a float pair
     float bin_hi, bin_lo;    // bin_ns as a float pair
     float echo_offset_f;     // echo_offset_ns in FP32
+    float inv_s2;            // Gaussian: 1 / sigma^2 [1/ns^2]
     int32_t q_default, pulse_shape, n_bins, max_echoes;
     int32_t deflector, n_az, n_el, n_pre;
 };

@@ -35,6 +35,10 @@ struct ScanParams {
     uint64_t seed;
     int32_t n_items, n_legs;
     int32_t s_cap, pc_cap, rays_cap, nb_cap;
+    int32_t w_stride;        // floats of per-warp waveform scratch in shared memory
+    int32_t pk_cap;          // pulse-shape taps 2 cb + 1 (moment path), 0: none
+    int32_t mom_cells, mom_cb;
+    long long* mom;          // per-warp moment bins (expected mode), NULL: direct sums
     int32_t* queue;
 };
 
@@ -68,6 +72,49 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
     }
 }
 
+// Expected-mode returns of one subray in summation order: the voxels along
+// the march (weight T_k (1 - e^{-sigma l}) at the segment midpoint), then the
+// triangle (weight T).  emit(R, weighted power, primitive id).
+template <bool GRID, class F>
+__device__ __forceinline__ void expected_returns(const DevScene& sc, const DevScanner& sn,
+                                                 const PulseFF& f, const SubrayConst& c,
+                                                 const RayRes& rr, uint32_t& fl, F&& emit) {
+    float T = 1.0f;
+    if (GRID && sc.has_grid) {
+        float dh[3], dl[3];
+        subray_dir_ff(f, c, dh, dl);
+        double o[3], d[3];
+        for (int a = 0; a < 3; ++a) {
+            o[a] = ff2d(f.oh[a], f.ol[a]);
+            d[a] = ff2d(dh[a], dl[a]);
+        }
+        double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+        March m;
+        if (march_init(sc, o, d, t_hi, m)) {
+            for (;;) {
+                VoxSeg v;
+                if (!march_current(sc, m, v)) break;
+                float dens = __ldg(&sc.density[v.vid]);
+                if (dens > 0.0f) {
+                    FF t_in, t_out;
+                    march_segment_ff(m, v, t_in, t_out);
+                    float len = ff_diff(t_out, t_in);
+                    if (len > 0.0f) {
+                        float xs = sc.G * dens * len;
+                        float w = -T * expm1f(-xs);
+                        T *= expf(-xs);
+                        FF R = ff_add_f(t_in, 0.5f * len);
+                        emit(R, w * return_power(sn, R.hi + R.lo, c.tan_a, sc.leaf_refl, 1.0f),
+                             sc.n_tri + (int32_t)v.vid);
+                    }
+                }
+                if (!march_step(m, v, fl)) break;
+            }
+        }
+    }
+    if (rr.id >= 0) emit(ff_norm(rr.Rh, rr.Rl), T * rr.P, rr.id);
+}
+
 template <int MODE, bool GRID, int NL>
 __global__ void __launch_bounds__(256)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
@@ -78,9 +125,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
     uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
     float* s_noise = reinterpret_cast<float*>(s_pflag + P.pc_cap);   // [pc_cap][2]
+    float* s_pk = s_noise + 2 * P.pc_cap;                              // [pk_cap]
     // the per-warp waveform rows start 16-byte aligned (float4 reads below)
     float* s_w = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(s_noise + 2 * P.pc_cap) + 15u) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(s_pk + P.pk_cap) + 15u) & ~uintptr_t(15));
     __shared__ int s_item;
     __shared__ int s_cached_leg;
     __shared__ double s_rot[6];
@@ -124,6 +172,12 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         __syncthreads();
         if (new_leg) {
             for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
+            if (MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0) {
+                for (int k = tid; k < 2 * P.mom_cb + 1; k += blockDim.x) {
+                    float x = (float)(k - P.mom_cb) * dt;
+                    s_pk[k] = exp2f(-x * x * sn.gk2);
+                }
+            }
             if (tid == 0) {
                 sincos(lg.rpy[0], &s_rot[0], &s_rot[1]);
                 sincos(lg.rpy[1], &s_rot[2], &s_rot[3]);
@@ -260,7 +314,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
 
         // ---------------- phase 2: waveform + echoes, one warp per pulse ----------------
         const int nbw = P.nb_cap;
-        float* W = s_w + (size_t)warp * nbw * (MODE == 1 ? 3 : 1);
+        float* W = s_w + (size_t)warp * P.w_stride;
+        const bool mom_path = MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0;
         float* best = W + nbw;
         int32_t* bid = reinterpret_cast<int32_t*>(W + 2 * nbw);
         for (int pl = warp; pl < pc; pl += nwarps) {
@@ -333,7 +388,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             const bool in_regs = MODE == 0 && whi - wlo < 128;
             for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
                 *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (MODE == 1) {
+                if (MODE == 1 && !mom_path) {
                     *reinterpret_cast<float4*>(best + b) = make_float4(0.f, 0.f, 0.f, 0.f);
                     *reinterpret_cast<int4*>(bid + b) = make_int4(-1, -1, -1, -1);
                 }
@@ -372,6 +427,91 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     RayRes rr = rrp[s];
                     if (rr.id < 0) continue;
                     accumulate(W, nb, sn, dt, taup[s], rr.P, lane);
+                }
+            } else if (mom_path) {
+                // Expected transmittance via Hermite moments: a return at delay
+                // tau = j bin + delta (|delta| <= bin/2) adds
+                // P p(k bin - delta) = P p(k bin) sum_n (delta/sigma)^n/n! He_n(k bin/sigma)
+                // at bin j + k; the series is cut after n = 3 (error below
+                // 4e-6 P for bin 0.25 ns, sigma 1.7 ns).  Lanes (subrays) march
+                // independently and add P delta^n/n! to per-warp bins as 64-bit
+                // fixed-point integers (order-free, hence deterministic); a tiled
+                // convolution with the Hermite kernels then forms the waveform.
+                const PulseFF& f = s_pf[pl];
+                const int ncell = P.mom_cells, cb = P.mom_cb;
+                long long* M = P.mom + ((size_t)blockIdx.x * nwarps + warp) * 4 * (size_t)ncell;
+                unsigned long long* Mu = reinterpret_cast<unsigned long long*>(M);
+                const float rm = rmin.hi;
+                const float scale = ldexpf(rm * rm / sn.pconst, 40);
+                int clo = INT_MAX, chi = -1;
+                uint32_t fl = 0;
+                for (int s0 = 0; s0 < S; s0 += 32) {
+                    const int s = s0 + lane;
+                    if (s >= S) continue;
+                    expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl,
+                                           [&](const FF& R, float Pw, int32_t id) {
+                        (void)id;
+                        float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                        float jf = rintf(tau * sn.inv_bin);
+                        if (!(jf >= (float)(-cb - 1) && jf <= (float)(nb + cb))) return;
+                        float dl = fmaf(-jf, dt, tau);
+                        float a = Pw * scale;
+                        int c = (int)jf + cb + 1;
+                        atomicAdd(Mu + c, (unsigned long long)llrintf(a));
+                        atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
+                        atomicAdd(Mu + 2 * ncell + c, (unsigned long long)llrintf(a * dl * dl * 0.5f));
+                        atomicAdd(Mu + 3 * ncell + c,
+                                  (unsigned long long)llrintf(a * dl * dl * dl * (1.0f / 6.0f)));
+                        clo = min(clo, c);
+                        chi = max(chi, c);
+                    });
+                }
+                if (fl) atomicOr(&s_pflag[pl], fl);
+                for (int o = 16; o > 0; o >>= 1) {
+                    clo = min(clo, __shfl_xor_sync(full, clo, o));
+                    chi = max(chi, __shfl_xor_sync(full, chi, o));
+                }
+                __syncwarp();
+                if (chi >= clo) {
+                    const int blo = max(0, clo - 2 * cb - 1), bhi = min(nb - 1, chi - 1);
+                    float4* tile = reinterpret_cast<float4*>(best);   // 128 + 2 cb cells
+                    const float inv_scale = 1.0f / scale, is2 = sn.inv_s2;
+                    for (int t0 = blo; t0 <= bhi; t0 += 128) {
+                        // tile entry i <-> cell t0 + 1 + i <-> bin j = t0 - cb + i
+                        for (int i = lane; i < 128 + 2 * cb; i += 32) {
+                            const int c = t0 + 1 + i;
+                            float m0 = __ll2float_rn(__ldcg(M + c)) * inv_scale;
+                            float m1 = __ll2float_rn(__ldcg(M + ncell + c)) * inv_scale;
+                            float m2 = __ll2float_rn(__ldcg(M + 2 * ncell + c)) * inv_scale;
+                            float m3 = __ll2float_rn(__ldcg(M + 3 * ncell + c)) * inv_scale;
+                            // sum_n m_n sigma^-n He_n(k bin/sigma) as a cubic in k
+                            float4 q;
+                            q.x = fmaf(-m2, is2, m0);
+                            q.y = dt * fmaf(-3.0f * m3, is2, m1) * is2;
+                            q.z = m2 * dt * dt * is2 * is2;
+                            q.w = m3 * dt * dt * dt * is2 * is2 * is2;
+                            tile[i] = q;
+                        }
+                        __syncwarp();
+                        for (int r = 0; r < 4; ++r) {
+                            const int bb = lane + 32 * r, b = t0 + bb;
+                            if (b <= bhi) {
+                                float acc = 0.0f;
+                                for (int k = -cb; k <= cb; ++k) {
+                                    const float4 q = tile[bb + cb - k];
+                                    const float kf = (float)k;
+                                    const float poly = fmaf(fmaf(fmaf(q.w, kf, q.z), kf, q.y), kf, q.x);
+                                    acc = fmaf(s_pk[k + cb], poly, acc);
+                                }
+                                W[b] = acc;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    // return the used cells to zero for the warp's next pulse
+                    for (int n = 0; n < 4; ++n)
+                        for (int c = clo + lane; c <= chi; c += 32) __stcg(M + n * ncell + c, 0ll);
+                    __syncwarp();
                 }
             } else {
                 // expected transmittance: every crossed voxel returns
@@ -476,7 +616,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 if (ismax && pos < K) {
                     int32_t obj = -1;
                     if (MODE == 1) {
-                        obj = bid[b];
+                        if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
+                        else obj = bid[b];
                     } else {
                         float bv = -1.0f;
                         float tbin = (float)b * dt;
@@ -503,9 +644,60 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
                     if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
                     if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
-                    if (P.out.echo_object) P.out.echo_object[eb + pos] = obj;
+                    if (P.out.echo_object && !mom_path) P.out.echo_object[eb + pos] = obj;
                 }
                 count += __popc(mk);
+            }
+            if (MODE == 1 && mom_path && P.out.echo_object && count > 0) {
+                // echo objects: re-march and evaluate every return at the echo
+                // bins only; the strongest contribution wins, ties to the first
+                // return in summation order (subray, then march order)
+                __syncwarp();
+                const int ne = min(count, K);
+                const int32_t* ebin = reinterpret_cast<const int32_t*>(best);
+                const PulseFF& f = s_pf[pl];
+                for (int e0 = 0; e0 < ne; e0 += 4) {
+                    float tbin[4], bv[4];
+                    int bs[4], bo[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        tbin[i] = e0 + i < ne ? (float)ebin[e0 + i] * dt : 1.0e30f;
+                        bv[i] = -1.0f;
+                        bs[i] = INT_MAX;
+                        bo[i] = -1;
+                    }
+                    for (int s0 = 0; s0 < S; s0 += 32) {
+                        const int s = s0 + lane;
+                        if (s >= S) continue;
+                        uint32_t fl2 = 0;
+                        expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
+                                               [&](const FF& R, float Pw, int32_t id) {
+                            float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                float x = tbin[i] - tau;
+                                if (x >= -sn.cut_lo && x <= sn.cut_hi) {
+                                    float v = Pw * pulse_shape(sn, x);
+                                    if (v > bv[i]) { bv[i] = v; bs[i] = s; bo[i] = id; }
+                                }
+                            }
+                        });
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        for (int o = 16; o > 0; o >>= 1) {
+                            float ov = __shfl_xor_sync(full, bv[i], o);
+                            int os = __shfl_xor_sync(full, bs[i], o);
+                            int oo = __shfl_xor_sync(full, bo[i], o);
+                            if (ov > bv[i] || (ov == bv[i] && os < bs[i])) { bv[i] = ov; bs[i] = os; bo[i] = oo; }
+                        }
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (e0 + i < ne) P.out.echo_object[eb + e0 + i] = bo[i];
+                    }
+                }
             }
             // unused echo slots
             for (int e = count + lane; e < K; e += 32) {
@@ -578,12 +770,35 @@ static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int 
                 : launch_one<1, false, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
 }
 
-static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads) {
+// floats of per-warp shared waveform scratch: W, plus (expected mode) either
+// the best-contributor arrays of the direct path or the moment tile
+static int warp_stride(int mode, int nb_cap, int cb) {
+    if (mode != 1) return nb_cap;
+    int extra = 2 * nb_cap;
+    if (cb > 0) extra = max(extra, 4 * (128 + 2 * cb));
+    return nb_cap + extra;
+}
+
+static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads,
+                         int pk_cap = 0, int cb = 0) {
     size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
-               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap;
+               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
+               sizeof(float) * pk_cap;
     b = (b + 15) & ~size_t(15);
-    b += (size_t)(threads / 32) * nb_cap * sizeof(float) * (mode == 1 ? 3 : 1);
+    b += (size_t)(threads / 32) * warp_stride(mode, nb_cap, cb) * sizeof(float);
     return b;
+}
+
+template <int MODE, bool GRID, int NL>
+static int max_grid(int threads, int blocks_per_sm, size_t smem) {
+    auto kern = scan_kernel<MODE, GRID, NL>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    int bps = blocks_per_sm > 0 ? min(blocks_per_sm, occ) : occ;
+    return sms * max(bps, 0);
 }
 
 helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
@@ -598,10 +813,39 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         nb_cap = max(nb_cap, L.scanners[lg.scanner].n_bins);
     }
     nb_cap = (nb_cap + 3) & ~3;
-    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads);
-    if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     bool any_grid = false;
     for (const DevLeg& lg : L.legs) any_grid |= L.scenes[lg.scene].has_grid != 0;
+    // expected mode with a Gaussian pulse: moment bins in stream-ordered scratch
+    int cb = 0;
+    if (L.mode == 1) {
+        for (const DevLeg& lg : L.legs) {
+            const DevScanner& sn = L.scanners[lg.scanner];
+            if (sn.pulse_shape == 0) cb = max(cb, (int)ceilf(sn.cut_hi * sn.inv_bin) + 1);
+        }
+        if (cb > 256) cb = 0;   // very long pulses: direct sums
+    }
+    const int pk_cap = cb > 0 ? 2 * cb + 1 : 0;
+    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb);
+    if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
+    long long* mom = nullptr;
+    int mom_cells = 0;
+    if (cb > 0) {
+        int grid = L.persistent ? (any_grid ? max_grid<1, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                            : max_grid<1, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                                : (any_grid ? max_grid<1, true, 1>(threads, L.blocks_per_sm, smem)
+                                            : max_grid<1, false, 1>(threads, L.blocks_per_sm, smem));
+        mom_cells = nb_cap + 2 * cb + 132;
+        size_t bytes = (size_t)grid * (threads / 32) * 4 * mom_cells * sizeof(long long);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mom), bytes, st);
+        if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(moment bins)", e);
+        e = cudaMemsetAsync(mom, 0, bytes, st);
+        if (e != cudaSuccess) { cudaFreeAsync(mom, st); return set_cuda_error("cudaMemsetAsync(moment bins)", e); }
+    }
+    struct Free {
+        long long* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } free_mom{mom, st};
+    const int w_stride = warp_stride(L.mode, nb_cap, cb);
 
     if (!L.persistent) {
         for (int l = 0; l < n_legs; ++l) {
@@ -618,6 +862,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             if (items == 0) continue;
             p.n_items = (int32_t)items;
             p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
+            p.w_stride = w_stride; p.pk_cap = pk_cap; p.mom = mom; p.mom_cells = mom_cells; p.mom_cb = cb;
             p.queue = nullptr;
             bool g = L.scenes[L.legs[l].scene].has_grid != 0;
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
@@ -645,6 +890,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         p->n_legs = nl;
         p->n_items = (int32_t)items;
         p->s_cap = s_cap; p->pc_cap = pc_cap; p->rays_cap = rays_cap; p->nb_cap = nb_cap;
+        p->w_stride = w_stride; p->pk_cap = pk_cap; p->mom = mom; p->mom_cells = mom_cells; p->mom_cb = cb;
         int32_t* q = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int32_t), st);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(queue)", e); }
@@ -744,6 +990,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         p.n_legs = nl;
         p.n_items = (int32_t)items;
         p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
+        p.w_stride = warp_stride(mode, nb_cap, 0);
         p.queue = g_static_ptr[dev] + g;
         helios_status s = dispatch<kMaxLegs>(p, mode, any_grid, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;
