@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     for (;;) {
                         VoxSeg v;
                         if (!march_current(sc, mch, v)) break;
-                        float dens = __ldg(&sc.density[v.vid]);
+                        float dens = voxel_density(sc, mch, v);
                         if (dens > 0.0f) {
                             FF t_in, t_out;
                             march_segment_ff(mch, v, t_in, t_out);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     for (;;) {
                         VoxSeg v;
                         if (!march_current(sc, mch, v)) break;
-                        float dens = __ldg(&sc.density[v.vid]);
+                        float dens = voxel_density(sc, mch, v);
                         if (dens > 0.0f) {
                             FF t_in, t_out;
                             march_segment_ff(mch, v, t_in, t_out);

@@ -345,6 +345,58 @@ cudaError_t exclusive_scan(uint32_t* data, int n, StreamBufs& B) {
 
 }  // namespace
 
+// Bit b of the mask is set when brick b (kBrick^3 voxels, x fastest) holds a
+// voxel of density > 0.  One thread per brick; each warp covers 32 consecutive
+// bricks, i.e. one 32-bit word, so the words are written without atomics.
+__global__ void k_occupancy(const float* __restrict__ dens, int dx, int dy, int dz, int bx, int by,
+                            int64_t n_bricks, uint32_t* __restrict__ occ) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (b < n_bricks) {
+        const int x0 = (int)(b % bx) * kBrick;
+        const int64_t r = b / bx;
+        const int y0 = (int)(r % by) * kBrick, z0 = (int)(r / by) * kBrick;
+        const int x1 = min(x0 + kBrick, dx), y1 = min(y0 + kBrick, dy), z1 = min(z0 + kBrick, dz);
+        for (int z = z0; z < z1; ++z)
+            for (int y = y0; y < y1; ++y) {
+                const float* row = dens + ((int64_t)z * dy + y) * dx;
+                for (int x = x0; x < x1; ++x) any |= __ldg(row + x) > 0.0f;
+            }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if ((threadIdx.x & 31) == 0 && b < n_bricks) occ[b >> 5] = m;
+}
+
+OccupancyMasks::~OccupancyMasks() {
+    for (void* p : bufs) cudaFreeAsync(p, st);
+}
+
+helios_status build_occupancy(std::vector<DevScene>& scenes, cudaStream_t st, OccupancyMasks& keep) {
+    keep.st = st;
+    for (DevScene& d : scenes) {
+        d.occ = nullptr;
+        if (!d.has_grid || d.density == nullptr) continue;
+        int64_t nb = 1;
+        for (int a = 0; a < 3; ++a) {
+            d.bdims[a] = (d.dims[a] + kBrick - 1) >> kBrickLog2;
+            nb *= d.bdims[a];
+        }
+        if (nb <= 0 || nb >= ((int64_t)1 << 31)) continue;   // no mask: plain density reads
+        const int64_t words = (nb + 31) >> 5;
+        uint32_t* occ = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&occ), words * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(occupancy)", e);
+        keep.bufs.push_back(occ);
+        const int threads = 256;
+        k_occupancy<<<(unsigned)((nb + threads - 1) / threads), threads, 0, st>>>(
+            d.density, d.dims[0], d.dims[1], d.dims[2], d.bdims[0], d.bdims[1], nb, occ);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error("occupancy kernel launch", e);
+        d.occ = occ;
+    }
+    return HELIOS_OK;
+}
+
 helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st) {
     const int n = (int)s->n_tri;
     MeshTable mt;

@@ -394,6 +394,9 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     L.threads = threads;
     L.blocks_per_sm = opts->blocks_per_sm;
     if (P.total_pulses == 0) return HELIOS_OK;
+    OccupancyMasks masks;
+    st = build_occupancy(L.scenes, (cudaStream_t)cuda_stream, masks);
+    if (st != HELIOS_OK) return st;
     return launch_scan(L, (cudaStream_t)cuda_stream);
 }
 
@@ -432,6 +435,9 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     L.subray_hit = subray_hit;
     L.threads = threads;
     if (P.total_pulses == 0) return HELIOS_OK;
+    OccupancyMasks masks;
+    st = build_occupancy(L.scenes, (cudaStream_t)cuda_stream, masks);
+    if (st != HELIOS_OK) return st;
     return launch_adjoint(L, (cudaStream_t)cuda_stream);
 }
 

@@ -35,6 +35,10 @@ constexpr float kHalfCns = (float)(0.5e-9 * kC);
 // child0 is the lower child along `axis`, so the near child of a ray with
 // d[axis] >= 0 is child0.  Triangle t occupies tris[3t .. 3t+2]:
 //   (v0, global id), (v1, mesh), (v2, face).
+constexpr int kReturnListCap = 256;   // expected-mode returns listed per lane and pulse
+constexpr int kBrickLog2 = 2;   // 4^3-voxel bricks for empty-space skipping
+constexpr int kBrick = 1 << kBrickLog2;
+
 struct DevScene {
     const float4* nodes;
     const float4* tris;
@@ -46,7 +50,8 @@ struct DevScene {
     int32_t dims[3];
     float G, leaf_refl, cell;
     float g0[3];
-    int32_t pad;
+    int32_t bdims[3];           // bricks of kBrick^3 voxels per axis
+    const uint32_t* occ;        // brick occupancy bits (x fastest), NULL: not used
 };
 
 // Instrument constants derived once per call (host side, FP64).
@@ -689,6 +694,18 @@ __device__ __forceinline__ bool march_current(const DevScene& S, const March& m,
     v.exit_axis = a;
     v.t_out32 = tn;
     return true;
+}
+
+// Density of the current voxel.  A voxel inside a brick whose occupancy bit is
+// clear has density <= 0 (or NaN) by construction of the mask, so the grid is
+// not read there; every caller treats such a voxel as empty.
+__device__ __forceinline__ float voxel_density(const DevScene& S, const March& m, const VoxSeg& v) {
+    if (S.occ != nullptr) {
+        int b = ((m.iz >> kBrickLog2) * S.bdims[1] + (m.iy >> kBrickLog2)) * S.bdims[0] +
+                (m.ix >> kBrickLog2);
+        if (!((__ldg(&S.occ[b >> 5]) >> (b & 31)) & 1u)) return 0.0f;
+    }
+    return __ldg(&S.density[v.vid]);
 }
 
 // float-float segment of the current voxel, clipped to [t_enter, t_end]

@@ -67,4 +67,14 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st);
 
 helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st);
 
+// Brick occupancy masks of the scenes' voxel grids, formed in stream order from
+// the densities as they are when the stream reaches them; sets DevScene::occ
+// and frees the masks (stream-ordered) when destroyed.
+struct OccupancyMasks {
+    std::vector<void*> bufs;
+    cudaStream_t st = nullptr;
+    ~OccupancyMasks();
+};
+helios_status build_occupancy(std::vector<DevScene>& scenes, cudaStream_t st, OccupancyMasks& keep);
+
 }  // namespace hg

@@ -39,6 +39,8 @@ struct ScanParams {
     int32_t pk_cap;          // pulse-shape taps 2 cb + 1 (moment path), 0: none
     int32_t mom_cells, mom_cb;
     long long* mom;          // per-warp moment bins (expected mode), NULL: direct sums
+    float* rlist;            // per-warp return lists (expected mode): tau, power, id
+    int32_t rl_cap;          // entries per lane
     int32_t* queue;
 };
 
@@ -94,7 +96,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
             for (;;) {
                 VoxSeg v;
                 if (!march_current(sc, m, v)) break;
-                float dens = __ldg(&sc.density[v.vid]);
+                float dens = voxel_density(sc, m, v);
                 if (dens > 0.0f) {
                     FF t_in, t_out;
                     march_segment_ff(m, v, t_in, t_out);
@@ -260,7 +262,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         for (;;) {
                             VoxSeg v;
                             if (!march_current(sc, m, v)) break;
-                            float dens = __ldg(&sc.density[v.vid]);
+                            float dens = voxel_density(sc, m, v);
                             if (dens > 0.0f) {
                                 FF t_in, t_out;
                                 march_segment_ff(m, v, t_in, t_out);
@@ -386,6 +388,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             const int zlo = wlo & ~3, zhi = whi < wlo ? zlo : min(nbw, (whi | 3) + 1);
             // a compact window (<= 128 bins) is summed in registers, lanes owning bins
             const bool in_regs = MODE == 0 && whi - wlo < 128;
+            int n_rl = 0;            // this lane's entries in the warp's return list
             for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
                 *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (MODE == 1 && !mom_path) {
@@ -445,18 +448,33 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 const float scale = ldexpf(rm * rm / sn.pconst, 40);
                 int clo = INT_MAX, chi = -1;
                 uint32_t fl = 0;
+                // return list [3][rl_cap][32]: what the echo-object pass reads
+                // instead of marching again (a chunk of 32 subrays ends with id -1)
+                const size_t RLs = (size_t)P.rl_cap * 32;
+                float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
                 for (int s0 = 0; s0 < S; s0 += 32) {
                     const int s = s0 + lane;
                     if (s >= S) continue;
+                    if (s0 > 0) {
+                        if (n_rl < P.rl_cap)
+                            __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + (size_t)n_rl * 32 + lane, -1);
+                        ++n_rl;
+                    }
                     expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl,
                                            [&](const FF& R, float Pw, int32_t id) {
-                        (void)id;
                         float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                         float jf = rintf(tau * sn.inv_bin);
                         if (!(jf >= (float)(-cb - 1) && jf <= (float)(nb + cb))) return;
                         float dl = fmaf(-jf, dt, tau);
                         float a = Pw * scale;
                         int c = (int)jf + cb + 1;
+                        if (n_rl < P.rl_cap) {
+                            const size_t e = (size_t)n_rl * 32 + lane;
+                            __stcg(RL + e, tau);
+                            __stcg(RL + RLs + e, Pw);
+                            __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + e, id);
+                        }
+                        ++n_rl;
                         atomicAdd(Mu + c, (unsigned long long)llrintf(a));
                         atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
                         atomicAdd(Mu + 2 * ncell + c, (unsigned long long)llrintf(a * dl * dl * 0.5f));
@@ -552,7 +570,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         while (on) {
                             VoxSeg v;
                             if (!march_current(sc, mch, v)) { on = false; break; }
-                            float dens = __ldg(&sc.density[v.vid]);
+                            float dens = voxel_density(sc, mch, v);
                             if (dens > 0.0f) {
                                 FF t_in, t_out;
                                 march_segment_ff(mch, v, t_in, t_out);
@@ -649,6 +667,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 count += __popc(mk);
             }
             if (MODE == 1 && mom_path && P.out.echo_object && count > 0) {
+                const bool rl_ok = __all_sync(full, n_rl <= P.rl_cap);
                 // echo objects: re-march and evaluate every return at the echo
                 // bins only; the strongest contribution wins, ties to the first
                 // return in summation order (subray, then march order)
@@ -666,22 +685,40 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         bs[i] = INT_MAX;
                         bo[i] = -1;
                     }
-                    for (int s0 = 0; s0 < S; s0 += 32) {
-                        const int s = s0 + lane;
-                        if (s >= S) continue;
-                        uint32_t fl2 = 0;
-                        expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
-                                               [&](const FF& R, float Pw, int32_t id) {
-                            float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                    auto consider = [&](float tau, float Pw, int32_t id, int s) {
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                float x = tbin[i] - tau;
-                                if (x >= -sn.cut_lo && x <= sn.cut_hi) {
-                                    float v = Pw * pulse_shape(sn, x);
-                                    if (v > bv[i]) { bv[i] = v; bs[i] = s; bo[i] = id; }
-                                }
+                        for (int i = 0; i < 4; ++i) {
+                            float x = tbin[i] - tau;
+                            if (x >= -sn.cut_lo && x <= sn.cut_hi) {
+                                float v = Pw * pulse_shape(sn, x);
+                                if (v > bv[i]) { bv[i] = v; bs[i] = s; bo[i] = id; }
                             }
-                        });
+                        }
+                    };
+                    if (rl_ok) {
+                        const size_t RLs = (size_t)P.rl_cap * 32;
+                        const float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
+                        int s = lane;
+                        for (int e = 0; e < n_rl; ++e) {
+                            const size_t o = (size_t)e * 32 + lane;
+                            const int32_t id = __ldcg(reinterpret_cast<const int32_t*>(RL + 2 * RLs) + o);
+                            if (id < 0) { s += 32; continue; }
+                            consider(__ldcg(RL + o), __ldcg(RL + RLs + o), id, s);
+                        }
+                    } else {
+                        for (int s0 = 0; s0 < S; s0 += 32) {
+                            const int s = s0 + lane;
+                            if (s >= S) continue;
+                            uint32_t fl2 = 0;
+                            expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
+                                                   [&](const FF& R, float Pw, int32_t id) {
+                                const float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                                if (!(rintf(tau * sn.inv_bin) >= (float)(-P.mom_cb - 1) &&
+                                      rintf(tau * sn.inv_bin) <= (float)(nb + P.mom_cb)))
+                                    return;
+                                consider(tau, Pw, id, s);
+                            });
+                        }
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -772,20 +809,20 @@ static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int 
 
 // floats of per-warp shared waveform scratch: W, plus (expected mode) either
 // the best-contributor arrays of the direct path or the moment tile
-static int warp_stride(int mode, int nb_cap, int cb) {
+static int warp_stride(int mode, int nb_cap, int cb, bool direct) {
     if (mode != 1) return nb_cap;
-    int extra = 2 * nb_cap;
+    int extra = direct ? 2 * nb_cap : 0;
     if (cb > 0) extra = max(extra, 4 * (128 + 2 * cb));
     return nb_cap + extra;
 }
 
 static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads,
-                         int pk_cap = 0, int cb = 0) {
+                         int pk_cap = 0, int cb = 0, bool direct = true) {
     size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
                sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
                sizeof(float) * pk_cap;
     b = (b + 15) & ~size_t(15);
-    b += (size_t)(threads / 32) * warp_stride(mode, nb_cap, cb) * sizeof(float);
+    b += (size_t)(threads / 32) * warp_stride(mode, nb_cap, cb, direct) * sizeof(float);
     return b;
 }
 
@@ -817,35 +854,48 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
     for (const DevLeg& lg : L.legs) any_grid |= L.scenes[lg.scene].has_grid != 0;
     // expected mode with a Gaussian pulse: moment bins in stream-ordered scratch
     int cb = 0;
+    bool direct = L.mode == 1;   // some leg sums its waveform directly
     if (L.mode == 1) {
+        direct = false;
         for (const DevLeg& lg : L.legs) {
             const DevScanner& sn = L.scanners[lg.scanner];
             if (sn.pulse_shape == 0) cb = max(cb, (int)ceilf(sn.cut_hi * sn.inv_bin) + 1);
+            else direct = true;
         }
-        if (cb > 256) cb = 0;   // very long pulses: direct sums
+        if (cb > 256) { cb = 0; direct = true; }   // very long pulses: direct sums
     }
     const int pk_cap = cb > 0 ? 2 * cb + 1 : 0;
-    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb);
+    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     long long* mom = nullptr;
-    int mom_cells = 0;
+    float* rlist = nullptr;
+    int mom_cells = 0, rl_cap = 0;
+    struct Free {
+        void* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } free_mom{nullptr, st}, free_rl{nullptr, st};
     if (cb > 0) {
         int grid = L.persistent ? (any_grid ? max_grid<1, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
                                             : max_grid<1, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
                                 : (any_grid ? max_grid<1, true, 1>(threads, L.blocks_per_sm, smem)
                                             : max_grid<1, false, 1>(threads, L.blocks_per_sm, smem));
+        const size_t slots = (size_t)grid * (threads / 32);
         mom_cells = nb_cap + 2 * cb + 132;
-        size_t bytes = (size_t)grid * (threads / 32) * 4 * mom_cells * sizeof(long long);
+        size_t bytes = slots * 4 * mom_cells * sizeof(long long);
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mom), bytes, st);
         if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(moment bins)", e);
+        free_mom.p = mom;
         e = cudaMemsetAsync(mom, 0, bytes, st);
-        if (e != cudaSuccess) { cudaFreeAsync(mom, st); return set_cuda_error("cudaMemsetAsync(moment bins)", e); }
+        if (e != cudaSuccess) return set_cuda_error("cudaMemsetAsync(moment bins)", e);
+        if (L.out.echo_object) {
+            // longer lists (more than kReturnListCap returns of one lane) march again
+            rl_cap = kReturnListCap;
+            e = cudaMallocAsync(reinterpret_cast<void**>(&rlist), slots * 3 * rl_cap * 32 * sizeof(float), st);
+            if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(return lists)", e);
+            free_rl.p = rlist;
+        }
     }
-    struct Free {
-        long long* p; cudaStream_t s;
-        ~Free() { if (p) cudaFreeAsync(p, s); }
-    } free_mom{mom, st};
-    const int w_stride = warp_stride(L.mode, nb_cap, cb);
+    const int w_stride = warp_stride(L.mode, nb_cap, cb, direct);
 
     if (!L.persistent) {
         for (int l = 0; l < n_legs; ++l) {
@@ -863,6 +913,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             p.n_items = (int32_t)items;
             p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
             p.w_stride = w_stride; p.pk_cap = pk_cap; p.mom = mom; p.mom_cells = mom_cells; p.mom_cb = cb;
+            p.rlist = rlist; p.rl_cap = rl_cap;
             p.queue = nullptr;
             bool g = L.scenes[L.legs[l].scene].has_grid != 0;
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
@@ -891,6 +942,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         p->n_items = (int32_t)items;
         p->s_cap = s_cap; p->pc_cap = pc_cap; p->rays_cap = rays_cap; p->nb_cap = nb_cap;
         p->w_stride = w_stride; p->pk_cap = pk_cap; p->mom = mom; p->mom_cells = mom_cells; p->mom_cb = cb;
+        p->rlist = rlist; p->rl_cap = rl_cap;
         int32_t* q = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int32_t), st);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(queue)", e); }
@@ -990,7 +1042,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         p.n_legs = nl;
         p.n_items = (int32_t)items;
         p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
-        p.w_stride = warp_stride(mode, nb_cap, 0);
+        p.w_stride = warp_stride(mode, nb_cap, 0, true);
         p.queue = g_static_ptr[dev] + g;
         helios_status s = dispatch<kMaxLegs>(p, mode, any_grid, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;

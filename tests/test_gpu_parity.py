@@ -67,6 +67,41 @@ def test_uls_voxels_small(hg, mode):
     assert stats["echoes"] > 1000
 
 
+def test_expected_mode_gaussian_and_carlsson_legs_in_one_launch(hg):
+    """Expected mode: a Gaussian leg (Hermite-moment waveform) and an Eq. beam_time
+    leg (direct sums) share one persistent launch and its shared-memory layout."""
+    import dataclasses
+    w = scenes.uls_voxels(seed=6, n=48, n_pulses=1500, n_bins=512, agl=12.0, speed=1.0,
+                          prf=2000.0)
+    sc2 = dataclasses.replace(w.scanners[0], pulse_shape=scenes.PULSE_CARLSSON, pulse_length_ns=3.5)
+    leg2 = dataclasses.replace(w.legs[0], scanner_index=1, leg_id=7, n_pulses=1200)
+    w = scenes.Workload("mixed", w.scenes, [w.scanners[0], sc2], [w.legs[0], leg2])
+    _, _, res = run_both(hg, w, mode=1, seed=11, persistent=True)
+    for g, ref in res:
+        stats = compare(g, ref, expected_mode=True)
+        assert stats["echoes"] > 500
+
+
+def test_expected_mode_long_voxel_column(hg):
+    """Expected mode down a 400-voxel column of non-zero density: each subray has
+    more returns than a lane's return list holds, so the echo objects come from
+    the second march."""
+    dens = np.full((400, 8, 8), 0.05, np.float32)
+    grid = scenes.VoxelGrid(origin=(-0.2, -0.2, 0.0), cell=0.05, dims=(8, 8, 400), density=dens,
+                            G=0.5, leaf_reflectance=0.5)
+    ground = scenes.Mesh(np.array([[-5, -5, -0.5], [5, -5, -0.5], [0, 6, -0.5]], np.float32),
+                         np.array([[0, 1, 2]], np.int32), np.array([0.4], np.float32))
+    scene = scenes.Scene(meshes=[ground], grids=[grid])
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=8, grid_n_el=8,
+                        el_min_rad=-1.5707, el_max_rad=-1.5697, n_bins=1024, max_echoes=8)
+    leg = scenes.Leg(scene_index=0, n_pulses=64, leg_id=4, start=(0.01, 0.02, 25.0))
+    w = scenes.Workload("column", [scene], [sc], [leg])
+    _, _, res = run_both(hg, w, mode=1, seed=3)
+    g, ref = res[0]
+    compare(g, ref, expected_mode=True)
+    assert (ref["echo_count"] > 0).all()
+
+
 @pytest.mark.parametrize("q", [0, 1, 3])
 def test_subray_qualities_and_carlsson_pulse(hg, q):
     """S = 1, 7, 37 (more subrays than warp lanes) with the Eq. beam_time pulse."""
