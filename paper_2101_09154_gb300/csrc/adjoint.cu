@@ -7,8 +7,11 @@
 //   dL/dsigma_j = A_j T_j l_j e^{-sigma_j l_j} - l_j (sum_{k>j} A_k w_k + A_tri rho T_{K+1})
 //   dL/ddensity_j = G dL/dsigma_j,    dL/drho = A_tri T_{K+1}.
 // The hit set and the window start are held fixed.  One warp per pulse,
-// lanes = subrays.  Pass A accumulates the total sum_k A_k w_k (FP64), pass B
-// re-marches and emits each gradient with the suffix = total - prefix.
+// lanes = subrays.  For a Gaussian pulse A comes from per-pulse Hermite
+// correlation tables (see corr_tab).  Pass A marches once and lists each
+// voxel's terms; pass B walks the list back to front, so the suffix sum is
+// built term by term.  A lane whose list overflows marches a second time and
+// takes the suffix as total - prefix in FP64.
 #include "hg_device.cuh"
 #include "hg_host.h"
 
@@ -24,6 +27,10 @@ struct AdjParams {
     const int32_t* window;
     const int32_t* subray_hit;
     int32_t n_items, s_cap, pc_cap, nb_cap;
+    int32_t cb;              // Gaussian: halo bins of the correlation tables, 0: direct sums
+    int32_t ncell;           // table cells per warp (bins -cb-1 .. nb+cb)
+    float* list;             // per-warp voxel return lists [4][rl_cap][32], NULL: none
+    int32_t rl_cap;
 };
 
 __device__ __forceinline__ float corr(const float* g, int nb, const DevScanner& sn, float dt,
@@ -35,28 +42,64 @@ __device__ __forceinline__ float corr(const float* g, int nb, const DevScanner& 
     return acc;
 }
 
+// A(tau) = sum_b g_b p(b bin - tau).  With tau = j bin + delta, j even and
+// |delta| <= bin, and the Gaussian's Taylor series in Hermite form,
+//   A = sum_{n<=3} delta^n/n! C_n[j],  C_n[j] = sigma^-n sum_k g_{j+k} p(k bin) He_n(k bin/sigma),
+// so one table per pulse (every second bin) replaces a (2 cb + 1)-bin dot
+// product per return.  The first dropped term is below 6e-5 of the peak
+// for bin/sigma <= 0.15.
+__device__ __forceinline__ float corr_tab(const float4* C, int c0, int ncell, float dt2,
+                                          float inv_bin2, float tau) {
+    const float jf = rintf(tau * inv_bin2);          // j / 2
+    const int c = (int)fmaxf(fminf(jf, 1.0e9f), -1.0e9f) + c0;
+    if (c < 0 || c >= ncell) return 0.0f;
+    const float4 t = C[c];
+    const float d = fmaf(-jf, dt2, tau);
+    return fmaf(d, fmaf(d * 0.5f, fmaf(d * (1.0f / 3.0f), t.w, t.z), t.y), t.x);
+}
+
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PulseFF* s_pf = reinterpret_cast<PulseFF*>(smem);
+    const int tab = P.cb > 0;
+    float4* s_h = reinterpret_cast<float4*>(smem);                      // [2 cb + 1] (tab)
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_h + (tab ? 2 * P.cb + 1 : 0));
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
-    float* s_g = reinterpret_cast<float*>(s_sc + P.s_cap);
+    float* s_w = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(s_sc + P.s_cap) + 15u) & ~uintptr_t(15));
     __shared__ double s_rot[6];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const DevLeg& lg = P.leg;
     const DevScanner& sn = P.scanners[lg.scanner];
     const DevScene& sc = P.scenes[lg.scene];
-    const int S = lg.S, nb = sn.n_bins;
+    const int S = lg.S, nb = sn.n_bins, cb = P.cb;
+    const int c0 = (cb + 3) >> 1;     // table cell of bin 0
     const float dt = (float)sn.bin_ns;
     float* const* drefl = P.d_refl[lg.scene];
     float* ddens = P.d_dens[lg.scene];
     for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
+    if (tab) {
+        // h_k = p(k bin) (1, u/sigma, (u^2-1)/sigma^2, (u^3-3u)/sigma^3), u = k bin/sigma
+        const float is = sqrtf(sn.inv_s2);
+        for (int k = tid; k < 2 * cb + 1; k += blockDim.x) {
+            const float x = (float)(k - cb) * dt, u = x * is;
+            const float p = exp2f(-x * x * sn.gk2);
+            s_h[k] = make_float4(p, p * u * is, p * (u * u - 1.0f) * is * is,
+                                 p * (u * u * u - 3.0f * u) * is * is * is);
+        }
+    }
     if (tid == 0) {
         sincos(lg.rpy[0], &s_rot[0], &s_rot[1]);
         sincos(lg.rpy[1], &s_rot[2], &s_rot[3]);
         sincos(lg.rpy[2], &s_rot[4], &s_rot[5]);
     }
     __syncthreads();
-    float* g = s_g + (size_t)warp * P.nb_cap;
+    // per warp: the correlation table and a g tile (tab), else the g row
+    const int wstride = tab ? 4 * P.ncell + 2 * (128 + cb + 1) : P.nb_cap;
+    float* wbuf = s_w + (size_t)warp * ((wstride + 3) & ~3);
+    float4* C = reinterpret_cast<float4*>(wbuf);
+    float* g = tab ? wbuf + 4 * P.ncell : wbuf;
+    const size_t RLs = (size_t)P.rl_cap * 32;
+    float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 4 * RLs : nullptr;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t p0 = (int64_t)item * lg.pulses_per_item;
         const int pc = (int)min((int64_t)lg.pulses_per_item, lg.n_pulses - p0);
@@ -75,8 +118,41 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
             two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
             mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
             const float* grow = P.g + lg.wave_off + k * nb;
-            for (int b = lane; b < nb; b += 32) g[b] = __ldcs(grow + b);
-            __syncwarp();
+            if (tab) {
+                // table cell c <-> bin j = 2 (c - c0) needs g over [j - cb, j + cb];
+                // the tile keeps g's even and odd bins apart (no bank conflicts)
+                float* ge = g;
+                float* go = g + 128 + cb + 1;
+                for (int t0 = 0; t0 < P.ncell; t0 += 128) {
+                    const int b0 = 2 * (t0 - c0) - cb;
+                    for (int i = lane; i < 2 * (128 + cb + 1); i += 32) {
+                        const int b = b0 + i;
+                        const float v = (b >= 0 && b < nb) ? __ldcs(grow + b) : 0.0f;
+                        if (i & 1) go[i >> 1] = v; else ge[i >> 1] = v;
+                    }
+                    __syncwarp();
+                    for (int i = lane; i < 128 && t0 + i < P.ncell; i += 32) {
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int kk = 0; kk <= 2 * cb; ++kk) {
+                            const float gv = (kk & 1) ? go[i + (kk >> 1)] : ge[i + (kk >> 1)];
+                            const float4 h = s_h[kk];
+                            a.x = fmaf(gv, h.x, a.x);
+                            a.y = fmaf(gv, h.y, a.y);
+                            a.z = fmaf(gv, h.z, a.z);
+                            a.w = fmaf(gv, h.w, a.w);
+                        }
+                        C[t0 + i] = a;
+                    }
+                    __syncwarp();
+                }
+            } else {
+                for (int b = lane; b < nb; b += 32) g[b] = __ldcs(grow + b);
+                __syncwarp();
+            }
+            auto amp = [&](float tau) {
+                return tab ? corr_tab(C, c0, P.ncell, 2.0f * dt, 0.5f * sn.inv_bin, tau)
+                           : corr(g, nb, sn, dt, tau);
+            };
             const PulseFF& f = s_pf[pl];
             for (int s0 = 0; s0 < S; s0 += 32) {
                 const int s = s0 + lane;
@@ -122,10 +198,13 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     if (!(t_tri > 0.0)) { t_tri = CUDART_INF; hit = -1; }
                 }
                 const bool grid = sc.has_grid != 0;
-                // ---- pass A: total of A_k w_k and the triangle term ----
+                // ---- pass A: march once; total of A_k w_k, and each voxel's
+                // terms in the lane's list [vid, G A T l e^{-sigma l}, G l, A w] ----
                 double total = 0.0;
                 float T = 1.0f;
                 uint32_t fl = 0;
+                int n = 0;
+                const bool listing = RL != nullptr && ddens != nullptr;
                 March mch;
                 if (grid && march_init(sc, o, d, t_tri, mch)) {
                     for (;;) {
@@ -138,12 +217,21 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                             float len = ff_diff(t_out, t_in);
                             if (len > 0.0f) {
                                 float xs = sc.G * dens * len;
+                                float a = expf(-xs);
                                 float w = -T * expm1f(-xs);
                                 FF R = ff_add_f(t_in, 0.5f * len);
                                 float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
+                                          amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                 total += (double)A * (double)w;
-                                T *= expf(-xs);
+                                if (listing && n < P.rl_cap) {
+                                    const size_t e = (size_t)n * 32 + lane;
+                                    __stcg(reinterpret_cast<int32_t*>(RL) + e, (int32_t)v.vid);
+                                    __stcg(RL + RLs + e, sc.G * A * T * len * a);
+                                    __stcg(RL + 2 * RLs + e, sc.G * len);
+                                    __stcg(RL + 3 * RLs + e, A * w);
+                                }
+                                ++n;
+                                T *= a;
                             }
                         }
                         if (!march_step(mch, v, fl)) break;
@@ -152,12 +240,28 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 float A_tri = 0.0f;
                 if (hit >= 0) {
                     A_tri = return_power(sn, t32 + dt32, tan_a, 1.0f, cosi) *
-                            corr(g, nb, sn, dt, ff_mul_sub(ff_norm(t32, dt32), kDelayHi, kDelayLo, mdt_h, mdt_l));
+                            amp(ff_mul_sub(ff_norm(t32, dt32), kDelayHi, kDelayLo, mdt_h, mdt_l));
                     total += (double)A_tri * (double)rho * (double)T;
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
                 }
-                // ---- pass B: per-voxel gradients ----
-                if (grid && ddens && march_init(sc, o, d, t_tri, mch)) {
+                if (!grid || !ddens || n == 0) continue;
+                if (listing && n <= P.rl_cap) {
+                    // ---- pass B from the list, back to front: the suffix
+                    // sum_{k>j} A_k w_k + A_tri rho T_{K+1} grows term by term ----
+                    float suffix = A_tri * rho * T;
+                    for (int e = n - 1; e >= 0; --e) {
+                        const size_t o2 = (size_t)e * 32 + lane;
+                        const int32_t vid = __ldcg(reinterpret_cast<const int32_t*>(RL) + o2);
+                        const float t1 = __ldcg(RL + RLs + o2);
+                        const float gl = __ldcg(RL + 2 * RLs + o2);
+                        const float aw = __ldcg(RL + 3 * RLs + o2);
+                        atomicAdd(&ddens[vid], fmaf(-gl, suffix, t1));
+                        suffix += aw;
+                    }
+                    continue;
+                }
+                // ---- pass B by a second march (list too long): suffix = total - prefix ----
+                if (march_init(sc, o, d, t_tri, mch)) {
                     double prefix = 0.0;
                     float Tb = 1.0f;
                     for (;;) {
@@ -174,7 +278,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float w = -Tb * expm1f(-xs);
                                 FF R = ff_add_f(t_in, 0.5f * len);
                                 float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
-                                          corr(g, nb, sn, dt, ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
+                                          amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;
                                 double dsig = (double)A * Tb * len * a - len * suffix;
@@ -197,6 +301,9 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (size_t l = 0; l < L.legs.size(); ++l) {
+        const DevLeg& lg = L.legs[l];
+        int64_t items = (lg.n_pulses + lg.pulses_per_item - 1) / lg.pulses_per_item;
+        if (items == 0) continue;
         AdjParams* p = new AdjParams();
         memset(p, 0, sizeof(*p));
         for (size_t i = 0; i < L.scenes.size(); ++i) {
@@ -205,19 +312,28 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
             p->d_dens[i] = L.d_density[i];
         }
         for (size_t i = 0; i < L.scanners.size(); ++i) p->scanners[i] = L.scanners[i];
-        p->leg = L.legs[l];
+        p->leg = lg;
         p->g = L.g;
         p->window = L.window;
         p->subray_hit = L.subray_hit;
-        const DevLeg& lg = L.legs[l];
-        int64_t items = (lg.n_pulses + lg.pulses_per_item - 1) / lg.pulses_per_item;
-        if (items == 0) { delete p; continue; }
         p->n_items = (int32_t)items;
         p->s_cap = lg.S;
         p->pc_cap = lg.pulses_per_item;
-        p->nb_cap = (L.scanners[lg.scanner].n_bins + 3) & ~3;
-        size_t smem = sizeof(PulseFF) * p->pc_cap + sizeof(SubrayConst) * p->s_cap +
-                      sizeof(float) * (size_t)(L.threads / 32) * p->nb_cap;
+        const DevScanner& sn = L.scanners[lg.scanner];
+        p->nb_cap = (sn.n_bins + 3) & ~3;
+        int cb = sn.pulse_shape == 0 ? (int)ceilf(sn.cut_hi * sn.inv_bin) + 1 : 0;
+        if (cb > 256) cb = 0;
+        p->cb = cb;
+        // even bins -cb-2 .. nb+cb+1 (cells 0 .. ncell-1, bin 0 at cell (cb+3)/2)
+        p->ncell = cb > 0 ? (cb + 3) / 2 + (sn.n_bins + cb + 2) / 2 + 1 : 0;
+        const int wstride = cb > 0 ? 4 * p->ncell + 2 * (128 + cb + 1) : p->nb_cap;
+        size_t smem = (cb > 0 ? sizeof(float4) * (2 * cb + 1) : 0) + sizeof(PulseFF) * p->pc_cap +
+                      sizeof(SubrayConst) * p->s_cap;
+        smem = ((smem + 15) & ~size_t(15)) + sizeof(float) * (size_t)(L.threads / 32) * ((wstride + 3) & ~3);
+        if (smem > 227 * 1024) {
+            delete p;
+            return set_error(HELIOS_ERR_UNSUPPORTED, "adjoint work item needs %zu bytes of shared memory", smem);
+        }
         cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaFuncSetAttribute(adjoint)", e); }
         int occ = 0;
@@ -225,8 +341,20 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         if (occ < 1) { delete p; return set_error(HELIOS_ERR_UNSUPPORTED, "adjoint kernel does not fit"); }
         int64_t cap = (int64_t)sms * occ;
         int grid = (int)(items < cap ? items : cap);
+        // voxel return lists (ids must fit int32); longer paths march twice
+        float* list = nullptr;
+        const DevScene& sc = L.scenes[lg.scene];
+        const int64_t nvox = sc.has_grid ? (int64_t)sc.dims[0] * sc.dims[1] * sc.dims[2] : 0;
+        if (nvox > 0 && nvox < INT32_MAX && L.d_density[lg.scene]) {
+            p->rl_cap = kReturnListCap;
+            e = cudaMallocAsync(reinterpret_cast<void**>(&list),
+                                (size_t)grid * (L.threads / 32) * 4 * p->rl_cap * 32 * sizeof(float), st);
+            if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(adjoint lists)", e); }
+            p->list = list;
+        }
         adjoint_kernel<<<grid, L.threads, smem, st>>>(*p);
         e = cudaGetLastError();
+        if (list) cudaFreeAsync(list, st);
         delete p;
         if (e != cudaSuccess) return set_cuda_error("adjoint kernel launch", e);
     }
