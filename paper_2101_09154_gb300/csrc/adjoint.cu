@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     const size_t RLs = (size_t)P.rl_cap * 32;
     float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 4 * RLs : nullptr;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
-        const int64_t p0 = (int64_t)item * lg.pulses_per_item;
-        const int pc = (int)min((int64_t)lg.pulses_per_item, lg.n_pulses - p0);
+        const int64_t p0 = (int64_t)item * lg.pulses_per_sub;
+        const int pc = (int)min((int64_t)lg.pulses_per_sub, lg.n_pulses - p0);
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
             pulse_frame(sn, lg, s_rot, p0 + t, f);
@@ -302,7 +302,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (size_t l = 0; l < L.legs.size(); ++l) {
         const DevLeg& lg = L.legs[l];
-        int64_t items = (lg.n_pulses + lg.pulses_per_item - 1) / lg.pulses_per_item;
+        int64_t items = (lg.n_pulses + lg.pulses_per_sub - 1) / lg.pulses_per_sub;
         if (items == 0) continue;
         AdjParams* p = new AdjParams();
         memset(p, 0, sizeof(*p));
@@ -318,7 +318,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         p->subray_hit = L.subray_hit;
         p->n_items = (int32_t)items;
         p->s_cap = lg.S;
-        p->pc_cap = lg.pulses_per_item;
+        p->pc_cap = lg.pulses_per_sub;
         const DevScanner& sn = L.scanners[lg.scanner];
         p->nb_cap = (sn.n_bins + 3) & ~3;
         int cb = sn.pulse_shape == 0 ? (int)ceilf(sn.cut_hi * sn.inv_bin) + 1 : 0;

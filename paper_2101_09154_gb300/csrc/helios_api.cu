@@ -194,7 +194,10 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         d.q = q;
         d.S = subray_count(q);
         int ppi = rays_per_item / d.S;
-        d.pulses_per_item = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        // an item holds whole batches, up to 256 pulses (the cone walk
+        // groups 32 pulses per warp)
+        d.pulses_per_item = d.pulses_per_sub * (256 / d.pulses_per_sub);
         d.leg_id = L.leg_id;
         d.pulse_off = P.total_pulses;
         d.wave_off = P.wave;
@@ -527,7 +530,8 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         d.q = q;
         d.S = subray_count(q);
         int ppi = rays / d.S;
-        d.pulses_per_item = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
+        d.pulses_per_item = d.pulses_per_sub * (256 / d.pulses_per_sub);
         d.leg_id = L.leg_id;
         d.pulse_off = pulses;
         d.wave_off = wave;

@@ -36,6 +36,7 @@ constexpr float kHalfCns = (float)(0.5e-9 * kC);
 // d[axis] >= 0 is child0.  Triangle t occupies tris[3t .. 3t+2]:
 //   (v0, global id), (v1, mesh), (v2, face).
 constexpr int kReturnListCap = 256;   // expected-mode returns listed per lane and pulse
+constexpr int kConeCap = 16;          // candidate triangles kept per pulse
 constexpr int kBrickLog2 = 2;   // 4^3-voxel bricks for empty-space skipping
 constexpr int kBrick = 1 << kBrickLog2;
 
@@ -89,9 +90,9 @@ struct DevLeg {
     int64_t pulse_off, wave_off, sub_off, echo_off;
     int64_t item_begin;      // first work item of this leg
     int32_t scene, scanner, platform, q;
-    int32_t S, pulses_per_item;
+    int32_t S, pulses_per_item;    // pulses per work item
     uint32_t leg_id;
-    int32_t pad;
+    int32_t pulses_per_sub;        // pulses per subray/waveform batch within an item
 };
 
 struct Outputs {
@@ -524,6 +525,100 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
             // cf is internal: leaves were tested when `parent` was entered
             cur = cf; ++depth; down = true;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Beam-cone candidate search.  The subrays of a pulse leave one origin inside
+// a cone of half-angle atan(ta) around the pulse axis: a subray point at
+// distance t lies within t * ta of the axis point at the same t.  A box that
+// a subray meets is therefore met by the axis ray once it is grown by ta
+// times its farthest-corner distance (bounded by the L1 norm; ta carries a
+// margin for FP32 rounding).  The warp walks the union of its lanes' cones
+// (one pulse per lane) with the stackless scheme of traverse(), without range
+// culling; the leaves met are the pulse's candidate triangles, in walk order.
+// The closest hit of every subray is among them, so testing a subray against
+// the list gives its traversal result.  n > cap: the list overflowed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool cone_box(const RayF& r, float ta, const float b[6]) {
+    const float fx = fmaxf(fabsf(b[0] - r.ox), fabsf(b[3] - r.ox));
+    const float fy = fmaxf(fabsf(b[1] - r.oy), fabsf(b[4] - r.oy));
+    const float fz = fmaxf(fabsf(b[2] - r.oz), fabsf(b[5] - r.oz));
+    const float R = ta * (fx + fy + fz);
+    return slab(r, b[0] - R, b[1] - R, b[2] - R, b[3] + R, b[4] + R, b[5] + R, 3.0e38f);
+}
+
+__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, float ta,
+                                                bool active, int32_t* cand, int cap, int& n) {
+    const unsigned full = 0xffffffffu;
+    n = 0;
+    if (S.n_tri == 0) return;
+    if (S.n_int == 0) {
+        if (active) cand[n++] = 0;
+        return;
+    }
+    unsigned am = __ballot_sync(full, active);
+    if (am == 0u) return;
+    int rep = __ffs(am) - 1;
+    const bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
+    const bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
+    const bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
+    uint64_t trail0 = 0, trail1 = 0;   // bit d: far child at depth d still pending
+    int cur = 0, depth = 0;
+    bool down = true, live = active;
+    const int max_steps = 3 * S.n_int + 8;
+    for (int step = 0;; ++step) {
+        if (step >= max_steps) {
+            if (live) n = cap + 1;
+            break;
+        }
+        const float4* nd = S.nodes + 4 * (size_t)cur;
+        if (down) {
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            int axis = __float_as_int(n3.w) & 3;
+            bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
+            int cn = pos ? c0 : c1, cf = pos ? c1 : c0;
+            float bn[6], bf[6];
+            child_box(n0, n1, n2, !pos, bn);
+            child_box(n0, n1, n2, pos, bf);
+            bool hn = live && cone_box(r, ta, bn);
+            bool hf = live && cone_box(r, ta, bf);
+            if (cn < 0) {
+                if (hn) { if (n < cap) cand[n] = ~cn; ++n; }
+                hn = false;
+            }
+            if (cf < 0) {
+                if (hf) { if (n < cap) cand[n] = ~cf; ++n; }
+                hf = false;
+            }
+            live = live && n <= cap;
+            bool an = __any_sync(full, hn && live), af = __any_sync(full, hf && live);
+            if (an) {
+                if (af) { if (depth < 64) trail0 |= 1ull << depth; else trail1 |= 1ull << (depth - 64); }
+                cur = cn; ++depth;
+                continue;
+            }
+            if (af) { cur = cf; ++depth; continue; }
+            down = false;
+            continue;
+        }
+        if (cur == 0) break;
+        int parent = __float_as_int(__ldg(nd + 3).z);
+        --depth;
+        bool pending = depth < 64 ? ((trail0 >> depth) & 1ull) : ((trail1 >> (depth - 64)) & 1ull);
+        cur = parent;
+        if (!pending) continue;
+        if (depth < 64) trail0 &= ~(1ull << depth); else trail1 &= ~(1ull << (depth - 64));
+        if (!__any_sync(full, live)) break;
+        // some lane met the far child when `parent` was entered; no range
+        // culling here, so that still holds: descend without a re-test
+        float4 n3 = __ldg(S.nodes + 4 * (size_t)parent + 3);
+        int axis = __float_as_int(n3.w) & 3;
+        bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
+        cur = pos ? __float_as_int(n3.y) : __float_as_int(n3.x);
+        ++depth;
+        down = true;
     }
 }
 

@@ -128,9 +128,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
     float* s_noise = reinterpret_cast<float*>(s_pflag + P.pc_cap);   // [pc_cap][2]
     float* s_pk = s_noise + 2 * P.pc_cap;                              // [pk_cap]
+    int32_t* s_ncand = reinterpret_cast<int32_t*>(s_pk + P.pk_cap);    // [pc_cap]
+    int32_t* s_cand = s_ncand + P.pc_cap;                              // [pc_cap][kConeCap]
     // the per-warp waveform rows start 16-byte aligned (float4 reads below)
     float* s_w = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(s_pk + P.pk_cap) + 15u) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(s_cand + (size_t)P.pc_cap * kConeCap) + 15u) & ~uintptr_t(15));
     __shared__ int s_item;
     __shared__ int s_cached_leg;
     __shared__ double s_rot[6];
@@ -209,564 +211,604 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         }
         __syncthreads();
 
-        // ---------------- phase 1: subrays, ray-major packets ----------------
-        const int n_rays = pc * S;
-        for (int pk = warp; pk * 32 < n_rays; pk += nwarps) {
-            int r = pk * 32 + lane;
-            bool active = r < n_rays;
-            int pl = active ? r / S : 0;
-            int s = active ? r - pl * S : 0;
-            const PulseFF& f = s_pf[pl];
-            float dh[3], dl[3];
-            subray_dir_ff(f, s_sc[s], dh, dl);
-            RayF ray;
-            make_ray(f.oh, dh, ray);
-            float tb = 3.0e38f;
-            int hit = -1;
-            uint32_t fl = 0;
-            traverse(sc, ray, active, tb, hit, fl);
-            RayRes rr;
-            rr.Rh = CUDART_INF_F;
-            rr.Rl = 0.0f;
-            rr.R2h = CUDART_INF_F;
-            rr.R2l = 0.0f;
-            rr.P = 0.0f;
-            rr.id = -1;
-            float tan_a = s_sc[s].tan_a;
-            float dt_hit = 0.0f;
-            if (active) {
-                float cosi = 0.0f;
-                double t_tri = CUDART_INF;
-                int gid = -1;
-                float rho = 0.0f;
-                if (hit >= 0) {
-                    dt_hit = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
-                    t_tri = GRID ? (double)tb + (double)dt_hit : 0.0;
-                    const float4* tp = sc.tris + 3 * (size_t)hit;
-                    gid = __float_as_int(__ldg(&tp[0].w));
-                    int mesh = __float_as_int(__ldg(&tp[1].w));
-                    int face = __float_as_int(__ldg(&tp[2].w));
-                    rho = __ldg(&sc.refl[mesh][face]);
-                    if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
-                }
-                bool voxel_event = false;
-                if (GRID && sc.has_grid) {
-                    double o[3], d[3];
-                    for (int a = 0; a < 3; ++a) {
-                        o[a] = ff2d(f.oh[a], f.ol[a]);
-                        d[a] = ff2d(dh[a], dl[a]);
-                    }
-                    March m;
-                    if (march_init(sc, o, d, t_tri, m)) {
-                        const int64_t k = p0 + pl;
-                        for (;;) {
-                            VoxSeg v;
-                            if (!march_current(sc, m, v)) break;
-                            float dens = voxel_density(sc, m, v);
-                            if (dens > 0.0f) {
-                                FF t_in, t_out;
-                                march_segment_ff(m, v, t_in, t_out);
-                                float len = ff_diff(t_out, t_in);
-                                if (len > 0.0f) {
-                                    float sigma = sc.G * dens;
-                                    if (MODE == 0) {
-                                        // Eq. intersection_dist: s = -ln(u)/sigma
-                                        uint64_t w[4];
-                                        philox4x64((uint64_t)k, (uint64_t)(uint32_t)s,
-                                                   (uint64_t)v.vid, (uint64_t)lg.leg_id,
-                                                   P.seed, 0ull, w);
-                                        float sdist = -logf(uniform23(w[0])) / sigma;
-                                        if (sdist < len) {
-                                            FF R = ff_add_f(t_in, sdist);
-                                            rr.Rh = R.hi;
-                                            rr.Rl = R.lo;
-                                            rr.id = sc.n_tri + (int32_t)v.vid;
-                                            rr.P = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
-                                            voxel_event = true;
-                                            break;
-                                        }
-                                    } else {
-                                        FF R2 = ff_add_f(t_in, 0.5f * len);
-                                        rr.R2h = R2.hi;
-                                        rr.R2l = R2.lo;
-                                        break;
-                                    }
-                                }
-                            }
-                            if (!march_step(m, v, fl)) break;
+        // ---------------- phase 1a: candidate triangles per pulse cone ----------------
+        const bool use_cone = S > 1 && sc.n_tri > 0;
+        if (use_cone) {
+            // every warp walks a contiguous share of the item's pulses: the walk
+            // is latency-bound, so more warps beat fuller ones
+            const float ta = fmaf(tanf((float)sn.theta_r), 1.001f, 1.0e-6f);
+            const int ppw = min(32, (pc + nwarps - 1) / nwarps);
+            for (int pb = warp * ppw; pb < pc; pb += nwarps * ppw) {
+                const int pl = pb + lane;
+                const bool act = lane < ppw && pl < pc;
+                const PulseFF& f = s_pf[act ? pl : 0];
+                float dh[3], dl[3];
+                subray_dir_ff(f, s_sc[0], dh, dl);     // subray 0: the pulse axis
+                RayF ray;
+                make_ray(f.oh, dh, ray);
+                int n;
+                cone_candidates(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, n);
+                if (act) s_ncand[pl] = n;
+            }
+            __syncthreads();
+        }
+
+        // phases 1 and 2 run on batches of pulses_per_sub pulses: the per-ray
+        // arrays hold one batch
+        for (int sb = 0; sb < pc; sb += lg.pulses_per_sub) {
+            const int pe = min(pc, sb + lg.pulses_per_sub);
+            // ---------------- phase 1: subrays, ray-major packets ----------------
+            const int n_rays = (pe - sb) * S;
+            for (int pk = warp; pk * 32 < n_rays; pk += nwarps) {
+                int r = pk * 32 + lane;
+                bool active = r < n_rays;
+                int pl = sb + (active ? r / S : 0);
+                int s = active ? r - (pl - sb) * S : 0;
+                const PulseFF& f = s_pf[pl];
+                float dh[3], dl[3];
+                subray_dir_ff(f, s_sc[s], dh, dl);
+                RayF ray;
+                make_ray(f.oh, dh, ray);
+                float tb = 3.0e38f;
+                int hit = -1;
+                uint32_t fl = 0;
+                bool walk = active;
+                if (use_cone && active) {
+                    const int nc = s_ncand[pl];
+                    if (nc <= kConeCap) {
+                        walk = false;
+                        const int32_t* cl = s_cand + (size_t)pl * kConeCap;
+                        for (int i = 0; i < nc; ++i) {
+                            const int t = cl[i];
+                            const float4* tp = sc.tris + 3 * (size_t)t;
+                            if (tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tb)) hit = t;
                         }
                     }
                 }
-                if (!voxel_event && gid >= 0) {
-                    rr.Rh = tb;
-                    rr.Rl = dt_hit;
-                    rr.id = gid;
-                    rr.P = return_power(sn, tb + dt_hit, tan_a, rho, cosi);
-                }
-                s_rr[r] = rr;
-                if (fl) atomicOr(&s_pflag[pl], fl);
-                if (P.out.subray_hit) {
-                    int64_t so = lg.sub_off + (p0 + pl) * S + s;
-                    P.out.subray_hit[so] = rr.id;
-                    if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? rr.Rh + rr.Rl : 0.0f;
+                traverse(sc, ray, walk, tb, hit, fl);   // pulses whose list overflowed
+                RayRes rr;
+                rr.Rh = CUDART_INF_F;
+                rr.Rl = 0.0f;
+                rr.R2h = CUDART_INF_F;
+                rr.R2l = 0.0f;
+                rr.P = 0.0f;
+                rr.id = -1;
+                float tan_a = s_sc[s].tan_a;
+                float dt_hit = 0.0f;
+                if (active) {
+                    float cosi = 0.0f;
+                    double t_tri = CUDART_INF;
+                    int gid = -1;
+                    float rho = 0.0f;
+                    if (hit >= 0) {
+                        dt_hit = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
+                        t_tri = GRID ? (double)tb + (double)dt_hit : 0.0;
+                        const float4* tp = sc.tris + 3 * (size_t)hit;
+                        gid = __float_as_int(__ldg(&tp[0].w));
+                        int mesh = __float_as_int(__ldg(&tp[1].w));
+                        int face = __float_as_int(__ldg(&tp[2].w));
+                        rho = __ldg(&sc.refl[mesh][face]);
+                        if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
+                    }
+                    bool voxel_event = false;
+                    if (GRID && sc.has_grid) {
+                        double o[3], d[3];
+                        for (int a = 0; a < 3; ++a) {
+                            o[a] = ff2d(f.oh[a], f.ol[a]);
+                            d[a] = ff2d(dh[a], dl[a]);
+                        }
+                        March m;
+                        if (march_init(sc, o, d, t_tri, m)) {
+                            const int64_t k = p0 + pl;
+                            for (;;) {
+                                VoxSeg v;
+                                if (!march_current(sc, m, v)) break;
+                                float dens = voxel_density(sc, m, v);
+                                if (dens > 0.0f) {
+                                    FF t_in, t_out;
+                                    march_segment_ff(m, v, t_in, t_out);
+                                    float len = ff_diff(t_out, t_in);
+                                    if (len > 0.0f) {
+                                        float sigma = sc.G * dens;
+                                        if (MODE == 0) {
+                                            // Eq. intersection_dist: s = -ln(u)/sigma
+                                            uint64_t w[4];
+                                            philox4x64((uint64_t)k, (uint64_t)(uint32_t)s,
+                                                       (uint64_t)v.vid, (uint64_t)lg.leg_id,
+                                                       P.seed, 0ull, w);
+                                            float sdist = -logf(uniform23(w[0])) / sigma;
+                                            if (sdist < len) {
+                                                FF R = ff_add_f(t_in, sdist);
+                                                rr.Rh = R.hi;
+                                                rr.Rl = R.lo;
+                                                rr.id = sc.n_tri + (int32_t)v.vid;
+                                                rr.P = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
+                                                voxel_event = true;
+                                                break;
+                                            }
+                                        } else {
+                                            FF R2 = ff_add_f(t_in, 0.5f * len);
+                                            rr.R2h = R2.hi;
+                                            rr.R2l = R2.lo;
+                                            break;
+                                        }
+                                    }
+                                }
+                                if (!march_step(m, v, fl)) break;
+                            }
+                        }
+                    }
+                    if (!voxel_event && gid >= 0) {
+                        rr.Rh = tb;
+                        rr.Rl = dt_hit;
+                        rr.id = gid;
+                        rr.P = return_power(sn, tb + dt_hit, tan_a, rho, cosi);
+                    }
+                    s_rr[r] = rr;
+                    if (fl) atomicOr(&s_pflag[pl], fl);
+                    if (P.out.subray_hit) {
+                        int64_t so = lg.sub_off + (p0 + pl) * S + s;
+                        P.out.subray_hit[so] = rr.id;
+                        if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? rr.Rh + rr.Rl : 0.0f;
+                    }
                 }
             }
-        }
-        __syncthreads();
+            __syncthreads();
 
-        // ---------------- phase 2: waveform + echoes, one warp per pulse ----------------
-        const int nbw = P.nb_cap;
-        float* W = s_w + (size_t)warp * P.w_stride;
-        const bool mom_path = MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0;
-        float* best = W + nbw;
-        int32_t* bid = reinterpret_cast<int32_t*>(W + 2 * nbw);
-        for (int pl = warp; pl < pc; pl += nwarps) {
-            const int64_t k = p0 + pl;
-            const int64_t gp = lg.pulse_off + k;
-            const RayRes* rrp = s_rr + (size_t)pl * S;
-            FF rmin = {CUDART_INF_F, 0.0f};
-            for (int s = lane; s < S; s += 32) {
-                RayRes rr = rrp[s];
-                if (rr.id >= 0) {
-                    FF r = ff_norm(rr.Rh, rr.Rl);
-                    if (ff_less(r, rmin)) rmin = r;
+            // ---------------- phase 2: waveform + echoes, one warp per pulse ----------------
+            const int nbw = P.nb_cap;
+            float* W = s_w + (size_t)warp * P.w_stride;
+            const bool mom_path = MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0;
+            float* best = W + nbw;
+            int32_t* bid = reinterpret_cast<int32_t*>(W + 2 * nbw);
+            for (int pl = sb + warp; pl < pe; pl += nwarps) {
+                const int64_t k = p0 + pl;
+                const int64_t gp = lg.pulse_off + k;
+                const RayRes* rrp = s_rr + (size_t)(pl - sb) * S;
+                FF rmin = {CUDART_INF_F, 0.0f};
+                for (int s = lane; s < S; s += 32) {
+                    RayRes rr = rrp[s];
+                    if (rr.id >= 0) {
+                        FF r = ff_norm(rr.Rh, rr.Rl);
+                        if (ff_less(r, rmin)) rmin = r;
+                    }
+                    if (MODE == 1) {
+                        FF r = ff_norm(rr.R2h, rr.R2l);
+                        if (ff_less(r, rmin)) rmin = r;
+                    }
                 }
-                if (MODE == 1) {
-                    FF r = ff_norm(rr.R2h, rr.R2l);
-                    if (ff_less(r, rmin)) rmin = r;
+                for (int o = 16; o > 0; o >>= 1) {
+                    FF other = {__shfl_xor_sync(full, rmin.hi, o), __shfl_xor_sync(full, rmin.lo, o)};
+                    if (ff_less(other, rmin)) rmin = other;
                 }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                FF other = {__shfl_xor_sync(full, rmin.hi, o), __shfl_xor_sync(full, rmin.lo, o)};
-                if (ff_less(other, rmin)) rmin = other;
-            }
-            uint32_t pflag = s_pflag[pl];
-            float* row = P.out.waveform + lg.wave_off + k * nb;
-            const int64_t eb = lg.echo_off + k * K;
-            if (rmin.hi == CUDART_INF_F) {
-                for (int b = lane; b < nb; b += 32) __stcs(row + b, 0.0f);
-                for (int e = lane; e < K; e += 32) {
+                uint32_t pflag = s_pflag[pl];
+                float* row = P.out.waveform + lg.wave_off + k * nb;
+                const int64_t eb = lg.echo_off + k * K;
+                if (rmin.hi == CUDART_INF_F) {
+                    for (int b = lane; b < nb; b += 32) __stcs(row + b, 0.0f);
+                    for (int e = lane; e < K; e += 32) {
+                        P.out.echo_range[eb + e] = 0.0f;
+                        if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
+                        if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
+                        if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
+                    }
+                    if (lane == 0) {
+                        P.out.window_bin[gp] = kNoWindow;
+                        P.out.echo_count[gp] = 0;
+                        if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)(pflag | kPfNoReturn);
+                    }
+                    continue;
+                }
+                int32_t m = ff_floor_mul(rmin, sn.bpm_hi, sn.bpm_lo) - sn.n_pre;
+                // window start time m * bin as a float pair (exact product)
+                float mdt_h, mdt_l;
+                two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
+                mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
+                // bins [wlo, whi] can be non-zero: the union of the returns' supports
+                int wlo = 0, whi = nb - 1;
+                if (MODE == 0) {
+                    // each subray's delay relative to the window, formed once
+                    int lo = nb, hi = -1;
+                    for (int s = lane; s < S; s += 32) {
+                        RayRes rr = rrp[s];
+                        float tau = rr.id >= 0 ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
+                        s_tau[(size_t)(pl - sb) * S + s] = tau;
+                        if (rr.id >= 0) {
+                            lo = min(lo, max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin)));
+                            hi = max(hi, min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin)));
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lo = min(lo, __shfl_xor_sync(full, lo, o));
+                        hi = max(hi, __shfl_xor_sync(full, hi, o));
+                    }
+                    wlo = lo;
+                    whi = hi;
+                }
+                // zero the window's rows in 16-byte groups [zlo, zhi)
+                const int zlo = wlo & ~3, zhi = whi < wlo ? zlo : min(nbw, (whi | 3) + 1);
+                // a compact window (<= 128 bins) is summed in registers, lanes owning bins
+                const bool in_regs = MODE == 0 && whi - wlo < 128;
+                int n_rl = 0;            // this lane's entries in the warp's return list
+                for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
+                    *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (MODE == 1 && !mom_path) {
+                        *reinterpret_cast<float4*>(best + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<int4*>(bid + b) = make_int4(-1, -1, -1, -1);
+                    }
+                }
+                __syncwarp();
+                const float* taup = s_tau + (size_t)(pl - sb) * S;
+                if (MODE == 0 && in_regs) {
+                    // every return at every owned bin, in subray order; terms beyond
+                    // the pulse support underflow to (near) zero as in the plain sum
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    float tb0 = (float)(wlo + lane) * dt;
+                    for (int s = 0; s < S; ++s) {
+                        RayRes rr = rrp[s];
+                        if (rr.id < 0) continue;
+                        float tau = taup[s];
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float x = fmaf((float)(32 * j), dt, tb0) - tau;
+                            acc[j] = fmaf(rr.P, pulse_shape(sn, x), acc[j]);
+                        }
+                    }
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        int b = wlo + lane + 32 * j;
+                        if (b <= whi) W[b] = acc[j];
+                    }
+                    // alignment pads of the 16-byte groups around [wlo, whi]
+                    if (lane < 4) {
+                        int b = zlo + lane;
+                        if (b < wlo) W[b] = 0.0f;
+                        b = whi + 1 + lane;
+                        if (b < zhi) W[b] = 0.0f;
+                    }
+                } else if (MODE == 0) {
+                    for (int s = 0; s < S; ++s) {
+                        RayRes rr = rrp[s];
+                        if (rr.id < 0) continue;
+                        accumulate(W, nb, sn, dt, taup[s], rr.P, lane);
+                    }
+                } else if (mom_path) {
+                    // Expected transmittance via Hermite moments: a return at delay
+                    // tau = j bin + delta (|delta| <= bin/2) adds
+                    // P p(k bin - delta) = P p(k bin) sum_n (delta/sigma)^n/n! He_n(k bin/sigma)
+                    // at bin j + k; the series is cut after n = 3 (error below
+                    // 4e-6 P for bin 0.25 ns, sigma 1.7 ns).  Lanes (subrays) march
+                    // independently and add P delta^n/n! to per-warp bins as 64-bit
+                    // fixed-point integers (order-free, hence deterministic); a tiled
+                    // convolution with the Hermite kernels then forms the waveform.
+                    const PulseFF& f = s_pf[pl];
+                    const int ncell = P.mom_cells, cb = P.mom_cb;
+                    long long* M = P.mom + ((size_t)blockIdx.x * nwarps + warp) * 4 * (size_t)ncell;
+                    unsigned long long* Mu = reinterpret_cast<unsigned long long*>(M);
+                    const float rm = rmin.hi;
+                    const float scale = ldexpf(rm * rm / sn.pconst, 40);
+                    int clo = INT_MAX, chi = -1;
+                    uint32_t fl = 0;
+                    // return list [3][rl_cap][32]: what the echo-object pass reads
+                    // instead of marching again (a chunk of 32 subrays ends with id -1)
+                    const size_t RLs = (size_t)P.rl_cap * 32;
+                    float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
+                    for (int s0 = 0; s0 < S; s0 += 32) {
+                        const int s = s0 + lane;
+                        if (s >= S) continue;
+                        if (s0 > 0) {
+                            if (n_rl < P.rl_cap)
+                                __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + (size_t)n_rl * 32 + lane, -1);
+                            ++n_rl;
+                        }
+                        expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl,
+                                               [&](const FF& R, float Pw, int32_t id) {
+                            float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                            float jf = rintf(tau * sn.inv_bin);
+                            if (!(jf >= (float)(-cb - 1) && jf <= (float)(nb + cb))) return;
+                            float dl = fmaf(-jf, dt, tau);
+                            float a = Pw * scale;
+                            int c = (int)jf + cb + 1;
+                            if (n_rl < P.rl_cap) {
+                                const size_t e = (size_t)n_rl * 32 + lane;
+                                __stcg(RL + e, tau);
+                                __stcg(RL + RLs + e, Pw);
+                                __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + e, id);
+                            }
+                            ++n_rl;
+                            atomicAdd(Mu + c, (unsigned long long)llrintf(a));
+                            atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
+                            atomicAdd(Mu + 2 * ncell + c, (unsigned long long)llrintf(a * dl * dl * 0.5f));
+                            atomicAdd(Mu + 3 * ncell + c,
+                                      (unsigned long long)llrintf(a * dl * dl * dl * (1.0f / 6.0f)));
+                            clo = min(clo, c);
+                            chi = max(chi, c);
+                        });
+                    }
+                    if (fl) atomicOr(&s_pflag[pl], fl);
+                    for (int o = 16; o > 0; o >>= 1) {
+                        clo = min(clo, __shfl_xor_sync(full, clo, o));
+                        chi = max(chi, __shfl_xor_sync(full, chi, o));
+                    }
+                    __syncwarp();
+                    if (chi >= clo) {
+                        const int blo = max(0, clo - 2 * cb - 1), bhi = min(nb - 1, chi - 1);
+                        float4* tile = reinterpret_cast<float4*>(best);   // 128 + 2 cb cells
+                        const float inv_scale = 1.0f / scale, is2 = sn.inv_s2;
+                        for (int t0 = blo; t0 <= bhi; t0 += 128) {
+                            // tile entry i <-> cell t0 + 1 + i <-> bin j = t0 - cb + i
+                            for (int i = lane; i < 128 + 2 * cb; i += 32) {
+                                const int c = t0 + 1 + i;
+                                float m0 = __ll2float_rn(__ldcg(M + c)) * inv_scale;
+                                float m1 = __ll2float_rn(__ldcg(M + ncell + c)) * inv_scale;
+                                float m2 = __ll2float_rn(__ldcg(M + 2 * ncell + c)) * inv_scale;
+                                float m3 = __ll2float_rn(__ldcg(M + 3 * ncell + c)) * inv_scale;
+                                // sum_n m_n sigma^-n He_n(k bin/sigma) as a cubic in k
+                                float4 q;
+                                q.x = fmaf(-m2, is2, m0);
+                                q.y = dt * fmaf(-3.0f * m3, is2, m1) * is2;
+                                q.z = m2 * dt * dt * is2 * is2;
+                                q.w = m3 * dt * dt * dt * is2 * is2 * is2;
+                                tile[i] = q;
+                            }
+                            __syncwarp();
+                            for (int r = 0; r < 4; ++r) {
+                                const int bb = lane + 32 * r, b = t0 + bb;
+                                if (b <= bhi) {
+                                    float acc = 0.0f;
+                                    for (int k = -cb; k <= cb; ++k) {
+                                        const float4 q = tile[bb + cb - k];
+                                        const float kf = (float)k;
+                                        const float poly = fmaf(fmaf(fmaf(q.w, kf, q.z), kf, q.y), kf, q.x);
+                                        acc = fmaf(s_pk[k + cb], poly, acc);
+                                    }
+                                    W[b] = acc;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                        // return the used cells to zero for the warp's next pulse
+                        for (int n = 0; n < 4; ++n)
+                            for (int c = clo + lane; c <= chi; c += 32) __stcg(M + n * ncell + c, 0ll);
+                        __syncwarp();
+                    }
+                } else {
+                    // expected transmittance: every crossed voxel returns
+                    // w = T (1 - e^{-sigma l}) at its midpoint, the triangle T.
+                    const PulseFF& f = s_pf[pl];
+                    for (int s0 = 0; s0 < S; s0 += 32) {
+                        int s = s0 + lane;
+                        bool lane_on = s < S;
+                        RayRes rr;
+                        rr.id = -1;
+                        rr.Rh = CUDART_INF_F;
+                        rr.Rl = 0.0f;
+                        rr.P = 0.0f;
+                        float T = 1.0f;
+                        float tan_a = 0.0f;
+                        if (lane_on) {
+                            rr = rrp[s];
+                            tan_a = s_sc[s].tan_a;
+                        }
+                        bool on = false;
+                        March mch;
+                        uint32_t fl = 0;
+                        if (GRID && sc.has_grid && lane_on) {
+                            double o[3], d[3];
+                            float dh[3], dl[3];
+                            subray_dir_ff(f, s_sc[s], dh, dl);
+                            for (int a = 0; a < 3; ++a) {
+                                o[a] = ff2d(f.oh[a], f.ol[a]);
+                                d[a] = ff2d(dh[a], dl[a]);
+                            }
+                            double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+                            on = march_init(sc, o, d, t_hi, mch);
+                        }
+                        while (__any_sync(full, on)) {
+                            bool has = false;
+                            float tau = 0.0f, pv = 0.0f;
+                            int32_t vid = 0;
+                            while (on) {
+                                VoxSeg v;
+                                if (!march_current(sc, mch, v)) { on = false; break; }
+                                float dens = voxel_density(sc, mch, v);
+                                if (dens > 0.0f) {
+                                    FF t_in, t_out;
+                                    march_segment_ff(mch, v, t_in, t_out);
+                                    float len = ff_diff(t_out, t_in);
+                                    if (len > 0.0f) {
+                                        float xs = sc.G * dens * len;
+                                        float w = -T * expm1f(-xs);
+                                        T *= expf(-xs);
+                                        FF R = ff_add_f(t_in, 0.5f * len);
+                                        pv = w * return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
+                                        tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                                        vid = sc.n_tri + (int32_t)v.vid;
+                                        has = true;
+                                    }
+                                }
+                                if (!march_step(mch, v, fl)) on = false;
+                                if (has) break;
+                            }
+                            unsigned hm = __ballot_sync(full, has);
+                            while (hm) {
+                                int src = __ffs(hm) - 1;
+                                hm &= hm - 1;
+                                float tb = __shfl_sync(full, tau, src);
+                                float pb = __shfl_sync(full, pv, src);
+                                int32_t ib = __shfl_sync(full, vid, src);
+                                accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
+                            }
+                        }
+                        if (fl) atomicOr(&s_pflag[pl], fl);
+                        bool has_tri = lane_on && rr.id >= 0;
+                        float ttau = has_tri ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
+                        float tp = T * rr.P;
+                        unsigned hm = __ballot_sync(full, has_tri);
+                        while (hm) {
+                            int src = __ffs(hm) - 1;
+                            hm &= hm - 1;
+                            float tb = __shfl_sync(full, ttau, src);
+                            float pb = __shfl_sync(full, tp, src);
+                            int32_t ib = __shfl_sync(full, rr.id, src);
+                            accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
+                        }
+                    }
+                }
+                __syncwarp();
+                // ---- echoes: 3-bin local maxima at or above thr * max(W) ----
+                float wmax = 0.0f;
+                for (int b = wlo + lane; b <= whi; b += 32) wmax = fmaxf(wmax, W[b]);
+                wmax = warp_maxf(wmax);
+                const float thr = sn.thr_rel * wmax;
+                int count = 0;
+                // outside [wlo, whi] the waveform is exactly zero: no maxima there
+                for (int base = wlo; base <= whi; base += 32) {
+                    int b = base + lane;
+                    bool in = b <= whi;
+                    float c = in ? W[b] : 0.0f;
+                    float l = (in && b > wlo) ? W[b - 1] : 0.0f;
+                    float rgt = (b + 1 <= whi) ? W[b + 1] : 0.0f;
+                    bool ismax = in && c > l && c >= rgt && c >= thr && c > 0.0f;
+                    unsigned mk = __ballot_sync(full, ismax);
+                    int pos = count + __popc(mk & lanemask_lt());
+                    if (ismax && pos < K) {
+                        int32_t obj = -1;
+                        if (MODE == 1) {
+                            if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
+                            else obj = bid[b];
+                        } else {
+                            float bv = -1.0f;
+                            float tbin = (float)b * dt;
+                            for (int s = 0; s < S; ++s) {
+                                RayRes rr = rrp[s];
+                                if (rr.id < 0) continue;
+                                float v = rr.P * pulse_shape(sn, tbin - taup[s]);
+                                if (v > bv) { bv = v; obj = rr.id; }
+                            }
+                        }
+                        // echo range in FP32: (m + b) bin - offset is exact or within 1 ulp,
+                        // so the range is good to ~4e-5 m at kilometre scale
+                        float Rc = fmaf((float)(m + b), sn.bin_hi, -sn.echo_offset_f) * kHalfCns;
+                        float z;
+                        if (pos < 2) {
+                            z = s_noise[2 * pl + pos];
+                        } else {
+                            uint64_t w[4];
+                            philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
+                                       (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                            float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
+                            z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+                        }
+                        P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
+                        if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
+                        if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
+                        if (P.out.echo_object && !mom_path) P.out.echo_object[eb + pos] = obj;
+                    }
+                    count += __popc(mk);
+                }
+                if (MODE == 1 && mom_path && P.out.echo_object && count > 0) {
+                    const bool rl_ok = __all_sync(full, n_rl <= P.rl_cap);
+                    // echo objects: re-march and evaluate every return at the echo
+                    // bins only; the strongest contribution wins, ties to the first
+                    // return in summation order (subray, then march order)
+                    __syncwarp();
+                    const int ne = min(count, K);
+                    const int32_t* ebin = reinterpret_cast<const int32_t*>(best);
+                    const PulseFF& f = s_pf[pl];
+                    for (int e0 = 0; e0 < ne; e0 += 4) {
+                        float tbin[4], bv[4];
+                        int bs[4], bo[4];
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            tbin[i] = e0 + i < ne ? (float)ebin[e0 + i] * dt : 1.0e30f;
+                            bv[i] = -1.0f;
+                            bs[i] = INT_MAX;
+                            bo[i] = -1;
+                        }
+                        auto consider = [&](float tau, float Pw, int32_t id, int s) {
+    #pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                float x = tbin[i] - tau;
+                                if (x >= -sn.cut_lo && x <= sn.cut_hi) {
+                                    float v = Pw * pulse_shape(sn, x);
+                                    if (v > bv[i]) { bv[i] = v; bs[i] = s; bo[i] = id; }
+                                }
+                            }
+                        };
+                        if (rl_ok) {
+                            const size_t RLs = (size_t)P.rl_cap * 32;
+                            const float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
+                            int s = lane;
+                            for (int e = 0; e < n_rl; ++e) {
+                                const size_t o = (size_t)e * 32 + lane;
+                                const int32_t id = __ldcg(reinterpret_cast<const int32_t*>(RL + 2 * RLs) + o);
+                                if (id < 0) { s += 32; continue; }
+                                consider(__ldcg(RL + o), __ldcg(RL + RLs + o), id, s);
+                            }
+                        } else {
+                            for (int s0 = 0; s0 < S; s0 += 32) {
+                                const int s = s0 + lane;
+                                if (s >= S) continue;
+                                uint32_t fl2 = 0;
+                                expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
+                                                       [&](const FF& R, float Pw, int32_t id) {
+                                    const float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                                    if (!(rintf(tau * sn.inv_bin) >= (float)(-P.mom_cb - 1) &&
+                                          rintf(tau * sn.inv_bin) <= (float)(nb + P.mom_cb)))
+                                        return;
+                                    consider(tau, Pw, id, s);
+                                });
+                            }
+                        }
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            for (int o = 16; o > 0; o >>= 1) {
+                                float ov = __shfl_xor_sync(full, bv[i], o);
+                                int os = __shfl_xor_sync(full, bs[i], o);
+                                int oo = __shfl_xor_sync(full, bo[i], o);
+                                if (ov > bv[i] || (ov == bv[i] && os < bs[i])) { bv[i] = ov; bs[i] = os; bo[i] = oo; }
+                            }
+                        }
+                        if (lane == 0) {
+    #pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (e0 + i < ne) P.out.echo_object[eb + e0 + i] = bo[i];
+                        }
+                    }
+                }
+                // unused echo slots
+                for (int e = count + lane; e < K; e += 32) {
                     P.out.echo_range[eb + e] = 0.0f;
                     if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
                     if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
                     if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
                 }
                 if (lane == 0) {
-                    P.out.window_bin[gp] = kNoWindow;
-                    P.out.echo_count[gp] = 0;
-                    if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)(pflag | kPfNoReturn);
-                }
-                continue;
-            }
-            int32_t m = ff_floor_mul(rmin, sn.bpm_hi, sn.bpm_lo) - sn.n_pre;
-            // window start time m * bin as a float pair (exact product)
-            float mdt_h, mdt_l;
-            two_prod((float)m, sn.bin_hi, mdt_h, mdt_l);
-            mdt_l = fmaf((float)m, sn.bin_lo, mdt_l);
-            // bins [wlo, whi] can be non-zero: the union of the returns' supports
-            int wlo = 0, whi = nb - 1;
-            if (MODE == 0) {
-                // each subray's delay relative to the window, formed once
-                int lo = nb, hi = -1;
-                for (int s = lane; s < S; s += 32) {
-                    RayRes rr = rrp[s];
-                    float tau = rr.id >= 0 ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
-                    s_tau[(size_t)pl * S + s] = tau;
-                    if (rr.id >= 0) {
-                        lo = min(lo, max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin)));
-                        hi = max(hi, min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin)));
+                    if (count > K) {
+                        pflag |= kPfEchoOverflow;
+                        if (P.out.status) atomicOr(P.out.status, kStEchoOverflow);
                     }
+                    if (P.out.status && (pflag & kPfTraversalCap)) atomicOr(P.out.status, kStTraversalCap);
+                    if (P.out.status && (pflag & kPfMarchCap)) atomicOr(P.out.status, kStMarchCap);
+                    P.out.window_bin[gp] = m;
+                    P.out.echo_count[gp] = min(count, K);
+                    if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)pflag;
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = min(lo, __shfl_xor_sync(full, lo, o));
-                    hi = max(hi, __shfl_xor_sync(full, hi, o));
-                }
-                wlo = lo;
-                whi = hi;
-            }
-            // zero the window's rows in 16-byte groups [zlo, zhi)
-            const int zlo = wlo & ~3, zhi = whi < wlo ? zlo : min(nbw, (whi | 3) + 1);
-            // a compact window (<= 128 bins) is summed in registers, lanes owning bins
-            const bool in_regs = MODE == 0 && whi - wlo < 128;
-            int n_rl = 0;            // this lane's entries in the warp's return list
-            for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
-                *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (MODE == 1 && !mom_path) {
-                    *reinterpret_cast<float4*>(best + b) = make_float4(0.f, 0.f, 0.f, 0.f);
-                    *reinterpret_cast<int4*>(bid + b) = make_int4(-1, -1, -1, -1);
-                }
-            }
-            __syncwarp();
-            const float* taup = s_tau + (size_t)pl * S;
-            if (MODE == 0 && in_regs) {
-                // every return at every owned bin, in subray order; terms beyond
-                // the pulse support underflow to (near) zero as in the plain sum
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                float tb0 = (float)(wlo + lane) * dt;
-                for (int s = 0; s < S; ++s) {
-                    RayRes rr = rrp[s];
-                    if (rr.id < 0) continue;
-                    float tau = taup[s];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float x = fmaf((float)(32 * j), dt, tb0) - tau;
-                        acc[j] = fmaf(rr.P, pulse_shape(sn, x), acc[j]);
+                // ---- waveform row: 16-byte streaming stores when aligned ----
+                if (((reinterpret_cast<uintptr_t>(row) & 15u) == 0) && (nb & 3) == 0) {
+                    for (int b = lane * 4; b < nb; b += 128) {
+                        float4 v = (b >= zlo && b < zhi) ? *reinterpret_cast<const float4*>(W + b)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                        __stcs(reinterpret_cast<float4*>(row + b), v);
                     }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    int b = wlo + lane + 32 * j;
-                    if (b <= whi) W[b] = acc[j];
-                }
-                // alignment pads of the 16-byte groups around [wlo, whi]
-                if (lane < 4) {
-                    int b = zlo + lane;
-                    if (b < wlo) W[b] = 0.0f;
-                    b = whi + 1 + lane;
-                    if (b < zhi) W[b] = 0.0f;
-                }
-            } else if (MODE == 0) {
-                for (int s = 0; s < S; ++s) {
-                    RayRes rr = rrp[s];
-                    if (rr.id < 0) continue;
-                    accumulate(W, nb, sn, dt, taup[s], rr.P, lane);
-                }
-            } else if (mom_path) {
-                // Expected transmittance via Hermite moments: a return at delay
-                // tau = j bin + delta (|delta| <= bin/2) adds
-                // P p(k bin - delta) = P p(k bin) sum_n (delta/sigma)^n/n! He_n(k bin/sigma)
-                // at bin j + k; the series is cut after n = 3 (error below
-                // 4e-6 P for bin 0.25 ns, sigma 1.7 ns).  Lanes (subrays) march
-                // independently and add P delta^n/n! to per-warp bins as 64-bit
-                // fixed-point integers (order-free, hence deterministic); a tiled
-                // convolution with the Hermite kernels then forms the waveform.
-                const PulseFF& f = s_pf[pl];
-                const int ncell = P.mom_cells, cb = P.mom_cb;
-                long long* M = P.mom + ((size_t)blockIdx.x * nwarps + warp) * 4 * (size_t)ncell;
-                unsigned long long* Mu = reinterpret_cast<unsigned long long*>(M);
-                const float rm = rmin.hi;
-                const float scale = ldexpf(rm * rm / sn.pconst, 40);
-                int clo = INT_MAX, chi = -1;
-                uint32_t fl = 0;
-                // return list [3][rl_cap][32]: what the echo-object pass reads
-                // instead of marching again (a chunk of 32 subrays ends with id -1)
-                const size_t RLs = (size_t)P.rl_cap * 32;
-                float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
-                for (int s0 = 0; s0 < S; s0 += 32) {
-                    const int s = s0 + lane;
-                    if (s >= S) continue;
-                    if (s0 > 0) {
-                        if (n_rl < P.rl_cap)
-                            __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + (size_t)n_rl * 32 + lane, -1);
-                        ++n_rl;
-                    }
-                    expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl,
-                                           [&](const FF& R, float Pw, int32_t id) {
-                        float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                        float jf = rintf(tau * sn.inv_bin);
-                        if (!(jf >= (float)(-cb - 1) && jf <= (float)(nb + cb))) return;
-                        float dl = fmaf(-jf, dt, tau);
-                        float a = Pw * scale;
-                        int c = (int)jf + cb + 1;
-                        if (n_rl < P.rl_cap) {
-                            const size_t e = (size_t)n_rl * 32 + lane;
-                            __stcg(RL + e, tau);
-                            __stcg(RL + RLs + e, Pw);
-                            __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + e, id);
-                        }
-                        ++n_rl;
-                        atomicAdd(Mu + c, (unsigned long long)llrintf(a));
-                        atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
-                        atomicAdd(Mu + 2 * ncell + c, (unsigned long long)llrintf(a * dl * dl * 0.5f));
-                        atomicAdd(Mu + 3 * ncell + c,
-                                  (unsigned long long)llrintf(a * dl * dl * dl * (1.0f / 6.0f)));
-                        clo = min(clo, c);
-                        chi = max(chi, c);
-                    });
-                }
-                if (fl) atomicOr(&s_pflag[pl], fl);
-                for (int o = 16; o > 0; o >>= 1) {
-                    clo = min(clo, __shfl_xor_sync(full, clo, o));
-                    chi = max(chi, __shfl_xor_sync(full, chi, o));
+                } else {
+                    for (int b = lane; b < nb; b += 32) __stcs(row + b, (b >= zlo && b < zhi) ? W[b] : 0.0f);
                 }
                 __syncwarp();
-                if (chi >= clo) {
-                    const int blo = max(0, clo - 2 * cb - 1), bhi = min(nb - 1, chi - 1);
-                    float4* tile = reinterpret_cast<float4*>(best);   // 128 + 2 cb cells
-                    const float inv_scale = 1.0f / scale, is2 = sn.inv_s2;
-                    for (int t0 = blo; t0 <= bhi; t0 += 128) {
-                        // tile entry i <-> cell t0 + 1 + i <-> bin j = t0 - cb + i
-                        for (int i = lane; i < 128 + 2 * cb; i += 32) {
-                            const int c = t0 + 1 + i;
-                            float m0 = __ll2float_rn(__ldcg(M + c)) * inv_scale;
-                            float m1 = __ll2float_rn(__ldcg(M + ncell + c)) * inv_scale;
-                            float m2 = __ll2float_rn(__ldcg(M + 2 * ncell + c)) * inv_scale;
-                            float m3 = __ll2float_rn(__ldcg(M + 3 * ncell + c)) * inv_scale;
-                            // sum_n m_n sigma^-n He_n(k bin/sigma) as a cubic in k
-                            float4 q;
-                            q.x = fmaf(-m2, is2, m0);
-                            q.y = dt * fmaf(-3.0f * m3, is2, m1) * is2;
-                            q.z = m2 * dt * dt * is2 * is2;
-                            q.w = m3 * dt * dt * dt * is2 * is2 * is2;
-                            tile[i] = q;
-                        }
-                        __syncwarp();
-                        for (int r = 0; r < 4; ++r) {
-                            const int bb = lane + 32 * r, b = t0 + bb;
-                            if (b <= bhi) {
-                                float acc = 0.0f;
-                                for (int k = -cb; k <= cb; ++k) {
-                                    const float4 q = tile[bb + cb - k];
-                                    const float kf = (float)k;
-                                    const float poly = fmaf(fmaf(fmaf(q.w, kf, q.z), kf, q.y), kf, q.x);
-                                    acc = fmaf(s_pk[k + cb], poly, acc);
-                                }
-                                W[b] = acc;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                    // return the used cells to zero for the warp's next pulse
-                    for (int n = 0; n < 4; ++n)
-                        for (int c = clo + lane; c <= chi; c += 32) __stcg(M + n * ncell + c, 0ll);
-                    __syncwarp();
-                }
-            } else {
-                // expected transmittance: every crossed voxel returns
-                // w = T (1 - e^{-sigma l}) at its midpoint, the triangle T.
-                const PulseFF& f = s_pf[pl];
-                for (int s0 = 0; s0 < S; s0 += 32) {
-                    int s = s0 + lane;
-                    bool lane_on = s < S;
-                    RayRes rr;
-                    rr.id = -1;
-                    rr.Rh = CUDART_INF_F;
-                    rr.Rl = 0.0f;
-                    rr.P = 0.0f;
-                    float T = 1.0f;
-                    float tan_a = 0.0f;
-                    if (lane_on) {
-                        rr = rrp[s];
-                        tan_a = s_sc[s].tan_a;
-                    }
-                    bool on = false;
-                    March mch;
-                    uint32_t fl = 0;
-                    if (GRID && sc.has_grid && lane_on) {
-                        double o[3], d[3];
-                        float dh[3], dl[3];
-                        subray_dir_ff(f, s_sc[s], dh, dl);
-                        for (int a = 0; a < 3; ++a) {
-                            o[a] = ff2d(f.oh[a], f.ol[a]);
-                            d[a] = ff2d(dh[a], dl[a]);
-                        }
-                        double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
-                        on = march_init(sc, o, d, t_hi, mch);
-                    }
-                    while (__any_sync(full, on)) {
-                        bool has = false;
-                        float tau = 0.0f, pv = 0.0f;
-                        int32_t vid = 0;
-                        while (on) {
-                            VoxSeg v;
-                            if (!march_current(sc, mch, v)) { on = false; break; }
-                            float dens = voxel_density(sc, mch, v);
-                            if (dens > 0.0f) {
-                                FF t_in, t_out;
-                                march_segment_ff(mch, v, t_in, t_out);
-                                float len = ff_diff(t_out, t_in);
-                                if (len > 0.0f) {
-                                    float xs = sc.G * dens * len;
-                                    float w = -T * expm1f(-xs);
-                                    T *= expf(-xs);
-                                    FF R = ff_add_f(t_in, 0.5f * len);
-                                    pv = w * return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
-                                    tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                    vid = sc.n_tri + (int32_t)v.vid;
-                                    has = true;
-                                }
-                            }
-                            if (!march_step(mch, v, fl)) on = false;
-                            if (has) break;
-                        }
-                        unsigned hm = __ballot_sync(full, has);
-                        while (hm) {
-                            int src = __ffs(hm) - 1;
-                            hm &= hm - 1;
-                            float tb = __shfl_sync(full, tau, src);
-                            float pb = __shfl_sync(full, pv, src);
-                            int32_t ib = __shfl_sync(full, vid, src);
-                            accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
-                        }
-                    }
-                    if (fl) atomicOr(&s_pflag[pl], fl);
-                    bool has_tri = lane_on && rr.id >= 0;
-                    float ttau = has_tri ? ff_mul_sub(ff_norm(rr.Rh, rr.Rl), kDelayHi, kDelayLo, mdt_h, mdt_l) : 0.0f;
-                    float tp = T * rr.P;
-                    unsigned hm = __ballot_sync(full, has_tri);
-                    while (hm) {
-                        int src = __ffs(hm) - 1;
-                        hm &= hm - 1;
-                        float tb = __shfl_sync(full, ttau, src);
-                        float pb = __shfl_sync(full, tp, src);
-                        int32_t ib = __shfl_sync(full, rr.id, src);
-                        accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
-                    }
-                }
             }
-            __syncwarp();
-            // ---- echoes: 3-bin local maxima at or above thr * max(W) ----
-            float wmax = 0.0f;
-            for (int b = wlo + lane; b <= whi; b += 32) wmax = fmaxf(wmax, W[b]);
-            wmax = warp_maxf(wmax);
-            const float thr = sn.thr_rel * wmax;
-            int count = 0;
-            // outside [wlo, whi] the waveform is exactly zero: no maxima there
-            for (int base = wlo; base <= whi; base += 32) {
-                int b = base + lane;
-                bool in = b <= whi;
-                float c = in ? W[b] : 0.0f;
-                float l = (in && b > wlo) ? W[b - 1] : 0.0f;
-                float rgt = (b + 1 <= whi) ? W[b + 1] : 0.0f;
-                bool ismax = in && c > l && c >= rgt && c >= thr && c > 0.0f;
-                unsigned mk = __ballot_sync(full, ismax);
-                int pos = count + __popc(mk & lanemask_lt());
-                if (ismax && pos < K) {
-                    int32_t obj = -1;
-                    if (MODE == 1) {
-                        if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
-                        else obj = bid[b];
-                    } else {
-                        float bv = -1.0f;
-                        float tbin = (float)b * dt;
-                        for (int s = 0; s < S; ++s) {
-                            RayRes rr = rrp[s];
-                            if (rr.id < 0) continue;
-                            float v = rr.P * pulse_shape(sn, tbin - taup[s]);
-                            if (v > bv) { bv = v; obj = rr.id; }
-                        }
-                    }
-                    // echo range in FP32: (m + b) bin - offset is exact or within 1 ulp,
-                    // so the range is good to ~4e-5 m at kilometre scale
-                    float Rc = fmaf((float)(m + b), sn.bin_hi, -sn.echo_offset_f) * kHalfCns;
-                    float z;
-                    if (pos < 2) {
-                        z = s_noise[2 * pl + pos];
-                    } else {
-                        uint64_t w[4];
-                        philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
-                                   (uint64_t)lg.leg_id, P.seed, 0ull, w);
-                        float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
-                        z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-                    }
-                    P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
-                    if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
-                    if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
-                    if (P.out.echo_object && !mom_path) P.out.echo_object[eb + pos] = obj;
-                }
-                count += __popc(mk);
-            }
-            if (MODE == 1 && mom_path && P.out.echo_object && count > 0) {
-                const bool rl_ok = __all_sync(full, n_rl <= P.rl_cap);
-                // echo objects: re-march and evaluate every return at the echo
-                // bins only; the strongest contribution wins, ties to the first
-                // return in summation order (subray, then march order)
-                __syncwarp();
-                const int ne = min(count, K);
-                const int32_t* ebin = reinterpret_cast<const int32_t*>(best);
-                const PulseFF& f = s_pf[pl];
-                for (int e0 = 0; e0 < ne; e0 += 4) {
-                    float tbin[4], bv[4];
-                    int bs[4], bo[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        tbin[i] = e0 + i < ne ? (float)ebin[e0 + i] * dt : 1.0e30f;
-                        bv[i] = -1.0f;
-                        bs[i] = INT_MAX;
-                        bo[i] = -1;
-                    }
-                    auto consider = [&](float tau, float Pw, int32_t id, int s) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float x = tbin[i] - tau;
-                            if (x >= -sn.cut_lo && x <= sn.cut_hi) {
-                                float v = Pw * pulse_shape(sn, x);
-                                if (v > bv[i]) { bv[i] = v; bs[i] = s; bo[i] = id; }
-                            }
-                        }
-                    };
-                    if (rl_ok) {
-                        const size_t RLs = (size_t)P.rl_cap * 32;
-                        const float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
-                        int s = lane;
-                        for (int e = 0; e < n_rl; ++e) {
-                            const size_t o = (size_t)e * 32 + lane;
-                            const int32_t id = __ldcg(reinterpret_cast<const int32_t*>(RL + 2 * RLs) + o);
-                            if (id < 0) { s += 32; continue; }
-                            consider(__ldcg(RL + o), __ldcg(RL + RLs + o), id, s);
-                        }
-                    } else {
-                        for (int s0 = 0; s0 < S; s0 += 32) {
-                            const int s = s0 + lane;
-                            if (s >= S) continue;
-                            uint32_t fl2 = 0;
-                            expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
-                                                   [&](const FF& R, float Pw, int32_t id) {
-                                const float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                if (!(rintf(tau * sn.inv_bin) >= (float)(-P.mom_cb - 1) &&
-                                      rintf(tau * sn.inv_bin) <= (float)(nb + P.mom_cb)))
-                                    return;
-                                consider(tau, Pw, id, s);
-                            });
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        for (int o = 16; o > 0; o >>= 1) {
-                            float ov = __shfl_xor_sync(full, bv[i], o);
-                            int os = __shfl_xor_sync(full, bs[i], o);
-                            int oo = __shfl_xor_sync(full, bo[i], o);
-                            if (ov > bv[i] || (ov == bv[i] && os < bs[i])) { bv[i] = ov; bs[i] = os; bo[i] = oo; }
-                        }
-                    }
-                    if (lane == 0) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (e0 + i < ne) P.out.echo_object[eb + e0 + i] = bo[i];
-                    }
-                }
-            }
-            // unused echo slots
-            for (int e = count + lane; e < K; e += 32) {
-                P.out.echo_range[eb + e] = 0.0f;
-                if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
-                if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
-                if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
-            }
-            if (lane == 0) {
-                if (count > K) {
-                    pflag |= kPfEchoOverflow;
-                    if (P.out.status) atomicOr(P.out.status, kStEchoOverflow);
-                }
-                if (P.out.status && (pflag & kPfTraversalCap)) atomicOr(P.out.status, kStTraversalCap);
-                if (P.out.status && (pflag & kPfMarchCap)) atomicOr(P.out.status, kStMarchCap);
-                P.out.window_bin[gp] = m;
-                P.out.echo_count[gp] = min(count, K);
-                if (P.out.pulse_flags) P.out.pulse_flags[gp] = (uint8_t)pflag;
-            }
-            // ---- waveform row: 16-byte streaming stores when aligned ----
-            if (((reinterpret_cast<uintptr_t>(row) & 15u) == 0) && (nb & 3) == 0) {
-                for (int b = lane * 4; b < nb; b += 128) {
-                    float4 v = (b >= zlo && b < zhi) ? *reinterpret_cast<const float4*>(W + b)
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                    __stcs(reinterpret_cast<float4*>(row + b), v);
-                }
-            } else {
-                for (int b = lane; b < nb; b += 32) __stcs(row + b, (b >= zlo && b < zhi) ? W[b] : 0.0f);
-            }
-            __syncwarp();
+            __syncthreads();   // the batch arrays are reused
         }
-        __syncthreads();
     }
 }
 
@@ -820,7 +862,7 @@ static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_c
                          int pk_cap = 0, int cb = 0, bool direct = true) {
     size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
                sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
-               sizeof(float) * pk_cap;
+               sizeof(float) * pk_cap + sizeof(int32_t) * (size_t)pc_cap * (kConeCap + 1);
     b = (b + 15) & ~size_t(15);
     b += (size_t)(threads / 32) * warp_stride(mode, nb_cap, cb, direct) * sizeof(float);
     return b;
@@ -846,7 +888,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
     for (const DevLeg& lg : L.legs) {
         s_cap = max(s_cap, lg.S);
         pc_cap = max(pc_cap, lg.pulses_per_item);
-        rays_cap = max(rays_cap, lg.S * lg.pulses_per_item);
+        rays_cap = max(rays_cap, lg.S * lg.pulses_per_sub);
         nb_cap = max(nb_cap, L.scanners[lg.scanner].n_bins);
     }
     nb_cap = (nb_cap + 3) & ~3;
@@ -1013,7 +1055,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
     for (int l = 0; l < n_legs; ++l) {
         s_cap = max(s_cap, legs[l].S);
         pc_cap = max(pc_cap, legs[l].pulses_per_item);
-        rays_cap = max(rays_cap, legs[l].S * legs[l].pulses_per_item);
+        rays_cap = max(rays_cap, legs[l].S * legs[l].pulses_per_sub);
         nb_cap = max(nb_cap, scanners[legs[l].scanner].n_bins);
         any_grid |= scenes[legs[l].scene].has_grid != 0;
     }
