@@ -531,24 +531,53 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
 // ---------------------------------------------------------------------------
 // Beam-cone candidate search.  The subrays of a pulse leave one origin inside
 // a cone of half-angle atan(ta) around the pulse axis: a subray point at
-// distance t lies within t * ta of the axis point at the same t.  A box that
-// a subray meets is therefore met by the axis ray once it is grown by ta
-// times its farthest-corner distance (bounded by the L1 norm; ta carries a
-// margin for FP32 rounding).  The warp walks the union of its lanes' cones
-// (one pulse per lane) with the stackless scheme of traverse(), without range
-// culling; the leaves met are the pulse's candidate triangles, in walk order.
-// The closest hit of every subray is among them, so testing a subray against
-// the list gives its traversal result.  n > cap: the list overflowed.
+// distance t lies within t * ta of the axis point at the same t.  Every point
+// of the scene is within D (the L1 distance from the origin to the farthest
+// corner of the root box) of the origin, so a box that a subray meets is met
+// by the axis ray once it is grown by R = ta * D on every side: on axis a
+// that widens the slab interval by w_a = R / |d_a| (ta carries a margin for
+// FP32 rounding).  The warp walks the union of its lanes' cones (one pulse
+// per lane) with the stackless scheme of traverse(), without range culling;
+// the leaves met are the pulse's candidate triangles, in walk order.  The
+// closest hit of every subray is among them, so testing a subray against the
+// list gives its traversal result.  n > cap: the list overflowed.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool cone_box(const RayF& r, float ta, const float b[6]) {
-    const float fx = fmaxf(fabsf(b[0] - r.ox), fabsf(b[3] - r.ox));
-    const float fy = fmaxf(fabsf(b[1] - r.oy), fabsf(b[4] - r.oy));
-    const float fz = fmaxf(fabsf(b[2] - r.oz), fabsf(b[5] - r.oz));
-    const float R = ta * (fx + fy + fz);
-    return slab(r, b[0] - R, b[1] - R, b[2] - R, b[3] + R, b[4] + R, b[5] + R, 3.0e38f);
+__device__ __forceinline__ bool cone_slab(const RayF& r, const float w[3], const float b[6]) {
+    float tx0 = fmaf(b[0], r.idx, -r.oix), tx1 = fmaf(b[3], r.idx, -r.oix);
+    float ty0 = fmaf(b[1], r.idy, -r.oiy), ty1 = fmaf(b[4], r.idy, -r.oiy);
+    float tz0 = fmaf(b[2], r.idz, -r.oiz), tz1 = fmaf(b[5], r.idz, -r.oiz);
+    float tmn = fmaxf(fmaxf(fminf(tx0, tx1) - w[0], fminf(ty0, ty1) - w[1]),
+                      fmaxf(fminf(tz0, tz1) - w[2], 0.0f));
+    float tmx = fminf(fminf(fmaxf(tx0, tx1) + w[0], fmaxf(ty0, ty1) + w[1]), fmaxf(tz0, tz1) + w[2]);
+    return tmn <= tmx;
 }
 
-__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, float ta,
+// per-axis slab widening of a pulse's cone (see above)
+__device__ __forceinline__ void cone_widths(const DevScene& S, const RayF& r, float ta, float w[3]) {
+    float b0[6], b1[6];
+    if (S.n_int > 0) {
+        const float4 n0 = __ldg(S.nodes), n1 = __ldg(S.nodes + 1), n2 = __ldg(S.nodes + 2);
+        child_box(n0, n1, n2, false, b0);
+        child_box(n0, n1, n2, true, b1);
+    } else {
+        const float4 a = __ldg(S.tris), b = __ldg(S.tris + 1), c = __ldg(S.tris + 2);
+        b0[0] = fminf(a.x, fminf(b.x, c.x)); b0[1] = fminf(a.y, fminf(b.y, c.y)); b0[2] = fminf(a.z, fminf(b.z, c.z));
+        b0[3] = fmaxf(a.x, fmaxf(b.x, c.x)); b0[4] = fmaxf(a.y, fmaxf(b.y, c.y)); b0[5] = fmaxf(a.z, fmaxf(b.z, c.z));
+        for (int i = 0; i < 6; ++i) b1[i] = b0[i];
+    }
+    const float o[3] = {r.ox, r.oy, r.oz};
+    float D = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const float lo = fminf(b0[a], b1[a]), hi = fmaxf(b0[a + 3], b1[a + 3]);
+        D += fmaxf(fabsf(lo - o[a]), fabsf(hi - o[a]));
+    }
+    const float R = ta * D;
+    w[0] = R * fabsf(r.idx);
+    w[1] = R * fabsf(r.idy);
+    w[2] = R * fabsf(r.idz);
+}
+
+__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, const float w[3],
                                                 bool active, int32_t* cand, int cap, int& n) {
     const unsigned full = 0xffffffffu;
     n = 0;
@@ -582,8 +611,8 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
             float bn[6], bf[6];
             child_box(n0, n1, n2, !pos, bn);
             child_box(n0, n1, n2, pos, bf);
-            bool hn = live && cone_box(r, ta, bn);
-            bool hf = live && cone_box(r, ta, bf);
+            bool hn = live && cone_slab(r, w, bn);
+            bool hf = live && cone_slab(r, w, bf);
             if (cn < 0) {
                 if (hn) { if (n < cap) cand[n] = ~cn; ++n; }
                 hn = false;

@@ -36,7 +36,8 @@ struct ScanParams {
     int32_t n_items, n_legs;
     int32_t s_cap, pc_cap, rays_cap, nb_cap;
     int32_t w_stride;        // floats of per-warp waveform scratch in shared memory
-    int32_t pk_cap;          // pulse-shape taps 2 cb + 1 (moment path), 0: none
+    int32_t pk_cap;          // floats of the pulse-shape table region
+    int32_t ht_cb;           // stochastic mode: Hermite table half-width (bins), 0: direct sums
     int32_t mom_cells, mom_cb;
     long long* mom;          // per-warp moment bins (expected mode), NULL: direct sums
     float* rlist;            // per-warp return lists (expected mode): tau, power, id
@@ -128,6 +129,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
     float* s_noise = reinterpret_cast<float*>(s_pflag + P.pc_cap);   // [pc_cap][2]
     float* s_pk = s_noise + 2 * P.pc_cap;                              // [pk_cap]
+    // stochastic mode: p(k bin) (1, He_1, He_2, He_3 of k bin/sigma, over sigma^n), |k| <= ht_cb
+    float4* s_ht = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(s_pk) + 15u) & ~uintptr_t(15));
     int32_t* s_ncand = reinterpret_cast<int32_t*>(s_pk + P.pk_cap);    // [pc_cap]
     int32_t* s_cand = s_ncand + P.pc_cap;                              // [pc_cap][kConeCap]
     // the per-warp waveform rows start 16-byte aligned (float4 reads below)
@@ -182,6 +185,15 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     s_pk[k] = exp2f(-x * x * sn.gk2);
                 }
             }
+            if (MODE == 0 && P.ht_cb > 0 && sn.pulse_shape == 0) {
+                const float is = sqrtf(sn.inv_s2);
+                for (int k = tid; k < 2 * P.ht_cb + 1; k += blockDim.x) {
+                    const float x = (float)(k - P.ht_cb) * dt, u = x * is;
+                    const float p = exp2f(-x * x * sn.gk2);
+                    s_ht[k] = make_float4(p, p * u * is, p * (u * u - 1.0f) * is * is,
+                                          p * (u * u * u - 3.0f * u) * is * is * is);
+                }
+            }
             if (tid == 0) {
                 sincos(lg.rpy[0], &s_rot[0], &s_rot[1]);
                 sincos(lg.rpy[1], &s_rot[2], &s_rot[3]);
@@ -226,8 +238,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 subray_dir_ff(f, s_sc[0], dh, dl);     // subray 0: the pulse axis
                 RayF ray;
                 make_ray(f.oh, dh, ray);
+                float w[3];
+                cone_widths(sc, ray, ta, w);
                 int n;
-                cone_candidates(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, n);
+                cone_candidates(sc, ray, w, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, n);
                 if (act) s_ncand[pl] = n;
             }
             __syncthreads();
@@ -440,21 +454,70 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 __syncwarp();
                 const float* taup = s_tau + (size_t)(pl - sb) * S;
                 if (MODE == 0 && in_regs) {
-                    // every return at every owned bin, in subray order; terms beyond
-                    // the pulse support underflow to (near) zero as in the plain sum
                     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                    float tb0 = (float)(wlo + lane) * dt;
-                    for (int s = 0; s < S; ++s) {
-                        RayRes rr = rrp[s];
-                        if (rr.id < 0) continue;
-                        float tau = taup[s];
-    #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            float x = fmaf((float)(32 * j), dt, tb0) - tau;
-                            acc[j] = fmaf(rr.P, pulse_shape(sn, x), acc[j]);
+                    bool merged = false;
+                    if (P.ht_cb > 0 && sn.pulse_shape == 0 && S <= 32) {
+                        // Returns in the same bin cell c (tau = c bin + delta, |delta| <=
+                        // bin/2) are merged into the moments P delta^n/n!; each cell's
+                        // waveform is then sum_n M_n sigma^-n He_n(k bin/sigma) p(k bin)
+                        // at bin c + k (the Gaussian's Taylor series, cut after n = 3:
+                        // below 4e-6 of the peak for bin/sigma <= 0.15).  Worth it when
+                        // few cells hold the returns, as on a surface met by the whole beam.
+                        int c = INT_MIN;
+                        float4 mm = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (lane < S) {
+                            const RayRes rr = rrp[lane];
+                            if (rr.id >= 0) {
+                                const float tau = taup[lane];
+                                const float cf = rintf(tau * sn.inv_bin);
+                                const float d = fmaf(-cf, dt, tau);
+                                c = (int)cf;
+                                mm = make_float4(rr.P, rr.P * d, rr.P * d * d * 0.5f,
+                                                 rr.P * d * d * d * (1.0f / 6.0f));
+                            }
+                        }
+                        const unsigned peers = __match_any_sync(full, c);
+                        unsigned lead = __ballot_sync(full, c != INT_MIN && lane == __ffs(peers) - 1);
+                        if (3 * __popc(lead) <= S) {
+                            merged = true;
+                            while (lead) {
+                                const int ld = __ffs(lead) - 1;
+                                lead &= lead - 1;
+                                const int cc = __shfl_sync(full, c, ld);
+                                float4 g = c == cc ? mm : make_float4(0.f, 0.f, 0.f, 0.f);
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    g.x += __shfl_xor_sync(full, g.x, o);
+                                    g.y += __shfl_xor_sync(full, g.y, o);
+                                    g.z += __shfl_xor_sync(full, g.z, o);
+                                    g.w += __shfl_xor_sync(full, g.w, o);
+                                }
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const int kk = wlo + lane + 32 * j - cc;
+                                    if (kk >= -P.ht_cb && kk <= P.ht_cb) {
+                                        const float4 t = s_ht[kk + P.ht_cb];
+                                        acc[j] = fmaf(g.x, t.x, fmaf(g.y, t.y, fmaf(g.z, t.z, fmaf(g.w, t.w, acc[j]))));
+                                    }
+                                }
+                            }
                         }
                     }
-    #pragma unroll
+                    if (!merged) {
+                        // every return at every owned bin, in subray order; terms beyond
+                        // the pulse support underflow to (near) zero as in the plain sum
+                        const float tb0 = (float)(wlo + lane) * dt;
+                        for (int s = 0; s < S; ++s) {
+                            RayRes rr = rrp[s];
+                            if (rr.id < 0) continue;
+                            float tau = taup[s];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                float x = fmaf((float)(32 * j), dt, tb0) - tau;
+                                acc[j] = fmaf(rr.P, pulse_shape(sn, x), acc[j]);
+                            }
+                        }
+                    }
+#pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         int b = wlo + lane + 32 * j;
                         if (b <= whi) W[b] = acc[j];
@@ -672,12 +735,37 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     bool ismax = in && c > l && c >= rgt && c >= thr && c > 0.0f;
                     unsigned mk = __ballot_sync(full, ismax);
                     int pos = count + __popc(mk & lanemask_lt());
+                    int32_t obj = -1;
+                    if (MODE == 0 && S <= 32 && P.out.echo_object) {
+                        // each echo's object: the subray with the largest contribution
+                        // at the echo bin (ties to the lower subray), one lane per subray
+                        unsigned todo = mk & ((count < K) ? ~0u : 0u);
+                        while (todo) {
+                            const int src = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            if (count + __popc(mk & ((1u << src) - 1u)) >= K) break;
+                            const float tbin = (float)(base + src) * dt;
+                            float v = -1.0f;
+                            int32_t id = -1;
+                            if (lane < S) {
+                                const RayRes rr = rrp[lane];
+                                if (rr.id >= 0) { v = rr.P * pulse_shape(sn, tbin - taup[lane]); id = rr.id; }
+                            }
+                            int sl = lane;
+                            for (int o = 16; o > 0; o >>= 1) {
+                                const float ov = __shfl_xor_sync(full, v, o);
+                                const int os = __shfl_xor_sync(full, sl, o);
+                                const int32_t oi = __shfl_xor_sync(full, id, o);
+                                if (ov > v || (ov == v && os < sl)) { v = ov; sl = os; id = oi; }
+                            }
+                            if (lane == src) obj = id;
+                        }
+                    }
                     if (ismax && pos < K) {
-                        int32_t obj = -1;
                         if (MODE == 1) {
                             if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
                             else obj = bid[b];
-                        } else {
+                        } else if (!(S <= 32 && P.out.echo_object)) {
                             float bv = -1.0f;
                             float tbin = (float)b * dt;
                             for (int s = 0; s < S; ++s) {
@@ -719,7 +807,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     for (int e0 = 0; e0 < ne; e0 += 4) {
                         float tbin[4], bv[4];
                         int bs[4], bo[4];
-    #pragma unroll
+#pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             tbin[i] = e0 + i < ne ? (float)ebin[e0 + i] * dt : 1.0e30f;
                             bv[i] = -1.0f;
@@ -727,7 +815,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             bo[i] = -1;
                         }
                         auto consider = [&](float tau, float Pw, int32_t id, int s) {
-    #pragma unroll
+#pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 float x = tbin[i] - tau;
                                 if (x >= -sn.cut_lo && x <= sn.cut_hi) {
@@ -761,7 +849,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 });
                             }
                         }
-    #pragma unroll
+#pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             for (int o = 16; o > 0; o >>= 1) {
                                 float ov = __shfl_xor_sync(full, bv[i], o);
@@ -771,7 +859,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             }
                         }
                         if (lane == 0) {
-    #pragma unroll
+#pragma unroll
                             for (int i = 0; i < 4; ++i)
                                 if (e0 + i < ne) P.out.echo_object[eb + e0 + i] = bo[i];
                         }
@@ -906,7 +994,16 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         }
         if (cb > 256) { cb = 0; direct = true; }   // very long pulses: direct sums
     }
-    const int pk_cap = cb > 0 ? 2 * cb + 1 : 0;
+    // stochastic mode with a Gaussian pulse: Hermite table for merged returns
+    int ht_cb = 0;
+    if (L.mode == 0) {
+        for (const DevLeg& lg : L.legs) {
+            const DevScanner& sn = L.scanners[lg.scanner];
+            if (sn.pulse_shape == 0) ht_cb = max(ht_cb, (int)ceilf(sn.cut_hi * sn.inv_bin) + 1);
+        }
+        if (ht_cb > 256) ht_cb = 0;
+    }
+    const int pk_cap = cb > 0 ? 2 * cb + 1 : (ht_cb > 0 ? 4 * (2 * ht_cb + 1) + 4 : 0);
     size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     long long* mom = nullptr;
@@ -955,7 +1052,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             p.n_items = (int32_t)items;
             p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
             p.w_stride = w_stride; p.pk_cap = pk_cap; p.mom = mom; p.mom_cells = mom_cells; p.mom_cb = cb;
-            p.rlist = rlist; p.rl_cap = rl_cap;
+            p.rlist = rlist; p.rl_cap = rl_cap; p.ht_cb = ht_cb;
             p.queue = nullptr;
             bool g = L.scenes[L.legs[l].scene].has_grid != 0;
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
@@ -984,7 +1081,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         p->n_items = (int32_t)items;
         p->s_cap = s_cap; p->pc_cap = pc_cap; p->rays_cap = rays_cap; p->nb_cap = nb_cap;
         p->w_stride = w_stride; p->pk_cap = pk_cap; p->mom = mom; p->mom_cells = mom_cells; p->mom_cb = cb;
-        p->rlist = rlist; p->rl_cap = rl_cap;
+        p->rlist = rlist; p->rl_cap = rl_cap; p->ht_cb = ht_cb;
         int32_t* q = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int32_t), st);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(queue)", e); }
