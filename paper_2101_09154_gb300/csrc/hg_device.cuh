@@ -36,7 +36,8 @@ constexpr float kHalfCns = (float)(0.5e-9 * kC);
 // d[axis] >= 0 is child0.  Triangle t occupies tris[3t .. 3t+2]:
 //   (v0, global id), (v1, mesh), (v2, face).
 constexpr int kReturnListCap = 256;   // expected-mode returns listed per lane and pulse
-constexpr int kConeCap = 16;          // candidate triangles kept per pulse
+constexpr int kConeCap = 16;          // candidate triangles per pulse in shared memory
+constexpr int kConeExt = 112;         // more in global scratch (non-static scans)
 constexpr int kBrickLog2 = 2;   // 4^3-voxel bricks for empty-space skipping
 constexpr int kBrick = 1 << kBrickLog2;
 
@@ -540,7 +541,7 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
 // per lane) with the stackless scheme of traverse(), without range culling;
 // the leaves met are the pulse's candidate triangles, in walk order.  The
 // closest hit of every subray is among them, so testing a subray against the
-// list gives its traversal result.  n > cap: the list overflowed.
+// list gives its traversal result.  n > cap + ecap: the list overflowed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool cone_slab(const RayF& r, const float w[3], const float b[6]) {
     float tx0 = fmaf(b[0], r.idx, -r.oix), tx1 = fmaf(b[3], r.idx, -r.oix);
@@ -550,6 +551,14 @@ __device__ __forceinline__ bool cone_slab(const RayF& r, const float w[3], const
                       fmaxf(fminf(tz0, tz1) - w[2], 0.0f));
     float tmx = fminf(fminf(fmaxf(tx0, tx1) + w[0], fmaxf(ty0, ty1) + w[1]), fmaxf(tz0, tz1) + w[2]);
     return tmn <= tmx;
+}
+
+// candidate i of a pulse: the first cap in shared memory, the next ecap in
+// global scratch
+__device__ __forceinline__ void cone_store(int32_t* cand, int cap, int32_t* ext, int ecap, int i,
+                                           int32_t t) {
+    if (i < cap) cand[i] = t;
+    else if (i < cap + ecap) ext[i - cap] = t;
 }
 
 // per-axis slab widening of a pulse's cone (see above)
@@ -578,7 +587,8 @@ __device__ __forceinline__ void cone_widths(const DevScene& S, const RayF& r, fl
 }
 
 __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, const float w[3],
-                                                bool active, int32_t* cand, int cap, int& n) {
+                                                bool active, int32_t* cand, int cap, int32_t* ext,
+                                                int ecap, int& n) {
     const unsigned full = 0xffffffffu;
     n = 0;
     if (S.n_tri == 0) return;
@@ -598,7 +608,7 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
     const int max_steps = 3 * S.n_int + 8;
     for (int step = 0;; ++step) {
         if (step >= max_steps) {
-            if (live) n = cap + 1;
+            if (live) n = cap + ecap + 1;
             break;
         }
         const float4* nd = S.nodes + 4 * (size_t)cur;
@@ -614,14 +624,14 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
             bool hn = live && cone_slab(r, w, bn);
             bool hf = live && cone_slab(r, w, bf);
             if (cn < 0) {
-                if (hn) { if (n < cap) cand[n] = ~cn; ++n; }
+                if (hn) { cone_store(cand, cap, ext, ecap, n, ~cn); ++n; }
                 hn = false;
             }
             if (cf < 0) {
-                if (hf) { if (n < cap) cand[n] = ~cf; ++n; }
+                if (hf) { cone_store(cand, cap, ext, ecap, n, ~cf); ++n; }
                 hf = false;
             }
-            live = live && n <= cap;
+            live = live && n <= cap + ecap;
             bool an = __any_sync(full, hn && live), af = __any_sync(full, hf && live);
             if (an) {
                 if (af) { if (depth < 64) trail0 |= 1ull << depth; else trail1 |= 1ull << (depth - 64); }

@@ -38,6 +38,8 @@ struct ScanParams {
     int32_t w_stride;        // floats of per-warp waveform scratch in shared memory
     int32_t pk_cap;          // floats of the pulse-shape table region
     int32_t ht_cb;           // stochastic mode: Hermite table half-width (bins), 0: direct sums
+    int32_t* cext;           // per-block candidate overflow [grid][pc_cap][cext_cap], NULL: none
+    int32_t cext_cap;
     int32_t mom_cells, mom_cb;
     long long* mom;          // per-warp moment bins (expected mode), NULL: direct sums
     float* rlist;            // per-warp return lists (expected mode): tau, power, id
@@ -240,8 +242,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 make_ray(f.oh, dh, ray);
                 float w[3];
                 cone_widths(sc, ray, ta, w);
+                int32_t* ext = P.cext ? P.cext + ((size_t)blockIdx.x * P.pc_cap + (act ? pl : 0)) * P.cext_cap
+                                      : nullptr;
                 int n;
-                cone_candidates(sc, ray, w, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, n);
+                cone_candidates(sc, ray, w, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, ext,
+                                P.cext_cap, n);
                 if (act) s_ncand[pl] = n;
             }
             __syncthreads();
@@ -269,11 +274,13 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 bool walk = active;
                 if (use_cone && active) {
                     const int nc = s_ncand[pl];
-                    if (nc <= kConeCap) {
+                    if (nc <= kConeCap + P.cext_cap) {
                         walk = false;
                         const int32_t* cl = s_cand + (size_t)pl * kConeCap;
+                        const int32_t* ce = P.cext ? P.cext + ((size_t)blockIdx.x * P.pc_cap + pl) * P.cext_cap
+                                                   : nullptr;
                         for (int i = 0; i < nc; ++i) {
-                            const int t = cl[i];
+                            const int t = i < kConeCap ? cl[i] : __ldcg(ce + (i - kConeCap));
                             const float4* tp = sc.tris + 3 * (size_t)t;
                             if (tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tb)) hit = t;
                         }
@@ -1012,12 +1019,27 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
     struct Free {
         void* p; cudaStream_t s;
         ~Free() { if (p) cudaFreeAsync(p, s); }
-    } free_mom{nullptr, st}, free_rl{nullptr, st};
+    } free_mom{nullptr, st}, free_rl{nullptr, st}, free_cext{nullptr, st};
+    // the most blocks any launch below can have: per-block and per-warp scratch
+    int grid = 0;
+    if (L.mode == 0)
+        grid = L.persistent ? (any_grid ? max_grid<0, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                        : max_grid<0, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                            : (any_grid ? max_grid<0, true, 1>(threads, L.blocks_per_sm, smem)
+                                        : max_grid<0, false, 1>(threads, L.blocks_per_sm, smem));
+    else
+        grid = L.persistent ? (any_grid ? max_grid<1, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                        : max_grid<1, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                            : (any_grid ? max_grid<1, true, 1>(threads, L.blocks_per_sm, smem)
+                                        : max_grid<1, false, 1>(threads, L.blocks_per_sm, smem));
+    // candidate lists longer than kConeCap continue in global scratch
+    int32_t* cext = nullptr;
+    const int cext_cap = kConeExt;
+    cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&cext),
+                                     (size_t)grid * pc_cap * cext_cap * sizeof(int32_t), st);
+    if (ce != cudaSuccess) return set_cuda_error("cudaMallocAsync(candidate lists)", ce);
+    free_cext.p = cext;
     if (cb > 0) {
-        int grid = L.persistent ? (any_grid ? max_grid<1, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
-                                            : max_grid<1, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
-                                : (any_grid ? max_grid<1, true, 1>(threads, L.blocks_per_sm, smem)
-                                            : max_grid<1, false, 1>(threads, L.blocks_per_sm, smem));
         const size_t slots = (size_t)grid * (threads / 32);
         mom_cells = nb_cap + 2 * cb + 132;
         size_t bytes = slots * 4 * mom_cells * sizeof(long long);
@@ -1053,6 +1075,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
             p.w_stride = w_stride; p.pk_cap = pk_cap; p.mom = mom; p.mom_cells = mom_cells; p.mom_cb = cb;
             p.rlist = rlist; p.rl_cap = rl_cap; p.ht_cb = ht_cb;
+            p.cext = cext; p.cext_cap = cext_cap;
             p.queue = nullptr;
             bool g = L.scenes[L.legs[l].scene].has_grid != 0;
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
@@ -1082,6 +1105,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         p->s_cap = s_cap; p->pc_cap = pc_cap; p->rays_cap = rays_cap; p->nb_cap = nb_cap;
         p->w_stride = w_stride; p->pk_cap = pk_cap; p->mom = mom; p->mom_cells = mom_cells; p->mom_cb = cb;
         p->rlist = rlist; p->rl_cap = rl_cap; p->ht_cb = ht_cb;
+        p->cext = cext; p->cext_cap = cext_cap;
         int32_t* q = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int32_t), st);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(queue)", e); }
