@@ -309,26 +309,24 @@ def run_ours(args, D):
 
 def e2e(w, gsc, layout, out, args, stream, D):
     """Same metric through the public API with host buffers: each step uploads
-    the per-step input (the meshes' reflectance) from pinned host memory,
-    scans, and reads the whole result (waveform + echoes + window) back into
-    pinned host memory."""
+    the per-step input (the meshes' reflectance) from pinned host memory and
+    runs helios_scan_legs_host, which returns the whole result (waveform +
+    echoes + window) in pinned host memory, copying each chunk of pulses to the
+    host while the next one is scanned."""
     import torch
     import paper_2101_09154_gb300 as hg
     host_refl = [[r.cpu().pin_memory() for r in s.reflectance] for s in gsc]
-    keys = ["waveform", "window_bin", "echo_count", "echo_range", "echo_amp", "echo_bin",
-            "echo_object", "pulse_flags"]
-    host_out = {k: torch.empty(out[k].shape, dtype=out[k].dtype, pin_memory=True) for k in keys}
+    host_out = hg.alloc_host_outputs(layout, gsc[0].device, subrays=False)
     h2d = sum(t.numel() * t.element_size() for s in host_refl for t in s)
-    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    d2h = sum(t.numel() * t.element_size() for k, t in host_out.items() if k != "status")
     persistent = args.workload == "batched"
 
     def step():
         for s, hs in zip(gsc, host_refl):
             for r, h in zip(s.reflectance, hs):
                 r.copy_(h, non_blocking=True)
-        hg.scan(gsc, w.scanners, w.legs, seed=12345, persistent=persistent, out=out, subrays=False)
-        for k in keys:
-            host_out[k].copy_(out[k], non_blocking=True)
+        hg.scan_to_host(gsc, w.scanners, w.legs, seed=12345, persistent=persistent, host_out=host_out,
+                        chunk_pulses=1 << 18)
 
     for _ in range(2):
         step()

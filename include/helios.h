@@ -257,8 +257,9 @@ HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n
  * device memory is owned by another allocator (a framework's caching
  * allocator holding the budget), code running while a CUDA graph is captured
  * into a memory pool it does not control, and real-time loops that cannot let
- * an allocation fail or stall mid-run.  helios_scan_legs allocates its work
- * queue counter with cudaMallocAsync; this variant keeps the counters in a
+ * an allocation fail or stall mid-run.  helios_scan_legs allocates its
+ * scratch (work-queue counter, candidate lists, occupancy masks, moment bins)
+ * with cudaMallocAsync; this variant keeps the queue counters in a
  * static device array of 16 int32 (64 bytes, held by every GPU that loads the
  * library until exit), so it takes at most 16 x 128 = 2048 legs per call and
  * returns HELIOS_ERR_INVALID_ARG beyond that.  Host-side staging is static too
@@ -273,6 +274,27 @@ HELIOS_API helios_status helios_scan_legs_static(helios_scene* const* scenes, in
                                                  int32_t n_scanners, const helios_leg_desc* legs,
                                                  int32_t n_legs, const helios_scan_opts* opts,
                                                  const helios_outputs* out, void* cuda_stream);
+
+/* helios_scan_legs with the outputs in HOST memory.  The paper has no
+ * counterpart; this is the end-to-end form for callers that consume the
+ * results on the host.  host_out holds host pointers with the layout of
+ * helios_outputs (status alone stays a device pointer, or NULL).  The pulses
+ * are cut into chunks of whole work items of about chunk_pulses pulses
+ * (> 0); each chunk is scanned on cuda_stream into one of two device staging
+ * slots (stream-ordered allocations, freed on cuda_stream) and copied to the
+ * host on a second stream while the next chunk is scanned.  Each pulse is
+ * computed exactly as by helios_scan_legs, so the results are identical.  The
+ * call returns once the work is queued: the host buffers are complete when
+ * cuda_stream reaches the point after this call (synchronise it before
+ * reading them).  Copies overlap the scan only for page-locked host buffers;
+ * pageable ones are still filled correctly.  Errors: those of
+ * helios_scan_legs. */
+HELIOS_API helios_status helios_scan_legs_host(helios_scene* const* scenes, int32_t n_scenes,
+                                               const helios_scanner_desc* scanners,
+                                               int32_t n_scanners, const helios_leg_desc* legs,
+                                               int32_t n_legs, const helios_scan_opts* opts,
+                                               const helios_outputs* host_out,
+                                               int64_t chunk_pulses, void* cuda_stream);
 
 /* Gradient buffers of one scene: d_reflectance[i] (device float[n_faces of
  * mesh i], or NULL to skip) and d_density[j] (device float[n voxels of grid

@@ -139,6 +139,11 @@ def lib():
                                               C.c_int32, C.POINTER(LegDesc), C.c_int32,
                                               C.POINTER(ScanOpts), C.POINTER(Outputs), C.c_void_p]
         l.helios_scan_legs_static.restype = st
+        l.helios_scan_legs_host.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ScannerDesc),
+                                            C.c_int32, C.POINTER(LegDesc), C.c_int32,
+                                            C.POINTER(ScanOpts), C.POINTER(Outputs), C.c_int64,
+                                            C.c_void_p]
+        l.helios_scan_legs_host.restype = st
         l.helios_scan_adjoint.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ScannerDesc),
                                           C.c_int32, C.POINTER(LegDesc), C.c_int32,
                                           C.POINTER(ScanOpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -308,6 +313,22 @@ def alloc_outputs(layout, device, subrays=True, status=True):
     return out
 
 
+def alloc_host_outputs(layout, device, subrays=False, status=True):
+    """Page-locked host tensors for ``scan_to_host`` (``status`` stays on the device)."""
+    torch = _torch()
+    dev = alloc_outputs({"total_pulses": 0, "waveform_floats": 0, "echo_elems": 0, "subray_elems": 0},
+                        "cpu", subrays=subrays, status=False)
+    P = int(layout["total_pulses"])
+    sizes = {"waveform": layout["waveform_floats"], "window_bin": P, "echo_count": P,
+             "echo_range": layout["echo_elems"], "echo_amp": layout["echo_elems"],
+             "echo_bin": layout["echo_elems"], "echo_object": layout["echo_elems"], "pulse_flags": P,
+             "subray_hit": layout["subray_elems"], "subray_range": layout["subray_elems"]}
+    out = {k: torch.empty(int(sizes[k]), dtype=t.dtype, pin_memory=True) for k, t in dev.items()}
+    if status:
+        out["status"] = torch.zeros(1, dtype=torch.int32, device=device)
+    return out
+
+
 def _outputs_struct(out) -> Outputs:
     o = Outputs()
     for name, _ in Outputs._fields_:
@@ -338,6 +359,32 @@ def scan(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, persistent=False,
     _check(lib().helios_scan_legs(sh, len(scenes), sd, len(scanners), ld, len(legs), C.byref(opts),
                                   C.byref(o), _stream_handle(stream)))
     return out, layout
+
+
+def scan_to_host(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, persistent=False,
+                 host_out=None, subrays=False, chunk_pulses=1 << 18, stream=None, block_threads=0,
+                 rays_per_block=0, blocks_per_sm=0):
+    """helios_scan_legs_host: the scan with its outputs in (page-locked) host memory.
+
+    Chunks of about ``chunk_pulses`` pulses are scanned into device staging
+    buffers while the previous chunk is copied to the host on a second
+    stream.  Returns (host outputs dict, layout); the host tensors are
+    complete once ``stream`` (default: the current stream) is synchronised.
+    """
+    scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
+    layout = output_layout(scanners, legs)
+    if host_out is None:
+        host_out = alloc_host_outputs(layout, scenes[0].device, subrays=subrays)
+    sh = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    sd = (ScannerDesc * len(scanners))(*[scanner_desc(s) for s in scanners])
+    ld = (LegDesc * max(len(legs), 1))(*[leg_desc(l) for l in legs])
+    opts = ScanOpts(mode=int(mode), persistent=int(bool(persistent)), seed=int(seed) & (2 ** 64 - 1),
+                    block_threads=int(block_threads), rays_per_block=int(rays_per_block),
+                    blocks_per_sm=int(blocks_per_sm))
+    o = _outputs_struct(host_out)
+    _check(lib().helios_scan_legs_host(sh, len(scenes), sd, len(scanners), ld, len(legs), C.byref(opts),
+                                       C.byref(o), int(chunk_pulses), _stream_handle(stream)))
+    return host_out, layout
 
 
 def scan_static(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, out=None, subrays=True,

@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     const size_t RLs = (size_t)P.rl_cap * 32;
     float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 4 * RLs : nullptr;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
-        const int64_t p0 = (int64_t)item * lg.pulses_per_sub;
-        const int pc = (int)min((int64_t)lg.pulses_per_sub, lg.n_pulses - p0);
+        const int64_t p0 = lg.k_first + (int64_t)item * lg.pulses_per_sub;
+        const int pc = (int)min((int64_t)lg.pulses_per_sub, lg.k_first + lg.n_pulses - p0);
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
             pulse_frame(sn, lg, s_rot, p0 + t, f);

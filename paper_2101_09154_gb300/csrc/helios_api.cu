@@ -2,6 +2,7 @@
 // validation, derived instrument constants, scene lifetime and launches.
 #include "hg_host.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -560,4 +561,204 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
     return launch_scan_static(g_plan_scenes, n_scenes, g_plan_scanners, n_scanners, g_plan_legs,
                               n_legs, o, opts->seed, opts->mode, threads, opts->blocks_per_sm,
                               (cudaStream_t)cuda_stream);
+}
+
+// ---------------------------------------------------------------------------
+// helios_scan_legs_host: the scan with outputs in host memory.  The pulses
+// are cut into chunks of whole work items (so every pulse is computed exactly
+// as by helios_scan_legs); chunk c is scanned on the caller's stream into
+// staging slot c % 2 while a second stream copies chunk c - 1 to the host.
+// ---------------------------------------------------------------------------
+namespace hg {
+namespace {
+
+// one contiguous run of a leg's pulses inside a chunk
+struct Piece {
+    int leg;
+    int64_t k0, n;
+};
+
+// output positions (pulse, waveform float, echo slot, subray slot) of global pulse g
+struct Pos {
+    int64_t p, w, e, s;
+};
+
+Pos out_pos(const LegPlan& P, const helios_scanner_desc* sc, int64_t g) {
+    for (const DevLeg& d : P.legs) {
+        if (d.n_pulses > 0 && g >= d.pulse_off && g < d.pulse_off + d.n_pulses) {
+            const int64_t k = g - d.pulse_off;
+            return {g, d.wave_off + k * sc[d.scanner].n_bins, d.echo_off + k * sc[d.scanner].max_echoes,
+                    d.sub_off + k * d.S};
+        }
+    }
+    return {P.total_pulses, P.wave, P.echo, P.sub};
+}
+
+struct HostStaging {
+    void* buf[2] = {nullptr, nullptr};
+    cudaStream_t s0 = nullptr, s1 = nullptr;
+    cudaEvent_t scanned[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    ~HostStaging() {
+        // the caller's stream waits for the last copies before the slots are freed
+        for (int i = 0; i < 2; ++i)
+            if (copied[i]) cudaStreamWaitEvent(s0, copied[i], 0);
+        for (int i = 0; i < 2; ++i) {
+            if (buf[i]) cudaFreeAsync(buf[i], s0);
+            if (scanned[i]) cudaEventDestroy(scanned[i]);
+            if (copied[i]) cudaEventDestroy(copied[i]);
+        }
+        if (s1) cudaStreamDestroy(s1);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace hg
+
+extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int32_t n_scenes,
+                                               const helios_scanner_desc* scanners,
+                                               int32_t n_scanners, const helios_leg_desc* legs,
+                                               int32_t n_legs, const helios_scan_opts* opts,
+                                               const helios_outputs* host_out,
+                                               int64_t chunk_pulses, void* cuda_stream) {
+    using namespace hg;
+    g_err.clear();
+    helios_status st = check_scenes(scenes, n_scenes);
+    if (st != HELIOS_OK) return st;
+    if (!opts || !host_out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and host_out must not be NULL");
+    if (opts->mode != HELIOS_MODE_STOCHASTIC && opts->mode != HELIOS_MODE_EXPECTED)
+        return set_error(HELIOS_ERR_INVALID_ARG, "unknown mode");
+    if (!host_out->waveform || !host_out->window_bin || !host_out->echo_count || !host_out->echo_range)
+        return set_error(HELIOS_ERR_INVALID_ARG, "waveform, window_bin, echo_count, echo_range are required");
+    if (host_out->subray_range && !host_out->subray_hit)
+        return set_error(HELIOS_ERR_INVALID_ARG, "subray_range needs subray_hit");
+    if (chunk_pulses <= 0) return set_error(HELIOS_ERR_INVALID_ARG, "chunk_pulses must be positive");
+    int threads = opts->block_threads > 0 ? opts->block_threads : 256;
+    if (threads % 32 != 0 || threads < 64 || threads > 256)
+        return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
+    int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
+    if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
+    LegPlan P;
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, P);
+    if (st != HELIOS_OK) return st;
+    if (P.total_pulses == 0) return HELIOS_OK;
+
+    // chunks of whole work items, about chunk_pulses pulses each
+    std::vector<std::vector<Piece>> chunks(1);
+    int64_t in_chunk = 0;
+    for (int l = 0; l < (int)P.legs.size(); ++l) {
+        const DevLeg& d = P.legs[l];
+        int64_t k = 0;
+        while (k < d.n_pulses) {
+            if (in_chunk >= chunk_pulses) { chunks.emplace_back(); in_chunk = 0; }
+            const int64_t want = chunk_pulses - in_chunk;
+            const int64_t items = (want + d.pulses_per_item - 1) / d.pulses_per_item;
+            const int64_t n = std::min(d.n_pulses - k, items * d.pulses_per_item);
+            chunks.back().push_back({l, k, n});
+            k += n;
+            in_chunk += n;
+        }
+    }
+    // staging slot size: the largest chunk's outputs
+    int64_t mx_p = 0, mx_w = 0, mx_e = 0, mx_s = 0;
+    std::vector<std::pair<Pos, Pos>> span;
+    for (const auto& c : chunks) {
+        const DevLeg& a = P.legs[c.front().leg];
+        const DevLeg& b = P.legs[c.back().leg];
+        const Pos lo = out_pos(P, scanners, a.pulse_off + c.front().k0);
+        const Pos hi = out_pos(P, scanners, b.pulse_off + c.back().k0 + c.back().n);
+        span.push_back({lo, hi});
+        mx_p = std::max(mx_p, hi.p - lo.p);
+        mx_w = std::max(mx_w, hi.w - lo.w);
+        mx_e = std::max(mx_e, hi.e - lo.e);
+        mx_s = std::max(mx_s, hi.s - lo.s);
+    }
+    const helios_outputs& H = *host_out;
+    const bool sub = H.subray_hit != nullptr;
+    size_t off[10], bytes = 0;
+    const size_t sz[10] = {sizeof(float) * mx_w, sizeof(int32_t) * mx_p, sizeof(int32_t) * mx_p,
+                           sizeof(float) * mx_e, H.echo_amp ? sizeof(float) * mx_e : 0,
+                           H.echo_bin ? sizeof(int32_t) * mx_e : 0, H.echo_object ? sizeof(int32_t) * mx_e : 0,
+                           H.pulse_flags ? sizeof(uint8_t) * mx_p : 0, sub ? sizeof(int32_t) * mx_s : 0,
+                           H.subray_range ? sizeof(float) * mx_s : 0};
+    for (int i = 0; i < 10; ++i) { off[i] = bytes; bytes += align256(sz[i]); }
+
+    HostStaging hs;
+    hs.s0 = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&hs.s1, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { hs.s1 = nullptr; return set_cuda_error("cudaStreamCreate", e); }
+    for (int i = 0; i < 2; ++i) {
+        e = cudaEventCreateWithFlags(&hs.scanned[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) { hs.scanned[i] = nullptr; return set_cuda_error("cudaEventCreate", e); }
+        e = cudaEventCreateWithFlags(&hs.copied[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) { hs.copied[i] = nullptr; return set_cuda_error("cudaEventCreate", e); }
+        e = cudaMallocAsync(&hs.buf[i], bytes, hs.s0);
+        if (e != cudaSuccess) { hs.buf[i] = nullptr; return set_cuda_error("cudaMallocAsync(staging)", e); }
+    }
+    ScanLaunch L;
+    for (int i = 0; i < n_scenes; ++i) L.scenes.push_back(dev_scene(scenes[i]));
+    for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
+    OccupancyMasks masks;
+    st = build_occupancy(L.scenes, hs.s0, masks);
+    if (st != HELIOS_OK) return st;
+    L.seed = opts->seed;
+    L.mode = opts->mode;
+    L.persistent = opts->persistent;
+    L.threads = threads;
+    L.blocks_per_sm = opts->blocks_per_sm;
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const int slot = (int)(c & 1);
+        const Pos lo = span[c].first, hi = span[c].second;
+        if (c >= 2) cudaStreamWaitEvent(hs.s0, hs.copied[slot], 0);
+        char* base = static_cast<char*>(hs.buf[slot]);
+        L.out.waveform = reinterpret_cast<float*>(base + off[0]);
+        L.out.window_bin = reinterpret_cast<int32_t*>(base + off[1]);
+        L.out.echo_count = reinterpret_cast<int32_t*>(base + off[2]);
+        L.out.echo_range = reinterpret_cast<float*>(base + off[3]);
+        L.out.echo_amp = H.echo_amp ? reinterpret_cast<float*>(base + off[4]) : nullptr;
+        L.out.echo_bin = H.echo_bin ? reinterpret_cast<int32_t*>(base + off[5]) : nullptr;
+        L.out.echo_object = H.echo_object ? reinterpret_cast<int32_t*>(base + off[6]) : nullptr;
+        L.out.pulse_flags = H.pulse_flags ? reinterpret_cast<uint8_t*>(base + off[7]) : nullptr;
+        L.out.subray_hit = sub ? reinterpret_cast<int32_t*>(base + off[8]) : nullptr;
+        L.out.subray_range = H.subray_range ? reinterpret_cast<float*>(base + off[9]) : nullptr;
+        L.out.status = H.status;
+        // the chunk's legs, their outputs indexed from the slot's start
+        L.legs.clear();
+        for (const Piece& pc : chunks[c]) {
+            DevLeg d = P.legs[pc.leg];
+            d.k_first = pc.k0;
+            d.n_pulses = pc.n;
+            d.pulse_off -= lo.p;
+            d.wave_off -= lo.w;
+            d.echo_off -= lo.e;
+            d.sub_off -= lo.s;
+            L.legs.push_back(d);
+        }
+        st = launch_scan(L, hs.s0);
+        if (st != HELIOS_OK) return st;
+        e = cudaEventRecord(hs.scanned[slot], hs.s0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.s1, hs.scanned[slot], 0);
+        if (e != cudaSuccess) return set_cuda_error("chunk event", e);
+        struct Copy { void* dst; const void* src; size_t n; };
+        const Copy cp[10] = {
+            {H.waveform + lo.w, L.out.waveform, sizeof(float) * (hi.w - lo.w)},
+            {H.window_bin + lo.p, L.out.window_bin, sizeof(int32_t) * (hi.p - lo.p)},
+            {H.echo_count + lo.p, L.out.echo_count, sizeof(int32_t) * (hi.p - lo.p)},
+            {H.echo_range + lo.e, L.out.echo_range, sizeof(float) * (hi.e - lo.e)},
+            {H.echo_amp ? H.echo_amp + lo.e : nullptr, L.out.echo_amp, sizeof(float) * (hi.e - lo.e)},
+            {H.echo_bin ? H.echo_bin + lo.e : nullptr, L.out.echo_bin, sizeof(int32_t) * (hi.e - lo.e)},
+            {H.echo_object ? H.echo_object + lo.e : nullptr, L.out.echo_object, sizeof(int32_t) * (hi.e - lo.e)},
+            {H.pulse_flags ? H.pulse_flags + lo.p : nullptr, L.out.pulse_flags, sizeof(uint8_t) * (hi.p - lo.p)},
+            {sub ? H.subray_hit + lo.s : nullptr, L.out.subray_hit, sizeof(int32_t) * (hi.s - lo.s)},
+            {H.subray_range ? H.subray_range + lo.s : nullptr, L.out.subray_range, sizeof(float) * (hi.s - lo.s)}};
+        for (const Copy& x : cp) {
+            if (!x.dst || x.n == 0) continue;
+            e = cudaMemcpyAsync(x.dst, x.src, x.n, cudaMemcpyDeviceToHost, hs.s1);
+            if (e != cudaSuccess) return set_cuda_error("cudaMemcpyAsync(D2H)", e);
+        }
+        e = cudaEventRecord(hs.copied[slot], hs.s1);
+        if (e != cudaSuccess) return set_cuda_error("chunk event", e);
+    }
+    return HELIOS_OK;
 }

@@ -87,8 +87,9 @@ struct DevLeg {
     double dir[3];           // unit vector start -> end (linear platform)
     double length, speed, t0;
     double rpy[3];           // roll, pitch, yaw (heading included)
-    int64_t n_pulses;
-    int64_t pulse_off, wave_off, sub_off, echo_off;
+    int64_t n_pulses;        // pulses scanned: leg pulse indices k_first .. k_first + n_pulses - 1
+    int64_t k_first;
+    int64_t pulse_off, wave_off, sub_off, echo_off;   // output index of leg pulse k: off + k (x row size)
     int64_t item_begin;      // first work item of this leg
     int32_t scene, scanner, platform, q;
     int32_t S, pulses_per_item;    // pulses per work item

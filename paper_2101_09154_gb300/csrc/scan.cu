@@ -170,8 +170,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         const DevScanner& sn = P.scanners[lg.scanner];
         const DevScene& sc = P.scenes[lg.scene];
         const int S = lg.S;
-        const int64_t p0 = (int64_t)(item - lg.item_begin) * lg.pulses_per_item;
-        const int pc = (int)min((int64_t)lg.pulses_per_item, lg.n_pulses - p0);
+        const int64_t p0 = lg.k_first + (int64_t)(item - lg.item_begin) * lg.pulses_per_item;
+        const int pc = (int)min((int64_t)lg.pulses_per_item, lg.k_first + lg.n_pulses - p0);
         const int nb = sn.n_bins;
         const int K = sn.max_echoes;
         const float dt = (float)sn.bin_ns;

@@ -73,3 +73,7 @@ def test_invalid_arguments_return_codes_without_a_gpu(lib):
     code = lib.helios_scan_legs(None, 0, None, 0, None, 0, ctypes.byref(opts), ctypes.byref(outs), None)
     assert code == -1
     assert b"n_scenes" in lib.helios_last_error()
+    code = lib.helios_scan_legs_host(None, 0, None, 0, None, 0, ctypes.byref(opts), ctypes.byref(outs),
+                                     1024, None)
+    assert code == -1
+    assert b"n_scenes" in lib.helios_last_error()
