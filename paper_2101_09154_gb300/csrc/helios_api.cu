@@ -146,9 +146,17 @@ struct LegPlan {
     int64_t total_pulses = 0, wave = 0, sub = 0, echo = 0;
 };
 
+// Pulses per work item: whole batches of `sub` pulses.  Stochastic scans take
+// up to 256 (the cone walk groups ~32 pulses per warp); expected-mode scans
+// keep one batch, since their larger per-warp scratch leaves no shared memory
+// for a longer item at two blocks per SM.
+static int32_t item_pulses(int32_t sub, int mode) {
+    return mode == HELIOS_MODE_EXPECTED ? sub : sub * (256 / sub);
+}
+
 static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_scanners,
                                const helios_leg_desc* legs, int32_t n_legs, int32_t n_scenes,
-                               int rays_per_item, LegPlan& P) {
+                               int rays_per_item, int mode, LegPlan& P) {
     if (n_legs < 0 || (n_legs > 0 && !legs)) return set_error(HELIOS_ERR_INVALID_ARG, "legs is NULL");
     if (n_scanners < 1 || n_scanners > kMaxScanners || !scanners)
         return set_error(HELIOS_ERR_INVALID_ARG, "n_scanners must be in 1..%d", kMaxScanners);
@@ -196,9 +204,7 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         d.S = subray_count(q);
         int ppi = rays_per_item / d.S;
         d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
-        // an item holds whole batches, up to 256 pulses (the cone walk
-        // groups 32 pulses per warp)
-        d.pulses_per_item = d.pulses_per_sub * (256 / d.pulses_per_sub);
+        d.pulses_per_item = item_pulses(d.pulses_per_sub, mode);
         d.leg_id = L.leg_id;
         d.pulse_off = P.total_pulses;
         d.wave_off = P.wave;
@@ -337,7 +343,7 @@ helios_status helios_output_layout(const helios_scanner_desc* scanners, int32_t 
                                    helios_layout* totals) {
     g_err.clear();
     LegPlan P;
-    helios_status st = plan_legs(scanners, n_scanners, legs, n_legs, -1, 768, P);
+    helios_status st = plan_legs(scanners, n_scanners, legs, n_legs, -1, 768, HELIOS_MODE_STOCHASTIC, P);
     if (st != HELIOS_OK) return st;
     for (int l = 0; l < n_legs; ++l) {
         if (pulse_offset) pulse_offset[l] = P.legs[l].pulse_off;
@@ -375,7 +381,7 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
     if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
     LegPlan P;
-    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, P);
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, opts->mode, P);
     if (st != HELIOS_OK) return st;
     ScanLaunch L;
     for (int i = 0; i < n_scenes; ++i) L.scenes.push_back(dev_scene(scenes[i]));
@@ -421,7 +427,7 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     if (threads % 32 != 0 || threads < 64 || threads > 256)
         return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
     LegPlan P;
-    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, 256, P);
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, 256, HELIOS_MODE_EXPECTED, P);
     if (st != HELIOS_OK) return st;
     AdjointLaunch L;
     for (int i = 0; i < n_scenes; ++i) {
@@ -532,7 +538,7 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         d.S = subray_count(q);
         int ppi = rays / d.S;
         d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
-        d.pulses_per_item = d.pulses_per_sub * (256 / d.pulses_per_sub);
+        d.pulses_per_item = item_pulses(d.pulses_per_sub, opts->mode);
         d.leg_id = L.leg_id;
         d.pulse_off = pulses;
         d.wave_off = wave;
@@ -640,7 +646,7 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
     int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
     if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
     LegPlan P;
-    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, P);
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, opts->mode, P);
     if (st != HELIOS_OK) return st;
     if (P.total_pulses == 0) return HELIOS_OK;
 
