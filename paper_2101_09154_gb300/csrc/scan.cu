@@ -51,11 +51,6 @@ __device__ __forceinline__ double warp_min(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-__device__ __forceinline__ float warp_maxf(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // add one return (delay tau relative to the window start, power P) to the
 // warp's waveform; every bin is touched by one lane, returns come in order
 __device__ __forceinline__ void accumulate(float* W, int nb, const DevScanner& sn, float dt,
@@ -398,9 +393,17 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (ff_less(r, rmin)) rmin = r;
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    FF other = {__shfl_xor_sync(full, rmin.hi, o), __shfl_xor_sync(full, rmin.lo, o)};
-                    if (ff_less(other, rmin)) rmin = other;
+                {
+                    // warp minimum of the float pairs: the hi parts are >= 0, so their
+                    // bits order as unsigned integers; then the least lo among the
+                    // lanes holding that hi (lo mapped to an order-preserving key)
+                    const unsigned hk = __reduce_min_sync(full, __float_as_uint(rmin.hi));
+                    const unsigned lb = __float_as_uint(rmin.lo + 0.0f);
+                    const unsigned lk = __float_as_uint(rmin.hi) == hk
+                                            ? ((lb & 0x80000000u) ? ~lb : (lb | 0x80000000u)) : 0xffffffffu;
+                    const unsigned lm = __reduce_min_sync(full, lk);
+                    rmin.hi = __uint_as_float(hk);
+                    rmin.lo = __uint_as_float((lm & 0x80000000u) ? (lm & 0x7fffffffu) : ~lm);
                 }
                 uint32_t pflag = s_pflag[pl];
                 float* row = P.out.waveform + lg.wave_off + k * nb;
@@ -439,12 +442,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             hi = max(hi, min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin)));
                         }
                     }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        lo = min(lo, __shfl_xor_sync(full, lo, o));
-                        hi = max(hi, __shfl_xor_sync(full, hi, o));
-                    }
-                    wlo = lo;
-                    whi = hi;
+                    wlo = __reduce_min_sync(full, lo);
+                    whi = __reduce_max_sync(full, hi);
                 }
                 // zero the window's rows in 16-byte groups [zlo, zhi)
                 const int zlo = wlo & ~3, zhi = whi < wlo ? zlo : min(nbw, (whi | 3) + 1);
@@ -729,7 +728,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 // ---- echoes: 3-bin local maxima at or above thr * max(W) ----
                 float wmax = 0.0f;
                 for (int b = wlo + lane; b <= whi; b += 32) wmax = fmaxf(wmax, W[b]);
-                wmax = warp_maxf(wmax);
+                wmax = __uint_as_float(__reduce_max_sync(full, __float_as_uint(fmaxf(wmax, 0.0f))));
                 const float thr = sn.thr_rel * wmax;
                 int count = 0;
                 // outside [wlo, whi] the waveform is exactly zero: no maxima there
@@ -752,19 +751,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             todo &= todo - 1;
                             if (count + __popc(mk & ((1u << src) - 1u)) >= K) break;
                             const float tbin = (float)(base + src) * dt;
-                            float v = -1.0f;
+                            unsigned key = 0u;       // 0: no return; else order of the value
                             int32_t id = -1;
                             if (lane < S) {
                                 const RayRes rr = rrp[lane];
-                                if (rr.id >= 0) { v = rr.P * pulse_shape(sn, tbin - taup[lane]); id = rr.id; }
+                                if (rr.id >= 0) {
+                                    key = __float_as_uint(rr.P * pulse_shape(sn, tbin - taup[lane])) + 1u;
+                                    id = rr.id;
+                                }
                             }
-                            int sl = lane;
-                            for (int o = 16; o > 0; o >>= 1) {
-                                const float ov = __shfl_xor_sync(full, v, o);
-                                const int os = __shfl_xor_sync(full, sl, o);
-                                const int32_t oi = __shfl_xor_sync(full, id, o);
-                                if (ov > v || (ov == v && os < sl)) { v = ov; sl = os; id = oi; }
-                            }
+                            const unsigned kmax = __reduce_max_sync(full, key);
+                            const int win = __ffs(__ballot_sync(full, key == kmax && key != 0u)) - 1;
+                            id = __shfl_sync(full, id, win < 0 ? 0 : win);
                             if (lane == src) obj = id;
                         }
                     }
