@@ -533,24 +533,29 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
 // ---------------------------------------------------------------------------
 // Beam-cone candidate search.  The subrays of a pulse leave one origin inside
 // a cone of half-angle atan(ta) around the pulse axis: a subray point at
-// distance t lies within t * ta of the axis point at the same t.  Every point
-// of the scene is within D (the L1 distance from the origin to the farthest
-// corner of the root box) of the origin, so a box that a subray meets is met
-// by the axis ray once it is grown by R = ta * D on every side: on axis a
-// that widens the slab interval by w_a = R / |d_a| (ta carries a margin for
-// FP32 rounding).  The warp walks the union of its lanes' cones (one pulse
-// per lane) with the stackless scheme of traverse(), without range culling;
-// the leaves met are the pulse's candidate triangles, in walk order.  The
-// closest hit of every subray is among them, so testing a subray against the
-// list gives its traversal result.  n > cap + ecap: the list overflowed.
+// distance t lies within t * ta of the axis point at the same t.  A box all of
+// whose points are within D of the origin (D: distance to its farthest
+// corner) and that a subray meets is therefore met by the axis ray once it is
+// grown by R = ta * D on every side: on axis a that widens the slab interval
+// by R / |d_a| (ta carries a margin for FP32 rounding).  The warp walks the
+// union of its lanes' cones (one pulse per lane) with the stackless scheme of
+// traverse(), without range culling; the leaves met are the pulse's candidate
+// triangles, in walk order.  The closest hit of every subray is among them,
+// so testing a subray against the list gives its traversal result.
+// n > cap + ecap: the list overflowed.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool cone_slab(const RayF& r, const float w[3], const float b[6]) {
+__device__ __forceinline__ bool cone_slab(const RayF& r, float ta, const float ad[3], const float b[6]) {
+    const float fx = fmaxf(fabsf(b[0] - r.ox), fabsf(b[3] - r.ox));
+    const float fy = fmaxf(fabsf(b[1] - r.oy), fabsf(b[4] - r.oy));
+    const float fz = fmaxf(fabsf(b[2] - r.oz), fabsf(b[5] - r.oz));
+    const float R = ta * sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
     float tx0 = fmaf(b[0], r.idx, -r.oix), tx1 = fmaf(b[3], r.idx, -r.oix);
     float ty0 = fmaf(b[1], r.idy, -r.oiy), ty1 = fmaf(b[4], r.idy, -r.oiy);
     float tz0 = fmaf(b[2], r.idz, -r.oiz), tz1 = fmaf(b[5], r.idz, -r.oiz);
-    float tmn = fmaxf(fmaxf(fminf(tx0, tx1) - w[0], fminf(ty0, ty1) - w[1]),
-                      fmaxf(fminf(tz0, tz1) - w[2], 0.0f));
-    float tmx = fminf(fminf(fmaxf(tx0, tx1) + w[0], fmaxf(ty0, ty1) + w[1]), fmaxf(tz0, tz1) + w[2]);
+    float tmn = fmaxf(fmaxf(fminf(tx0, tx1) - R * ad[0], fminf(ty0, ty1) - R * ad[1]),
+                      fmaxf(fminf(tz0, tz1) - R * ad[2], 0.0f));
+    float tmx = fminf(fminf(fmaxf(tx0, tx1) + R * ad[0], fmaxf(ty0, ty1) + R * ad[1]),
+                      fmaxf(tz0, tz1) + R * ad[2]);
     return tmn <= tmx;
 }
 
@@ -562,32 +567,7 @@ __device__ __forceinline__ void cone_store(int32_t* cand, int cap, int32_t* ext,
     else if (i < cap + ecap) ext[i - cap] = t;
 }
 
-// per-axis slab widening of a pulse's cone (see above)
-__device__ __forceinline__ void cone_widths(const DevScene& S, const RayF& r, float ta, float w[3]) {
-    float b0[6], b1[6];
-    if (S.n_int > 0) {
-        const float4 n0 = __ldg(S.nodes), n1 = __ldg(S.nodes + 1), n2 = __ldg(S.nodes + 2);
-        child_box(n0, n1, n2, false, b0);
-        child_box(n0, n1, n2, true, b1);
-    } else {
-        const float4 a = __ldg(S.tris), b = __ldg(S.tris + 1), c = __ldg(S.tris + 2);
-        b0[0] = fminf(a.x, fminf(b.x, c.x)); b0[1] = fminf(a.y, fminf(b.y, c.y)); b0[2] = fminf(a.z, fminf(b.z, c.z));
-        b0[3] = fmaxf(a.x, fmaxf(b.x, c.x)); b0[4] = fmaxf(a.y, fmaxf(b.y, c.y)); b0[5] = fmaxf(a.z, fmaxf(b.z, c.z));
-        for (int i = 0; i < 6; ++i) b1[i] = b0[i];
-    }
-    const float o[3] = {r.ox, r.oy, r.oz};
-    float D = 0.0f;
-    for (int a = 0; a < 3; ++a) {
-        const float lo = fminf(b0[a], b1[a]), hi = fmaxf(b0[a + 3], b1[a + 3]);
-        D += fmaxf(fabsf(lo - o[a]), fabsf(hi - o[a]));
-    }
-    const float R = ta * D;
-    w[0] = R * fabsf(r.idx);
-    w[1] = R * fabsf(r.idy);
-    w[2] = R * fabsf(r.idz);
-}
-
-__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, const float w[3],
+__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, float ta,
                                                 bool active, int32_t* cand, int cap, int32_t* ext,
                                                 int ecap, int& n) {
     const unsigned full = 0xffffffffu;
@@ -603,6 +583,7 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
     const bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
     const bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
     const bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
+    const float ad[3] = {fabsf(r.idx), fabsf(r.idy), fabsf(r.idz)};
     uint64_t trail0 = 0, trail1 = 0;   // bit d: far child at depth d still pending
     int cur = 0, depth = 0;
     bool down = true, live = active;
@@ -622,8 +603,8 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
             float bn[6], bf[6];
             child_box(n0, n1, n2, !pos, bn);
             child_box(n0, n1, n2, pos, bf);
-            bool hn = live && cone_slab(r, w, bn);
-            bool hf = live && cone_slab(r, w, bf);
+            bool hn = live && cone_slab(r, ta, ad, bn);
+            bool hf = live && cone_slab(r, ta, ad, bf);
             if (cn < 0) {
                 if (hn) { cone_store(cand, cap, ext, ecap, n, ~cn); ++n; }
                 hn = false;

@@ -235,12 +235,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 subray_dir_ff(f, s_sc[0], dh, dl);     // subray 0: the pulse axis
                 RayF ray;
                 make_ray(f.oh, dh, ray);
-                float w[3];
-                cone_widths(sc, ray, ta, w);
                 int32_t* ext = P.cext ? P.cext + ((size_t)blockIdx.x * P.pc_cap + (act ? pl : 0)) * P.cext_cap
                                       : nullptr;
                 int n;
-                cone_candidates(sc, ray, w, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, ext,
+                cone_candidates(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap, ext,
                                 P.cext_cap, n);
                 if (act) s_ncand[pl] = n;
             }
