@@ -310,6 +310,73 @@ __global__ void k_refit(const float4* tris, int n, const int* child, const int* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// 4-wide collapse for the beam-cone walk: every internal node at even depth
+// becomes a node of the 4-wide tree holding its grandchildren (or a leaf child
+// directly), so the walk takes half as many dependent steps.  Node layout
+// (8 x float4): lo.x, lo.y, lo.z, hi.x, hi.y, hi.z of slots 0..3, the slot
+// references (>= 0: 4-wide node, < 0: leaf ~triangle), then (parent, valid
+// slot mask, 0, 0).
+// ---------------------------------------------------------------------------
+__global__ void k_depth(const float4* nodes, int n_int, uint32_t* even) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0, p = __float_as_int(nodes[4 * (size_t)i + 3].z);
+    for (int guard = 0; p >= 0 && guard < 4096; ++guard) {
+        ++d;
+        p = __float_as_int(nodes[4 * (size_t)p + 3].z);
+    }
+    even[i] = (d & 1) ? 0u : 1u;
+}
+
+__global__ void k_fill4(const float4* nodes, int n_int, const uint32_t* even, const uint32_t* idx,
+                        float4* nodes4) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || !even[i]) return;
+    const float4* nd = nodes + 4 * (size_t)i;
+    const float4 n3 = nd[3];
+    float lo[3][4], hi[3][4];
+    int ref[4] = {0, 0, 0, 0}, valid = 0, k = 0;
+    for (int c = 0; c < 2; ++c) {
+        const int ch = __float_as_int(c == 0 ? n3.x : n3.y);
+        float b[6];
+        child_box(nd[0], nd[1], nd[2], c == 1, b);
+        if (ch < 0) {
+            for (int a = 0; a < 3; ++a) { lo[a][k] = b[a]; hi[a][k] = b[3 + a]; }
+            ref[k] = ch;
+            valid |= 1 << k;
+            ++k;
+        } else {
+            const float4* cd = nodes + 4 * (size_t)ch;
+            const float4 c3 = cd[3];
+            for (int g = 0; g < 2; ++g) {
+                const int gc = __float_as_int(g == 0 ? c3.x : c3.y);
+                float gb[6];
+                child_box(cd[0], cd[1], cd[2], g == 1, gb);
+                for (int a = 0; a < 3; ++a) { lo[a][k] = gb[a]; hi[a][k] = gb[3 + a]; }
+                ref[k] = gc < 0 ? gc : (int)idx[gc];
+                valid |= 1 << k;
+                ++k;
+            }
+        }
+    }
+    for (; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) { lo[a][k] = 0.0f; hi[a][k] = 0.0f; }
+        ref[k] = 0;
+    }
+    int parent = -1;
+    const int p1 = __float_as_int(n3.z);
+    if (p1 >= 0) parent = (int)idx[__float_as_int(nodes[4 * (size_t)p1 + 3].z)];
+    float4* o = nodes4 + 8 * (size_t)idx[i];
+    for (int a = 0; a < 3; ++a) {
+        o[a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+        o[3 + a] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+    }
+    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
+                       __int_as_float(ref[3]));
+    o[7] = make_float4(__int_as_float(parent), __int_as_float(valid), 0.0f, 0.0f);
+}
+
 int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 struct StreamBufs {
@@ -450,11 +517,37 @@ helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStre
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error("BVH build kernels", e);
+    // 4-wide tree: flag even-depth internal nodes, number them, count them
+    const int ni = n > 1 ? n - 1 : 0;
+    uint32_t* even = nullptr;
+    uint32_t* idx = nullptr;
+    if (ni > 0) {
+        even = (uint32_t*)B.get(sizeof(uint32_t) * (size_t)ni);
+        idx = (uint32_t*)B.get(sizeof(uint32_t) * (size_t)ni);
+        if (B.err != cudaSuccess) return set_error(HELIOS_ERR_OOM, "BVH scratch allocation failed: %s", cudaGetErrorString(B.err));
+        k_depth<<<blocks_for(ni, 256), 256, 0, st>>>(s->nodes, ni, even);
+        e = cudaMemcpyAsync(idx, even, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = exclusive_scan(idx, ni, B);
+        if (e != cudaSuccess) return set_cuda_error("BVH 4-wide numbering", e);
+    }
     int flag = 0;
+    uint32_t last[2] = {0, 0};
     e = cudaMemcpyAsync(&flag, bounds + 6, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ni > 0) e = cudaMemcpyAsync(&last[0], idx + ni - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ni > 0) e = cudaMemcpyAsync(&last[1], even + ni - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_cuda_error("BVH build", e);
     if (flag) return set_error(HELIOS_ERR_INVALID_ARG, "a face index is outside its mesh's vertex range");
+    if (ni > 0) {
+        s->n_node4 = (int64_t)last[0] + last[1];
+        e = cudaMalloc(&s->nodes4, sizeof(float4) * 8 * (size_t)s->n_node4);
+        if (e != cudaSuccess) return set_cuda_error("4-wide node allocation", e);
+        s->bytes += (int64_t)sizeof(float4) * 8 * s->n_node4;
+        k_fill4<<<blocks_for(ni, 256), 256, 0, st>>>(s->nodes, ni, even, idx, s->nodes4);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_cuda_error("BVH 4-wide fill", e);
+    }
     return HELIOS_OK;
 }
 

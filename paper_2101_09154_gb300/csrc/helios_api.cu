@@ -120,6 +120,8 @@ static DevScene dev_scene(const helios_scene* s) {
     DevScene d;
     memset(&d, 0, sizeof(d));
     d.nodes = s->nodes;
+    d.nodes4 = s->nodes4;
+    d.n_node4 = (int32_t)s->n_node4;
     d.tris = s->tris;
     d.tri_index = s->tri_index;
     for (int m = 0; m < s->n_mesh; ++m) d.refl[m] = s->refl[m];
@@ -301,6 +303,7 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
     helios_status r = build_bvh(s, desc, st);
     if (r != HELIOS_OK) {
         cudaStreamSynchronize(st);
+        cudaFree(s->nodes4);
         cudaFree(s->nodes);
         cudaFree(s->tris);
         cudaFree(s->tri_index);
@@ -318,6 +321,7 @@ helios_status helios_free_scene(helios_scene* scene) {
     cudaGetDevice(&cur);
     if (cur != scene->device) cudaSetDevice(scene->device);
     cudaFree(scene->nodes);
+    cudaFree(scene->nodes4);
     cudaFree(scene->tris);
     cudaFree(scene->tri_index);
     if (cur != scene->device) cudaSetDevice(cur);

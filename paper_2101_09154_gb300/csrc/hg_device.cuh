@@ -43,12 +43,14 @@ constexpr int kBrick = 1 << kBrickLog2;
 
 struct DevScene {
     const float4* nodes;
+    const float4* nodes4;       // 4-wide collapse of the same tree (8 float4 per node)
     const float4* tris;
     const int32_t* tri_index;   // global triangle id -> packed (sorted) position
     const float* refl[kMaxMesh];
     const float* density;
     int32_t mesh_first[kMaxMesh + 1];
     int32_t n_tri, n_int, n_mesh, has_grid;
+    int32_t n_node4;
     int32_t dims[3];
     float G, leaf_refl, cell;
     float g0[3];
@@ -638,6 +640,90 @@ __device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r
         int axis = __float_as_int(n3.w) & 3;
         bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
         cur = pos ? __float_as_int(n3.y) : __float_as_int(n3.x);
+        ++depth;
+        down = true;
+    }
+}
+
+// The same walk over the 4-wide collapse: a node's four slot boxes are tested
+// per lane, leaves met go to the lane's list, and the slots of internal
+// children met by any lane are visited in slot order; a 4-bit mask per level
+// (192 bits for the 48 levels a 95-level binary tree collapses to) holds the
+// slots still pending.
+__device__ __forceinline__ float f4c(const float4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ int i4c(const int4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void cone_candidates4(const DevScene& S, const RayF& r, float ta,
+                                                 bool active, int32_t* cand, int cap,
+                                                 int32_t* ext, int ecap, int& n) {
+    const unsigned full = 0xffffffffu;
+    n = 0;
+    if (S.n_tri == 0) return;
+    if (S.n_int == 0) {
+        if (active) cand[n++] = 0;
+        return;
+    }
+    if (__ballot_sync(full, active) == 0u) return;
+    const float ad[3] = {fabsf(r.idx), fabsf(r.idy), fabsf(r.idz)};
+    uint64_t tr0 = 0, tr1 = 0, tr2 = 0;   // 4 bits per level: slots still pending
+    int cur = 0, depth = 0;
+    bool down = true, live = active;
+    const int max_steps = 4 * S.n_node4 + 8;
+    for (int step = 0;; ++step) {
+        if (step >= max_steps || depth >= 48) {
+            if (live) n = cap + ecap + 1;
+            break;
+        }
+        const float4* nd = S.nodes4 + 8 * (size_t)cur;
+        if (down) {
+            const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+            const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
+            const int4 rf = __ldg(reinterpret_cast<const int4*>(nd + 6));
+            const int vm = __ldg(reinterpret_cast<const int4*>(nd + 7)).y;
+            unsigned hm = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float b[6] = {f4c(lx, k), f4c(ly, k), f4c(lz, k), f4c(hx, k), f4c(hy, k), f4c(hz, k)};
+                if (live && ((vm >> k) & 1) && cone_slab(r, ta, ad, b)) {
+                    const int ref = i4c(rf, k);
+                    if (ref < 0) {
+                        cone_store(cand, cap, ext, ecap, n, ~ref);
+                        ++n;
+                    } else {
+                        hm |= 1u << k;
+                    }
+                }
+            }
+            live = live && n <= cap + ecap;
+            const unsigned m = __reduce_or_sync(full, live ? hm : 0u);
+            if (m) {
+                const int first = __ffs(m) - 1;
+                const uint64_t rest = (uint64_t)(m & (m - 1)) << (4 * (depth & 15));
+                if (depth < 16) tr0 |= rest; else if (depth < 32) tr1 |= rest; else tr2 |= rest;
+                cur = i4c(rf, first);
+                ++depth;
+                continue;
+            }
+            down = false;
+            continue;
+        }
+        if (cur == 0) break;
+        const int parent = __ldg(reinterpret_cast<const int4*>(nd + 7)).x;
+        --depth;
+        const int sh = 4 * (depth & 15);
+        const uint64_t tw = depth < 16 ? tr0 : (depth < 32 ? tr1 : tr2);
+        const unsigned rest = (unsigned)(tw >> sh) & 15u;
+        cur = parent;
+        if (!rest) continue;
+        if (!__any_sync(full, live)) break;
+        const int first = __ffs(rest) - 1;
+        const uint64_t clr = ~((uint64_t)(1u << first) << sh);
+        if (depth < 16) tr0 &= clr; else if (depth < 32) tr1 &= clr; else tr2 &= clr;
+        cur = i4c(__ldg(reinterpret_cast<const int4*>(S.nodes4 + 8 * (size_t)parent + 6)), first);
         ++depth;
         down = true;
     }

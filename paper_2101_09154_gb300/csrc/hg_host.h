@@ -18,6 +18,8 @@ struct helios_scene {
     float4* nodes;            // [n_int][4]
     float4* tris;             // [n_tri][3]
     int32_t* tri_index;       // [n_tri] global id -> packed position
+    float4* nodes4;           // [n_node4][8]: 4-wide collapse (beam-cone walk)
+    int64_t n_node4;
     const float* refl[hg::kMaxMesh];
     int32_t mesh_first[hg::kMaxMesh + 1];
     int64_t mesh_faces[hg::kMaxMesh];
