@@ -362,22 +362,33 @@ __device__ __forceinline__ float sel3(int k, float x, float y, float z) {
     return k == 0 ? x : (k == 1 ? y : z);
 }
 
-__device__ __forceinline__ void make_ray(const float o[3], const float d[3], RayF& r) {
+// origin and watertight-test setup (Woop, Benthin & Wald, JCGT 2013): all a
+// ray needs for tri_hit
+__device__ __forceinline__ void make_ray_tri(const float o[3], const float d[3], RayF& r) {
     r.ox = o[0]; r.oy = o[1]; r.oz = o[2];
-    float dx = d[0], dy = d[1], dz = d[2];
-    r.idx = safe_inv(dx); r.idy = safe_inv(dy); r.idz = safe_inv(dz);
-    r.oix = r.ox * r.idx; r.oiy = r.oy * r.idy; r.oiz = r.oz * r.idz;
-    // watertight test setup (Woop, Benthin & Wald, JCGT 2013)
-    float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    const float dx = d[0], dy = d[1], dz = d[2];
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
     int ky = kx == 2 ? 0 : kx + 1;
-    float dkz = sel3(kz, dx, dy, dz);
+    const float dkz = sel3(kz, dx, dy, dz);
     if (dkz < 0.0f) { int t = kx; kx = ky; ky = t; }
     r.kx = kx; r.ky = ky; r.kz = kz;
-    r.sx = sel3(kx, dx, dy, dz) / dkz;
-    r.sy = sel3(ky, dx, dy, dz) / dkz;
-    r.sz = 1.0f / dkz;
+    const float inv = 1.0f / dkz;
+    r.sx = sel3(kx, dx, dy, dz) * inv;
+    r.sy = sel3(ky, dx, dy, dz) * inv;
+    r.sz = inv;
+}
+
+// slab-test setup (box tests of the traversals)
+__device__ __forceinline__ void make_ray_slab(const float d[3], RayF& r) {
+    r.idx = safe_inv(d[0]); r.idy = safe_inv(d[1]); r.idz = safe_inv(d[2]);
+    r.oix = r.ox * r.idx; r.oiy = r.oy * r.idy; r.oiz = r.oz * r.idz;
+}
+
+__device__ __forceinline__ void make_ray(const float o[3], const float d[3], RayF& r) {
+    make_ray_tri(o, d, r);
+    make_ray_slab(d, r);
 }
 
 // slab test of one box against [0, tmax]
@@ -757,7 +768,7 @@ __device__ __forceinline__ float refine_hit_ff(const DevScene& S, int t, const f
     float den = nx * dh[0] + ny * dh[1] + nz * dh[2];
     float n2 = nx * nx + ny * ny + nz * nz;
     cos_inc = fminf(fabsf(den) * rsqrtf(n2), 1.0f);
-    return num / den;
+    return __fdividef(num, den);
 }
 
 // FP32 plane distance along dh from oh to triangle t: an anchor for
@@ -963,8 +974,8 @@ __device__ __forceinline__ float return_power(const DevScanner& sn, float R, flo
     float z = sn.zk * (R - sn.focus);
     float w2 = sn.w0sq * (1.0f + z * z);
     float r = R * tan_a;
-    float Is = expf(-2.0f * r * r / w2);
-    return sn.pconst * Is * rho * cos_inc / (R * R);
+    float Is = __expf(__fdividef(-2.0f * r * r, w2));
+    return __fdividef(sn.pconst * Is * rho * cos_inc, R * R);
 }
 
 // pulse shape at time x (ns) relative to the return's delay

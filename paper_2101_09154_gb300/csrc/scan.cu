@@ -264,7 +264,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 float dh[3], dl[3];
                 subray_dir_ff(f, s_sc[s], dh, dl);
                 RayF ray;
-                make_ray(f.oh, dh, ray);
+                make_ray_tri(f.oh, dh, ray);
                 float tb = 3.0e38f;
                 int hit = -1;
                 uint32_t fl = 0;
@@ -283,6 +283,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         }
                     }
                 }
+                if (walk) make_ray_slab(dh, ray);
                 traverse(sc, ray, walk, tb, hit, fl);   // pulses whose list overflowed
                 RayRes rr;
                 rr.Rh = CUDART_INF_F;
