@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     for (;;) {
                         VoxSeg v;
                         if (!march_current(sc, mch, v)) break;
-                        float dens = voxel_density(sc, mch, v);
+                        float dens = voxel_density<true>(sc, mch, v);
                         if (dens > 0.0f) {
                             FF t_in, t_out;
                             march_segment_ff(mch, v, t_in, t_out);
@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 T *= a;
                             }
                         }
-                        if (!march_step(mch, v, fl)) break;
+                        // an empty brick is crossed in one jump
+                        if (!(dens < 0.0f ? march_skip_brick(sc, mch, fl) : march_step(mch, v, fl))) break;
                     }
                 }
                 float A_tri = 0.0f;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     for (;;) {
                         VoxSeg v;
                         if (!march_current(sc, mch, v)) break;
-                        float dens = voxel_density(sc, mch, v);
+                        float dens = voxel_density<true>(sc, mch, v);
                         if (dens > 0.0f) {
                             FF t_in, t_out;
                             march_segment_ff(mch, v, t_in, t_out);
@@ -286,7 +287,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 Tb *= a;
                             }
                         }
-                        if (!march_step(mch, v, fl)) break;
+                        // an empty brick is crossed in one jump
+                        if (!(dens < 0.0f ? march_skip_brick(sc, mch, fl) : march_step(mch, v, fl))) break;
                     }
                 }
             }

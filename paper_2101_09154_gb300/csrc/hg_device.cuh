@@ -551,9 +551,8 @@ __device__ __forceinline__ void traverse(const DevScene& S, const RayF& r, bool 
 // corner) and that a subray meets is therefore met by the axis ray once it is
 // grown by R = ta * D on every side: on axis a that widens the slab interval
 // by R / |d_a| (ta carries a margin for FP32 rounding).  The warp walks the
-// union of its lanes' cones (one pulse per lane) with the stackless scheme of
-// traverse(), without range culling; the leaves met are the pulse's candidate
-// triangles, in walk order.  The closest hit of every subray is among them,
+// union of its lanes' cones (one pulse per lane), without range culling; the
+// leaves met are the pulse's candidate triangles, in walk order.  The closest hit of every subray is among them,
 // so testing a subray against the list gives its traversal result.
 // n > cap + ecap: the list overflowed.
 // ---------------------------------------------------------------------------
@@ -580,87 +579,11 @@ __device__ __forceinline__ void cone_store(int32_t* cand, int cap, int32_t* ext,
     else if (i < cap + ecap) ext[i - cap] = t;
 }
 
-__device__ __forceinline__ void cone_candidates(const DevScene& S, const RayF& r, float ta,
-                                                bool active, int32_t* cand, int cap, int32_t* ext,
-                                                int ecap, int& n) {
-    const unsigned full = 0xffffffffu;
-    n = 0;
-    if (S.n_tri == 0) return;
-    if (S.n_int == 0) {
-        if (active) cand[n++] = 0;
-        return;
-    }
-    unsigned am = __ballot_sync(full, active);
-    if (am == 0u) return;
-    int rep = __ffs(am) - 1;
-    const bool px = __shfl_sync(full, r.idx, rep) >= 0.0f;
-    const bool py = __shfl_sync(full, r.idy, rep) >= 0.0f;
-    const bool pz = __shfl_sync(full, r.idz, rep) >= 0.0f;
-    const float ad[3] = {fabsf(r.idx), fabsf(r.idy), fabsf(r.idz)};
-    uint64_t trail0 = 0, trail1 = 0;   // bit d: far child at depth d still pending
-    int cur = 0, depth = 0;
-    bool down = true, live = active;
-    const int max_steps = 3 * S.n_int + 8;
-    for (int step = 0;; ++step) {
-        if (step >= max_steps) {
-            if (live) n = cap + ecap + 1;
-            break;
-        }
-        const float4* nd = S.nodes + 4 * (size_t)cur;
-        if (down) {
-            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-            int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-            int axis = __float_as_int(n3.w) & 3;
-            bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
-            int cn = pos ? c0 : c1, cf = pos ? c1 : c0;
-            float bn[6], bf[6];
-            child_box(n0, n1, n2, !pos, bn);
-            child_box(n0, n1, n2, pos, bf);
-            bool hn = live && cone_slab(r, ta, ad, bn);
-            bool hf = live && cone_slab(r, ta, ad, bf);
-            if (cn < 0) {
-                if (hn) { cone_store(cand, cap, ext, ecap, n, ~cn); ++n; }
-                hn = false;
-            }
-            if (cf < 0) {
-                if (hf) { cone_store(cand, cap, ext, ecap, n, ~cf); ++n; }
-                hf = false;
-            }
-            live = live && n <= cap + ecap;
-            bool an = __any_sync(full, hn && live), af = __any_sync(full, hf && live);
-            if (an) {
-                if (af) { if (depth < 64) trail0 |= 1ull << depth; else trail1 |= 1ull << (depth - 64); }
-                cur = cn; ++depth;
-                continue;
-            }
-            if (af) { cur = cf; ++depth; continue; }
-            down = false;
-            continue;
-        }
-        if (cur == 0) break;
-        int parent = __float_as_int(__ldg(nd + 3).z);
-        --depth;
-        bool pending = depth < 64 ? ((trail0 >> depth) & 1ull) : ((trail1 >> (depth - 64)) & 1ull);
-        cur = parent;
-        if (!pending) continue;
-        if (depth < 64) trail0 &= ~(1ull << depth); else trail1 &= ~(1ull << (depth - 64));
-        if (!__any_sync(full, live)) break;
-        // some lane met the far child when `parent` was entered; no range
-        // culling here, so that still holds: descend without a re-test
-        float4 n3 = __ldg(S.nodes + 4 * (size_t)parent + 3);
-        int axis = __float_as_int(n3.w) & 3;
-        bool pos = axis == 0 ? px : (axis == 1 ? py : pz);
-        cur = pos ? __float_as_int(n3.y) : __float_as_int(n3.x);
-        ++depth;
-        down = true;
-    }
-}
-
-// The same walk over the 4-wide collapse: a node's four slot boxes are tested
-// per lane, leaves met go to the lane's list, and the slots of internal
-// children met by any lane are visited in slot order; a 4-bit mask per level
-// (192 bits for the 48 levels a 95-level binary tree collapses to) holds the
-// slots still pending.
+// The walk runs over the 4-wide collapse of the tree: a node's four slot
+// boxes are tested per lane, leaves met go to the lane's list, and the slots
+// of internal children met by any lane are visited in slot order; a 4-bit
+// mask per level (192 bits for the 48 levels a 95-level binary tree collapses
+// to) holds the slots still pending.
 __device__ __forceinline__ float f4c(const float4& v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
@@ -911,12 +834,14 @@ __device__ __forceinline__ bool march_current(const DevScene& S, const March& m,
 
 // Density of the current voxel.  A voxel inside a brick whose occupancy bit is
 // clear has density <= 0 (or NaN) by construction of the mask, so the grid is
-// not read there; every caller treats such a voxel as empty.
+// not read there; 0 is returned, or with MARK_EMPTY -1, which a march may
+// answer with march_skip_brick.  Every caller treats either as empty.
+template <bool MARK_EMPTY = false>
 __device__ __forceinline__ float voxel_density(const DevScene& S, const March& m, const VoxSeg& v) {
     if (S.occ != nullptr) {
         int b = ((m.iz >> kBrickLog2) * S.bdims[1] + (m.iy >> kBrickLog2)) * S.bdims[0] +
                 (m.ix >> kBrickLog2);
-        if (!((__ldg(&S.occ[b >> 5]) >> (b & 31)) & 1u)) return 0.0f;
+        if (!((__ldg(&S.occ[b >> 5]) >> (b & 31)) & 1u)) return MARK_EMPTY ? -1.0f : 0.0f;
     }
     return __ldg(&S.density[v.vid]);
 }
@@ -962,6 +887,92 @@ __device__ __forceinline__ bool march_step(March& m, const VoxSeg& v, uint32_t& 
         m.tnz = cross32(m.sz > 0 ? m.iz + 1 : m.iz, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
     }
     m.entry_axis = a;
+    return true;
+}
+
+// float-float crossing time of voxel-boundary plane `plane` on axis a
+__device__ __forceinline__ FF plane_ff_at(const March& m, int a, int plane) {
+    const int p0 = a == 0 ? m.px : (a == 1 ? m.py : m.pz);
+    const float f0h = a == 0 ? m.f0hx : (a == 1 ? m.f0hy : m.f0hz);
+    const float f0l = a == 0 ? m.f0lx : (a == 1 ? m.f0ly : m.f0lz);
+    const float ivh = a == 0 ? m.ivhx : (a == 1 ? m.ivhy : m.ivhz);
+    const float ivl = a == 0 ? m.ivlx : (a == 1 ? m.ivly : m.ivlz);
+    float ph, pl;
+    two_prod((float)(plane - p0), m.cell, ph, pl);
+    float sh, sl;
+    two_sum(f0h, ph, sh, sl);
+    sl += f0l + pl;
+    FF n = ff_norm(sh, sl);
+    float th, tl;
+    two_prod(n.hi, ivh, th, tl);
+    tl = fmaf(n.hi, ivl, fmaf(n.lo, ivh, tl));
+    return ff_norm(th, tl);
+}
+
+// From a voxel of an empty brick, jump to the first voxel past the brick.
+// The one-voxel march takes crossings in (time, axis) order, each axis's
+// crossing times being non-decreasing; so it leaves the brick at the least
+// (time, axis) among the three exit planes, and before that it crosses, on
+// every other axis, exactly the inner planes ordered before that event.
+// Taking those crossings here gives the voxel, next-crossing times and entry
+// axis the one-voxel march would reach.  false: the march ends in the brick.
+__device__ __forceinline__ bool march_skip_brick(const DevScene& S, March& m, uint32_t& flags) {
+    const int bx0 = m.ix & ~(kBrick - 1), by0 = m.iy & ~(kBrick - 1), bz0 = m.iz & ~(kBrick - 1);
+    const int bx1 = min(bx0 + kBrick - 1, S.dims[0] - 1);
+    const int by1 = min(by0 + kBrick - 1, S.dims[1] - 1);
+    const int bz1 = min(bz0 + kBrick - 1, S.dims[2] - 1);
+    // exit planes (voxel-boundary indices) in the step directions
+    const int ex = m.sx > 0 ? bx1 + 1 : bx0, ey = m.sy > 0 ? by1 + 1 : by0, ez = m.sz > 0 ? bz1 + 1 : bz0;
+    const float Tx = cross32(ex, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
+    const float Ty = cross32(ey, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
+    const float Tz = cross32(ez, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
+    int a = 0;
+    float T = Tx;
+    if (Ty < T) { a = 1; T = Ty; }
+    if (Tz < T) { a = 2; T = Tz; }
+    if (T >= m.t_end.hi) {
+        // FP32 ordering says the march may end in the brick; confirm in float-float
+        if (!ff_less(plane_ff_at(m, a, a == 0 ? ex : (a == 1 ? ey : ez)), m.t_end)) return false;
+    }
+    const int ox = m.ix, oy = m.iy, oz = m.iz;
+    // the other axes: inner crossings ordered before (T, a)
+    if (a != 0 && m.sx != 0) {
+        for (int k = 0; k < kBrick; ++k) {
+            const int pl = m.sx > 0 ? m.ix + 1 : m.ix;
+            if (pl == ex) break;
+            const float t = cross32(pl, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
+            if (!(t < T || t == T)) break;      // ties go to x, the lowest axis
+            m.ix += m.sx;
+        }
+    }
+    if (a != 1 && m.sy != 0) {
+        for (int k = 0; k < kBrick; ++k) {
+            const int pl = m.sy > 0 ? m.iy + 1 : m.iy;
+            if (pl == ey) break;
+            const float t = cross32(pl, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
+            if (!(t < T || (t == T && a == 2))) break;
+            m.iy += m.sy;
+        }
+    }
+    if (a != 2 && m.sz != 0) {
+        for (int k = 0; k < kBrick; ++k) {
+            const int pl = m.sz > 0 ? m.iz + 1 : m.iz;
+            if (pl == ez) break;
+            const float t = cross32(pl, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
+            if (!(t < T)) break;                // z loses every tie
+            m.iz += m.sz;
+        }
+    }
+    // the exit axis: through the brick and out of it
+    if (a == 0) m.ix = m.sx > 0 ? bx1 + 1 : bx0 - 1;
+    else if (a == 1) m.iy = m.sy > 0 ? by1 + 1 : by0 - 1;
+    else m.iz = m.sz > 0 ? bz1 + 1 : bz0 - 1;
+    m.tnx = cross32(m.sx > 0 ? m.ix + 1 : m.ix, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
+    m.tny = cross32(m.sy > 0 ? m.iy + 1 : m.iy, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
+    m.tnz = cross32(m.sz > 0 ? m.iz + 1 : m.iz, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
+    m.entry_axis = a;
+    m.steps_left -= abs(m.ix - ox) + abs(m.iy - oy) + abs(m.iz - oz);
+    if (m.steps_left <= 0) { flags |= kPfMarchCap; return false; }
     return true;
 }
 

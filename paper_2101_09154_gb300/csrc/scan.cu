@@ -238,12 +238,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 int32_t* ext = P.cext ? P.cext + ((size_t)blockIdx.x * P.pc_cap + (act ? pl : 0)) * P.cext_cap
                                       : nullptr;
                 int n;
-                if (sc.nodes4 != nullptr)
-                    cone_candidates4(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap,
-                                     ext, P.cext_cap, n);
-                else
-                    cone_candidates(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap,
-                                    ext, P.cext_cap, n);
+                cone_candidates4(sc, ray, ta, act, s_cand + (size_t)(act ? pl : 0) * kConeCap, kConeCap,
+                                 ext, P.cext_cap, n);
                 if (act) s_ncand[pl] = n;
             }
             __syncthreads();
