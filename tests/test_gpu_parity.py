@@ -204,6 +204,59 @@ def test_adjoint_matches_oracle(hg):
     assert np.allclose(gd2, gd, rtol=1e-4, atol=1e-7 * scale)
 
 
+def test_adjoint_central_differences(hg):
+    """The GPU adjoint against central differences of the GPU forward: L2 loss
+    of the expected-mode waveform against a scan of perturbed densities, on 64
+    random traversed voxels (seed 2) and on each ground triangle's
+    reflectance.  The loss is summed in FP64; the tolerance covers the O(h^2)
+    difference error and the forward's and adjoint's Hermite truncations."""
+    w = scenes.uls_voxels(seed=4, n=32, n_pulses=1200, n_bins=384, agl=10.0, speed=1.0, prf=1000.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    ref_d = scenes.perturbed_density(w.scenes[0].grids[0].density, seed=1)
+    gref = hg.Scene(scenes.Scene(meshes=w.scenes[0].meshes,
+                                 grids=[scenes.VoxelGrid(**{**w.scenes[0].grids[0].__dict__,
+                                                           "density": ref_d})]))
+    Wref = hg.scan([gref], [sc], [leg], mode=1)[0]["waveform"].double()
+
+    def loss():
+        out, _ = hg.scan([gs], [sc], [leg], mode=1)
+        return float(((out["waveform"].double() - Wref) ** 2).sum())
+
+    out, _ = hg.scan([gs], [sc], [leg], mode=1)
+    gW = 2.0 * (out["waveform"] - Wref.float())
+    grads = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"])
+    torch.cuda.synchronize()
+    gd = to_np(grads[0]["density"][0]).ravel().astype(np.float64)
+    gr = to_np(grads[0]["reflectance"][0]).astype(np.float64)
+    dens = gs.density[0].view(-1)
+    d0 = to_np(dens).astype(np.float64)
+    traversed = np.nonzero((gd != 0.0) & (d0 > 0.0))[0]
+    assert traversed.size >= 64
+    pick = np.random.default_rng(2).choice(traversed, 64, replace=False)
+    scale = np.abs(gd).max()
+    for v in pick:
+        h = 0.05 * d0[v]
+        dens[v] = float(d0[v] + h)
+        lp = loss()
+        dens[v] = float(d0[v] - h)
+        lm = loss()
+        dens[v] = float(d0[v])
+        fd = (lp - lm) / (2.0 * h)
+        assert abs(fd - gd[v]) <= 3e-2 * abs(gd[v]) + 2e-3 * scale, (int(v), fd, gd[v])
+    refl = gs.reflectance[0]
+    r0 = to_np(refl).astype(np.float64)
+    for t in range(r0.size):
+        h = 0.05 * r0[t]
+        refl[t] = float(r0[t] + h)
+        lp = loss()
+        refl[t] = float(r0[t] - h)
+        lm = loss()
+        refl[t] = float(r0[t])
+        fd = (lp - lm) / (2.0 * h)
+        assert abs(fd - gr[t]) <= 1e-2 * abs(gr[t]) + 1e-6 * np.abs(gr).max(), (t, fd, gr[t])
+
+
 def test_autograd_function(hg):
     w = scenes.uls_voxels(seed=9, n=24, n_pulses=400, n_bins=256, agl=8.0, speed=1.0, prf=800.0)
     sc, leg = w.scanners[0], w.legs[0]
