@@ -461,7 +461,7 @@ def adjoint_ratio(args):
 # --------------------------------------------------------------------------
 # the oracle on the host cores
 # --------------------------------------------------------------------------
-def oracle_rate(w, target_s, pulses_cap=None):
+def oracle_rate(w, target_s, pulses_cap=None, one_core=False):
     """Time the FP64 oracle (as it stands) on an evenly strided pulse sample."""
     import oracle
     osc = oracle.OracleScene(w.scenes[w.legs[0].scene_index])
@@ -480,10 +480,18 @@ def oracle_rate(w, target_s, pulses_cap=None):
     oracle.scan(osc, sc, leg, rows, threads=cores)
     dt = time.time() - t0
     q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else sc.beam_sample_quality
-    return {"value": len(rows) / dt, "unit": "pulses/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(rows)} evenly spaced pulses of the {leg.n_pulses}-pulse leg "
-                      f"({oracle.subray_count(q)} subrays each), {dt:.1f} s of FP64 CPU work "
-                      f"on {cores} threads"}
+    res = {"value": len(rows) / dt, "unit": "pulses/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(rows)} evenly spaced pulses of the {leg.n_pulses}-pulse leg "
+                     f"({oracle.subray_count(q)} subrays each), {dt:.1f} s of FP64 CPU work "
+                     f"on {cores} threads"}
+    if one_core and cores > 1:
+        # the same oracle on one thread, on every (10 x cores)-th pulse of the
+        # sample (about a tenth of the multi-thread run's wall time)
+        r1 = rows[:: cores * 10] if len(rows) > 100 else rows
+        t0 = time.time()
+        oracle.scan(osc, sc, leg, r1, threads=1)
+        res["value_1core"] = len(r1) / (time.time() - t0)
+    return res
 
 
 def run_reference(args, D):
@@ -523,7 +531,7 @@ def main():
         res, w = run_ours(args, D)
         if D.rank == 0:
             if not args.no_extras and D.world == 1:
-                res["cpu_baseline"] = oracle_rate(w, args.cpu_sample_s)
+                res["cpu_baseline"] = oracle_rate(w, args.cpu_sample_s, one_core=True)
             print(json.dumps(res), flush=True)
     finally:
         D.close()
