@@ -398,6 +398,80 @@ def uls_voxels(seed: int = 2, n: int = 256, n_pulses: int = 1_000_000, n_bins: i
                          f"PRF {prf/1e3:.0f} kHz, q=2, N_b={n_bins}")
 
 
+def _rect_mesh(p0, e1, e2, cell):
+    """Planar rectangle p0 + u e1 + v e2 (u, v in [0, 1]) in square-ish cells of
+    about ``cell`` metres, two triangles per cell."""
+    p0, e1, e2 = (np.asarray(x, dtype=np.float64) for x in (p0, e1, e2))
+    nu = max(1, int(round(np.linalg.norm(e1) / cell)))
+    nv = max(1, int(round(np.linalg.norm(e2) / cell)))
+    u = np.linspace(0.0, 1.0, nu + 1)
+    v = np.linspace(0.0, 1.0, nv + 1)
+    U, V = np.meshgrid(u, v, indexing="ij")
+    verts = p0 + U[..., None] * e1 + V[..., None] * e2
+    idx = np.arange((nu + 1) * (nv + 1)).reshape(nu + 1, nv + 1)
+    a, b = idx[:-1, :-1].ravel(), idx[1:, :-1].ravel()
+    c, d = idx[1:, 1:].ravel(), idx[:-1, 1:].ravel()
+    faces = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)], 0)
+    return verts.reshape(-1, 3), faces
+
+
+def urban_scene(rng, length=2000.0, facade_cell=0.17, ground_cell=1.0, half_width=50.0):
+    """Street planes along x plus extruded rectangular building footprints on
+    both sides, facades and roofs tessellated at ``facade_cell``.  Mesh 0 is
+    the street, mesh 1 the buildings; reflectance is seeded per building
+    (U[0.2, 0.8]) plus per-triangle N(0, 0.05), and U[0.1, 0.3] on the street."""
+    gv, gf = _rect_mesh((-30.0, -half_width, 0.0), (length + 60.0, 0.0, 0.0),
+                        (0.0, 2.0 * half_width, 0.0), ground_cell)
+    street = _mesh(gv, gf, rng.uniform(0.1, 0.3, size=gf.shape[0]), 1)
+    verts, faces, refl, nv = [], [], [], 0
+    for side in (-1.0, 1.0):
+        x = -20.0
+        while x < length + 20.0:
+            w = rng.uniform(8.0, 25.0)
+            depth = rng.uniform(8.0, 20.0)
+            setback = rng.uniform(8.0, 14.0)
+            h = rng.uniform(6.0, 30.0)
+            base = rng.uniform(0.2, 0.8)
+            y0 = setback if side > 0 else -setback - depth
+            y1 = y0 + depth
+            parts = [((x, y0, 0.0), (w, 0.0, 0.0), (0.0, 0.0, h)),        # facade at y0
+                     ((x, y1, 0.0), (w, 0.0, 0.0), (0.0, 0.0, h)),        # facade at y1
+                     ((x, y0, 0.0), (0.0, depth, 0.0), (0.0, 0.0, h)),    # gable at x
+                     ((x + w, y0, 0.0), (0.0, depth, 0.0), (0.0, 0.0, h)),
+                     ((x, y0, h), (w, 0.0, 0.0), (0.0, depth, 0.0))]      # roof
+            for p0, e1, e2 in parts:
+                v, f = _rect_mesh(p0, e1, e2, facade_cell)
+                verts.append(v)
+                faces.append(f + nv)
+                refl.append(np.clip(base + rng.normal(0.0, 0.05, size=f.shape[0]), 0.05, 0.95))
+                nv += v.shape[0]
+            x += w + rng.uniform(0.0, 4.0)
+    buildings = _mesh(np.concatenate(verts, 0), np.concatenate(faces, 0), np.concatenate(refl, 0), 2)
+    return Scene(meshes=[street, buildings])
+
+
+def urban_mls(seed: int = 4, length: float = 2000.0, speed: float = 10.0, prf: float = 100_000.0,
+              facade_cell: float = 0.17, n_bins: int = 512, q: int = 3) -> Workload:
+    """Mobile laser scanning along an urban street: a profile scanner (head
+    rotating 100 rev/s, its spin plane across the street) on a vehicle at
+    2.5 m driving ``length`` metres at ``speed``."""
+    rng = np.random.default_rng(seed)
+    scene = urban_scene(rng, length=length, facade_cell=facade_cell)
+    sc = Scanner(prf_hz=prf, divergence_rad=0.3e-3, beam_sample_quality=q,
+                 pulse_shape=PULSE_GAUSSIAN, pulse_fwhm_ns=4.0, bin_ns=0.25, n_bins=n_bins,
+                 max_echoes=8, echo_threshold_rel=0.05, range_noise_sigma_m=0.01,
+                 deflector=DEFL_ROTATING_HEAD, head_rate_rad_s=2.0 * math.pi * 100.0,
+                 scan_freq_hz=1.0, scan_angle_max_rad=0.0)
+    n_pulses = int(round(length / speed * prf))
+    leg = Leg(scene_index=0, platform=PLATFORM_LINEAR, start=(0.0, 0.0, 2.5), end=(length, 0.0, 2.5),
+              speed_mps=speed, attitude_rpy=(0.0, math.pi / 2, 0.0), n_pulses=n_pulses, t0=0.0,
+              leg_id=4)
+    return Workload(f"urban_mls_{scene.n_triangles}tri_{n_pulses}p", [scene], [sc], [leg],
+                    note=f"street + extruded buildings ({scene.n_triangles} triangles, facade cell "
+                         f"{facade_cell} m), {length:.0f} m at {speed} m/s, profile head 100 rev/s, "
+                         f"PRF {prf/1e3:.0f} kHz, q={q}, N_b={n_bins}")
+
+
 def perturbed_density(density: np.ndarray, seed: int = 1, rel: float = 0.1) -> np.ndarray:
     """Reference-scan densities: non-empty voxels scaled by (1 + rel * N(0,1))."""
     rng = np.random.default_rng(seed)

@@ -102,6 +102,16 @@ def test_expected_mode_long_voxel_column(hg):
     assert (ref["echo_count"] > 0).all()
 
 
+def test_urban_mls_rotating_head_37_subrays(hg):
+    """Street + extruded buildings scanned by a rotating profile head (pitched
+    attitude) on a moving vehicle, 37 subrays; every 7th pulse of 300 000."""
+    w = scenes.urban_mls(length=30.0, facade_cell=0.5)
+    rows = np.arange(0, w.legs[0].n_pulses, 7)
+    _, _, res = run_both(hg, w, seed=6, rows=rows)
+    stats = compare(*res[0])
+    assert stats["echoes"] > 30000
+
+
 @pytest.mark.parametrize("q", [0, 1, 3])
 def test_subray_qualities_and_carlsson_pulse(hg, q):
     """S = 1, 7, 37 (more subrays than warp lanes) with the Eq. beam_time pulse."""
