@@ -20,6 +20,8 @@ seeded stand-ins with the same structure are used):
                      ground, flown with a rotating polygon mirror.
 * ``batched_legs`` - many legs of uneven length and subray quality over a pool
                      of terrain tiles and voxel blocks.
+* ``urban_mls``    - a street with extruded building footprints scanned by a
+                     rotating profile head on a vehicle (mobile laser scanning).
 """
 from __future__ import annotations
 
