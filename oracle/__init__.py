@@ -26,7 +26,7 @@ _lib = None
 
 NO_WINDOW = -(2 ** 31)
 F_EDGE, F_TIE, F_VOX, F_WIN, F_ECHO, F_OBJ = 1, 2, 4, 8, 16, 32
-F_OVERFLOW, F_NOHIT = 256, 512
+F_OVERFLOW, F_NOHIT, F_FIT = 256, 512, 1024
 F_GEOMETRY = F_EDGE | F_TIE | F_VOX | F_WIN        # waveform may differ
 F_DECISION = F_GEOMETRY | F_ECHO | F_OBJ           # echo lists may differ
 
@@ -77,7 +77,8 @@ class SceneIn(C.Structure):
 class Out(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("window_bin", "waveform", "echo_count", "echo_bin",
                                             "echo_amp", "echo_range", "echo_range_clean",
-                                            "echo_object", "subray_hit", "subray_range", "flags")]
+                                            "echo_object", "echo_width", "subray_hit", "subray_range",
+                                            "flags")]
 
 
 def lib():
@@ -98,6 +99,8 @@ def lib():
                 getattr(l, f).argtypes = [C.POINTER(Scanner), C.c_double]
                 getattr(l, f).restype = C.c_double
             l.or_subray_intensity.argtypes = [C.POINTER(Scanner), C.c_double, C.c_double]
+            l.or_echo_width.argtypes = [d3, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]
+            l.or_echo_width.restype = C.c_double
             l.or_subray_intensity.restype = C.c_double
             l.or_pulse_shape.argtypes = [C.POINTER(Scanner), C.c_double]
             l.or_pulse_shape.restype = C.c_double
@@ -327,9 +330,20 @@ def triangle_power(scanner, Is, R, refl, cos_inc):
     return lib().or_triangle_power(C.byref(scanner_struct(scanner)), Is, R, refl, cos_inc)
 
 
+def echo_width(W, p, sigma_b):
+    """Fitted Gaussian sigma (bins) of the echo at bin p of waveform W (Sec. 3.4
+    echo width); returns (sigma, near_tie)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    tie = C.c_int(0)
+    s = lib().or_echo_width(W.ctypes.data_as(C.POINTER(C.c_double)), int(W.shape[0]), int(p),
+                            float(sigma_b), C.byref(tie))
+    return s, bool(tie.value)
+
+
 def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_window=None,
-         threads=0):
-    """Simulate the given pulse indices of one leg; returns a dict of numpy arrays."""
+         threads=0, echo_width=False):
+    """Simulate the given pulse indices of one leg; returns a dict of numpy arrays
+    (with ``echo_width``, the fitted echo widths in ns, Gaussian pulses only)."""
     if pulses is None:
         pulses = np.arange(leg.n_pulses, dtype=np.int64)
     pulses = np.ascontiguousarray(pulses, dtype=np.int64)
@@ -343,6 +357,8 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
              echo_range_clean=np.zeros((n, K)), echo_object=np.zeros((n, K), np.int32),
              subray_hit=np.zeros((n, S), np.int32), subray_range=np.zeros((n, S)),
              flags=np.zeros(n, np.uint32))
+    if echo_width:
+        r["echo_width"] = np.zeros((n, K))
     out = Out(**{k: _ptr(v) for k, v in r.items()})
     fw = None
     if fixed_window is not None:

@@ -68,6 +68,7 @@ typedef struct {
     double* echo_range;          /* [n][K]     with range noise */
     double* echo_range_clean;    /* [n][K]     without noise */
     int32_t* echo_object;        /* [n][K]     primitive id (tri, or n_tri + voxel) */
+    double* echo_width;          /* [n][K]     fitted Gaussian sigma (ns); NULL: no fit */
     int32_t* subray_hit;         /* [n][S]     event primitive, -1 none */
     double* subray_range;        /* [n][S] */
     uint32_t* flags;             /* [n]        OR_F_* */
@@ -84,6 +85,7 @@ typedef struct {
 #define OR_F_OBJ       (1u << 5)  /* echo object argmax near-tie */
 #define OR_F_OVERFLOW  (1u << 8)  /* more echoes than max_echoes */
 #define OR_F_NOHIT     (1u << 9)  /* no subray returned */
+#define OR_F_FIT       (1u << 10) /* an echo-width fit step decided within tolerance */
 
 void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 double or_uniform24(uint64_t w);
@@ -95,6 +97,13 @@ void or_subray_dir(const or_scanner* sn, int q, int s, const double d[3], double
 double or_beam_width(const or_scanner* sn, double R);
 double or_subray_intensity(const or_scanner* sn, double R, double alpha);
 double or_pulse_shape(const or_scanner* sn, double t_ns);
+/* Echo width (Sec. 3.4, optional output): Gaussian fit to W[0..nb) around the
+ * echo at bin p over bins p -/+ ceil(2 sigma_b), sigma_b the emitted pulse's
+ * sigma in bins; 10 Levenberg-Marquardt iterations from (W[p], p, sigma_b).
+ * Returns the fitted sigma in bins; *near_tie is set when an accept/reject
+ * decision on a step of more than 1e-5 s was within 1e-6 of the window's
+ * energy (sum of W^2). */
+double or_echo_width(const double* W, int nb, int p, double sigma_b, int* near_tie);
 double or_triangle_power(const or_scanner* sn, double Is, double R, double refl, double cos_inc);
 
 or_scene* or_scene_build(const or_scene_in* in);

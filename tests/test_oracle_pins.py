@@ -537,3 +537,43 @@ def test_adjoint_matches_central_differences():
         fd = (loss(refl=rp) - loss(refl=rm)) / (2 * hh)
         assert abs(fd - d_refl[t]) <= 1e-6 * abs(d_refl[t]) + 1e-12
     scene.meshes[0].reflectance[:] = refl0
+
+
+# --------------------------------------------------------------------------
+# echo width (Sec. 3.4: optional non-linear least-squares estimate)
+# --------------------------------------------------------------------------
+
+def test_echo_width_fit_recovers_an_exact_gaussian():
+    """Samples of A exp(-(b - mu)^2 / (2 s^2)) are fitted back to s, from the
+    standard start (the peak bin, the peak value, the emitted pulse's sigma)."""
+    b = np.arange(120, dtype=np.float64)
+    for A, mu, s in [(3.0, 40.3, 6.1), (0.7, 55.8, 8.9), (1.0, 60.0, 6.8), (2.5, 70.45, 5.2)]:
+        W = A * np.exp(-0.5 * ((b - mu) / s) ** 2)
+        got, _ = oracle.echo_width(W, int(round(mu)), 6.8)
+        assert abs(got - s) < 1e-8 * s
+    # a model error (wrong Jacobian, sign, or damping) shows as a miss here:
+    # two overlapping Gaussians are not one, and the fit must not claim so
+    W = np.exp(-0.5 * ((b - 50) / 6.8) ** 2) + 0.6 * np.exp(-0.5 * ((b - 58) / 6.8) ** 2)
+    got, _ = oracle.echo_width(W, 50, 6.8)
+    assert got > 7.0
+
+
+def test_single_flat_target_echo_width_is_the_pulse_sigma():
+    """One target at normal incidence returns the emitted pulse shape, so the
+    fitted width is the pulse's sigma; a tilted target spreads the subrays'
+    delays and widens the echo."""
+    sc, leg = _nadir_leg()
+    sig = sc.pulse_fwhm_ns / (2 * math.sqrt(2 * math.log(2)))
+    osc = oracle.OracleScene(scenes.flat_target(31.7, 0.0, half=100.0))
+    r = oracle.scan(osc, sc, leg, mode=0, seed=1, echo_width=True)
+    assert r["echo_count"][0] == 1
+    assert abs(r["echo_width"][0, 0] - sig) < 1e-6 * sig
+    assert (r["echo_width"][0, 1:] == 0).all()
+    widths = []
+    sc.beam_sample_quality = 3
+    sc.divergence_rad = 20e-3          # a wide beam: metres of range spread on a tilt
+    for tilt in np.radians([0.0, 30.0, 60.0]):
+        osc = oracle.OracleScene(scenes.flat_target(31.7, tilt, half=100.0))
+        r = oracle.scan(osc, sc, leg, mode=0, seed=1, echo_width=True)
+        widths.append(r["echo_width"][0, 0])
+    assert widths[0] < widths[1] < widths[2]
