@@ -309,9 +309,24 @@ def run_ours(args, D):
             res["adjoint_forward_ratio"] = res["adjoint"]["adjoint_forward_ratio"]
             if args.workload == "als":
                 res["batched"] = batched_compare(args)
+                res["echo_width_fit"] = echo_width_cost(w, gsc, layout, args)
             if args.workload == "mls":
                 res["reflectance_fit"] = reflectance_fit(args)
     return res, w
+
+
+def echo_width_cost(w, gsc, layout, args):
+    """The same scan with the optional echo-width fit on (Sec. 3.4: the paper
+    prices it at x1.3 of the run time): device time and ratio."""
+    import torch
+    import paper_2101_09154_gb300 as hg
+    dev = gsc[0].device
+    o0 = hg.alloc_outputs(layout, dev, subrays=False)
+    o1 = hg.alloc_outputs(layout, dev, subrays=False, echo_width=True)
+    t0 = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, seed=12345, out=o0, subrays=False), 3, 2)
+    t1 = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, seed=12345, out=o1, subrays=False), 3, 2)
+    ne = int(o1["echo_count"].clamp(max=w.scanners[0].max_echoes).sum())
+    return {"ms_without": t0, "ms_with": t1, "ratio": t1 / t0, "echoes_fitted": ne}
 
 
 def reflectance_fit(args):

@@ -221,6 +221,11 @@ typedef struct {
     int32_t* subray_hit;          /* optional: event primitive or -1 */
     float* subray_range;          /* optional */
     uint32_t* status;             /* optional: one word, OR-ed HELIOS_ST_* */
+    float* echo_width;            /* optional [total_pulses][K]: echo width (Sec. 3.4), the sigma
+                                     in ns of a Gaussian fitted to the waveform over the bins
+                                     within 2 pulse sigmas of the echo by 10 Levenberg-Marquardt
+                                     steps; Gaussian pulses only (0 otherwise and in unused
+                                     slots); NULL: not fitted (no cost) */
 } helios_outputs;
 
 typedef struct {

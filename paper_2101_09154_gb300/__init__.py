@@ -95,7 +95,7 @@ class ScanOpts(C.Structure):
 class Outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("waveform", "window_bin", "echo_count", "echo_range",
                                             "echo_amp", "echo_bin", "echo_object", "pulse_flags",
-                                            "subray_hit", "subray_range", "status")]
+                                            "subray_hit", "subray_range", "status", "echo_width")]
 
 
 class Layout(C.Structure):
@@ -292,7 +292,7 @@ def output_layout(scanners, legs):
             "echo_elems": tot.echo_elems}
 
 
-def alloc_outputs(layout, device, subrays=True, status=True):
+def alloc_outputs(layout, device, subrays=True, status=True, echo_width=False):
     torch = _torch()
     P = int(layout["total_pulses"])
     out = {
@@ -310,19 +310,22 @@ def alloc_outputs(layout, device, subrays=True, status=True):
         out["subray_range"] = torch.empty(int(layout["subray_elems"]), dtype=torch.float32, device=device)
     if status:
         out["status"] = torch.zeros(1, dtype=torch.int32, device=device)
+    if echo_width:
+        out["echo_width"] = torch.empty(int(layout["echo_elems"]), dtype=torch.float32, device=device)
     return out
 
 
-def alloc_host_outputs(layout, device, subrays=False, status=True):
+def alloc_host_outputs(layout, device, subrays=False, status=True, echo_width=False):
     """Page-locked host tensors for ``scan_to_host`` (``status`` stays on the device)."""
     torch = _torch()
     dev = alloc_outputs({"total_pulses": 0, "waveform_floats": 0, "echo_elems": 0, "subray_elems": 0},
-                        "cpu", subrays=subrays, status=False)
+                        "cpu", subrays=subrays, status=False, echo_width=echo_width)
     P = int(layout["total_pulses"])
     sizes = {"waveform": layout["waveform_floats"], "window_bin": P, "echo_count": P,
              "echo_range": layout["echo_elems"], "echo_amp": layout["echo_elems"],
              "echo_bin": layout["echo_elems"], "echo_object": layout["echo_elems"], "pulse_flags": P,
-             "subray_hit": layout["subray_elems"], "subray_range": layout["subray_elems"]}
+             "subray_hit": layout["subray_elems"], "subray_range": layout["subray_elems"],
+             "echo_width": layout["echo_elems"]}
     out = {k: torch.empty(int(sizes[k]), dtype=t.dtype, pin_memory=True) for k, t in dev.items()}
     if status:
         out["status"] = torch.zeros(1, dtype=torch.int32, device=device)
@@ -342,13 +345,15 @@ def _as_list(x):
 
 
 def scan(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, persistent=False, out=None,
-         subrays=True, stream=None, block_threads=0, rays_per_block=0, blocks_per_sm=0):
-    """Run helios_scan_legs; returns (outputs dict of device tensors, layout)."""
+         subrays=True, stream=None, block_threads=0, rays_per_block=0, blocks_per_sm=0,
+         echo_width=False):
+    """Run helios_scan_legs; returns (outputs dict of device tensors, layout).
+    ``echo_width`` adds the fitted echo widths (an optional, costed output)."""
     scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
     layout = output_layout(scanners, legs)
     dev = scenes[0].device
     if out is None:
-        out = alloc_outputs(layout, dev, subrays=subrays)
+        out = alloc_outputs(layout, dev, subrays=subrays, echo_width=echo_width)
     sh = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     sd = (ScannerDesc * len(scanners))(*[scanner_desc(s) for s in scanners])
     ld = (LegDesc * max(len(legs), 1))(*[leg_desc(l) for l in legs])

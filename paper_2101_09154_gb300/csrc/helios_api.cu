@@ -84,6 +84,7 @@ static DevScanner derive_scanner(const helios_scanner_desc& s) {
         double gk2 = 1.4426950408889634 / (2.0 * sig * sig);
         d.gk2 = (float)gk2;
         d.inv_s2 = (float)(1.0 / (sig * sig));
+        d.sigma_bins = (float)(sig / s.bin_ns);
         d.cut_lo = d.cut_hi = (float)std::sqrt(30.0 / gk2);
         d.n_pre = (int32_t)std::ceil(3.0 * sig / s.bin_ns);
         d.echo_offset_ns = 0.0;
@@ -402,6 +403,7 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     L.out.subray_hit = out->subray_hit;
     L.out.subray_range = out->subray_range;
     L.out.status = out->status;
+    L.out.echo_width = out->echo_width;
     L.seed = opts->seed;
     L.mode = opts->mode;
     L.persistent = opts->persistent;
@@ -567,6 +569,7 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
     o.subray_hit = out->subray_hit;
     o.subray_range = out->subray_range;
     o.status = out->status;
+    o.echo_width = out->echo_width;
     if (pulses == 0) return HELIOS_OK;
     return launch_scan_static(g_plan_scenes, n_scenes, g_plan_scanners, n_scanners, g_plan_legs,
                               n_legs, o, opts->seed, opts->mode, threads, opts->blocks_per_sm,
@@ -686,13 +689,14 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
     }
     const helios_outputs& H = *host_out;
     const bool sub = H.subray_hit != nullptr;
-    size_t off[10], bytes = 0;
-    const size_t sz[10] = {sizeof(float) * mx_w, sizeof(int32_t) * mx_p, sizeof(int32_t) * mx_p,
+    size_t off[11], bytes = 0;
+    const size_t sz[11] = {sizeof(float) * mx_w, sizeof(int32_t) * mx_p, sizeof(int32_t) * mx_p,
                            sizeof(float) * mx_e, H.echo_amp ? sizeof(float) * mx_e : 0,
                            H.echo_bin ? sizeof(int32_t) * mx_e : 0, H.echo_object ? sizeof(int32_t) * mx_e : 0,
                            H.pulse_flags ? sizeof(uint8_t) * mx_p : 0, sub ? sizeof(int32_t) * mx_s : 0,
-                           H.subray_range ? sizeof(float) * mx_s : 0};
-    for (int i = 0; i < 10; ++i) { off[i] = bytes; bytes += align256(sz[i]); }
+                           H.subray_range ? sizeof(float) * mx_s : 0,
+                           H.echo_width ? sizeof(float) * mx_e : 0};
+    for (int i = 0; i < 11; ++i) { off[i] = bytes; bytes += align256(sz[i]); }
 
     HostStaging hs;
     hs.s0 = (cudaStream_t)cuda_stream;
@@ -733,6 +737,7 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
         L.out.subray_hit = sub ? reinterpret_cast<int32_t*>(base + off[8]) : nullptr;
         L.out.subray_range = H.subray_range ? reinterpret_cast<float*>(base + off[9]) : nullptr;
         L.out.status = H.status;
+        L.out.echo_width = H.echo_width ? reinterpret_cast<float*>(base + off[10]) : nullptr;
         // the chunk's legs, their outputs indexed from the slot's start
         L.legs.clear();
         for (const Piece& pc : chunks[c]) {
@@ -751,7 +756,7 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.s1, hs.scanned[slot], 0);
         if (e != cudaSuccess) return set_cuda_error("chunk event", e);
         struct Copy { void* dst; const void* src; size_t n; };
-        const Copy cp[10] = {
+        const Copy cp[11] = {
             {H.waveform + lo.w, L.out.waveform, sizeof(float) * (hi.w - lo.w)},
             {H.window_bin + lo.p, L.out.window_bin, sizeof(int32_t) * (hi.p - lo.p)},
             {H.echo_count + lo.p, L.out.echo_count, sizeof(int32_t) * (hi.p - lo.p)},
@@ -761,7 +766,8 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
             {H.echo_object ? H.echo_object + lo.e : nullptr, L.out.echo_object, sizeof(int32_t) * (hi.e - lo.e)},
             {H.pulse_flags ? H.pulse_flags + lo.p : nullptr, L.out.pulse_flags, sizeof(uint8_t) * (hi.p - lo.p)},
             {sub ? H.subray_hit + lo.s : nullptr, L.out.subray_hit, sizeof(int32_t) * (hi.s - lo.s)},
-            {H.subray_range ? H.subray_range + lo.s : nullptr, L.out.subray_range, sizeof(float) * (hi.s - lo.s)}};
+            {H.subray_range ? H.subray_range + lo.s : nullptr, L.out.subray_range, sizeof(float) * (hi.s - lo.s)},
+            {H.echo_width ? H.echo_width + lo.e : nullptr, L.out.echo_width, sizeof(float) * (hi.e - lo.e)}};
         for (const Copy& x : cp) {
             if (!x.dst || x.n == 0) continue;
             e = cudaMemcpyAsync(x.dst, x.src, x.n, cudaMemcpyDeviceToHost, hs.s1);

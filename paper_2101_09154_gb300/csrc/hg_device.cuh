@@ -79,6 +79,7 @@ struct DevScanner {
     float bin_hi, bin_lo;    // bin_ns as a float pair
     float echo_offset_f;     // echo_offset_ns in FP32
     float inv_s2;            // Gaussian: 1 / sigma^2 [1/ns^2]
+    float sigma_bins;        // Gaussian: sigma / bin
     int32_t q_default, pulse_shape, n_bins, max_echoes;
     int32_t deflector, n_az, n_el, n_pre;
 };
@@ -111,6 +112,7 @@ struct Outputs {
     int32_t* subray_hit;
     float* subray_range;
     uint32_t* status;
+    float* echo_width;           // optional: fitted echo sigma (ns), Gaussian pulses
 };
 
 // FP64 pulse pose (origin, unit direction, ONB axes), computed once per pulse.

@@ -72,6 +72,72 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
     }
 }
 
+// sum over the warp by a fixed butterfly, lane 0's value to every lane (so all
+// lanes take the same decisions on it)
+__device__ __forceinline__ float warp_sum_uniform(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Echo width (Sec. 3.4, an optional non-linear least-squares estimate): fit
+// A exp(-(b - mu)^2 / (2 s^2)) to the waveform over the bins within
+// ceil(2 sigma) of the echo bin p (values outside [wlo, whi] are zero), by 10
+// Levenberg-Marquardt steps from (W[p], p, sigma) with the damping lambda on
+// the diagonal (1e-3, /10 on an accepted step, x10 on a rejected one); the
+// 3 x 3 system is solved by Cramer's rule.  Lanes take bins; returns s (bins).
+__device__ float echo_width_fit(const float* W, int nb, int wlo, int whi, int p, float sb, int lane) {
+    const int h = (int)ceilf(2.0f * sb);
+    const int lo = max(0, p - h), hi = min(nb - 1, p + h);
+    auto wv = [&](int b) { return (b >= wlo && b <= whi) ? W[b] : 0.0f; };
+    auto sse = [&](float a, float m, float sg) {
+        float e = 0.0f;
+        for (int b = lo + lane; b <= hi; b += 32) {
+            const float x = ((float)b - m) / sg;
+            const float r = wv(b) - a * expf(-0.5f * x * x);
+            e = fmaf(r, r, e);
+        }
+        return warp_sum_uniform(e);
+    };
+    float A = wv(p), mu = (float)p, sg = sb, lam = 1e-3f;
+    float E = sse(A, mu, sg);
+    for (int it = 0; it < 10; ++it) {
+        float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        const float is2 = 1.0f / (sg * sg);
+        for (int b = lo + lane; b <= hi; b += 32) {
+            const float u = (float)b - mu;
+            const float e = expf(-0.5f * u * u * is2);
+            const float j0 = e, j1 = A * e * u * is2, j2 = j1 * u / sg;
+            const float r = wv(b) - A * e;
+            h00 = fmaf(j0, j0, h00); h01 = fmaf(j0, j1, h01); h02 = fmaf(j0, j2, h02);
+            h11 = fmaf(j1, j1, h11); h12 = fmaf(j1, j2, h12); h22 = fmaf(j2, j2, h22);
+            g0 = fmaf(j0, r, g0); g1 = fmaf(j1, r, g1); g2 = fmaf(j2, r, g2);
+        }
+        h00 = warp_sum_uniform(h00); h01 = warp_sum_uniform(h01); h02 = warp_sum_uniform(h02);
+        h11 = warp_sum_uniform(h11); h12 = warp_sum_uniform(h12); h22 = warp_sum_uniform(h22);
+        g0 = warp_sum_uniform(g0); g1 = warp_sum_uniform(g1); g2 = warp_sum_uniform(g2);
+        const float m00 = h00 * (1.0f + lam), m11 = h11 * (1.0f + lam), m22 = h22 * (1.0f + lam);
+        // cofactors of the symmetric damped matrix
+        const float c00 = m11 * m22 - h12 * h12, c01 = h02 * h12 - h01 * m22, c02 = h01 * h12 - m11 * h02;
+        const float det = m00 * c00 + h01 * c01 + h02 * c02;
+        if (!(fabsf(det) > 0.0f)) break;
+        const float c11 = m00 * m22 - h02 * h02, c12 = h01 * h02 - m00 * h12, c22 = m00 * m11 - h01 * h01;
+        const float id = 1.0f / det;
+        const float dA = (c00 * g0 + c01 * g1 + c02 * g2) * id;
+        const float dm = (c01 * g0 + c11 * g1 + c12 * g2) * id;
+        const float ds = (c02 * g0 + c12 * g1 + c22 * g2) * id;
+        const float s2 = sg + ds;
+        const float E2 = s2 > 0.0f ? sse(A + dA, mu + dm, s2) : CUDART_INF_F;
+        if (E2 < E) {
+            A += dA; mu += dm; sg = s2; E = E2;
+            lam *= 0.1f;
+        } else {
+            lam *= 10.0f;
+        }
+    }
+    return sg;
+}
+
 // Expected-mode returns of one subray in summation order: the voxels along
 // the march (weight T_k (1 - e^{-sigma l}) at the segment midpoint), then the
 // triangle (weight T).  emit(R, weighted power, primitive id).
@@ -414,6 +480,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
                         if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
                         if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
+                        if (P.out.echo_width) P.out.echo_width[eb + e] = 0.0f;
                     }
                     if (lane == 0) {
                         P.out.window_bin[gp] = kNoWindow;
@@ -765,6 +832,17 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (lane == src) obj = id;
                         }
                     }
+                    float ewidth = 0.0f;
+                    if (P.out.echo_width != nullptr && sn.pulse_shape == 0) {
+                        unsigned todo = mk & ((count < K) ? ~0u : 0u);
+                        while (todo) {
+                            const int src = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            if (count + __popc(mk & ((1u << src) - 1u)) >= K) break;
+                            const float wd = echo_width_fit(W, nb, wlo, whi, base + src, sn.sigma_bins, lane);
+                            if (lane == src) ewidth = wd * dt;
+                        }
+                    }
                     if (ismax && pos < K) {
                         if (MODE == 1) {
                             if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
@@ -794,6 +872,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         }
                         P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
                         if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
+                        if (P.out.echo_width) P.out.echo_width[eb + pos] = ewidth;
                         if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
                         if (P.out.echo_object && !mom_path) P.out.echo_object[eb + pos] = obj;
                     }
@@ -875,6 +954,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
                     if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
                     if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
+                    if (P.out.echo_width) P.out.echo_width[eb + e] = 0.0f;
                 }
                 if (lane == 0) {
                     if (count > K) {

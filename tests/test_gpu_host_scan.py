@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 KEYS = ("waveform", "window_bin", "echo_count", "echo_range", "echo_amp", "echo_bin", "echo_object",
-        "pulse_flags", "subray_hit", "subray_range")
+        "pulse_flags", "subray_hit", "subray_range", "echo_width")
 
 
 @pytest.fixture(scope="module")
@@ -29,9 +29,11 @@ def test_host_scan_equals_device_scan(hg, mode, persistent, chunk):
     w = scenes.batched_legs(seed=21, n_legs=6, tile=64, block=24, n_terrain=2, n_voxel=2,
                             min_pulses=300, max_pulses=3000, n_bins=256)
     gsc = [hg.Scene(s) for s in w.scenes]
-    ref, lay = hg.scan(gsc, w.scanners, w.legs, mode=mode, seed=5, persistent=persistent)
+    ref, lay = hg.scan(gsc, w.scanners, w.legs, mode=mode, seed=5, persistent=persistent,
+                       echo_width=True)
+    host = hg.alloc_host_outputs(lay, gsc[0].device, subrays=True, echo_width=True)
     host, lay2 = hg.scan_to_host(gsc, w.scanners, w.legs, mode=mode, seed=5, persistent=persistent,
-                                 subrays=True, chunk_pulses=chunk)
+                                 host_out=host, chunk_pulses=chunk)
     torch.cuda.synchronize()
     assert lay2["total_pulses"] == lay["total_pulses"]
     if chunk < lay["total_pulses"]:

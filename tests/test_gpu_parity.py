@@ -326,3 +326,33 @@ def test_graph_replay_and_autotune_match_direct_call(hg):
     torch.cuda.synchronize()
     for k in ("waveform", "window_bin", "echo_count", "echo_range", "echo_object", "subray_hit"):
         assert torch.equal(out[k], ref[k]), k
+
+
+@pytest.mark.parametrize("name", ["tls", "als"])
+def test_echo_width_fit_matches_oracle(hg, name):
+    """Sec. 3.4 echo width: the GPU's FP32 Levenberg-Marquardt fit against the
+    oracle's FP64 one on the same waveforms, 1e-3 relative, on pulses with no
+    geometry, echo or fit-decision flag."""
+    if name == "tls":
+        w = scenes.tls_tiny(n_az=60, n_el=40)
+    else:
+        w = scenes.als_terrain(seed=5, size=128, n_trees=12, n_pulses=4001, n_bins=512, agl=120.0,
+                               speed=30.0, prf=50_000.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    out, lay = hg.scan([gs], [sc], [leg], seed=3, echo_width=True)
+    torch.cuda.synchronize()
+    ref = oracle.scan(oracle.OracleScene(w.scenes[0]), sc, leg, mode=0, seed=3, echo_width=True)
+    K = sc.max_echoes
+    gw = to_np(out["echo_width"]).reshape(-1, K)
+    gc = to_np(out["echo_count"])
+    ok = (ref["flags"] & (oracle.F_DECISION | oracle.F_OVERFLOW | oracle.F_FIT)) == 0
+    ok &= gc == ref["echo_count"]
+    n = 0
+    for i in np.nonzero(ok)[0]:
+        for e in range(min(gc[i], K)):
+            a, b = gw[i, e], ref["echo_width"][i, e]
+            assert abs(a - b) <= 1e-3 * b, (i, e, a, b)
+            n += 1
+        assert (gw[i, gc[i]:] == 0).all()
+    assert n > (300 if name == "tls" else 500)
