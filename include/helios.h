@@ -273,6 +273,7 @@ HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n
  * All calls share the array: each call zeroes the counters it uses on its
  * stream, and calls whose work overlaps on the GPU (e.g. on two streams) race
  * on them.  opts->persistent is ignored (always one launch per 128 legs).
+ * out->echo_width needs out->echo_bin here (the fit reads the bins back).
  * Arguments, outputs and results are those of helios_scan_legs. */
 HELIOS_API helios_status helios_scan_legs_static(helios_scene* const* scenes, int32_t n_scenes,
                                                  const helios_scanner_desc* scanners,

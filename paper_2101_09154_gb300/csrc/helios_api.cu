@@ -488,6 +488,8 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         return set_error(HELIOS_ERR_INVALID_ARG, "waveform, window_bin, echo_count, echo_range are required");
     if (out->subray_range && !out->subray_hit)
         return set_error(HELIOS_ERR_INVALID_ARG, "subray_range needs subray_hit");
+    if (out->echo_width && !out->echo_bin)
+        return set_error(HELIOS_ERR_INVALID_ARG, "echo_width needs echo_bin in the allocation-free scan");
     const int max_legs = static_scan_max_legs();
     if (n_legs < 0 || (n_legs > 0 && !legs)) return set_error(HELIOS_ERR_INVALID_ARG, "legs is NULL");
     if (n_legs > max_legs)

@@ -72,72 +72,6 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
     }
 }
 
-// sum over the warp by a fixed butterfly, lane 0's value to every lane (so all
-// lanes take the same decisions on it)
-__device__ __forceinline__ float warp_sum_uniform(float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
-
-// Echo width (Sec. 3.4, an optional non-linear least-squares estimate): fit
-// A exp(-(b - mu)^2 / (2 s^2)) to the waveform over the bins within
-// ceil(2 sigma) of the echo bin p (values outside [wlo, whi] are zero), by 10
-// Levenberg-Marquardt steps from (W[p], p, sigma) with the damping lambda on
-// the diagonal (1e-3, /10 on an accepted step, x10 on a rejected one); the
-// 3 x 3 system is solved by Cramer's rule.  Lanes take bins; returns s (bins).
-__device__ float echo_width_fit(const float* W, int nb, int wlo, int whi, int p, float sb, int lane) {
-    const int h = (int)ceilf(2.0f * sb);
-    const int lo = max(0, p - h), hi = min(nb - 1, p + h);
-    auto wv = [&](int b) { return (b >= wlo && b <= whi) ? W[b] : 0.0f; };
-    auto sse = [&](float a, float m, float sg) {
-        float e = 0.0f;
-        for (int b = lo + lane; b <= hi; b += 32) {
-            const float x = ((float)b - m) / sg;
-            const float r = wv(b) - a * expf(-0.5f * x * x);
-            e = fmaf(r, r, e);
-        }
-        return warp_sum_uniform(e);
-    };
-    float A = wv(p), mu = (float)p, sg = sb, lam = 1e-3f;
-    float E = sse(A, mu, sg);
-    for (int it = 0; it < 10; ++it) {
-        float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        const float is2 = 1.0f / (sg * sg);
-        for (int b = lo + lane; b <= hi; b += 32) {
-            const float u = (float)b - mu;
-            const float e = expf(-0.5f * u * u * is2);
-            const float j0 = e, j1 = A * e * u * is2, j2 = j1 * u / sg;
-            const float r = wv(b) - A * e;
-            h00 = fmaf(j0, j0, h00); h01 = fmaf(j0, j1, h01); h02 = fmaf(j0, j2, h02);
-            h11 = fmaf(j1, j1, h11); h12 = fmaf(j1, j2, h12); h22 = fmaf(j2, j2, h22);
-            g0 = fmaf(j0, r, g0); g1 = fmaf(j1, r, g1); g2 = fmaf(j2, r, g2);
-        }
-        h00 = warp_sum_uniform(h00); h01 = warp_sum_uniform(h01); h02 = warp_sum_uniform(h02);
-        h11 = warp_sum_uniform(h11); h12 = warp_sum_uniform(h12); h22 = warp_sum_uniform(h22);
-        g0 = warp_sum_uniform(g0); g1 = warp_sum_uniform(g1); g2 = warp_sum_uniform(g2);
-        const float m00 = h00 * (1.0f + lam), m11 = h11 * (1.0f + lam), m22 = h22 * (1.0f + lam);
-        // cofactors of the symmetric damped matrix
-        const float c00 = m11 * m22 - h12 * h12, c01 = h02 * h12 - h01 * m22, c02 = h01 * h12 - m11 * h02;
-        const float det = m00 * c00 + h01 * c01 + h02 * c02;
-        if (!(fabsf(det) > 0.0f)) break;
-        const float c11 = m00 * m22 - h02 * h02, c12 = h01 * h02 - m00 * h12, c22 = m00 * m11 - h01 * h01;
-        const float id = 1.0f / det;
-        const float dA = (c00 * g0 + c01 * g1 + c02 * g2) * id;
-        const float dm = (c01 * g0 + c11 * g1 + c12 * g2) * id;
-        const float ds = (c02 * g0 + c12 * g1 + c22 * g2) * id;
-        const float s2 = sg + ds;
-        const float E2 = s2 > 0.0f ? sse(A + dA, mu + dm, s2) : CUDART_INF_F;
-        if (E2 < E) {
-            A += dA; mu += dm; sg = s2; E = E2;
-            lam *= 0.1f;
-        } else {
-            lam *= 10.0f;
-        }
-    }
-    return sg;
-}
-
 // Expected-mode returns of one subray in summation order: the voxels along
 // the march (weight T_k (1 - e^{-sigma l}) at the segment midpoint), then the
 // triangle (weight T).  emit(R, weighted power, primitive id).
@@ -480,7 +414,6 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
                         if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
                         if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
-                        if (P.out.echo_width) P.out.echo_width[eb + e] = 0.0f;
                     }
                     if (lane == 0) {
                         P.out.window_bin[gp] = kNoWindow;
@@ -832,17 +765,6 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (lane == src) obj = id;
                         }
                     }
-                    float ewidth = 0.0f;
-                    if (P.out.echo_width != nullptr && sn.pulse_shape == 0) {
-                        unsigned todo = mk & ((count < K) ? ~0u : 0u);
-                        while (todo) {
-                            const int src = __ffs(todo) - 1;
-                            todo &= todo - 1;
-                            if (count + __popc(mk & ((1u << src) - 1u)) >= K) break;
-                            const float wd = echo_width_fit(W, nb, wlo, whi, base + src, sn.sigma_bins, lane);
-                            if (lane == src) ewidth = wd * dt;
-                        }
-                    }
                     if (ismax && pos < K) {
                         if (MODE == 1) {
                             if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
@@ -872,7 +794,6 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         }
                         P.out.echo_range[eb + pos] = fmaf(sn.noise_sigma, z, Rc);
                         if (P.out.echo_amp) P.out.echo_amp[eb + pos] = c;
-                        if (P.out.echo_width) P.out.echo_width[eb + pos] = ewidth;
                         if (P.out.echo_bin) P.out.echo_bin[eb + pos] = b;
                         if (P.out.echo_object && !mom_path) P.out.echo_object[eb + pos] = obj;
                     }
@@ -954,7 +875,6 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     if (P.out.echo_amp) P.out.echo_amp[eb + e] = 0.0f;
                     if (P.out.echo_bin) P.out.echo_bin[eb + e] = -1;
                     if (P.out.echo_object) P.out.echo_object[eb + e] = -1;
-                    if (P.out.echo_width) P.out.echo_width[eb + e] = 0.0f;
                 }
                 if (lane == 0) {
                     if (count > K) {
@@ -982,6 +902,100 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             __syncthreads();   // the batch arrays are reused
         }
     }
+}
+
+// Echo width (Sec. 3.4, an optional non-linear least-squares estimate): fit
+// A exp(-(b - mu)^2 / (2 s^2)) to the waveform row W over the bins within
+// ceil(2 sigma) of the echo bin p, by 10 Levenberg-Marquardt steps from
+// (W[p], p, sigma) with the damping lambda on the diagonal (1e-3, /10 on an
+// accepted step, x10 on a rejected one); the 3 x 3 system is solved by
+// Cramer's rule.  One thread, sums in bin order; returns s (bins).
+__device__ float echo_width_fit(const float* __restrict__ W, int nb, int p, float sb) {
+    const int h = (int)ceilf(2.0f * sb);
+    const int lo = max(0, p - h), hi = min(nb - 1, p + h);
+    auto sse = [&](float a, float m, float sg) {
+        float e = 0.0f;
+        for (int b = lo; b <= hi; ++b) {
+            const float x = ((float)b - m) / sg;
+            const float r = __ldg(W + b) - a * expf(-0.5f * x * x);
+            e = fmaf(r, r, e);
+        }
+        return e;
+    };
+    float A = __ldg(W + p), mu = (float)p, sg = sb, lam = 1e-3f;
+    float E = sse(A, mu, sg);
+    for (int it = 0; it < 10; ++it) {
+        float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        const float is2 = 1.0f / (sg * sg);
+        for (int b = lo; b <= hi; ++b) {
+            const float u = (float)b - mu;
+            const float e = expf(-0.5f * u * u * is2);
+            const float j0 = e, j1 = A * e * u * is2, j2 = j1 * u / sg;
+            const float r = __ldg(W + b) - A * e;
+            h00 = fmaf(j0, j0, h00); h01 = fmaf(j0, j1, h01); h02 = fmaf(j0, j2, h02);
+            h11 = fmaf(j1, j1, h11); h12 = fmaf(j1, j2, h12); h22 = fmaf(j2, j2, h22);
+            g0 = fmaf(j0, r, g0); g1 = fmaf(j1, r, g1); g2 = fmaf(j2, r, g2);
+        }
+        const float m00 = h00 * (1.0f + lam), m11 = h11 * (1.0f + lam), m22 = h22 * (1.0f + lam);
+        // cofactors of the symmetric damped matrix
+        const float c00 = m11 * m22 - h12 * h12, c01 = h02 * h12 - h01 * m22, c02 = h01 * h12 - m11 * h02;
+        const float det = m00 * c00 + h01 * c01 + h02 * c02;
+        if (!(fabsf(det) > 0.0f)) break;
+        const float c11 = m00 * m22 - h02 * h02, c12 = h01 * h02 - m00 * h12, c22 = m00 * m11 - h01 * h01;
+        const float id = 1.0f / det;
+        const float dA = (c00 * g0 + c01 * g1 + c02 * g2) * id;
+        const float dm = (c01 * g0 + c11 * g1 + c12 * g2) * id;
+        const float ds = (c02 * g0 + c12 * g1 + c22 * g2) * id;
+        const float s2 = sg + ds;
+        const float E2 = s2 > 0.0f ? sse(A + dA, mu + dm, s2) : CUDART_INF_F;
+        if (E2 < E) {
+            A += dA; mu += dm; sg = s2; E = E2;
+            lam *= 0.1f;
+        } else {
+            lam *= 10.0f;
+        }
+    }
+    return sg;
+}
+
+// Echo widths of one leg after its scan: one thread per pulse fits its echoes
+// from the stored waveform row (zeros outside the support are stored too);
+// unused slots and non-Gaussian pulses get 0.
+__global__ void __launch_bounds__(256)
+echo_width_kernel(const float* __restrict__ waveform, const int32_t* __restrict__ echo_count,
+                  const int32_t* __restrict__ echo_bin, float* __restrict__ echo_width, DevLeg lg,
+                  int nb, int K, float sigma_bins, float dt, int gaussian) {
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lg.n_pulses; i += nt) {
+        const int64_t k = lg.k_first + i;
+        const int64_t eb = lg.echo_off + k * K;
+        const int n = gaussian ? min(__ldg(echo_count + lg.pulse_off + k), K) : 0;
+        const float* row = waveform + lg.wave_off + k * nb;
+        for (int e = 0; e < K; ++e)
+            echo_width[eb + e] = e < n ? echo_width_fit(row, nb, __ldg(echo_bin + eb + e), sigma_bins) * dt : 0.0f;
+    }
+}
+
+// the echo-width pass of every leg (after the scan, same stream)
+static helios_status launch_echo_widths(const DevLeg* legs, int n_legs, const DevScanner* scanners,
+                                        const Outputs& out, float* echo_width, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int l = 0; l < n_legs; ++l) {
+        const DevLeg& lg = legs[l];
+        if (lg.n_pulses <= 0) continue;
+        const DevScanner& sn = scanners[lg.scanner];
+        const int64_t blocks = (lg.n_pulses + 255) / 256;
+        const int grid = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
+        echo_width_kernel<<<grid, 256, 0, st>>>(out.waveform, out.echo_count, out.echo_bin, echo_width, lg,
+                                                sn.n_bins, sn.max_echoes, sn.sigma_bins, (float)sn.bin_ns,
+                                                sn.pulse_shape == 0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error("echo width kernel launch", e);
+    }
+    return HELIOS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1134,6 +1148,24 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         }
     }
     const int w_stride = warp_stride(L.mode, nb_cap, cb, direct);
+    // the echo-width fit runs after the scan from the stored rows and echo bins
+    // (into stream-ordered scratch when the caller did not ask for the bins)
+    Outputs out = L.out;
+    out.echo_width = nullptr;
+    Free free_ebin{nullptr, st};
+    if (L.out.echo_width != nullptr && out.echo_bin == nullptr) {
+        int64_t ne = 0;
+        for (const DevLeg& lg : L.legs)
+            ne = std::max<int64_t>(ne, lg.echo_off + (lg.k_first + lg.n_pulses) * L.scanners[lg.scanner].max_echoes);
+        const cudaError_t e0 = cudaMallocAsync(reinterpret_cast<void**>(&out.echo_bin),
+                                               sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), st);
+        if (e0 != cudaSuccess) return set_cuda_error("cudaMallocAsync(echo bins)", e0);
+        free_ebin.p = out.echo_bin;
+    }
+    auto widths = [&]() -> helios_status {
+        if (L.out.echo_width == nullptr) return HELIOS_OK;
+        return launch_echo_widths(L.legs.data(), n_legs, L.scanners.data(), out, L.out.echo_width, st);
+    };
 
     if (!L.persistent) {
         for (int l = 0; l < n_legs; ++l) {
@@ -1143,7 +1175,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             for (size_t i = 0; i < L.scanners.size(); ++i) p.scanners[i] = L.scanners[i];
             p.legs[0] = L.legs[l];
             p.legs[0].item_begin = 0;
-            p.out = L.out;
+            p.out = out;
             p.seed = L.seed;
             p.n_legs = 1;
             int64_t items = (L.legs[l].n_pulses + L.legs[l].pulses_per_item - 1) / L.legs[l].pulses_per_item;
@@ -1158,7 +1190,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
             if (s != HELIOS_OK) return s;
         }
-        return HELIOS_OK;
+        return widths();
     }
     // persistent: one launch per group of up to kMaxLegs legs, fed by an atomic queue
     for (int l0 = 0; l0 < n_legs; l0 += kMaxLegs) {
@@ -1175,7 +1207,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
                      L.legs[l0 + l].pulses_per_item;
         }
         if (items >= INT32_MAX) { delete p; return set_error(HELIOS_ERR_UNSUPPORTED, "too many work items"); }
-        p->out = L.out;
+        p->out = out;
         p->seed = L.seed;
         p->n_legs = nl;
         p->n_items = (int32_t)items;
@@ -1194,7 +1226,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         delete p;
         if (s != HELIOS_OK) return s;
     }
-    return HELIOS_OK;
+    return widths();
 }
 
 static_assert(sizeof(ScanParams<kMaxLegs>) <= 32000, "kernel parameters must fit the 32 KB limit");
@@ -1287,6 +1319,8 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         helios_status s = dispatch<kMaxLegs>(p, mode, any_grid, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;
     }
+    // echo widths from the stored rows and bins (the caller provides echo_bin)
+    if (out.echo_width != nullptr) return launch_echo_widths(legs, n_legs, scanners, out, out.echo_width, st);
     return HELIOS_OK;
 }
 
