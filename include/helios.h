@@ -71,6 +71,8 @@ typedef int32_t helios_status;
 #define HELIOS_DEFL_OSCILLATING   1  /* swinging mirror: sinusoidal across track */
 #define HELIOS_DEFL_TLS_GRID      2  /* static scanner: azimuth x elevation grid */
 #define HELIOS_DEFL_ROTATING_HEAD 3  /* head turning at head_rate, polygon in elevation */
+#define HELIOS_DEFL_FIBRE         4  /* fibre-optic line: n_fibres fixed angles in turn */
+#define HELIOS_DEFL_PALMER        5  /* slanted rotating mirror: cone at scan_angle_max off nadir */
 #define HELIOS_PLATFORM_STATIC 0
 #define HELIOS_PLATFORM_LINEAR 1
 #define HELIOS_PULSE_GAUSSIAN  0
@@ -108,6 +110,8 @@ typedef struct {
     float G;
     float leaf_reflectance;
     int32_t object_id;
+    int32_t opaque;               /* 1: non-transmissive (Sec. 3.5.4): a voxel of density > 0
+                                     stops the subray where it enters, Lambertian on that face */
     const float* density;
 } helios_voxel_desc;
 
@@ -166,7 +170,8 @@ typedef struct {
     double range_noise_sigma_m;   /* sigma of the Gaussian ranging error */
     int32_t deflector;            /* HELIOS_DEFL_* */
     int32_t grid_n_az, grid_n_el; /* HELIOS_DEFL_TLS_GRID */
-    int32_t reserved;
+    int32_t n_fibres;             /* HELIOS_DEFL_FIBRE: pulse k leaves fibre k mod n_fibres, at
+                                     -max + 2 max i/(n_fibres - 1) across track (>= 1) */
     double scan_freq_hz;          /* mirror lines (polygon) or swings (oscillating) per second */
     double scan_angle_max_rad;
     double head_rate_rad_s;
@@ -188,7 +193,8 @@ typedef struct {
     double t0;
     int64_t n_pulses;
     uint32_t leg_id;
-    int32_t reserved;
+    float platform_noise_m;       /* sigma of an N(0, s) offset of the platform position on each
+                                     axis, drawn per pulse (Sec. 3.7 platform noise); 0: none */
 } helios_leg_desc;
 
 typedef struct {

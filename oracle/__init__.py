@@ -55,7 +55,7 @@ class Scanner(C.Structure):
                 ("n_bins", C.c_int32), ("max_echoes", C.c_int32),
                 ("echo_threshold_rel", C.c_double), ("range_noise_sigma_m", C.c_double),
                 ("deflector", C.c_int32), ("grid_n_az", C.c_int32), ("grid_n_el", C.c_int32),
-                ("pad0", C.c_int32),
+                ("n_fibres", C.c_int32),
                 ("scan_freq_hz", C.c_double), ("scan_angle_max_rad", C.c_double),
                 ("head_rate_rad_s", C.c_double), ("el_min_rad", C.c_double), ("el_max_rad", C.c_double)]
 
@@ -64,12 +64,12 @@ class Leg(C.Structure):
     _fields_ = [("platform", C.c_int32), ("quality", C.c_int32), ("leg_id", C.c_uint32),
                 ("pad0", C.c_int32), ("start", C.c_double * 3), ("end", C.c_double * 3),
                 ("speed_mps", C.c_double), ("attitude_rpy", C.c_double * 3), ("t0", C.c_double),
-                ("n_pulses", C.c_int64)]
+                ("n_pulses", C.c_int64), ("platform_noise_m", C.c_double)]
 
 
 class SceneIn(C.Structure):
     _fields_ = [("n_tri", C.c_int64), ("tri", C.c_void_p), ("refl", C.c_void_p),
-                ("has_grid", C.c_int32), ("pad0", C.c_int32), ("g_origin", C.c_double * 3),
+                ("has_grid", C.c_int32), ("g_opaque", C.c_int32), ("g_origin", C.c_double * 3),
                 ("g_cell", C.c_double), ("g_dims", C.c_int32 * 3), ("pad1", C.c_int32),
                 ("g_density", C.c_void_p), ("g_G", C.c_double), ("g_leaf_refl", C.c_double)]
 
@@ -93,7 +93,7 @@ def lib():
             l.or_subray_count.argtypes = [C.c_int]
             l.or_subray_angles.argtypes = [C.c_int, C.c_double, C.c_int, d3, d3]
             l.or_onb.argtypes = [d3, d3, d3]
-            l.or_pulse_ray.argtypes = [C.POINTER(Scanner), C.POINTER(Leg), C.c_int64, d3, d3]
+            l.or_pulse_ray.argtypes = [C.POINTER(Scanner), C.POINTER(Leg), C.c_int64, C.c_uint64, d3, d3]
             l.or_subray_dir.argtypes = [C.POINTER(Scanner), C.c_int, C.c_int, d3, d3]
             for f in ("or_beam_width",):
                 getattr(l, f).argtypes = [C.POINTER(Scanner), C.c_double]
@@ -162,6 +162,7 @@ def scanner_struct(sc) -> Scanner:
     s.deflector = sc.deflector
     s.grid_n_az = sc.grid_n_az
     s.grid_n_el = sc.grid_n_el
+    s.n_fibres = sc.n_fibres
     s.scan_freq_hz = sc.scan_freq_hz
     s.scan_angle_max_rad = sc.scan_angle_max_rad
     s.head_rate_rad_s = sc.head_rate_rad_s
@@ -181,6 +182,7 @@ def leg_struct(lg) -> Leg:
     l.attitude_rpy = _d3(lg.attitude_rpy)
     l.t0 = lg.t0
     l.n_pulses = lg.n_pulses
+    l.platform_noise_m = lg.platform_noise_m
     return l
 
 
@@ -216,6 +218,7 @@ class OracleScene:
             si.g_density = _ptr(self.density)
             si.g_G = float(np.float32(g.G))
             si.g_leaf_refl = float(np.float32(g.leaf_reflectance))
+            si.g_opaque = int(g.opaque)
             self.n_vox = int(np.prod(g.dims))
         else:
             self.density = None
@@ -300,10 +303,10 @@ def onb(n):
     return np.array(u[:]), np.array(v[:])
 
 
-def pulse_ray(scanner, leg, k):
+def pulse_ray(scanner, leg, k, seed=0):
     o, d = (C.c_double * 3)(), (C.c_double * 3)()
     s, l = scanner_struct(scanner), leg_struct(leg)
-    lib().or_pulse_ray(C.byref(s), C.byref(l), int(k), o, d)
+    lib().or_pulse_ray(C.byref(s), C.byref(l), int(k), int(seed) & (2 ** 64 - 1), o, d)
     return np.array(o[:]), np.array(d[:])
 
 

@@ -156,7 +156,8 @@ static void rot_rpy(const double rpy[3], const double in[3], double out[3]) {
     out[2] = z2;
 }
 
-void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, double o[3], double d[3]) {
+void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, uint64_t seed, double o[3],
+                  double d[3]) {
     double elapsed = (double)k / sn->prf_hz;
     double t = lg->t0 + elapsed;
     double rpy[3] = {lg->attitude_rpy[0], lg->attitude_rpy[1], lg->attitude_rpy[2]};
@@ -171,6 +172,18 @@ void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, double o[3]
             for (int a = 0; a < 3; ++a) o[a] = lg->start[a] + s * (D[a] / L);
             rpy[2] += atan2(D[1], D[0]); /* heading towards the next waypoint */
         }
+    }
+    /* platform noise (Sec. 3.7): N(0, sigma) on each axis, Box-Muller on the
+     * Philox draw of stream 2 for this pulse */
+    if (lg->platform_noise_m > 0.0) {
+        uint64_t w[4];
+        draw(seed, lg->leg_id, k, 2, 0, 0, w);
+        double u1 = or_uniform24(w[0]), u2 = or_uniform24(w[1]);
+        double u3 = or_uniform24(w[2]), u4 = or_uniform24(w[3]);
+        double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+        o[0] += lg->platform_noise_m * r1 * cos(2.0 * OR_PI * u2);
+        o[1] += lg->platform_noise_m * r1 * sin(2.0 * OR_PI * u2);
+        o[2] += lg->platform_noise_m * r2 * cos(2.0 * OR_PI * u4);
     }
     double dp[3];
     double amax = sn->scan_angle_max_rad;
@@ -194,6 +207,22 @@ void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, double o[3]
         if (sn->grid_n_el > 1)
             el = sn->el_min_rad + (sn->el_max_rad - sn->el_min_rad) * (double)j / (double)(sn->grid_n_el - 1);
         dp[0] = cos(el) * cos(az); dp[1] = cos(el) * sin(az); dp[2] = sin(el);
+        break;
+    }
+    case 4: { /* fibre-optic line (reading): pulse k leaves fibre k mod n, the
+               * fibres fanned evenly across track over [-max, max] */
+        int64_t n = sn->n_fibres > 0 ? sn->n_fibres : 1;
+        int64_t i = k % n;
+        double th = n > 1 ? -amax + 2.0 * amax * (double)i / (double)(n - 1) : 0.0;
+        dp[0] = 0.0; dp[1] = sin(th); dp[2] = -cos(th);
+        break;
+    }
+    case 5: { /* Palmer (slanted rotating mirror): a cone at max off nadir,
+               * azimuth 2 pi frac(f t) */
+        double ph = sn->scan_freq_hz * t;
+        ph -= floor(ph);
+        double az = 2.0 * OR_PI * ph;
+        dp[0] = sin(amax) * cos(az); dp[1] = sin(amax) * sin(az); dp[2] = -cos(amax);
         break;
     }
     case 3:
@@ -265,7 +294,7 @@ struct or_scene {
     bnode* nodes;
     int64_t n_nodes, cap_nodes;
     double eps_box;
-    int has_grid;
+    int has_grid, opaque;
     double g0[3], gc;
     int32_t gd[3];
     const float* dens;
@@ -361,6 +390,7 @@ or_scene* or_scene_build(const or_scene_in* in) {
     sc->n_nodes = 0;
     if (n > 0) build_rec(sc, 0, n);
     sc->has_grid = in->has_grid;
+    sc->opaque = in->g_opaque;
     if (in->has_grid) {
         for (int a = 0; a < 3; ++a) { sc->g0[a] = in->g_origin[a]; sc->gd[a] = in->g_dims[a]; }
         sc->gc = in->g_cell;
@@ -521,6 +551,7 @@ typedef struct {
     double sigma;
     int corner;      /* 1: another axis crossed within eps of the exit */
     int64_t alt_vid; /* the voxel an FP32 march could visit instead at that corner */
+    int axis;        /* axis of the face the ray entered through, -1: started inside */
 } vseg;
 
 typedef struct { vseg* v; int64_t n, cap; } vlist;
@@ -577,6 +608,10 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
         else tn[a] = INFINITY;
     }
     double t_in = t_enter;
+    int entry = -1;      /* the grid face crossed at t_enter (lowest axis on a tie) */
+    if (t_enter > 0.0)
+        for (int a = 2; a >= 0; --a)
+            if (d[a] != 0.0 && tlo[a] == t_enter) entry = a;
     const int64_t nx = sc->gd[0], ny = sc->gd[1];
     for (int64_t guard = 0; guard < 4 * (int64_t)(sc->gd[0] + sc->gd[1] + sc->gd[2]) + 8; ++guard) {
         int a = 0;
@@ -585,7 +620,7 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
         double t_out = tn[a] < t_end ? tn[a] : t_end;
         int64_t vid = (idx[2] * ny + idx[1]) * nx + idx[0];
         if (t_out > t_in) {
-            vseg s = {vid, t_in, t_out, sc->G * (double)sc->dens[vid], 0, -1};
+            vseg s = {vid, t_in, t_out, sc->G * (double)sc->dens[vid], 0, -1, entry};
             /* second-smallest crossing near the exit: order ambiguous in FP32 */
             for (int b = 0; b < 3; ++b) {
                 if (b == a || step[b] == 0) continue;
@@ -603,6 +638,7 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
         if (tn[a] >= t_end) break;
         idx[a] += step[a];
         if (idx[a] < 0 || idx[a] >= sc->gd[a]) break;
+        entry = a;
         t_in = tn[a] > t_in ? tn[a] : t_in;
         tn[a] = step[a] > 0 ? plane_t(sc, a, idx[a] + 1, o, d) : plane_t(sc, a, idx[a], o, d);
     }
@@ -711,6 +747,32 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
     if (J->mode == 0) {
         /* stochastic transmission (Eq. intersection_dist): s = -ln(u)/sigma; an
          * echo at entry + s if s < traversed length, else continue (Sec. 5.2). */
+        if (sc->opaque) {
+            /* non-transmissive voxels (Sec. 3.5.4): the first voxel of non-zero
+             * density stops the subray where it enters it, Lambertian on the
+             * face entered (cos = |d . n|; 1 when the ray starts inside) */
+            for (int64_t i = 0; i < L->n; ++i) {
+                vseg* v = &L->v[i];
+                if (v->corner && v->alt_vid >= 0 && (sc->dens[v->alt_vid] > 0.0f) != (v->sigma > 0.0))
+                    *flags |= OR_F_VOX;
+                if (v->sigma <= 0.0) continue;
+                double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
+                double Is = or_subray_intensity(sn, R, alpha);
+                ret_t r = {R, or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
+                rpush(&J->S.rl, r);
+                *ev_id = sc->n_tri + v->vid;
+                *ev_R = R;
+                return;
+            }
+            if (tri >= 0) {
+                double Is = or_subray_intensity(sn, t_tri, alpha);
+                ret_t r = {t_tri, or_triangle_power(sn, Is, t_tri, (double)sc->refl[tri], cos_tri), tri, s};
+                rpush(&J->S.rl, r);
+                *ev_id = tri;
+                *ev_R = t_tri;
+            }
+            return;
+        }
         for (int64_t i = 0; i < L->n; ++i) {
             vseg* v = &L->v[i];
             if (v->corner && v->alt_vid >= 0) {
@@ -755,6 +817,16 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
     for (int64_t i = 0; i < L->n; ++i) {
         vseg* v = &L->v[i];
         if (v->sigma <= 0.0) continue;
+        if (sc->opaque) {
+            /* an opaque voxel returns all that reaches it and passes nothing */
+            double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
+            double Is = or_subray_intensity(sn, R, alpha);
+            ret_t r = {R, or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
+            rpush(&J->S.rl, r);
+            *ev_id = sc->n_tri + v->vid;
+            *ev_R = R;
+            return;
+        }
         double len = v->t_out - v->t_in;
         double a = exp(-v->sigma * len);
         double R = 0.5 * (v->t_in + v->t_out);
@@ -839,7 +911,7 @@ static void simulate_pulse(job_t* J, int64_t row) {
     int S = or_subray_count(q);
     int nb = sn->n_bins, K = sn->max_echoes;
     double o[3], d[3];
-    or_pulse_ray(sn, lg, k, o, d);
+    or_pulse_ray(sn, lg, k, J->seed, o, d);
     uint32_t flags = 0;
     if (J->adjoint) {
         const double* g = &J->g[row * nb];

@@ -28,7 +28,7 @@ typedef struct {
     double pulse_fwhm_ns, pulse_length_ns, bin_ns;
     int32_t n_bins, max_echoes;
     double echo_threshold_rel, range_noise_sigma_m;
-    int32_t deflector, grid_n_az, grid_n_el, pad0;
+    int32_t deflector, grid_n_az, grid_n_el, n_fibres;   /* n_fibres: deflector 4 */
     double scan_freq_hz, scan_angle_max_rad, head_rate_rad_s, el_min_rad, el_max_rad;
 } or_scanner;
 
@@ -42,13 +42,14 @@ typedef struct {
     double attitude_rpy[3];
     double t0;
     int64_t n_pulses;
+    double platform_noise_m;     /* sigma of the per-pulse platform position noise (Sec. 3.7) */
 } or_leg;
 
 typedef struct {
     int64_t n_tri;
     const float* tri;            /* [n_tri][3][3] vertex coordinates */
     const float* refl;           /* [n_tri] Lambertian reflectance */
-    int32_t has_grid, pad0;
+    int32_t has_grid, g_opaque;  /* g_opaque: non-transmissive voxels (Sec. 3.5.4) */
     double g_origin[3];
     double g_cell;
     int32_t g_dims[3], pad1;     /* nx, ny, nz */
@@ -92,7 +93,8 @@ double or_uniform24(uint64_t w);
 int or_subray_count(int q);
 int or_subray_angles(int q, double theta_r, int s, double* alpha, double* phi);
 void or_onb(const double n[3], double u[3], double v[3]);
-void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, double o[3], double d[3]);
+void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, uint64_t seed, double o[3],
+                  double d[3]);
 void or_subray_dir(const or_scanner* sn, int q, int s, const double d[3], double ds[3]);
 double or_beam_width(const or_scanner* sn, double R);
 double or_subray_intensity(const or_scanner* sn, double R, double alpha);

@@ -51,7 +51,7 @@ class MeshDesc(C.Structure):
 class VoxelDesc(C.Structure):
     _fields_ = [("origin", C.c_float * 3), ("cell", C.c_float), ("dims", C.c_int32 * 3),
                 ("G", C.c_float), ("leaf_reflectance", C.c_float), ("object_id", C.c_int32),
-                ("density", C.c_void_p)]
+                ("opaque", C.c_int32), ("density", C.c_void_p)]
 
 
 class SceneDesc(C.Structure):
@@ -74,7 +74,7 @@ class ScannerDesc(C.Structure):
                 ("n_bins", C.c_int32), ("max_echoes", C.c_int32),
                 ("echo_threshold_rel", C.c_double), ("range_noise_sigma_m", C.c_double),
                 ("deflector", C.c_int32), ("grid_n_az", C.c_int32), ("grid_n_el", C.c_int32),
-                ("reserved", C.c_int32),
+                ("n_fibres", C.c_int32),
                 ("scan_freq_hz", C.c_double), ("scan_angle_max_rad", C.c_double),
                 ("head_rate_rad_s", C.c_double), ("el_min_rad", C.c_double), ("el_max_rad", C.c_double)]
 
@@ -83,7 +83,7 @@ class LegDesc(C.Structure):
     _fields_ = [("scene_index", C.c_int32), ("scanner_index", C.c_int32), ("platform", C.c_int32),
                 ("beam_sample_quality", C.c_int32), ("start", C.c_double * 3), ("end", C.c_double * 3),
                 ("speed_mps", C.c_double), ("attitude_rpy", C.c_double * 3), ("t0", C.c_double),
-                ("n_pulses", C.c_int64), ("leg_id", C.c_uint32), ("reserved", C.c_int32)]
+                ("n_pulses", C.c_int64), ("leg_id", C.c_uint32), ("platform_noise_m", C.c_float)]
 
 
 class ScanOpts(C.Structure):
@@ -207,6 +207,7 @@ def leg_desc(lg) -> LegDesc:
     d.t0 = lg.t0
     d.n_pulses = int(lg.n_pulses)
     d.leg_id = int(lg.leg_id)
+    d.platform_noise_m = float(lg.platform_noise_m)
     return d
 
 
@@ -247,6 +248,7 @@ class Scene:
             gd[i].G = float(g.G)
             gd[i].leaf_reflectance = float(g.leaf_reflectance)
             gd[i].object_id = g.object_id
+            gd[i].opaque = int(g.opaque)
             gd[i].density = dens.data_ptr()
         self._md, self._gd = md, gd
         desc = SceneDesc()

@@ -34,6 +34,8 @@ DEFL_POLYGON = 0       # rotating polygon mirror: sawtooth across-track angle
 DEFL_OSCILLATING = 1   # swinging mirror: sinusoidal across-track angle
 DEFL_TLS_GRID = 2      # static tripod: azimuth x elevation grid
 DEFL_ROTATING_HEAD = 3 # 360 deg head rotation with a polygon mirror in elevation
+DEFL_FIBRE = 4         # fibre-optic line scanner: fixed fibre angles across track, in turn
+DEFL_PALMER = 5        # slanted rotating mirror: conical pattern at a fixed off-nadir angle
 
 PLATFORM_STATIC = 0
 PLATFORM_LINEAR = 1
@@ -71,6 +73,7 @@ class Scanner:
     grid_n_el: int = 0
     el_min_rad: float = 0.0
     el_max_rad: float = 0.0
+    n_fibres: int = 0
 
 
 @dataclass
@@ -87,6 +90,7 @@ class Leg:
     t0: float = 0.0
     beam_sample_quality: int = -1         # -1: use the scanner's
     leg_id: int = 0
+    platform_noise_m: float = 0.0         # sigma of the per-pulse platform position noise
 
 
 @dataclass
@@ -106,6 +110,7 @@ class VoxelGrid:
     G: float = 0.5           # projection factor: sigma = G * density
     leaf_reflectance: float = 0.5
     object_id: int = 0
+    opaque: int = 0          # 1: non-transmissive voxels
 
 
 @dataclass

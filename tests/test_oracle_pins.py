@@ -577,3 +577,89 @@ def test_single_flat_target_echo_width_is_the_pulse_sigma():
         r = oracle.scan(osc, sc, leg, mode=0, seed=1, echo_width=True)
         widths.append(r["echo_width"][0, 0])
     assert widths[0] < widths[1] < widths[2]
+
+
+# --------------------------------------------------------------------------
+# deflectors (Sec. 3.3), platform noise (Sec. 3.7), opaque voxels (Sec. 3.5.4)
+# --------------------------------------------------------------------------
+
+def test_palmer_cone_and_fibre_line_directions():
+    """Palmer: every pulse at the cone angle off nadir, azimuth 2 pi frac(f t);
+    fibre line: pulse k leaves fibre k mod n at -max + 2 max i/(n-1) across track."""
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(1.0, -2.0, 30.0), n_pulses=500)
+    amax = math.radians(15.0)
+    sc = scenes.Scanner(deflector=scenes.DEFL_PALMER, scan_angle_max_rad=amax, scan_freq_hz=37.0,
+                        prf_hz=10_000.0)
+    for k in (0, 1, 77, 499):
+        o, d = oracle.pulse_ray(sc, leg, k)
+        assert np.allclose(o, leg.start)
+        assert abs(math.acos(-d[2]) - amax) < 1e-12
+        ph = (37.0 * k / 10_000.0) % 1.0
+        az = math.atan2(d[1], d[0]) % (2 * math.pi)
+        assert abs(az - 2 * math.pi * ph) < 1e-9 or abs(abs(az - 2 * math.pi * ph) - 2 * math.pi) < 1e-9
+    sc = scenes.Scanner(deflector=scenes.DEFL_FIBRE, scan_angle_max_rad=amax, n_fibres=5)
+    for k in range(12):
+        _, d = oracle.pulse_ray(sc, leg, k)
+        th = -amax + 2 * amax * (k % 5) / 4
+        assert np.allclose(d, [0.0, math.sin(th), -math.cos(th)], atol=1e-15)
+
+
+def test_platform_noise_moments_and_seed():
+    """Per-pulse N(0, sigma) offsets of the platform on each axis, uncorrelated,
+    keyed by (seed, leg, pulse); sigma 0 leaves the trajectory exact."""
+    sig = 0.05
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(3.0, 4.0, 5.0), n_pulses=4000,
+                     platform_noise_m=sig, leg_id=7)
+    sc = scenes.Scanner(deflector=scenes.DEFL_POLYGON)
+    off = np.array([oracle.pulse_ray(sc, leg, k, seed=11)[0] - leg.start for k in range(4000)])
+    n = off.shape[0]
+    assert np.all(np.abs(off.mean(0)) < 5 * sig / math.sqrt(n))
+    assert np.all(np.abs(off.std(0) / sig - 1) < 0.06)
+    c = np.corrcoef(off.T)
+    assert np.all(np.abs(c[np.triu_indices(3, 1)]) < 0.06)
+    o2 = oracle.pulse_ray(sc, leg, 5, seed=12)[0] - leg.start
+    assert not np.allclose(o2, off[5])
+    leg0 = scenes.replace(leg, platform_noise_m=0.0)
+    assert np.array_equal(oracle.pulse_ray(sc, leg0, 5, seed=11)[0], np.array(leg.start))
+
+
+def test_opaque_voxels_return_at_the_entry_face():
+    """Non-transmissive voxels: the first voxel of non-zero density stops the
+    subray where it enters, with the Lambertian cos of the face entered; an
+    empty column lets it through to the ground."""
+    dens = np.zeros((8, 4, 4), np.float32)          # [z][y][x], cell 0.5 m, z in [-4, 0)
+    dens[2, :, :2] = 1.0                            # a layer at z in [-3, -2.5) over x < 1
+    scene = _grid_scene(dens, origin=(-1.0, -1.0, -4.0), cell=0.5, ground_z=-10.0)
+    scene.grids[0].opaque = 1
+    osc = oracle.OracleScene(scene)
+    sc, leg = _nadir_leg()
+    leg = scenes.replace(leg, start=(-0.6, 0.3, 2.0))   # above the dense layer
+    r = oracle.scan(osc, sc, leg, mode=0, seed=1)
+    assert r["echo_count"][0] == 1
+    assert abs(r["echo_range_clean"][0, 0] - (2.0 + 2.5)) < C_LIGHT * sc.bin_ns * 1e-9 / 4 + 1e-9
+    hits = r["subray_hit"][0]
+    assert (hits >= osc.n_tri).all()
+    # the same in expected mode (deterministic), and the power is the radar
+    # equation with the leaf reflectance at normal incidence
+    re = oracle.scan(osc, sc, leg, mode=1, seed=1)
+    assert np.allclose(re["waveform"], r["waveform"], rtol=1e-12, atol=0)
+    P = oracle.triangle_power(sc, sc.peak_power_w, 4.5, 0.5, 1.0)
+    assert abs(r["waveform"][0].sum() * sc.bin_ns / (P * 4.0 / 2.3548200450309493 * math.sqrt(2 * math.pi)) - 1) < 1e-3
+    # over the empty half the ray reaches the ground at 12 m
+    leg2 = scenes.replace(leg, start=(0.6, 0.3, 2.0))
+    r2 = oracle.scan(osc, sc, leg2, mode=0, seed=1)
+    assert abs(r2["echo_range_clean"][0, 0] - 12.0) < C_LIGHT * sc.bin_ns * 1e-9 / 4 + 1e-9
+    # a slanted ray enters the layer through its top face (cos = |d_z|), one
+    # that enters the layer's side through the x face (cos = |d_x|)
+    d = np.array([0.3, 0.0, -1.0]) / math.sqrt(1.09)
+    o = np.array([-2.0, 0.3, 2.0])                 # reaches z = -2.5 at x = -0.65, in the layer
+    R, P, ids, _ = oracle.trace_returns(osc, sc, o, d, mode=0)
+    t_top = (o[2] - (-2.5)) / -d[2]
+    assert len(R) == 1 and abs(R[0] - t_top) < 1e-9
+    assert abs(P[0] / oracle.triangle_power(sc, sc.peak_power_w, t_top, 0.5, abs(d[2])) - 1) < 1e-12
+    d = np.array([-1.0, 0.0, -0.1]) / math.sqrt(1.01)
+    o = np.array([2.0, 0.3, -2.7])
+    R, P, ids, _ = oracle.trace_returns(osc, sc, o, d, mode=0)
+    t_side = (o[0] - 0.0) / -d[0]                  # the layer's x = 0 face
+    assert len(R) == 1 and abs(R[0] - t_side) < 1e-9
+    assert abs(P[0] / oracle.triangle_power(sc, sc.peak_power_w, t_side, 0.5, abs(d[0])) - 1) < 1e-12
