@@ -818,13 +818,17 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
         vseg* v = &L->v[i];
         if (v->sigma <= 0.0) continue;
         if (sc->opaque) {
-            /* an opaque voxel returns all that reaches it and passes nothing */
+            /* an opaque voxel returns all that reaches it and passes nothing;
+             * the subray record keeps the triangle hit, as in every expected-mode
+             * scan (it is the adjoint's checkpoint) */
             double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
             double Is = or_subray_intensity(sn, R, alpha);
-            ret_t r = {R, or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
+            ret_t r = {R, T * or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
             rpush(&J->S.rl, r);
-            *ev_id = sc->n_tri + v->vid;
-            *ev_R = R;
+            if (tri >= 0) {
+                *ev_id = tri;
+                *ev_R = t_tri;
+            }
             return;
         }
         double len = v->t_out - v->t_in;

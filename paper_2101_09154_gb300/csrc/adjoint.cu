@@ -31,6 +31,7 @@ struct AdjParams {
     int32_t ncell;           // table cells per warp (bins -cb-1 .. nb+cb)
     float* list;             // per-warp voxel return lists [4][rl_cap][32], NULL: none
     int32_t rl_cap;
+    uint64_t seed;           // the forward's seed (platform noise moves the poses)
 };
 
 __device__ __forceinline__ float corr(const float* g, int nb, const DevScanner& sn, float dt,
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
         const int pc = (int)min((int64_t)lg.pulses_per_sub, lg.k_first + lg.n_pulses - p0);
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
-            pulse_frame(sn, lg, s_rot, p0 + t, f);
+            pulse_frame(sn, lg, s_rot, p0 + t, P.seed, f);
             split_store(f, s_pf[t]);
         }
         __syncthreads();
@@ -318,6 +319,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         p->g = L.g;
         p->window = L.window;
         p->subray_hit = L.subray_hit;
+        p->seed = L.seed;
         p->n_items = (int32_t)items;
         p->s_cap = lg.S;
         p->pc_cap = lg.pulses_per_sub;

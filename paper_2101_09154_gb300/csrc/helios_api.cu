@@ -56,7 +56,8 @@ static helios_status check_scanner(const helios_scanner_desc& s, int idx) {
     } else {
         return bad("unknown pulse_shape");
     }
-    if (s.deflector < 0 || s.deflector > 3) return bad("unknown deflector");
+    if (s.deflector < 0 || s.deflector > 5) return bad("unknown deflector");
+    if (s.deflector == HELIOS_DEFL_FIBRE && s.n_fibres < 1) return bad("n_fibres must be >= 1");
     if (s.deflector == HELIOS_DEFL_TLS_GRID && (s.grid_n_az < 1 || s.grid_n_el < 1))
         return bad("TLS grid needs grid_n_az, grid_n_el >= 1");
     return HELIOS_OK;
@@ -114,6 +115,7 @@ static DevScanner derive_scanner(const helios_scanner_desc& s) {
     d.deflector = s.deflector;
     d.n_az = s.grid_n_az;
     d.n_el = s.grid_n_el;
+    d.n_fibres = s.n_fibres;
     return d;
 }
 
@@ -139,6 +141,7 @@ static DevScene dev_scene(const helios_scene* s) {
         }
         d.G = s->grid.G;
         d.leaf_refl = s->grid.leaf_reflectance;
+        d.opaque = s->grid.opaque != 0;
         d.cell = s->grid.cell;
     }
     return d;
@@ -177,6 +180,8 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (!(L.platform_noise_m >= 0.0f))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: speed_mps must be >= 0", l);
         const helios_scanner_desc& sc = scanners[L.scanner_index];
@@ -209,6 +214,7 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
         d.pulses_per_item = item_pulses(d.pulses_per_sub, mode);
         d.leg_id = L.leg_id;
+        d.platform_noise = L.platform_noise_m;
         d.pulse_off = P.total_pulses;
         d.wave_off = P.wave;
         d.sub_off = P.sub;
@@ -429,6 +435,9 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
         return set_error(HELIOS_ERR_INVALID_ARG, "opts, d_waveform, window_bin, grads must not be NULL");
     if (opts->mode != HELIOS_MODE_EXPECTED)
         return set_error(HELIOS_ERR_INVALID_ARG, "the adjoint is defined for mode EXPECTED only");
+    for (int i = 0; i < n_scenes; ++i)
+        if (scenes[i]->n_grid && scenes[i]->grid.opaque)
+            return set_error(HELIOS_ERR_UNSUPPORTED, "opaque voxels have no density gradient; the adjoint needs transmissive grids");
     int threads = opts->block_threads > 0 ? opts->block_threads : 256;
     if (threads % 32 != 0 || threads < 64 || threads > 256)
         return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
@@ -449,6 +458,7 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     L.g = d_waveform;
     L.window = window_bin;
     L.subray_hit = subray_hit;
+    L.seed = opts->seed;
     L.threads = threads;
     if (P.total_pulses == 0) return HELIOS_OK;
     OccupancyMasks masks;
@@ -517,6 +527,8 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (!(L.platform_noise_m >= 0.0f))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: speed_mps must be >= 0", l);
         const helios_scanner_desc& sc = scanners[L.scanner_index];
@@ -548,6 +560,7 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         d.pulses_per_sub = ppi < 1 ? 1 : (ppi > 256 ? 256 : ppi);
         d.pulses_per_item = item_pulses(d.pulses_per_sub, opts->mode);
         d.leg_id = L.leg_id;
+        d.platform_noise = L.platform_noise_m;
         d.pulse_off = pulses;
         d.wave_off = wave;
         d.sub_off = sub;

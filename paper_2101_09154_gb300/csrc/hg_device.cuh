@@ -51,6 +51,7 @@ struct DevScene {
     int32_t mesh_first[kMaxMesh + 1];
     int32_t n_tri, n_int, n_mesh, has_grid;
     int32_t n_node4;
+    int32_t opaque;             // the grid's voxels are non-transmissive
     int32_t dims[3];
     float G, leaf_refl, cell;
     float g0[3];
@@ -82,6 +83,7 @@ struct DevScanner {
     float sigma_bins;        // Gaussian: sigma / bin
     int32_t q_default, pulse_shape, n_bins, max_echoes;
     int32_t deflector, n_az, n_el, n_pre;
+    int32_t n_fibres, pad0;
 };
 
 // One leg, with offsets into the concatenated outputs.
@@ -90,6 +92,7 @@ struct DevLeg {
     double dir[3];           // unit vector start -> end (linear platform)
     double length, speed, t0;
     double rpy[3];           // roll, pitch, yaw (heading included)
+    double platform_noise;   // sigma of the per-pulse platform position noise (m)
     int64_t n_pulses;        // pulses scanned: leg pulse indices k_first .. k_first + n_pulses - 1
     int64_t k_first;
     int64_t pulse_off, wave_off, sub_off, echo_off;   // output index of leg pulse k: off + k (x row size)
@@ -180,7 +183,8 @@ __device__ __forceinline__ void rot_rpy(const double rot[6], double x, double y,
 }
 
 __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& lg,
-                                            const double rot[6], int64_t k, PulseFrame& f) {
+                                            const double rot[6], int64_t k, uint64_t seed,
+                                            PulseFrame& f) {
     double elapsed = (double)k / sn.prf;
     double t = lg.t0 + elapsed;
     for (int a = 0; a < 3; ++a) f.o[a] = lg.start[a];
@@ -188,6 +192,18 @@ __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& 
         double s = lg.speed * elapsed;
         if (s > lg.length) s = lg.length;
         for (int a = 0; a < 3; ++a) f.o[a] = lg.start[a] + s * lg.dir[a];
+    }
+    if (lg.platform_noise > 0.0) {
+        // platform noise (Sec. 3.7): N(0, sigma) per axis, Box-Muller on the
+        // Philox draw of stream 2 for this pulse
+        uint64_t w[4];
+        philox4x64((uint64_t)k, 2ull << 32, 0ull, (uint64_t)lg.leg_id, seed, 0ull, w);
+        const double r1 = sqrt(-2.0 * log((double)uniform23(w[0])));
+        const double r2 = sqrt(-2.0 * log((double)uniform23(w[2])));
+        const double a1 = 2.0 * kPi * (double)uniform23(w[1]), a2 = 2.0 * kPi * (double)uniform23(w[3]);
+        f.o[0] += lg.platform_noise * r1 * cos(a1);
+        f.o[1] += lg.platform_noise * r1 * sin(a1);
+        f.o[2] += lg.platform_noise * r2 * cos(a2);
     }
     double x, y, z;
     switch (sn.deflector) {
@@ -205,6 +221,26 @@ __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& 
         double st, ct;
         sincos(th, &st, &ct);
         x = 0.0; y = st; z = -ct;
+        break;
+    }
+    case 4: {
+        // fibre-optic line: pulse k leaves fibre k mod n, fanned over [-max, max]
+        const int64_t n = sn.n_fibres > 0 ? sn.n_fibres : 1;
+        const int64_t i = k % n;
+        const double th = n > 1 ? -sn.amax + 2.0 * sn.amax * (double)i / (double)(n - 1) : 0.0;
+        double st, ct;
+        sincos(th, &st, &ct);
+        x = 0.0; y = st; z = -ct;
+        break;
+    }
+    case 5: {
+        // Palmer (slanted rotating mirror): a cone at max off nadir, azimuth 2 pi frac(f t)
+        double ph = sn.scan_freq * t;
+        ph -= floor(ph);
+        double sa, ca, sm, cm;
+        sincos(2.0 * kPi * ph, &sa, &ca);
+        sincos(sn.amax, &sm, &cm);
+        x = sm * ca; y = sm * sa; z = -cm;
         break;
     }
     case 2: {
@@ -727,6 +763,7 @@ struct March {
     float cell;
     FF t_enter, t_end;
     int entry_axis;           // axis crossed to enter the current voxel, -1: grid entry
+    int face0;                // grid face crossed at t_enter (-1: the ray starts inside)
     int steps_left;
 };
 
@@ -787,6 +824,10 @@ __device__ __forceinline__ bool march_init(const DevScene& S, const double o[3],
     m.t_enter = ff_split(te);
     m.t_end = ff_split(tend);
     m.entry_axis = -1;
+    m.face0 = -1;
+    if (te > 0.0)
+        for (int a = 2; a >= 0; --a)
+            if (d[a] != 0.0 && tlo[a] == te) m.face0 = a;
     m.steps_left = dims[0] + dims[1] + dims[2] + 4;
     return true;
 }

@@ -62,6 +62,7 @@ struct AdjointLaunch {
     const float* g;
     const int32_t* window;
     const int32_t* subray_hit;
+    uint64_t seed;
     int threads;
 };
 

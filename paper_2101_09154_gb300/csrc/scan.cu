@@ -99,6 +99,15 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
                     FF t_in, t_out;
                     march_segment_ff(m, v, t_in, t_out);
                     float len = ff_diff(t_out, t_in);
+                    if (len > 0.0f && sc.opaque) {
+                        // an opaque voxel returns all that reaches it and passes
+                        // nothing: Lambertian on the face entered
+                        const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
+                        emit(t_in, T * return_power(sn, t_in.hi + t_in.lo, c.tan_a, sc.leaf_refl,
+                                                    ax >= 0 ? fabsf(dh[ax]) : 1.0f),
+                             sc.n_tri + (int32_t)v.vid);
+                        return;
+                    }
                     if (len > 0.0f) {
                         float xs = sc.G * dens * len;
                         float w = -T * expm1f(-xs);
@@ -202,7 +211,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         // ---------------- phase 0: pulse frames ----------------
         for (int t = tid; t < pc; t += blockDim.x) {
             PulseFrame f;
-            pulse_frame(sn, lg, s_rot, p0 + t, f);
+            pulse_frame(sn, lg, s_rot, p0 + t, P.seed, f);
             split_store(f, s_pf[t]);
             s_pflag[t] = 0u;
         }
@@ -323,6 +332,23 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                     FF t_in, t_out;
                                     march_segment_ff(m, v, t_in, t_out);
                                     float len = ff_diff(t_out, t_in);
+                                    if (len > 0.0f && sc.opaque) {
+                                        // non-transmissive voxel (Sec. 3.5.4): stop where
+                                        // the subray enters it, Lambertian on that face
+                                        if (MODE == 0) {
+                                            const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
+                                            rr.Rh = t_in.hi;
+                                            rr.Rl = t_in.lo;
+                                            rr.id = sc.n_tri + (int32_t)v.vid;
+                                            rr.P = return_power(sn, t_in.hi + t_in.lo, tan_a, sc.leaf_refl,
+                                                                ax >= 0 ? fabsf(dh[ax]) : 1.0f);
+                                            voxel_event = true;
+                                        } else {
+                                            rr.R2h = t_in.hi;
+                                            rr.R2l = t_in.lo;
+                                        }
+                                        break;
+                                    }
                                     if (len > 0.0f) {
                                         float sigma = sc.G * dens;
                                         if (MODE == 0) {
@@ -661,10 +687,12 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         bool on = false;
                         March mch;
                         uint32_t fl = 0;
+                        float dabs[3] = {1.0f, 1.0f, 1.0f};
                         if (GRID && sc.has_grid && lane_on) {
                             double o[3], d[3];
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
+                            for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
                             for (int a = 0; a < 3; ++a) {
                                 o[a] = ff2d(f.oh[a], f.ol[a]);
                                 d[a] = ff2d(dh[a], dl[a]);
@@ -684,6 +712,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                     FF t_in, t_out;
                                     march_segment_ff(mch, v, t_in, t_out);
                                     float len = ff_diff(t_out, t_in);
+                                    if (len > 0.0f && sc.opaque) {
+                                        // opaque: all of T returns here, nothing passes
+                                        const int ax = mch.entry_axis >= 0 ? mch.entry_axis : mch.face0;
+                                        pv = T * return_power(sn, t_in.hi + t_in.lo, tan_a, sc.leaf_refl,
+                                                              ax >= 0 ? dabs[ax] : 1.0f);
+                                        tau = ff_mul_sub(t_in, kDelayHi, kDelayLo, mdt_h, mdt_l);
+                                        vid = sc.n_tri + (int32_t)v.vid;
+                                        has = true;
+                                        T = 0.0f;
+                                        on = false;
+                                        break;
+                                    }
                                     if (len > 0.0f) {
                                         float xs = sc.G * dens * len;
                                         float w = -T * expm1f(-xs);

@@ -356,3 +356,44 @@ def test_echo_width_fit_matches_oracle(hg, name):
             n += 1
         assert (gw[i, gc[i]:] == 0).all()
     assert n > (300 if name == "tls" else 500)
+
+
+@pytest.mark.parametrize("defl", ["palmer", "fibre", "noise"])
+def test_palmer_fibre_deflectors_and_platform_noise(hg, defl):
+    """Sec. 3.3 deflectors (slanted rotating mirror; fibre-optic line) and
+    Sec. 3.7 platform noise over the terrain workload, against the oracle."""
+    w = scenes.als_terrain(seed=5, size=128, n_trees=12, n_pulses=5003, n_bins=512, agl=120.0,
+                           speed=30.0, prf=50_000.0)
+    if defl == "palmer":
+        w = scenes.with_scanner(w, deflector=scenes.DEFL_PALMER, scan_angle_max_rad=math.radians(12.0),
+                                scan_freq_hz=40.0)
+    elif defl == "fibre":
+        w = scenes.with_scanner(w, deflector=scenes.DEFL_FIBRE, n_fibres=37)
+    else:
+        import dataclasses
+        w = scenes.Workload(w.name, w.scenes, w.scanners,
+                            [dataclasses.replace(w.legs[0], platform_noise_m=0.05)])
+    _, _, res = run_both(hg, w, seed=13)
+    stats = compare(*res[0])
+    assert stats["echoes"] > 2500
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_opaque_voxels(hg, mode):
+    """Sec. 3.5.4 non-transmissive voxels: the first dense voxel stops the
+    subray at its entry face (stochastic and expected modes)."""
+    w = scenes.uls_voxels(seed=6, n=48, n_pulses=3001, n_bins=512, agl=12.0, speed=1.0, prf=2000.0)
+    w.scenes[0].grids[0].opaque = 1
+    _, _, res = run_both(hg, w, mode=mode, seed=11)
+    stats = compare(*res[0], expected_mode=(mode == 1))
+    assert stats["echoes"] > 1000
+
+
+def test_adjoint_rejects_opaque_grids(hg):
+    w = scenes.uls_voxels(seed=6, n=16, n_pulses=64, n_bins=128, agl=5.0, speed=1.0, prf=1000.0)
+    w.scenes[0].grids[0].opaque = 1
+    gs = hg.Scene(w.scenes[0])
+    out, _ = hg.scan([gs], w.scanners, w.legs, mode=1)
+    with pytest.raises(hg.HeliosError) as e:
+        hg.scan_adjoint([gs], w.scanners, w.legs, out["waveform"], out["window_bin"], out["subray_hit"])
+    assert e.value.code == -6
