@@ -252,10 +252,12 @@ HELIOS_API helios_status helios_output_layout(const helios_scanner_desc* scanner
 /* Simulate the legs: pulse generation (Sec. 3.2-3.3), subrays (Sec. 3.4),
  * intersection (Sec. 5.1-5.2), power (Eq. beamdiv, beamdiv_w,
  * ladlut_intensity), waveform (Sec. 3.4), echoes and range noise (Sec. 3.4,
- * 3.7).  With opts->persistent the legs share one launch fed by a work
- * queue (the queue counter is stream-ordered memory allocated and freed on
- * cuda_stream); otherwise one launch per leg.  Errors: INVALID_ARG,
- * UNSUPPORTED, OOM, CUDA. */
+ * 3.7), echo widths when out->echo_width is set.  With opts->persistent the
+ * legs share one launch fed by a work queue; otherwise one launch per leg.
+ * Scratch (the queue counter, candidate lists, voxel brick masks, moment bins
+ * and return lists in expected mode, echo bins for the width fit) is
+ * stream-ordered memory allocated and freed on cuda_stream.  The call returns
+ * once the work is queued.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
                                const helios_scanner_desc* scanners, int32_t n_scanners,
                                const helios_leg_desc* legs, int32_t n_legs,
