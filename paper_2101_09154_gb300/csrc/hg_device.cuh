@@ -217,7 +217,10 @@ __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& 
         break;
     }
     case 1: {
-        double th = sn.amax * sin(2.0 * kPi * sn.scan_freq * t);
+        // sin(2 pi f t) from the phase's fractional part: no FP64 argument reduction
+        double ph = sn.scan_freq * t;
+        ph -= floor(ph);
+        double th = sn.amax * sinpi(2.0 * ph);
         double st, ct;
         sincos(th, &st, &ct);
         x = 0.0; y = st; z = -ct;
@@ -267,16 +270,18 @@ __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& 
     }
     }
     rot_rpy(rot, x, y, z, f.d);
-    // orthonormal basis around d (Duff et al., JCGT 2017)
-    double sign = copysign(1.0, f.d[2]);
-    double a = -1.0 / (sign + f.d[2]);
-    double b = f.d[0] * f.d[1] * a;
-    f.u[0] = 1.0 + sign * f.d[0] * f.d[0] * a;
+    // orthonormal basis around d (Duff et al., JCGT 2017), in FP32: it only
+    // scales the sub-milliradian subray offsets, and is kept as floats
+    const float d0 = (float)f.d[0], d1 = (float)f.d[1], d2 = (float)f.d[2];
+    const float sign = copysignf(1.0f, d2);
+    const float a = -1.0f / (sign + d2);
+    const float b = d0 * d1 * a;
+    f.u[0] = 1.0f + sign * d0 * d0 * a;
     f.u[1] = sign * b;
-    f.u[2] = -sign * f.d[0];
+    f.u[2] = -sign * d0;
     f.v[0] = b;
-    f.v[1] = sign + f.d[1] * f.d[1] * a;
-    f.v[2] = -f.d[1];
+    f.v[1] = sign + d1 * d1 * a;
+    f.v[2] = -d1;
 }
 
 // subray s of quality q (Sec. 3.4): ring i at angle (i/q) theta_r, floor(2 pi i) per ring
