@@ -19,9 +19,10 @@
 
 namespace hg {
 
+// one subray's result in shared memory (16 bytes); expected mode keeps the
+// range of its first voxel return (+inf: none) in a float-pair array beside it
 struct RayRes {
     float Rh, Rl;    // event range (stochastic) / triangle range (expected), hi + lo
-    float R2h, R2l;  // expected mode: first voxel return range; +inf: none
     float P;         // return power (expected mode: triangle power at unit weight)
     int32_t id;      // event primitive / triangle id; -1: none
 };
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(256)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     RayRes* s_rr = reinterpret_cast<RayRes*>(smem);
-    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_rr + P.rays_cap);
+    float2* s_r2 = reinterpret_cast<float2*>(s_rr + P.rays_cap);       // [rays_cap], expected mode
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_r2 + (MODE == 1 ? P.rays_cap : 0));
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
     uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
@@ -293,10 +295,9 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 RayRes rr;
                 rr.Rh = CUDART_INF_F;
                 rr.Rl = 0.0f;
-                rr.R2h = CUDART_INF_F;
-                rr.R2l = 0.0f;
                 rr.P = 0.0f;
                 rr.id = -1;
+                float r2h = CUDART_INF_F, r2l = 0.0f;   // expected mode: first voxel return
                 float tan_a = s_sc[s].tan_a;
                 float dt_hit = 0.0f;
                 if (active) {
@@ -344,8 +345,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                                                 ax >= 0 ? fabsf(dh[ax]) : 1.0f);
                                             voxel_event = true;
                                         } else {
-                                            rr.R2h = t_in.hi;
-                                            rr.R2l = t_in.lo;
+                                            r2h = t_in.hi;
+                                            r2l = t_in.lo;
                                         }
                                         break;
                                     }
@@ -369,8 +370,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                             }
                                         } else {
                                             FF R2 = ff_add_f(t_in, 0.5f * len);
-                                            rr.R2h = R2.hi;
-                                            rr.R2l = R2.lo;
+                                            r2h = R2.hi;
+                                            r2l = R2.lo;
                                             break;
                                         }
                                     }
@@ -386,6 +387,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         rr.P = return_power(sn, tb + dt_hit, tan_a, rho, cosi);
                     }
                     s_rr[r] = rr;
+                    if (MODE == 1) s_r2[r] = make_float2(r2h, r2l);
                     if (fl) atomicOr(&s_pflag[pl], fl);
                     if (P.out.subray_hit) {
                         int64_t so = lg.sub_off + (p0 + pl) * S + s;
@@ -414,7 +416,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (ff_less(r, rmin)) rmin = r;
                     }
                     if (MODE == 1) {
-                        FF r = ff_norm(rr.R2h, rr.R2l);
+                        const float2 q = s_r2[(size_t)(pl - sb) * S + s];
+                        FF r = ff_norm(q.x, q.y);
                         if (ff_less(r, rmin)) rmin = r;
                     }
                 }
@@ -1086,7 +1089,8 @@ static int warp_stride(int mode, int nb_cap, int cb, bool direct) {
 
 static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads,
                          int pk_cap = 0, int cb = 0, bool direct = true) {
-    size_t b = sizeof(RayRes) * rays_cap + sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
+    size_t b = (sizeof(RayRes) + (mode == 1 ? sizeof(float2) : 0)) * rays_cap +
+               sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
                sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
                sizeof(float) * pk_cap + sizeof(int32_t) * (size_t)pc_cap * (kConeCap + 1);
     b = (b + 15) & ~size_t(15);
