@@ -71,7 +71,8 @@ class SceneIn(C.Structure):
     _fields_ = [("n_tri", C.c_int64), ("tri", C.c_void_p), ("refl", C.c_void_p),
                 ("has_grid", C.c_int32), ("g_opaque", C.c_int32), ("g_origin", C.c_double * 3),
                 ("g_cell", C.c_double), ("g_dims", C.c_int32 * 3), ("pad1", C.c_int32),
-                ("g_density", C.c_void_p), ("g_G", C.c_double), ("g_leaf_refl", C.c_double)]
+                ("g_density", C.c_void_p), ("g_G", C.c_double), ("g_leaf_refl", C.c_double),
+                ("g_lad", C.c_void_p), ("g_lad_n", C.c_int32), ("pad2", C.c_int32)]
 
 
 class Out(C.Structure):
@@ -219,6 +220,12 @@ class OracleScene:
             si.g_G = float(np.float32(g.G))
             si.g_leaf_refl = float(np.float32(g.leaf_reflectance))
             si.g_opaque = int(g.opaque)
+            lad = getattr(g, "lad", None)
+            if lad is not None:
+                # the library receives the table in FP32: use the same numbers
+                self.lad = np.ascontiguousarray(lad, dtype=np.float32)
+                si.g_lad = _ptr(self.lad)
+                si.g_lad_n = int(self.lad.shape[0])
             self.n_vox = int(np.prod(g.dims))
         else:
             self.density = None

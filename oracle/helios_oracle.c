@@ -299,6 +299,8 @@ struct or_scene {
     int32_t gd[3];
     const float* dens;
     double G, leaf_refl;
+    const float* lad;
+    int64_t lad_n;
 };
 
 static void tri_bounds(const double* v, double lo[3], double hi[3]) {
@@ -397,6 +399,8 @@ or_scene* or_scene_build(const or_scene_in* in) {
         sc->dens = in->g_density;
         sc->G = in->g_G;
         sc->leaf_refl = in->g_leaf_refl;
+        sc->lad = in->g_lad;
+        sc->lad_n = in->g_lad ? in->g_lad_n : 0;
         for (int a = 0; a < 3; ++a) {
             double e = fabs(sc->g0[a]) + sc->gd[a] * sc->gc;
             if (e > smax) smax = e;
@@ -564,6 +568,19 @@ static void vpush(vlist* L, vseg s) {
     L->v[L->n++] = s;
 }
 
+/* sigma = G * density (Eq. extinction).  With a leaf-angle table (Table ladlut)
+ * G depends on the subray direction: the table holds G at mu_i = i/(n-1) of
+ * mu = |d_z| (d a unit vector) and is read by linear interpolation. */
+static double proj_factor(const or_scene* sc, const double d[3]) {
+    if (sc->lad_n < 2) return sc->G;
+    double t = fabs(d[2]) * (double)(sc->lad_n - 1);
+    int64_t i = (int64_t)floor(t);
+    if (i > sc->lad_n - 2) i = sc->lad_n - 2;
+    double f = t - (double)i;
+    double g0 = (double)sc->lad[i], g1 = (double)sc->lad[i + 1];
+    return g0 + f * (g1 - g0);
+}
+
 static double plane_t(const or_scene* sc, int a, int64_t i, const double o[3], const double d[3]) {
     return (sc->g0[a] + (double)i * sc->gc - o[a]) / d[a];
 }
@@ -589,6 +606,7 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
     }
     double t_end = t_exit < t_hi ? t_exit : t_hi;
     if (!(t_enter < t_end)) return;
+    const double G = proj_factor(sc, d);
     int64_t idx[3];
     int step[3];
     double tn[3];
@@ -620,7 +638,7 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
         double t_out = tn[a] < t_end ? tn[a] : t_end;
         int64_t vid = (idx[2] * ny + idx[1]) * nx + idx[0];
         if (t_out > t_in) {
-            vseg s = {vid, t_in, t_out, sc->G * (double)sc->dens[vid], 0, -1, entry};
+            vseg s = {vid, t_in, t_out, G * (double)sc->dens[vid], 0, -1, entry};
             /* second-smallest crossing near the exit: order ambiguous in FP32 */
             for (int b = 0; b < 3; ++b) {
                 if (b == a || step[b] == 0) continue;
@@ -776,7 +794,7 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
         for (int64_t i = 0; i < L->n; ++i) {
             vseg* v = &L->v[i];
             if (v->corner && v->alt_vid >= 0) {
-                double sa = sc->G * (double)sc->dens[v->alt_vid];
+                double sa = proj_factor(sc, ds) * (double)sc->dens[v->alt_vid];
                 if (sa > 0.0) {
                     uint64_t w[4];
                     draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)v->alt_vid, w);
@@ -894,13 +912,14 @@ static void adjoint_subray(job_t* J, const double* g, int32_t m,
         gpush(&J->S, tri, acc * wtri);
         suffix = acc * (double)sc->refl[tri] * wtri;
     }
-    /* dL/dsigma_j = A_j T_j l_j e^{-sigma_j l_j} - l_j (sum_{k>j} A_k w_k + A_tri w_tri) */
+    /* dL/dsigma_j = A_j T_j l_j e^{-sigma_j l_j} - l_j (sum_{k>j} A_k w_k + A_tri w_tri);
+     * dL/ddensity_j = G(d) dL/dsigma_j */
     for (int64_t i = nv - 1; i >= 0; --i) {
         vseg* v = &L->v[i];
         double len = v->t_out - v->t_in;
         double a = exp(-v->sigma * len);
         double dsig = A[i] * T[i] * len * a - len * suffix;
-        gpush(&J->S, sc->n_tri + v->vid, sc->G * dsig);
+        gpush(&J->S, sc->n_tri + v->vid, proj_factor(sc, ds) * dsig);
         suffix += A[i] * wk[i];
     }
     free(A); free(T); free(wk);

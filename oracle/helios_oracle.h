@@ -54,8 +54,12 @@ typedef struct {
     double g_cell;
     int32_t g_dims[3], pad1;     /* nx, ny, nz */
     const float* g_density;      /* [nz][ny][nx] plant area density */
-    double g_G;                  /* sigma = G * density */
+    double g_G;                  /* sigma = G * density (no leaf-angle table) */
     double g_leaf_refl;
+    const float* g_lad;          /* [g_lad_n] leaf-angle table G(mu) at mu_i = i/(n-1), mu =
+                                    |vertical component| of the subray (Eq. extinction, Table
+                                    ladlut), linear in between; NULL: the constant g_G */
+    int32_t g_lad_n, pad2;
 } or_scene_in;
 
 typedef struct or_scene or_scene;

@@ -111,6 +111,7 @@ class VoxelGrid:
     leaf_reflectance: float = 0.5
     object_id: int = 0
     opaque: int = 0          # 1: non-transmissive voxels
+    lad: object = None       # leaf-angle table: float32 [n] of G at |d_z| = i/(n-1), or None
 
 
 @dataclass
