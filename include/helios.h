@@ -98,11 +98,17 @@ typedef struct {
     int32_t reserved;
 } helios_mesh_desc;
 
-/* One transmissive voxel part (Sec. 3.5.4, Eq. extinction with a constant
- * projection factor G: sigma = G * density).  density: device
- * float[dims[2]][dims[1]][dims[0]] plant area density in m^2/m^3, REFERENCED
- * (not copied) like mesh reflectance.  Voxel (x,y,z) spans
- * [origin + (x,y,z)*cell, origin + (x+1,y+1,z+1)*cell). */
+/* One transmissive voxel part (Sec. 3.5.4, Eq. extinction: sigma = G * density).
+ * density: device float[dims[2]][dims[1]][dims[0]] plant area density in
+ * m^2/m^3, REFERENCED (not copied) like mesh reflectance.  Voxel (x,y,z) spans
+ * [origin + (x,y,z)*cell, origin + (x+1,y+1,z+1)*cell).
+ * G is the constant projection factor, unless lad_table is given: then G
+ * depends on the subray's unit direction d through the leaf-angle table
+ * (Table ladlut), G(d) = linear interpolation of lad_table at mu = |d_z|
+ * between entries at mu_i = i/(lad_n - 1).  lad_table: device or host
+ * float[lad_n], 2 <= lad_n <= 65536, entries finite and >= 0 (INVALID_ARG
+ * otherwise); COPIED by helios_build_scene (the caller may free it after).
+ * helios_lad_table fills one for the distributions the paper names. */
 typedef struct {
     float origin[3];
     float cell;
@@ -113,6 +119,9 @@ typedef struct {
     int32_t opaque;               /* 1: non-transmissive (Sec. 3.5.4): a voxel of density > 0
                                      stops the subray where it enters, Lambertian on that face */
     const float* density;
+    const float* lad_table;       /* NULL: constant G */
+    int32_t lad_n;
+    int32_t reserved;
 } helios_voxel_desc;
 
 /* A scene: meshes are concatenated in order; triangle id = offset of its mesh
@@ -145,6 +154,27 @@ typedef struct {
  * 32 bits), OOM, CUDA. */
 HELIOS_API helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_stream,
                                  helios_scene** out);
+/* Leaf-angle distributions (de Wit) for helios_lad_table, Sec. 3.5.4. */
+#define HELIOS_LAD_PLANOPHILE   1    /* f(t) = (2/pi)(1 + cos 2t), t = leaf-normal zenith */
+#define HELIOS_LAD_ERECTOPHILE  2    /* (2/pi)(1 - cos 2t) */
+#define HELIOS_LAD_PLAGIOPHILE  3    /* (2/pi)(1 - cos 4t) */
+#define HELIOS_LAD_EXTREMOPHILE 4    /* (2/pi)(1 + cos 4t) */
+#define HELIOS_LAD_UNIFORM      5    /* 2/pi */
+#define HELIOS_LAD_SPHERICAL    6    /* sin t (G = 1/2 at every angle) */
+
+/* Fill a leaf-angle table for helios_voxel_desc.lad_table (Eq. extinction,
+ * Table ladlut): table[i] = G at a beam with |cos zenith| = mu_i = i/(n-1),
+ *   G(theta) = (1/2pi) int over leaf normals of g_L |Omega'.Omega_L| dOmega_L
+ *            = int_0^{pi/2} f(t) psi(theta, t) dt,
+ * psi Ross's azimuthal kernel, for azimuthally uniform leaves with inclination
+ * density f = `distribution` (HELIOS_LAD_*).  Computed on the device in FP64
+ * (composite Simpson on the two pieces split at t = pi/2 - theta), rounded to
+ * float.  table: DEVICE float[n], written asynchronously on cuda_stream.
+ * Errors: INVALID_ARG (unknown distribution, n outside 2..65536, NULL table),
+ * CUDA. */
+HELIOS_API helios_status helios_lad_table(int32_t distribution, int32_t n, float* table,
+                                          void* cuda_stream);
+
 /* Frees the scene's device buffers (synchronises the device first). */
 HELIOS_API helios_status helios_free_scene(helios_scene* scene);
 HELIOS_API helios_status helios_scene_get_info(const helios_scene* scene, helios_scene_info* info);

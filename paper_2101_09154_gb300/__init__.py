@@ -31,6 +31,9 @@ _lib = None
 OK = 0
 NO_WINDOW = -(2 ** 31)
 MODE_STOCHASTIC, MODE_EXPECTED = 0, 1
+# leaf-angle distributions of lad_table (de Wit), codes of HELIOS_LAD_*
+LAD_KINDS = {"planophile": 1, "erectophile": 2, "plagiophile": 3, "extremophile": 4,
+             "uniform": 5, "spherical": 6}
 PF_ECHO_OVERFLOW, PF_TRAVERSAL_CAP, PF_MARCH_CAP, PF_NO_RETURN = 1, 2, 4, 8
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "OVERFLOW",
           -6: "UNSUPPORTED"}
@@ -51,7 +54,8 @@ class MeshDesc(C.Structure):
 class VoxelDesc(C.Structure):
     _fields_ = [("origin", C.c_float * 3), ("cell", C.c_float), ("dims", C.c_int32 * 3),
                 ("G", C.c_float), ("leaf_reflectance", C.c_float), ("object_id", C.c_int32),
-                ("opaque", C.c_int32), ("density", C.c_void_p)]
+                ("opaque", C.c_int32), ("density", C.c_void_p), ("lad_table", C.c_void_p),
+                ("lad_n", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -149,6 +153,8 @@ def lib():
                                           C.POINTER(ScanOpts), C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.POINTER(SceneGrads), C.c_void_p]
         l.helios_scan_adjoint.restype = st
+        l.helios_lad_table.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+        l.helios_lad_table.restype = st
         l.helios_subray_count.argtypes = [C.c_int32]
         l.helios_subray_count.restype = C.c_int32
         l.helios_last_error.restype = C.c_char_p
@@ -169,6 +175,18 @@ def subray_count(q: int) -> int:
 def _torch():
     import torch
     return torch
+
+
+def lad_table(kind, n=91, device=None, stream=None):
+    """Leaf-angle table on the device: G at |cos zenith| = i/(n-1), i < n
+    (Eq. extinction), for a distribution name of LAD_KINDS or its code."""
+    torch = _torch()
+    code = LAD_KINDS[kind] if isinstance(kind, str) else int(kind)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(int(n), dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().helios_lad_table(code, int(n), C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def _ptr(t):
@@ -238,10 +256,19 @@ class Scene:
             md[i].reflectance = r.data_ptr()
             md[i].object_id = m.object_id
         self.density = []
+        lads = []
         gd = (VoxelDesc * max(len(scene.grids), 1))()
         for i, g in enumerate(scene.grids):
             dens = torch.as_tensor(np.ascontiguousarray(g.density, np.float32)).to(dev)
             self.density.append(dens)
+            lad = getattr(g, "lad", None)
+            if lad is not None:
+                # a device tensor (lad_table()) or host values; copied by the build
+                lt = (lad.to(dev, torch.float32).contiguous() if torch.is_tensor(lad)
+                      else torch.as_tensor(np.ascontiguousarray(lad, np.float32)).to(dev))
+                lads.append(lt)
+                gd[i].lad_table = lt.data_ptr()
+                gd[i].lad_n = lt.numel()
             gd[i].origin = (C.c_float * 3)(*[float(x) for x in g.origin])
             gd[i].cell = float(g.cell)
             gd[i].dims = (C.c_int32 * 3)(*[int(x) for x in g.dims])
@@ -261,6 +288,7 @@ class Scene:
         h = C.c_void_p()
         with torch.cuda.device(dev):
             _check(lib().helios_build_scene(C.byref(desc), _stream_handle(stream), C.byref(h)))
+        del lads
         self.handle = h
 
     def info(self) -> dict:

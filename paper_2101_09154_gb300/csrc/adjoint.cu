@@ -5,7 +5,7 @@
 // triangle behind returns rho * T_{K+1}.  With A_k = sum_b g_b P_k p(t_b - tau_k)
 // (g = dL/dW, P_k the return power at unit weight) the gradients are
 //   dL/dsigma_j = A_j T_j l_j e^{-sigma_j l_j} - l_j (sum_{k>j} A_k w_k + A_tri rho T_{K+1})
-//   dL/ddensity_j = G dL/dsigma_j,    dL/drho = A_tri T_{K+1}.
+//   dL/ddensity_j = G(d) dL/dsigma_j,    dL/drho = A_tri T_{K+1}.
 // The hit set and the window start are held fixed.  One warp per pulse,
 // lanes = subrays.  For a Gaussian pulse A comes from per-pulse Hermite
 // correlation tables (see corr_tab).  Pass A marches once and lists each
@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 const SubrayConst& c = s_sc[ss];
                 float dh[3], dl[3];
                 subray_dir_ff(f, c, dh, dl);
+                const float Gs = proj_factor(sc, dh[2]);   // sigma = Gs density
                 double o[3], d[3];
                 for (int a = 0; a < 3; ++a) {
                     o[a] = ff2d(f.oh[a], f.ol[a]);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                             march_segment_ff(mch, v, t_in, t_out);
                             float len = ff_diff(t_out, t_in);
                             if (len > 0.0f) {
-                                float xs = sc.G * dens * len;
+                                float xs = Gs * dens * len;
                                 float a = expf(-xs);
                                 float w = -T * expm1f(-xs);
                                 FF R = ff_add_f(t_in, 0.5f * len);
@@ -227,8 +228,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 if (listing && n < P.rl_cap) {
                                     const size_t e = (size_t)n * 32 + lane;
                                     __stcg(reinterpret_cast<int32_t*>(RL) + e, (int32_t)v.vid);
-                                    __stcg(RL + RLs + e, sc.G * A * T * len * a);
-                                    __stcg(RL + 2 * RLs + e, sc.G * len);
+                                    __stcg(RL + RLs + e, Gs * A * T * len * a);
+                                    __stcg(RL + 2 * RLs + e, Gs * len);
                                     __stcg(RL + 3 * RLs + e, A * w);
                                 }
                                 ++n;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                             march_segment_ff(mch, v, t_in, t_out);
                             float len = ff_diff(t_out, t_in);
                             if (len > 0.0f) {
-                                float xs = sc.G * dens * len;
+                                float xs = Gs * dens * len;
                                 float a = expf(-xs);
                                 float w = -Tb * expm1f(-xs);
                                 FF R = ff_add_f(t_in, 0.5f * len);
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;
                                 double dsig = (double)A * Tb * len * a - len * suffix;
-                                atomicAdd(&ddens[v.vid], (float)((double)sc.G * dsig));
+                                atomicAdd(&ddens[v.vid], (float)((double)Gs * dsig));
                                 Tb *= a;
                             }
                         }

@@ -143,6 +143,8 @@ static DevScene dev_scene(const helios_scene* s) {
         d.leaf_refl = s->grid.leaf_reflectance;
         d.opaque = s->grid.opaque != 0;
         d.cell = s->grid.cell;
+        d.lad = s->lad;
+        d.lad_n = s->lad_n;
     }
     return d;
 }
@@ -274,6 +276,8 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         if (!(g.cell > 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid cell must be > 0");
         if (!(g.G >= 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid G must be >= 0");
         if (!g.density) return set_error(HELIOS_ERR_INVALID_ARG, "grid density is NULL");
+        if (g.lad_table && (g.lad_n < 2 || g.lad_n > 65536))
+            return set_error(HELIOS_ERR_INVALID_ARG, "grid lad_n must be in 2..65536");
         n_vox = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
     }
     if (n_tri + n_vox >= (int64_t)INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many primitives for 32-bit ids");
@@ -295,21 +299,51 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
     s->mesh_first[desc->n_meshes] = (int32_t)off;
     if (desc->n_grids == 1) s->grid = desc->grids[0];
     cudaError_t e = cudaSuccess;
+    if (desc->n_grids == 1 && s->grid.lad_table) {
+        // leaf-angle table: read (host or device memory), checked, copied
+        const int32_t n = s->grid.lad_n;
+        std::vector<float> h((size_t)n);
+        e = cudaMemcpyAsync(h.data(), s->grid.lad_table, sizeof(float) * (size_t)n, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            delete s;
+            return set_cuda_error("reading the leaf-angle table", e);
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (!(h[i] >= 0.0f && h[i] <= 3.0e38f)) {
+                delete s;
+                return set_error(HELIOS_ERR_INVALID_ARG, "lad_table[%d] is negative or not finite", i);
+            }
+        e = cudaMalloc(&s->lad, sizeof(float) * (size_t)n);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->lad, h.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(s->lad);
+            delete s;
+            return set_cuda_error("leaf-angle table copy", e);
+        }
+        s->lad_n = n;
+        s->grid.lad_table = nullptr;     // the caller's pointer is not kept
+    }
     if (s->n_int > 0) e = cudaMalloc(&s->nodes, sizeof(float4) * 4 * (size_t)s->n_int);
     if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tris, sizeof(float4) * 3 * (size_t)n_tri);
     if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tri_index, sizeof(int32_t) * (size_t)n_tri);
     if (e != cudaSuccess) {
         helios_status r = set_cuda_error("scene allocation", e);
+        cudaFree(s->lad);
         cudaFree(s->nodes);
         cudaFree(s->tris);
         cudaFree(s->tri_index);
         delete s;
         return r;
     }
-    s->bytes = (int64_t)sizeof(float4) * (4 * s->n_int + 3 * n_tri) + (int64_t)sizeof(int32_t) * n_tri;
+    s->bytes = (int64_t)sizeof(float4) * (4 * s->n_int + 3 * n_tri) + (int64_t)sizeof(int32_t) * n_tri +
+               (int64_t)sizeof(float) * s->lad_n;
     helios_status r = build_bvh(s, desc, st);
     if (r != HELIOS_OK) {
         cudaStreamSynchronize(st);
+        cudaFree(s->lad);
         cudaFree(s->nodes4);
         cudaFree(s->nodes);
         cudaFree(s->tris);
@@ -331,9 +365,19 @@ helios_status helios_free_scene(helios_scene* scene) {
     cudaFree(scene->nodes4);
     cudaFree(scene->tris);
     cudaFree(scene->tri_index);
+    cudaFree(scene->lad);
     if (cur != scene->device) cudaSetDevice(cur);
     delete scene;
     return HELIOS_OK;
+}
+
+helios_status helios_lad_table(int32_t distribution, int32_t n, float* table, void* cuda_stream) {
+    g_err.clear();
+    if (distribution < HELIOS_LAD_PLANOPHILE || distribution > HELIOS_LAD_SPHERICAL)
+        return set_error(HELIOS_ERR_INVALID_ARG, "unknown leaf angle distribution %d", distribution);
+    if (n < 2 || n > 65536) return set_error(HELIOS_ERR_INVALID_ARG, "n must be in 2..65536");
+    if (!table) return set_error(HELIOS_ERR_INVALID_ARG, "table is NULL");
+    return launch_lad_table(distribution, n, table, (cudaStream_t)cuda_stream);
 }
 
 helios_status helios_scene_get_info(const helios_scene* scene, helios_scene_info* info) {

@@ -57,7 +57,22 @@ struct DevScene {
     float g0[3];
     int32_t bdims[3];           // bricks of kBrick^3 voxels per axis
     const uint32_t* occ;        // brick occupancy bits (x fastest), NULL: not used
+    const float* lad;           // leaf-angle table G(mu_i), mu_i = i/(lad_n-1)
+    int32_t lad_n;              // 0: constant G
 };
+
+// sigma = G density (Eq. extinction).  With a leaf-angle table (Table ladlut)
+// G depends on the subray direction: linear interpolation at mu = |d_z| of the
+// unit direction between entries at mu_i = i/(n-1); without one, the grid's
+// constant G.  Evaluated once per subray, before its march.
+__device__ __forceinline__ float proj_factor(const DevScene& sc, float dz) {
+    if (sc.lad_n < 2) return sc.G;
+    const float t = fabsf(dz) * (float)(sc.lad_n - 1);
+    const int i = min((int)t, sc.lad_n - 2);
+    const float f = t - (float)i;
+    const float g0 = __ldg(sc.lad + i), g1 = __ldg(sc.lad + i + 1);
+    return fmaf(f, g1 - g0, g0);
+}
 
 // Instrument constants derived once per call (host side, FP64).
 struct DevScanner {

@@ -24,6 +24,8 @@ struct helios_scene {
     int32_t mesh_first[hg::kMaxMesh + 1];
     int64_t mesh_faces[hg::kMaxMesh];
     helios_voxel_desc grid;
+    float* lad;               // [lad_n] copy of the grid's leaf-angle table, or NULL
+    int32_t lad_n;
     int64_t bytes;
 };
 
@@ -50,6 +52,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
                                  uint64_t seed, int mode, int threads, int blocks_per_sm,
                                  cudaStream_t st);
 int static_scan_max_legs();
+helios_status launch_lad_table(int kind, int n, float* table, cudaStream_t st);
 size_t scan_params_bytes();
 
 struct AdjointLaunch {

@@ -89,6 +89,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
             o[a] = ff2d(f.oh[a], f.ol[a]);
             d[a] = ff2d(dh[a], dl[a]);
         }
+        const float Gs = proj_factor(sc, dh[2]);
         double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
         March m;
         if (march_init(sc, o, d, t_hi, m)) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
                         return;
                     }
                     if (len > 0.0f) {
-                        float xs = sc.G * dens * len;
+                        float xs = Gs * dens * len;
                         float w = -T * expm1f(-xs);
                         T *= expf(-xs);
                         FF R = ff_add_f(t_in, 0.5f * len);
@@ -322,6 +323,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             o[a] = ff2d(f.oh[a], f.ol[a]);
                             d[a] = ff2d(dh[a], dl[a]);
                         }
+                        const float Gs = proj_factor(sc, dh[2]);
                         March m;
                         if (march_init(sc, o, d, t_tri, m)) {
                             const int64_t k = p0 + pl;
@@ -351,7 +353,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         break;
                                     }
                                     if (len > 0.0f) {
-                                        float sigma = sc.G * dens;
+                                        float sigma = Gs * dens;
                                         if (MODE == 0) {
                                             // Eq. intersection_dist: s = -ln(u)/sigma
                                             uint64_t w[4];
@@ -691,11 +693,13 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         March mch;
                         uint32_t fl = 0;
                         float dabs[3] = {1.0f, 1.0f, 1.0f};
+                        float Gs = sc.G;
                         if (GRID && sc.has_grid && lane_on) {
                             double o[3], d[3];
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
                             for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
+                            Gs = proj_factor(sc, dh[2]);
                             for (int a = 0; a < 3; ++a) {
                                 o[a] = ff2d(f.oh[a], f.ol[a]);
                                 d[a] = ff2d(dh[a], dl[a]);
@@ -728,7 +732,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         break;
                                     }
                                     if (len > 0.0f) {
-                                        float xs = sc.G * dens * len;
+                                        float xs = Gs * dens * len;
                                         float w = -T * expm1f(-xs);
                                         T *= expf(-xs);
                                         FF R = ff_add_f(t_in, 0.5f * len);

@@ -77,3 +77,39 @@ def test_invalid_arguments_return_codes_without_a_gpu(lib):
                                      1024, None)
     assert code == -1
     assert b"n_scenes" in lib.helios_last_error()
+    # leaf-angle tables: bad requests are refused before any launch
+    assert lib.helios_lad_table(0, 91, ctypes.c_void_p(16), None) == -1
+    assert lib.helios_lad_table(7, 91, ctypes.c_void_p(16), None) == -1
+    assert lib.helios_lad_table(2, 1, ctypes.c_void_p(16), None) == -1
+    assert lib.helios_lad_table(2, 65537, ctypes.c_void_p(16), None) == -1
+    assert lib.helios_lad_table(2, 91, None, None) == -1
+    assert b"NULL" in lib.helios_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import paper_2101_09154_gb300 as hg
+    structs = {"helios_voxel_desc": hg.VoxelDesc, "helios_mesh_desc": hg.MeshDesc,
+               "helios_scanner_desc": hg.ScannerDesc, "helios_leg_desc": hg.LegDesc,
+               "helios_outputs": hg.Outputs, "helios_scan_opts": hg.ScanOpts}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "helios.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (cname, field, got, int(val))

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import scenes
+from oracle import lad
 from parity import compare, leg_view, to_np
 
 torch = pytest.importorskip("torch")
@@ -180,10 +181,14 @@ def test_bad_face_index_is_rejected(hg):
     assert e.value.code == -1
 
 
-def test_adjoint_matches_oracle(hg):
+@pytest.mark.parametrize("lad_kind", [None, "erectophile"])
+def test_adjoint_matches_oracle(hg, lad_kind):
     """Expected-mode adjoint: GPU gradients vs the oracle's analytic gradients
-    (the latter pinned to FP64 central differences on the CPU)."""
+    (the latter pinned to FP64 central differences on the CPU), with the
+    constant G and with a leaf-angle table."""
     w = scenes.uls_voxels(seed=4, n=32, n_pulses=1200, n_bins=384, agl=10.0, speed=1.0, prf=1000.0)
+    if lad_kind:
+        w.scenes[0].grids[0].lad = lad.table(lad_kind, 23).astype(np.float32)
     sc, leg = w.scanners[0], w.legs[0]
     gs = hg.Scene(w.scenes[0])
     out, lay = hg.scan([gs], [sc], [leg], mode=1)
@@ -397,3 +402,38 @@ def test_adjoint_rejects_opaque_grids(hg):
     with pytest.raises(hg.HeliosError) as e:
         hg.scan_adjoint([gs], w.scanners, w.legs, out["waveform"], out["window_bin"], out["subray_hit"])
     assert e.value.code == -6
+
+
+@pytest.mark.parametrize("kind", lad.KINDS)
+def test_lad_table_generator_matches_oracle(hg, kind):
+    """helios_lad_table (Ross kernel, Simpson, FP64 on the device) against the
+    oracle's quadrature of Eq. extinction's double integral."""
+    for n in (2, 91, 1000):
+        got = to_np(hg.lad_table(kind, n)).astype(np.float64)
+        ref = lad.table(kind, n, quad=96) if n < 1000 else None
+        if ref is None:
+            idx = np.array([0, 1, 250, 499, 500, 777, 998, 999])
+            ref_s = np.array([lad.ross_G(kind, i / (n - 1), 96) for i in idx])
+            assert np.abs(got[idx] - ref_s).max() <= 1e-6
+        else:
+            assert np.abs(got - ref).max() <= 1e-6, np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_uls_voxels_with_leaf_angle_table(hg, mode):
+    """sigma = G(|d_z|) density from an erectophile table (Table ladlut), both
+    modes; the scene is also built from the library's own table, which must
+    give the same result within the table's rounding."""
+    w = scenes.uls_voxels(seed=6, n=48, n_pulses=3001, n_bins=512, agl=12.0, speed=1.0, prf=2000.0)
+    w.scanners[0].scan_angle_max_rad = 0.6            # oblique subrays: G varies across the scan
+    w.scenes[0].grids[0].lad = lad.table("erectophile", 46).astype(np.float32)
+    _, _, res = run_both(hg, w, mode=mode, seed=11)
+    stats = compare(*res[0], expected_mode=(mode == 1))
+    assert stats["echoes"] > 1000
+    if mode == 1:
+        gsc = hg.Scene(w.scenes[0])
+        a, _ = hg.scan([gsc], w.scanners, w.legs, mode=1)
+        w.scenes[0].grids[0].lad = hg.lad_table("erectophile", 46)
+        b, _ = hg.scan([hg.Scene(w.scenes[0])], w.scanners, w.legs, mode=1)
+        A, B = to_np(a["waveform"]), to_np(b["waveform"])
+        assert np.abs(A - B).max() <= 1e-5 * np.abs(A).max()
