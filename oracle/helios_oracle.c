@@ -573,7 +573,7 @@ static void vpush(vlist* L, vseg s) {
  * mu = |d_z| (d a unit vector) and is read by linear interpolation. */
 static double proj_factor(const or_scene* sc, const double d[3]) {
     if (sc->lad_n < 2) return sc->G;
-    double t = fabs(d[2]) * (double)(sc->lad_n - 1);
+    double t = fmin(fabs(d[2]), 1.0) * (double)(sc->lad_n - 1);
     int64_t i = (int64_t)floor(t);
     if (i > sc->lad_n - 2) i = sc->lad_n - 2;
     double f = t - (double)i;

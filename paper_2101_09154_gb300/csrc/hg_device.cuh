@@ -67,7 +67,7 @@ struct DevScene {
 // constant G.  Evaluated once per subray, before its march.
 __device__ __forceinline__ float proj_factor(const DevScene& sc, float dz) {
     if (sc.lad_n < 2) return sc.G;
-    const float t = fabsf(dz) * (float)(sc.lad_n - 1);
+    const float t = fminf(fabsf(dz), 1.0f) * (float)(sc.lad_n - 1);   // NaN -> the last entry
     const int i = min((int)t, sc.lad_n - 2);
     const float f = t - (float)i;
     const float g0 = __ldg(sc.lad + i), g1 = __ldg(sc.lad + i + 1);
