@@ -67,12 +67,15 @@ class Leg(C.Structure):
                 ("n_pulses", C.c_int64), ("platform_noise_m", C.c_double)]
 
 
+class GridIn(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("cell", C.c_double), ("dims", C.c_int32 * 3),
+                ("opaque", C.c_int32), ("density", C.c_void_p), ("G", C.c_double),
+                ("leaf_refl", C.c_double), ("lad", C.c_void_p), ("lad_n", C.c_int32), ("pad", C.c_int32)]
+
+
 class SceneIn(C.Structure):
     _fields_ = [("n_tri", C.c_int64), ("tri", C.c_void_p), ("refl", C.c_void_p),
-                ("has_grid", C.c_int32), ("g_opaque", C.c_int32), ("g_origin", C.c_double * 3),
-                ("g_cell", C.c_double), ("g_dims", C.c_int32 * 3), ("pad1", C.c_int32),
-                ("g_density", C.c_void_p), ("g_G", C.c_double), ("g_leaf_refl", C.c_double),
-                ("g_lad", C.c_void_p), ("g_lad_n", C.c_int32), ("pad2", C.c_int32)]
+                ("n_grids", C.c_int32), ("pad0", C.c_int32), ("grids", C.c_void_p)]
 
 
 class Out(C.Structure):
@@ -205,38 +208,43 @@ class OracleScene:
         si.n_tri = self.n_tri
         si.tri = _ptr(self.tri)
         si.refl = _ptr(self.refl)
-        if len(scene.grids) > 1:
-            raise ValueError("the oracle handles at most one voxel grid per scene")
-        self.grid = scene.grids[0] if scene.grids else None
-        if self.grid is not None:
-            g = self.grid
-            self.density = np.ascontiguousarray(g.density, dtype=np.float32)
-            si.has_grid = 1
-            # the GPU receives FP32 origin/cell: use the same real numbers
-            si.g_origin = _d3(np.float32(g.origin).astype(np.float64))
-            si.g_cell = float(np.float32(g.cell))
-            si.g_dims = (C.c_int32 * 3)(*[int(x) for x in g.dims])
-            si.g_density = _ptr(self.density)
-            si.g_G = float(np.float32(g.G))
-            si.g_leaf_refl = float(np.float32(g.leaf_reflectance))
-            si.g_opaque = int(g.opaque)
+        # grids: FP32 inputs as the GPU receives them (the same real numbers)
+        self.grids = list(scene.grids)
+        self.grid = self.grids[0] if self.grids else None
+        self._gin = (GridIn * max(len(self.grids), 1))()
+        self.densities, self.lads, self.vox_offsets = [], [], [0]
+        for i, g in enumerate(self.grids):
+            gi = self._gin[i]
+            dens = np.ascontiguousarray(g.density, dtype=np.float32)
+            self.densities.append(dens)
+            gi.origin = _d3(np.float32(g.origin).astype(np.float64))
+            gi.cell = float(np.float32(g.cell))
+            gi.dims = (C.c_int32 * 3)(*[int(x) for x in g.dims])
+            gi.opaque = int(g.opaque)
+            gi.density = _ptr(dens)
+            gi.G = float(np.float32(g.G))
+            gi.leaf_refl = float(np.float32(g.leaf_reflectance))
             lad = getattr(g, "lad", None)
             if lad is not None:
-                # the library receives the table in FP32: use the same numbers
-                self.lad = np.ascontiguousarray(lad, dtype=np.float32)
-                si.g_lad = _ptr(self.lad)
-                si.g_lad_n = int(self.lad.shape[0])
-            self.n_vox = int(np.prod(g.dims))
-        else:
-            self.density = None
-            self.n_vox = 0
+                lt = np.ascontiguousarray(lad, dtype=np.float32)
+                self.lads.append(lt)
+                gi.lad = _ptr(lt)
+                gi.lad_n = int(lt.shape[0])
+            self.vox_offsets.append(self.vox_offsets[-1] + int(np.prod(g.dims)))
+        si.n_grids = len(self.grids)
+        si.grids = C.cast(self._gin, C.c_void_p)
+        self.density = self.densities[0] if self.densities else None
+        self.n_vox = self.vox_offsets[-1]
         self._si = si
         self.handle = lib().or_scene_build(C.byref(si))
 
-    def set_density(self, density):
-        """Point the grid at another density array (same shape) without rebuilding."""
-        self.density = np.ascontiguousarray(density, dtype=np.float32)
-        self._si.g_density = _ptr(self.density)
+    def set_density(self, density, grid=0):
+        """Point a grid at another density array (same shape)."""
+        d = np.ascontiguousarray(density, dtype=np.float32)
+        self.densities[grid] = d
+        if grid == 0:
+            self.density = d
+        self._gin[grid].density = _ptr(d)
         lib().or_scene_free(self.handle)
         self.handle = lib().or_scene_build(C.byref(self._si))
 

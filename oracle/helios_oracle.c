@@ -285,6 +285,17 @@ typedef struct {
     int64_t start, count;
 } bnode;
 
+struct or_grid {
+    double g0[3], gc;
+    int32_t gd[3];
+    int opaque;
+    const float* dens;
+    double G, leaf_refl;
+    const float* lad;
+    int64_t lad_n;
+    int64_t vox_off;      /* voxels of the earlier grids */
+};
+
 struct or_scene {
     int64_t n_tri;
     double* tv;       /* [n][9] */
@@ -294,13 +305,8 @@ struct or_scene {
     bnode* nodes;
     int64_t n_nodes, cap_nodes;
     double eps_box;
-    int has_grid, opaque;
-    double g0[3], gc;
-    int32_t gd[3];
-    const float* dens;
-    double G, leaf_refl;
-    const float* lad;
-    int64_t lad_n;
+    int n_grid;
+    struct or_grid* grid;
 };
 
 static void tri_bounds(const double* v, double lo[3], double hi[3]) {
@@ -391,18 +397,24 @@ or_scene* or_scene_build(const or_scene_in* in) {
     sc->nodes = (bnode*)malloc(sizeof(bnode) * sc->cap_nodes);
     sc->n_nodes = 0;
     if (n > 0) build_rec(sc, 0, n);
-    sc->has_grid = in->has_grid;
-    sc->opaque = in->g_opaque;
-    if (in->has_grid) {
-        for (int a = 0; a < 3; ++a) { sc->g0[a] = in->g_origin[a]; sc->gd[a] = in->g_dims[a]; }
-        sc->gc = in->g_cell;
-        sc->dens = in->g_density;
-        sc->G = in->g_G;
-        sc->leaf_refl = in->g_leaf_refl;
-        sc->lad = in->g_lad;
-        sc->lad_n = in->g_lad ? in->g_lad_n : 0;
+    sc->n_grid = in->n_grids < 0 ? 0 : (in->n_grids > OR_MAX_GRIDS ? OR_MAX_GRIDS : in->n_grids);
+    sc->grid = (struct or_grid*)calloc(sc->n_grid > 0 ? sc->n_grid : 1, sizeof(struct or_grid));
+    int64_t off = 0;
+    for (int i = 0; i < sc->n_grid; ++i) {
+        const or_grid_in* gi = &in->grids[i];
+        struct or_grid* g = &sc->grid[i];
+        for (int a = 0; a < 3; ++a) { g->g0[a] = gi->origin[a]; g->gd[a] = gi->dims[a]; }
+        g->gc = gi->cell;
+        g->opaque = gi->opaque;
+        g->dens = gi->density;
+        g->G = gi->G;
+        g->leaf_refl = gi->leaf_refl;
+        g->lad = gi->lad;
+        g->lad_n = gi->lad ? gi->lad_n : 0;
+        g->vox_off = off;
+        off += (int64_t)g->gd[0] * g->gd[1] * g->gd[2];
         for (int a = 0; a < 3; ++a) {
-            double e = fabs(sc->g0[a]) + sc->gd[a] * sc->gc;
+            double e = fabs(g->g0[a]) + g->gd[a] * g->gc;
             if (e > smax) smax = e;
         }
     }
@@ -413,7 +425,7 @@ or_scene* or_scene_build(const or_scene_in* in) {
 
 void or_scene_free(or_scene* sc) {
     if (!sc) return;
-    free(sc->tv); free(sc->cen); free(sc->order); free(sc->nodes);
+    free(sc->tv); free(sc->cen); free(sc->order); free(sc->nodes); free(sc->grid);
     free(sc);
 }
 
@@ -550,12 +562,13 @@ int64_t or_intersect_brute(const or_scene* sc, const double o[3], const double d
 /* replaces the epsilon re-cast of Sec. 5.1 by exact plane crossings.       */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int64_t vid;
+    int64_t vid;     /* voxel index within grid gi */
     double t_in, t_out;
     double sigma;
     int corner;      /* 1: another axis crossed within eps of the exit */
     int64_t alt_vid; /* the voxel an FP32 march could visit instead at that corner */
     int axis;        /* axis of the face the ray entered through, -1: started inside */
+    int gi;          /* grid */
 } vseg;
 
 typedef struct { vseg* v; int64_t n, cap; } vlist;
@@ -571,58 +584,75 @@ static void vpush(vlist* L, vseg s) {
 /* sigma = G * density (Eq. extinction).  With a leaf-angle table (Table ladlut)
  * G depends on the subray direction: the table holds G at mu_i = i/(n-1) of
  * mu = |d_z| (d a unit vector) and is read by linear interpolation. */
-static double proj_factor(const or_scene* sc, const double d[3]) {
-    if (sc->lad_n < 2) return sc->G;
-    double t = fmin(fabs(d[2]), 1.0) * (double)(sc->lad_n - 1);
+static double proj_factor(const struct or_grid* g, const double d[3]) {
+    if (g->lad_n < 2) return g->G;
+    double t = fmin(fabs(d[2]), 1.0) * (double)(g->lad_n - 1);
     int64_t i = (int64_t)floor(t);
-    if (i > sc->lad_n - 2) i = sc->lad_n - 2;
+    if (i > g->lad_n - 2) i = g->lad_n - 2;
     double f = t - (double)i;
-    double g0 = (double)sc->lad[i], g1 = (double)sc->lad[i + 1];
+    double g0 = (double)g->lad[i], g1 = (double)g->lad[i + 1];
     return g0 + f * (g1 - g0);
 }
 
-static double plane_t(const or_scene* sc, int a, int64_t i, const double o[3], const double d[3]) {
-    return (sc->g0[a] + (double)i * sc->gc - o[a]) / d[a];
+/* voxel id in outputs and the index of its transmission draw */
+static int64_t vox_id(const or_scene* sc, const vseg* v, int64_t vid) {
+    return sc->n_tri + sc->grid[v->gi].vox_off + vid;
+}
+static int64_t vox_draw(const or_scene* sc, const vseg* v, int64_t vid) {
+    return sc->grid[v->gi].vox_off + vid;
 }
 
-/* all voxels with positive segment length in [max(t_enter,0), min(t_exit,t_hi)) */
-static void march(const or_scene* sc, const double o[3], const double d[3], double t_hi, vlist* L) {
-    L->n = 0;
-    if (!sc->has_grid) return;
-    double tlo[3], thi[3];
-    double t_enter = 0.0, t_exit = INFINITY;
+static double plane_t(const struct or_grid* g, int a, int64_t i, const double o[3], const double d[3]) {
+    return (g->g0[a] + (double)i * g->gc - o[a]) / d[a];
+}
+
+/* entry and exit of the ray o + t d (t >= 0) with grid g's box; 0: no overlap */
+static int grid_span(const struct or_grid* g, const double o[3], const double d[3],
+                     double tlo[3], double thi[3], double* t_enter, double* t_exit) {
+    *t_enter = 0.0;
+    *t_exit = INFINITY;
     for (int a = 0; a < 3; ++a) {
-        double lo = sc->g0[a], hi = sc->g0[a] + (double)sc->gd[a] * sc->gc;
+        double lo = g->g0[a], hi = g->g0[a] + (double)g->gd[a] * g->gc;
         if (d[a] == 0.0) {
-            if (o[a] < lo || o[a] >= hi) return;
+            if (o[a] < lo || o[a] >= hi) return 0;
             tlo[a] = -INFINITY; thi[a] = INFINITY;
         } else {
             double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
             tlo[a] = ta < tb ? ta : tb;
             thi[a] = ta < tb ? tb : ta;
         }
-        if (tlo[a] > t_enter) t_enter = tlo[a];
-        if (thi[a] < t_exit) t_exit = thi[a];
+        if (tlo[a] > *t_enter) *t_enter = tlo[a];
+        if (thi[a] < *t_exit) *t_exit = thi[a];
     }
+    return *t_enter < *t_exit;
+}
+
+/* all voxels of grid gi with positive segment length in [max(t_enter,0), min(t_exit,t_hi)) */
+static void march_grid(const or_scene* sc, int gi, const double o[3], const double d[3], double t_hi,
+                       vlist* L) {
+    const struct or_grid* g = &sc->grid[gi];
+    double tlo[3], thi[3];
+    double t_enter, t_exit;
+    if (!grid_span(g, o, d, tlo, thi, &t_enter, &t_exit)) return;
     double t_end = t_exit < t_hi ? t_exit : t_hi;
     if (!(t_enter < t_end)) return;
-    const double G = proj_factor(sc, d);
+    const double G = proj_factor(g, d);
     int64_t idx[3];
     int step[3];
     double tn[3];
     for (int a = 0; a < 3; ++a) {
         step[a] = d[a] > 0.0 ? 1 : (d[a] < 0.0 ? -1 : 0);
         if (t_enter > 0.0 && tlo[a] == t_enter && d[a] != 0.0) {
-            idx[a] = d[a] > 0.0 ? 0 : sc->gd[a] - 1;
+            idx[a] = d[a] > 0.0 ? 0 : g->gd[a] - 1;
         } else {
             double p = o[a] + t_enter * d[a];
-            double f = floor((p - sc->g0[a]) / sc->gc);
+            double f = floor((p - g->g0[a]) / g->gc);
             if (f < 0) f = 0;
-            if (f > sc->gd[a] - 1) f = sc->gd[a] - 1;
+            if (f > g->gd[a] - 1) f = g->gd[a] - 1;
             idx[a] = (int64_t)f;
         }
-        if (step[a] > 0) tn[a] = plane_t(sc, a, idx[a] + 1, o, d);
-        else if (step[a] < 0) tn[a] = plane_t(sc, a, idx[a], o, d);
+        if (step[a] > 0) tn[a] = plane_t(g, a, idx[a] + 1, o, d);
+        else if (step[a] < 0) tn[a] = plane_t(g, a, idx[a], o, d);
         else tn[a] = INFINITY;
     }
     double t_in = t_enter;
@@ -630,22 +660,22 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
     if (t_enter > 0.0)
         for (int a = 2; a >= 0; --a)
             if (d[a] != 0.0 && tlo[a] == t_enter) entry = a;
-    const int64_t nx = sc->gd[0], ny = sc->gd[1];
-    for (int64_t guard = 0; guard < 4 * (int64_t)(sc->gd[0] + sc->gd[1] + sc->gd[2]) + 8; ++guard) {
+    const int64_t nx = g->gd[0], ny = g->gd[1];
+    for (int64_t guard = 0; guard < 4 * (int64_t)(g->gd[0] + g->gd[1] + g->gd[2]) + 8; ++guard) {
         int a = 0;
         if (tn[1] < tn[a]) a = 1;
         if (tn[2] < tn[a]) a = 2;
         double t_out = tn[a] < t_end ? tn[a] : t_end;
         int64_t vid = (idx[2] * ny + idx[1]) * nx + idx[0];
         if (t_out > t_in) {
-            vseg s = {vid, t_in, t_out, G * (double)sc->dens[vid], 0, -1, entry};
+            vseg s = {vid, t_in, t_out, G * (double)g->dens[vid], 0, -1, entry, gi};
             /* second-smallest crossing near the exit: order ambiguous in FP32 */
             for (int b = 0; b < 3; ++b) {
                 if (b == a || step[b] == 0) continue;
                 if (tn[a] < t_end && tn[b] - tn[a] <= eps_rel(tn[a])) {
                     int64_t j[3] = {idx[0], idx[1], idx[2]};
                     j[b] += step[b];
-                    if (j[b] >= 0 && j[b] < sc->gd[b]) {
+                    if (j[b] >= 0 && j[b] < g->gd[b]) {
                         s.corner = 1;
                         s.alt_vid = (j[2] * ny + j[1]) * nx + j[0];
                     }
@@ -655,11 +685,32 @@ static void march(const or_scene* sc, const double o[3], const double d[3], doub
         }
         if (tn[a] >= t_end) break;
         idx[a] += step[a];
-        if (idx[a] < 0 || idx[a] >= sc->gd[a]) break;
+        if (idx[a] < 0 || idx[a] >= g->gd[a]) break;
         entry = a;
         t_in = tn[a] > t_in ? tn[a] : t_in;
-        tn[a] = step[a] > 0 ? plane_t(sc, a, idx[a] + 1, o, d) : plane_t(sc, a, idx[a], o, d);
+        tn[a] = step[a] > 0 ? plane_t(g, a, idx[a] + 1, o, d) : plane_t(g, a, idx[a], o, d);
     }
+}
+
+/* The voxels along the ray up to t_hi, over all grids: the grids' boxes have
+ * disjoint interiors, so their segments follow one another in the order of
+ * the boxes' entry points; each grid is marched in that order. */
+static void march(const or_scene* sc, const double o[3], const double d[3], double t_hi, vlist* L) {
+    L->n = 0;
+    if (sc->n_grid == 0) return;
+    double te_all[OR_MAX_GRIDS];
+    int order[OR_MAX_GRIDS];
+    int n = 0;
+    for (int gi = 0; gi < sc->n_grid; ++gi) {
+        double tlo[3], thi[3], te, tx;
+        if (!grid_span(&sc->grid[gi], o, d, tlo, thi, &te, &tx) || !(te < t_hi)) continue;
+        /* insertion by (entry, grid index) */
+        int j = n++;
+        while (j > 0 && te_all[order[j - 1]] > te) { order[j] = order[j - 1]; --j; }
+        order[j] = gi;
+        te_all[gi] = te;
+    }
+    for (int i = 0; i < n; ++i) march_grid(sc, order[i], o, d, t_hi, L);
 }
 
 int64_t or_march(const or_scene* sc, const double o[3], const double d[3], double t_hi,
@@ -668,7 +719,7 @@ int64_t or_march(const or_scene* sc, const double o[3], const double d[3], doubl
     march(sc, o, d, t_hi, &L);
     int64_t n = L.n;
     for (int64_t i = 0; i < n && i < cap; ++i) {
-        vid[i] = L.v[i].vid;
+        vid[i] = vox_draw(sc, &L.v[i], L.v[i].vid);
         t_in[i] = L.v[i].t_in;
         t_out[i] = L.v[i].t_out;
     }
@@ -719,9 +770,9 @@ static void gpush(scratch_t* S, int64_t id, double v) {
     S->gn++;
 }
 
-static double voxel_power(const or_scanner* sn, const or_scene* sc, double Is, double R) {
+static double voxel_power(const or_scanner* sn, const struct or_grid* g, double Is, double R) {
     /* Eq. ladlut_intensity for a voxel return; reading: leaf reflectance, cos := 1 */
-    return or_triangle_power(sn, Is, R, sc->leaf_refl, 1.0);
+    return or_triangle_power(sn, Is, R, g->leaf_refl, 1.0);
 }
 
 static double delay_ns(double R) { return 2.0 * R / OR_C * 1e9; }
@@ -764,47 +815,37 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
     vlist* L = &J->S.vl;
     if (J->mode == 0) {
         /* stochastic transmission (Eq. intersection_dist): s = -ln(u)/sigma; an
-         * echo at entry + s if s < traversed length, else continue (Sec. 5.2). */
-        if (sc->opaque) {
-            /* non-transmissive voxels (Sec. 3.5.4): the first voxel of non-zero
-             * density stops the subray where it enters it, Lambertian on the
-             * face entered (cos = |d . n|; 1 when the ray starts inside) */
-            for (int64_t i = 0; i < L->n; ++i) {
-                vseg* v = &L->v[i];
-                if (v->corner && v->alt_vid >= 0 && (sc->dens[v->alt_vid] > 0.0f) != (v->sigma > 0.0))
+         * echo at entry + s if s < traversed length, else continue (Sec. 5.2).
+         * Non-transmissive grids (Sec. 3.5.4): the first voxel of non-zero
+         * density stops the subray where it enters it, Lambertian on the face
+         * entered (cos = |d . n|; 1 when the ray starts inside). */
+        for (int64_t i = 0; i < L->n; ++i) {
+            vseg* v = &L->v[i];
+            const struct or_grid* g = &sc->grid[v->gi];
+            if (g->opaque) {
+                if (v->corner && v->alt_vid >= 0 && (g->dens[v->alt_vid] > 0.0f) != (v->sigma > 0.0))
                     *flags |= OR_F_VOX;
                 if (v->sigma <= 0.0) continue;
                 double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
                 double Is = or_subray_intensity(sn, R, alpha);
-                ret_t r = {R, or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
+                ret_t r = {R, or_triangle_power(sn, Is, R, g->leaf_refl, c), vox_id(sc, v, v->vid), s};
                 rpush(&J->S.rl, r);
-                *ev_id = sc->n_tri + v->vid;
+                *ev_id = r.id;
                 *ev_R = R;
                 return;
             }
-            if (tri >= 0) {
-                double Is = or_subray_intensity(sn, t_tri, alpha);
-                ret_t r = {t_tri, or_triangle_power(sn, Is, t_tri, (double)sc->refl[tri], cos_tri), tri, s};
-                rpush(&J->S.rl, r);
-                *ev_id = tri;
-                *ev_R = t_tri;
-            }
-            return;
-        }
-        for (int64_t i = 0; i < L->n; ++i) {
-            vseg* v = &L->v[i];
             if (v->corner && v->alt_vid >= 0) {
-                double sa = proj_factor(sc, ds) * (double)sc->dens[v->alt_vid];
+                double sa = proj_factor(g, ds) * (double)g->dens[v->alt_vid];
                 if (sa > 0.0) {
                     uint64_t w[4];
-                    draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)v->alt_vid, w);
+                    draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->alt_vid), w);
                     double sal = -log(or_uniform24(w[0])) / sa;
                     if (sal <= 2.0 * eps_rel(v->t_out)) *flags |= OR_F_VOX;
                 }
             }
             if (v->sigma <= 0.0) continue;
             uint64_t w[4];
-            draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)v->vid, w);
+            draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->vid), w);
             double u = or_uniform24(w[0]);
             double sdist = -log(u) / v->sigma;
             double len = v->t_out - v->t_in;
@@ -813,9 +854,9 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
             if (sdist < len) {
                 double R = v->t_in + sdist;
                 double Is = or_subray_intensity(sn, R, alpha);
-                ret_t r = {R, voxel_power(sn, sc, Is, R), sc->n_tri + v->vid, s};
+                ret_t r = {R, voxel_power(sn, g, Is, R), vox_id(sc, v, v->vid), s};
                 rpush(&J->S.rl, r);
-                *ev_id = sc->n_tri + v->vid;
+                *ev_id = r.id;
                 *ev_R = R;
                 return;
             }
@@ -834,14 +875,15 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
     double T = 1.0;
     for (int64_t i = 0; i < L->n; ++i) {
         vseg* v = &L->v[i];
+        const struct or_grid* g = &sc->grid[v->gi];
         if (v->sigma <= 0.0) continue;
-        if (sc->opaque) {
+        if (g->opaque) {
             /* an opaque voxel returns all that reaches it and passes nothing;
              * the subray record keeps the triangle hit, as in every expected-mode
              * scan (it is the adjoint's checkpoint) */
             double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
             double Is = or_subray_intensity(sn, R, alpha);
-            ret_t r = {R, T * or_triangle_power(sn, Is, R, sc->leaf_refl, c), sc->n_tri + v->vid, s};
+            ret_t r = {R, T * or_triangle_power(sn, Is, R, g->leaf_refl, c), vox_id(sc, v, v->vid), s};
             rpush(&J->S.rl, r);
             if (tri >= 0) {
                 *ev_id = tri;
@@ -853,7 +895,7 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
         double a = exp(-v->sigma * len);
         double R = 0.5 * (v->t_in + v->t_out);
         double Is = or_subray_intensity(sn, R, alpha);
-        ret_t r = {R, T * (1.0 - a) * voxel_power(sn, sc, Is, R), sc->n_tri + v->vid, s};
+        ret_t r = {R, T * (1.0 - a) * voxel_power(sn, g, Is, R), vox_id(sc, v, v->vid), s};
         rpush(&J->S.rl, r);
         T *= a;
     }
@@ -892,7 +934,7 @@ static void adjoint_subray(job_t* J, const double* g, int32_t m,
         double a = exp(-v->sigma * len);
         double R = 0.5 * (v->t_in + v->t_out);
         double Is = or_subray_intensity(sn, R, alpha);
-        double P = voxel_power(sn, sc, Is, R);
+        double P = voxel_power(sn, &sc->grid[v->gi], Is, R);
         double tau = delay_ns(R);
         double acc = 0.0;
         for (int b = 0; b < nb; ++b) acc += g[b] * P * or_pulse_shape(sn, (double)(m + b) * dt - tau);
@@ -919,7 +961,7 @@ static void adjoint_subray(job_t* J, const double* g, int32_t m,
         double len = v->t_out - v->t_in;
         double a = exp(-v->sigma * len);
         double dsig = A[i] * T[i] * len * a - len * suffix;
-        gpush(&J->S, sc->n_tri + v->vid, proj_factor(sc, ds) * dsig);
+        gpush(&J->S, vox_id(sc, v, v->vid), proj_factor(&sc->grid[v->gi], ds) * dsig);
         suffix += A[i] * wk[i];
     }
     free(A); free(T); free(wk);

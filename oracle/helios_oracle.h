@@ -45,22 +45,32 @@ typedef struct {
     double platform_noise_m;     /* sigma of the per-pulse platform position noise (Sec. 3.7) */
 } or_leg;
 
+/* One voxel grid (Sec. 3.5.4).  Voxel (x,y,z) spans origin + [x,x+1)*cell etc. */
+typedef struct {
+    double origin[3];
+    double cell;
+    int32_t dims[3];             /* nx, ny, nz */
+    int32_t opaque;              /* non-transmissive voxels (Sec. 3.5.4) */
+    const float* density;        /* [nz][ny][nx] plant area density */
+    double G;                    /* sigma = G * density (no leaf-angle table) */
+    double leaf_refl;
+    const float* lad;            /* [lad_n] leaf-angle table G(mu) at mu_i = i/(n-1), mu =
+                                    |vertical component| of the subray (Eq. extinction, Table
+                                    ladlut), linear in between; NULL: the constant G */
+    int32_t lad_n, pad;
+} or_grid_in;
+
+/* A scene: triangles of all meshes, and voxel grids whose boxes have disjoint
+ * interiors.  Voxel ids: n_tri + (voxels of the earlier grids) + (z*ny + y)*nx + x. */
 typedef struct {
     int64_t n_tri;
     const float* tri;            /* [n_tri][3][3] vertex coordinates */
     const float* refl;           /* [n_tri] Lambertian reflectance */
-    int32_t has_grid, g_opaque;  /* g_opaque: non-transmissive voxels (Sec. 3.5.4) */
-    double g_origin[3];
-    double g_cell;
-    int32_t g_dims[3], pad1;     /* nx, ny, nz */
-    const float* g_density;      /* [nz][ny][nx] plant area density */
-    double g_G;                  /* sigma = G * density (no leaf-angle table) */
-    double g_leaf_refl;
-    const float* g_lad;          /* [g_lad_n] leaf-angle table G(mu) at mu_i = i/(n-1), mu =
-                                    |vertical component| of the subray (Eq. extinction, Table
-                                    ladlut), linear in between; NULL: the constant g_G */
-    int32_t g_lad_n, pad2;
+    int32_t n_grids, pad0;       /* at most OR_MAX_GRIDS */
+    const or_grid_in* grids;
 } or_scene_in;
+
+#define OR_MAX_GRIDS 4096
 
 typedef struct or_scene or_scene;
 

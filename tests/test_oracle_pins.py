@@ -840,3 +840,127 @@ def test_lad_adjoint_matches_central_differences():
         fd = (loss(dp.reshape(base.shape)) - loss(dm.reshape(base.shape))) / (2 * hh)
         assert abs(fd - d_dens[v]) <= 1e-5 * abs(d_dens[v]) + 1e-9 * np.abs(d_dens).max()
     osc.set_density(base)
+
+
+# --------------------------------------------------------------------------
+# several voxel grids in one scene (boxes with disjoint interiors)
+# --------------------------------------------------------------------------
+
+def _split_grid_scene(dens, origin, cell, splits, ground_z=-30.0, order=None):
+    """The grid of `dens` cut into pieces along x at the voxel indices `splits`."""
+    nz, ny, nx = dens.shape
+    cuts = [0] + list(splits) + [nx]
+    grids = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        grids.append(scenes.VoxelGrid(origin=(origin[0] + a * cell, origin[1], origin[2]), cell=cell,
+                                      dims=(b - a, ny, nz),
+                                      density=np.ascontiguousarray(dens[:, :, a:b], np.float32), G=0.5,
+                                      leaf_reflectance=0.5))
+    if order is not None:
+        grids = [grids[i] for i in order]
+    scene = _grid_scene(np.zeros((1, 1, 1), np.float32), origin=(-900.0, -900.0, -900.0), cell=0.5,
+                        ground_z=ground_z)
+    return scenes.Scene(meshes=scene.meshes, grids=grids)
+
+
+def _voxel_rows(scene, sc, leg, mode=1):
+    osc = oracle.OracleScene(scene)
+    return osc, oracle.scan(osc, sc, leg, mode=mode, seed=2)
+
+
+def test_grids_split_into_pieces_give_the_same_waveform():
+    """Cutting one grid into adjacent grids (in any listed order) changes
+    voxel ids only: the expected waveform is the same (the crossing planes are
+    the same numbers), and the adjoint's density gradient is the same once the
+    pieces are put back together."""
+    rng = np.random.default_rng(11)
+    dens = np.where(rng.random((6, 8, 12)) < 0.5, rng.uniform(0.2, 1.5, (6, 8, 12)), 0.0).astype(np.float32)
+    origin, cell = (-3.0, -2.0, -3.0), 0.5
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=24, grid_n_el=10, el_min_rad=-1.45,
+                        el_max_rad=-0.6, n_bins=400, beam_sample_quality=2)
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, start=(0.1, 0.2, 4.0), n_pulses=240)
+    one = _split_grid_scene(dens, origin, cell, [])
+    o1, r1 = _voxel_rows(one, sc, leg)
+    assert (_voxel_rows(one, sc, leg, mode=0)[1]["subray_hit"] >= o1.n_tri).mean() > 0.2
+    for splits, order in (([5], None), ([3, 7, 10], [2, 0, 3, 1])):
+        many = _split_grid_scene(dens, origin, cell, splits, order=order)
+        om, rm = _voxel_rows(many, sc, leg)
+        assert np.array_equal(rm["window_bin"], r1["window_bin"])
+        scale = np.abs(r1["waveform"]).max()
+        assert np.abs(rm["waveform"] - r1["waveform"]).max() <= 1e-12 * scale
+        # the adjoint, gathered back into the one grid's layout
+        pulses = np.arange(leg.n_pulses)
+        g = np.sin(np.arange(r1["waveform"].size).reshape(r1["waveform"].shape))
+        _, d1 = oracle.adjoint(o1, sc, leg, pulses, g, r1["window_bin"])
+        _, dm = oracle.adjoint(om, sc, leg, pulses, g, rm["window_bin"])
+        back = np.zeros(dens.shape)
+        cuts = [0] + splits + [dens.shape[2]]
+        pieces = list(zip(cuts[:-1], cuts[1:]))
+        if order is not None:
+            pieces = [pieces[i] for i in order]
+        for i, (a, b) in enumerate(pieces):
+            back[:, :, a:b] = dm[om.vox_offsets[i]:om.vox_offsets[i + 1]].reshape(dens.shape[0], dens.shape[1], b - a)
+        d1 = d1.reshape(dens.shape)
+        assert np.abs(back - d1).max() <= 1e-12 * np.abs(d1).max()
+
+
+def test_grids_along_one_ray_multiply_transmittance_and_keep_their_own_G():
+    """Two separate grids on a vertical ray: exp(-G1 d1 L1) exp(-G2 d2 L2) reaches
+    the ground, with G2 from the second grid's leaf-angle table (linear in mu);
+    listing the grids in either order changes nothing."""
+    sc = scenes.Scanner()
+    top = scenes.VoxelGrid(origin=(-1.0, -1.0, 2.0), cell=0.5, dims=(4, 4, 2),
+                           density=np.full((2, 4, 4), 0.8, np.float32), G=0.5)
+    low = scenes.VoxelGrid(origin=(-1.0, -1.0, -1.0), cell=0.5, dims=(4, 4, 4),
+                           density=np.full((4, 4, 4), 0.3, np.float32), G=0.9,
+                           lad=np.array([0.25, 0.375, 0.5, 0.625, 0.75], np.float32))
+    ground = _grid_scene(np.zeros((1, 1, 1), np.float32), origin=(-900.0, -900.0, -900.0), cell=0.5,
+                         ground_z=-3.0).meshes
+    bare = oracle.OracleScene(scenes.Scene(meshes=ground, grids=[]))
+    for phi in (0.0, 0.2):
+        d = np.array([0.0, math.sin(phi), -math.cos(phi)])
+        o = np.array([0.0, -6.0 * math.tan(phi), 6.0])
+        ref = None
+        for grids in ([top, low], [low, top]):
+            osc = oracle.OracleScene(scenes.Scene(meshes=ground, grids=grids))
+            R, P, ids, _ = oracle.trace_returns(osc, sc, o, d, mode=1)
+            R0, P0, _, _ = oracle.trace_returns(bare, sc, o, d, mode=1)
+            T = P[-1] / P0[0]
+            want = (math.exp(-0.5 * _f32(0.8) * 1.0 / math.cos(phi)) *
+                    math.exp(-(0.25 + 0.5 * math.cos(phi)) * _f32(0.3) * 2.0 / math.cos(phi)))
+            assert abs(T - want) < 1e-12
+            assert np.all(np.diff(R[:-1]) > 0)              # returns in range order across grids
+            if ref is None:
+                ref = (R, P)
+            else:
+                assert np.allclose(R, ref[0], rtol=0, atol=1e-12)
+                assert np.allclose(P, ref[1], rtol=1e-13, atol=0)
+
+
+def test_opaque_grid_behind_a_transmissive_one():
+    """A transmissive grid above an opaque one: subrays that cross the first
+    stop at the opaque grid's top face; the ids tell the grids apart."""
+    sc = scenes.Scanner()
+    top = scenes.VoxelGrid(origin=(-1.0, -1.0, 2.0), cell=0.5, dims=(4, 4, 2),
+                           density=np.full((2, 4, 4), 0.6, np.float32), G=0.5)
+    low = scenes.VoxelGrid(origin=(-1.0, -1.0, -1.0), cell=0.5, dims=(4, 4, 4),
+                           density=np.full((4, 4, 4), 1.0, np.float32), G=0.5, opaque=1)
+    ground = _grid_scene(np.zeros((1, 1, 1), np.float32), origin=(-900.0, -900.0, -900.0), cell=0.5,
+                         ground_z=-3.0).meshes
+    osc = oracle.OracleScene(scenes.Scene(meshes=ground, grids=[top, low]))
+    n_top = 2 * 4 * 4
+    d = np.array([0.0, 0.0, -1.0])
+    o = np.array([0.1, 0.1, 6.0])
+    stops, through = 0, 0
+    for k in range(400):
+        R, P, ids, _ = oracle.trace_returns(osc, sc, o, d, mode=0, seed=9, pulse=k)
+        assert len(ids) == 1
+        vid = ids[0] - osc.n_tri
+        if vid < n_top:
+            stops += 1
+            assert 3.0 <= R[0] <= 4.0                       # inside the top grid (z in [2, 3])
+        else:
+            through += 1
+            assert abs(R[0] - 5.0) < 1e-9                   # the opaque grid's top face at z = 1
+    p = math.exp(-0.5 * _f32(0.6) * 1.0)
+    assert abs(through / 400 - p) < 4.5 * math.sqrt(p * (1 - p) / 400)
