@@ -125,9 +125,13 @@ typedef struct {
 } helios_voxel_desc;
 
 /* A scene: meshes are concatenated in order; triangle id = offset of its mesh
- * + face index.  This build supports at most 16 meshes and at most one voxel
- * grid per scene (HELIOS_ERR_UNSUPPORTED otherwise).  Voxel primitive ids are
- * n_triangles + (z*ny + y)*nx + x. */
+ * + face index.  At most 16 meshes and 4096 voxel grids per scene
+ * (HELIOS_ERR_UNSUPPORTED otherwise).  The grids' boxes must have disjoint
+ * interiors (touching faces are allowed; INVALID_ARG otherwise): a ray's
+ * segments in them then follow the order of its entry points, which is the
+ * order its transmission is applied in.  Voxel primitive ids are n_triangles +
+ * (voxels of the earlier grids) + (z*ny + y)*nx + x; the stochastic
+ * transmission draw of a voxel is keyed by that id minus n_triangles. */
 typedef struct {
     const helios_mesh_desc* meshes;
     int32_t n_meshes;
@@ -150,8 +154,10 @@ typedef struct {
  * complete on return.  Temporary buffers are stream-ordered allocations
  * (cudaMallocAsync) freed before return; the scene's own buffers come from
  * cudaMalloc.  Errors: INVALID_ARG (NULL or negative sizes, a face index
- * outside its mesh), UNSUPPORTED (more than 16 meshes or 1 grid, ids beyond
- * 32 bits), OOM, CUDA. */
+ * outside its mesh, overlapping grid boxes, a bad leaf-angle table),
+ * UNSUPPORTED (more than 16 meshes or 4096 grids, ids beyond 32 bits), OOM,
+ * CUDA.  With several grids the build also forms a BVH over their boxes (host,
+ * median split) and a device array of their descriptors. */
 HELIOS_API helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_stream,
                                  helios_scene** out);
 /* Leaf-angle distributions (de Wit) for helios_lad_table, Sec. 3.5.4. */

@@ -257,9 +257,13 @@ class Scene:
             md[i].object_id = m.object_id
         self.density = []
         lads = []
+        shared = {}      # grids that share one density array share its device copy
         gd = (VoxelDesc * max(len(scene.grids), 1))()
         for i, g in enumerate(scene.grids):
-            dens = torch.as_tensor(np.ascontiguousarray(g.density, np.float32)).to(dev)
+            key = id(g.density)
+            if key not in shared:
+                shared[key] = (g.density, torch.as_tensor(np.ascontiguousarray(g.density, np.float32)).to(dev))
+            dens = shared[key][1]
             self.density.append(dens)
             lad = getattr(g, "lad", None)
             if lad is not None:

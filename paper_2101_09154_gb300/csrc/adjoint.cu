@@ -22,7 +22,7 @@ struct AdjParams {
     DevScanner scanners[kMaxScanners];
     DevLeg leg;
     float* d_refl[kMaxScenes][kMaxMesh];
-    float* d_dens[kMaxScenes];
+    int32_t want_dens[kMaxScenes];   // some grid of the scene takes a density gradient
     const float* g;
     const int32_t* window;
     const int32_t* subray_hit;
@@ -59,6 +59,25 @@ __device__ __forceinline__ float corr_tab(const float4* C, int c0, int ncell, fl
     return fmaf(d, fmaf(d * 0.5f, fmaf(d * (1.0f / 3.0f), t.w, t.z), t.y), t.x);
 }
 
+// the grid holding voxel vx of the scene's concatenated voxels: its gradient
+// array (NULL: none wanted) and the voxel's index in it
+template <int GK>
+__device__ __forceinline__ void grid_of_voxel(const DevScene& sc, int32_t vx, float*& dd, int32_t& vid) {
+    if (GK == 1 || sc.n_grid == 1) {
+        dd = sc.grid.ddens;
+        vid = vx;
+        return;
+    }
+    int lo = 0, hi = sc.n_grid - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&sc.grids[mid].vox_off) <= vx) lo = mid; else hi = mid - 1;
+    }
+    dd = sc.grids[lo].ddens;
+    vid = vx - __ldg(&sc.grids[lo].vox_off);
+}
+
+template <int GK>
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tab = P.cb > 0;
@@ -76,7 +95,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     const int c0 = (cb + 3) >> 1;     // table cell of bin 0
     const float dt = (float)sn.bin_ns;
     float* const* drefl = P.d_refl[lg.scene];
-    float* ddens = P.d_dens[lg.scene];
     for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
     if (tab) {
         // h_k = p(k bin) (1, u/sigma, (u^2-1)/sigma^2, (u^3-3u)/sigma^3), u = k bin/sigma
@@ -162,7 +180,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 const SubrayConst& c = s_sc[ss];
                 float dh[3], dl[3];
                 subray_dir_ff(f, c, dh, dl);
-                const float Gs = proj_factor(sc, dh[2]);   // sigma = Gs density
                 double o[3], d[3];
                 for (int a = 0; a < 3; ++a) {
                     o[a] = ff2d(f.oh[a], f.ol[a]);
@@ -199,46 +216,52 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     rho = __ldg(&sc.refl[mesh][face]);
                     if (!(t_tri > 0.0)) { t_tri = CUDART_INF; hit = -1; }
                 }
-                const bool grid = sc.has_grid != 0;
-                // ---- pass A: march once; total of A_k w_k, and each voxel's
-                // terms in the lane's list [vid, G A T l e^{-sigma l}, G l, A w] ----
+                const bool grid = GK > 0 && sc.has_grid != 0;
+                // ---- pass A: march once, grid after grid in entry order; total
+                // of A_k w_k, and each voxel's terms in the lane's list
+                // [voxel, G A T l e^{-sigma l}, G l, A w] ----
                 double total = 0.0;
                 float T = 1.0f;
                 uint32_t fl = 0;
                 int n = 0;
-                const bool listing = RL != nullptr && ddens != nullptr;
-                March mch;
-                if (grid && march_init(sc, o, d, t_tri, mch)) {
-                    for (;;) {
-                        VoxSeg v;
-                        if (!march_current(sc, mch, v)) break;
-                        float dens = voxel_density<true>(sc, mch, v);
-                        if (dens > 0.0f) {
-                            FF t_in, t_out;
-                            march_segment_ff(mch, v, t_in, t_out);
-                            float len = ff_diff(t_out, t_in);
-                            if (len > 0.0f) {
-                                float xs = Gs * dens * len;
-                                float a = expf(-xs);
-                                float w = -T * expm1f(-xs);
-                                FF R = ff_add_f(t_in, 0.5f * len);
-                                float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
-                                          amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
-                                total += (double)A * (double)w;
-                                if (listing && n < P.rl_cap) {
-                                    const size_t e = (size_t)n * 32 + lane;
-                                    __stcg(reinterpret_cast<int32_t*>(RL) + e, (int32_t)v.vid);
-                                    __stcg(RL + RLs + e, Gs * A * T * len * a);
-                                    __stcg(RL + 2 * RLs + e, Gs * len);
-                                    __stcg(RL + 3 * RLs + e, A * w);
+                const bool want = P.want_dens[lg.scene] != 0;
+                const bool listing = RL != nullptr && want;
+                if (grid) {
+                    walk_grids<GK>(sc, o, d, t_tri, [&](const DevGrid& G, March& mch) -> bool {
+                        const float Gs = proj_factor(G, dh[2]);   // sigma = Gs density
+                        for (;;) {
+                            VoxSeg v;
+                            if (!march_current(G, mch, v)) return true;
+                            float dens = voxel_density<true>(G, mch, v);
+                            if (dens > 0.0f) {
+                                FF t_in, t_out;
+                                march_segment_ff(mch, v, t_in, t_out);
+                                float len = ff_diff(t_out, t_in);
+                                if (len > 0.0f) {
+                                    float xs = Gs * dens * len;
+                                    float a = expf(-xs);
+                                    float w = -T * expm1f(-xs);
+                                    FF R = ff_add_f(t_in, 0.5f * len);
+                                    float A = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f) *
+                                              amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
+                                    total += (double)A * (double)w;
+                                    if (listing && n < P.rl_cap) {
+                                        // the voxel's index over all of the scene's grids
+                                        const size_t e = (size_t)n * 32 + lane;
+                                        __stcg(reinterpret_cast<int32_t*>(RL) + e, G.vox_off + (int32_t)v.vid);
+                                        __stcg(RL + RLs + e, Gs * A * T * len * a);
+                                        __stcg(RL + 2 * RLs + e, Gs * len);
+                                        __stcg(RL + 3 * RLs + e, A * w);
+                                    }
+                                    ++n;
+                                    T *= a;
                                 }
-                                ++n;
-                                T *= a;
                             }
+                            // an empty brick is crossed in one jump
+                            if (!(dens < 0.0f ? march_skip_brick(G, mch, fl) : march_step(mch, v, fl)))
+                                return true;
                         }
-                        // an empty brick is crossed in one jump
-                        if (!(dens < 0.0f ? march_skip_brick(sc, mch, fl) : march_step(mch, v, fl))) break;
-                    }
+                    });
                 }
                 float A_tri = 0.0f;
                 if (hit >= 0) {
@@ -247,30 +270,34 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     total += (double)A_tri * (double)rho * (double)T;
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
                 }
-                if (!grid || !ddens || n == 0) continue;
+                if (!grid || !want || n == 0) continue;
                 if (listing && n <= P.rl_cap) {
                     // ---- pass B from the list, back to front: the suffix
                     // sum_{k>j} A_k w_k + A_tri rho T_{K+1} grows term by term ----
                     float suffix = A_tri * rho * T;
                     for (int e = n - 1; e >= 0; --e) {
                         const size_t o2 = (size_t)e * 32 + lane;
-                        const int32_t vid = __ldcg(reinterpret_cast<const int32_t*>(RL) + o2);
+                        const int32_t vx = __ldcg(reinterpret_cast<const int32_t*>(RL) + o2);
                         const float t1 = __ldcg(RL + RLs + o2);
                         const float gl = __ldcg(RL + 2 * RLs + o2);
                         const float aw = __ldcg(RL + 3 * RLs + o2);
-                        atomicAdd(&ddens[vid], fmaf(-gl, suffix, t1));
+                        float* dd;
+                        int32_t vid;
+                        grid_of_voxel<GK>(sc, vx, dd, vid);
+                        if (dd) atomicAdd(&dd[vid], fmaf(-gl, suffix, t1));
                         suffix += aw;
                     }
                     continue;
                 }
                 // ---- pass B by a second march (list too long): suffix = total - prefix ----
-                if (march_init(sc, o, d, t_tri, mch)) {
-                    double prefix = 0.0;
-                    float Tb = 1.0f;
+                double prefix = 0.0;
+                float Tb = 1.0f;
+                walk_grids<GK>(sc, o, d, t_tri, [&](const DevGrid& G, March& mch) -> bool {
+                    const float Gs = proj_factor(G, dh[2]);
                     for (;;) {
                         VoxSeg v;
-                        if (!march_current(sc, mch, v)) break;
-                        float dens = voxel_density<true>(sc, mch, v);
+                        if (!march_current(G, mch, v)) return true;
+                        float dens = voxel_density<true>(G, mch, v);
                         if (dens > 0.0f) {
                             FF t_in, t_out;
                             march_segment_ff(mch, v, t_in, t_out);
@@ -280,19 +307,20 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 float a = expf(-xs);
                                 float w = -Tb * expm1f(-xs);
                                 FF R = ff_add_f(t_in, 0.5f * len);
-                                float A = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f) *
+                                float A = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f) *
                                           amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                 prefix += (double)A * (double)w;
                                 double suffix = total - prefix;
                                 double dsig = (double)A * Tb * len * a - len * suffix;
-                                atomicAdd(&ddens[v.vid], (float)((double)Gs * dsig));
+                                if (G.ddens) atomicAdd(&G.ddens[v.vid], (float)((double)Gs * dsig));
                                 Tb *= a;
                             }
                         }
                         // an empty brick is crossed in one jump
-                        if (!(dens < 0.0f ? march_skip_brick(sc, mch, fl) : march_step(mch, v, fl))) break;
+                        if (!(dens < 0.0f ? march_skip_brick(G, mch, fl) : march_step(mch, v, fl)))
+                            return true;
                     }
-                }
+                });
             }
             __syncwarp();
         }
@@ -313,7 +341,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         for (size_t i = 0; i < L.scenes.size(); ++i) {
             p->scenes[i] = L.scenes[i];
             for (int m = 0; m < kMaxMesh; ++m) p->d_refl[i][m] = L.d_refl[i][m];
-            p->d_dens[i] = L.d_density[i];
+            p->want_dens[i] = L.want_dens[i];
         }
         for (size_t i = 0; i < L.scanners.size(); ++i) p->scanners[i] = L.scanners[i];
         p->leg = lg;
@@ -339,25 +367,25 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
             delete p;
             return set_error(HELIOS_ERR_UNSUPPORTED, "adjoint work item needs %zu bytes of shared memory", smem);
         }
-        cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const DevScene& sc = L.scenes[lg.scene];
+        auto kern = sc.n_grid > 1 ? adjoint_kernel<2> : adjoint_kernel<1>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { delete p; return set_cuda_error("cudaFuncSetAttribute(adjoint)", e); }
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel, L.threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, L.threads, smem);
         if (occ < 1) { delete p; return set_error(HELIOS_ERR_UNSUPPORTED, "adjoint kernel does not fit"); }
         int64_t cap = (int64_t)sms * occ;
         int grid = (int)(items < cap ? items : cap);
         // voxel return lists (ids must fit int32); longer paths march twice
         float* list = nullptr;
-        const DevScene& sc = L.scenes[lg.scene];
-        const int64_t nvox = sc.has_grid ? (int64_t)sc.dims[0] * sc.dims[1] * sc.dims[2] : 0;
-        if (nvox > 0 && nvox < INT32_MAX && L.d_density[lg.scene]) {
+        if (sc.n_grid > 0 && L.want_dens[lg.scene]) {
             p->rl_cap = kReturnListCap;
             e = cudaMallocAsync(reinterpret_cast<void**>(&list),
                                 (size_t)grid * (L.threads / 32) * 4 * p->rl_cap * 32 * sizeof(float), st);
             if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(adjoint lists)", e); }
             p->list = list;
         }
-        adjoint_kernel<<<grid, L.threads, smem, st>>>(*p);
+        kern<<<grid, L.threads, smem, st>>>(*p);
         e = cudaGetLastError();
         if (list) cudaFreeAsync(list, st);
         delete p;

@@ -438,28 +438,89 @@ OccupancyMasks::~OccupancyMasks() {
     for (void* p : bufs) cudaFreeAsync(p, st);
 }
 
-helios_status build_occupancy(std::vector<DevScene>& scenes, cudaStream_t st, OccupancyMasks& keep) {
+// The same masks for every grid of a scene with several: blockIdx.y = grid;
+// each grid's words start at its own occ pointer.
+__global__ void k_occupancy_grids(const DevGrid* __restrict__ grids) {
+    const DevGrid& G = grids[blockIdx.y];
+    const int64_t n_bricks = (int64_t)G.bdims[0] * G.bdims[1] * G.bdims[2];
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)blockIdx.x * blockDim.x >= n_bricks) return;   // whole block past this grid
+    bool any = false;
+    if (b < n_bricks) {
+        const int bx = G.bdims[0], by = G.bdims[1];
+        const int dx = G.dims[0], dy = G.dims[1], dz = G.dims[2];
+        const int x0 = (int)(b % bx) * kBrick;
+        const int64_t r = b / bx;
+        const int y0 = (int)(r % by) * kBrick, z0 = (int)(r / by) * kBrick;
+        const int x1 = min(x0 + kBrick, dx), y1 = min(y0 + kBrick, dy), z1 = min(z0 + kBrick, dz);
+        for (int z = z0; z < z1; ++z)
+            for (int y = y0; y < y1; ++y) {
+                const float* row = G.density + ((int64_t)z * dy + y) * dx;
+                for (int x = x0; x < x1; ++x) any |= __ldg(row + x) > 0.0f;
+            }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if ((threadIdx.x & 31) == 0 && b < n_bricks) const_cast<uint32_t*>(G.occ)[b >> 5] = m;
+}
+
+helios_status build_occupancy(std::vector<DevScene>& scenes, helios_scene* const* hs, cudaStream_t st,
+                              OccupancyMasks& keep, const helios_scene_grads* grads) {
     keep.st = st;
-    for (DevScene& d : scenes) {
-        d.occ = nullptr;
-        if (!d.has_grid || d.density == nullptr) continue;
-        int64_t nb = 1;
-        for (int a = 0; a < 3; ++a) {
-            d.bdims[a] = (d.dims[a] + kBrick - 1) >> kBrickLog2;
-            nb *= d.bdims[a];
+    for (size_t i = 0; i < scenes.size(); ++i) {
+        DevScene& d = scenes[i];
+        float* const* dd = grads ? grads[i].d_density : nullptr;
+        if (d.n_grid == 1) {
+            DevGrid& g = d.grid;
+            g.occ = nullptr;
+            g.ddens = dd ? dd[0] : nullptr;
+            int64_t nb = (int64_t)g.bdims[0] * g.bdims[1] * g.bdims[2];
+            if (nb <= 0 || nb >= ((int64_t)1 << 31)) continue;   // no mask: plain density reads
+            const int64_t words = (nb + 31) >> 5;
+            uint32_t* occ = nullptr;
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&occ), words * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(occupancy)", e);
+            keep.bufs.push_back(occ);
+            const int threads = 256;
+            k_occupancy<<<(unsigned)((nb + threads - 1) / threads), threads, 0, st>>>(
+                g.density, g.dims[0], g.dims[1], g.dims[2], g.bdims[0], g.bdims[1], nb, occ);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return set_cuda_error("occupancy kernel launch", e);
+            g.occ = occ;
+            continue;
         }
-        if (nb <= 0 || nb >= ((int64_t)1 << 31)) continue;   // no mask: plain density reads
-        const int64_t words = (nb + 31) >> 5;
+        if (d.n_grid < 2) continue;
+        // several grids: one mask buffer, one descriptor array for this call
+        std::vector<DevGrid> G = hs[i]->grids;
+        int64_t words = 0, max_nb = 0;
+        std::vector<int64_t> woff(G.size());
+        for (size_t k = 0; k < G.size(); ++k) {
+            const int64_t nb = (int64_t)G[k].bdims[0] * G[k].bdims[1] * G[k].bdims[2];
+            woff[k] = words;
+            words += (nb + 31) >> 5;
+            max_nb = std::max(max_nb, nb);
+        }
         uint32_t* occ = nullptr;
+        DevGrid* dg = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&occ), words * sizeof(uint32_t), st);
         if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(occupancy)", e);
         keep.bufs.push_back(occ);
+        e = cudaMallocAsync(reinterpret_cast<void**>(&dg), sizeof(DevGrid) * G.size(), st);
+        if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(grid descriptors)", e);
+        keep.bufs.push_back(dg);
+        for (size_t k = 0; k < G.size(); ++k) {
+            G[k].occ = occ + woff[k];
+            G[k].ddens = dd ? dd[k] : nullptr;
+        }
+        // pageable source: the call returns once the bytes are staged
+        e = cudaMemcpyAsync(dg, G.data(), sizeof(DevGrid) * G.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return set_cuda_error("grid descriptors copy", e);
         const int threads = 256;
-        k_occupancy<<<(unsigned)((nb + threads - 1) / threads), threads, 0, st>>>(
-            d.density, d.dims[0], d.dims[1], d.dims[2], d.bdims[0], d.bdims[1], nb, occ);
+        if (max_nb >= ((int64_t)1 << 31)) return set_error(HELIOS_ERR_UNSUPPORTED, "grid too large for masks");
+        dim3 grid((unsigned)((max_nb + threads - 1) / threads), (unsigned)G.size());
+        k_occupancy_grids<<<grid, threads, 0, st>>>(dg);
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_cuda_error("occupancy kernel launch", e);
-        d.occ = occ;
+        d.grids = dg;
     }
     return HELIOS_OK;
 }

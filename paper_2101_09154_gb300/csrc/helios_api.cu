@@ -3,6 +3,7 @@
 #include "hg_host.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -132,21 +133,171 @@ static DevScene dev_scene(const helios_scene* s) {
     d.n_tri = (int32_t)s->n_tri;
     d.n_int = (int32_t)s->n_int;
     d.n_mesh = s->n_mesh;
-    d.has_grid = s->n_grid;
-    if (s->n_grid) {
-        d.density = s->grid.density;
-        for (int a = 0; a < 3; ++a) {
-            d.dims[a] = s->grid.dims[a];
-            d.g0[a] = s->grid.origin[a];
-        }
-        d.G = s->grid.G;
-        d.leaf_refl = s->grid.leaf_reflectance;
-        d.opaque = s->grid.opaque != 0;
-        d.cell = s->grid.cell;
-        d.lad = s->lad;
-        d.lad_n = s->lad_n;
+    d.n_grid = s->n_grid;
+    d.has_grid = s->n_grid > 0;
+    if (s->n_grid == 1) d.grid = s->grids[0];
+    if (s->n_grid > 1) {
+        d.grids = s->grids_d;
+        d.gnodes = s->gnodes;
     }
     return d;
+}
+
+static void free_scene_buffers(helios_scene* s) {
+    cudaFree(s->nodes);
+    cudaFree(s->nodes4);
+    cudaFree(s->tris);
+    cudaFree(s->tri_index);
+    for (float* p : s->lads) cudaFree(p);
+    s->lads.clear();
+    cudaFree(s->grids_d);
+    cudaFree(s->gnodes);
+    s->nodes = s->tris = s->nodes4 = s->gnodes = nullptr;
+    s->tri_index = nullptr;
+    s->grids_d = nullptr;
+}
+
+// Boxes of a scene's grids must have disjoint interiors (touching faces are
+// fine): then a ray's segments in them follow the order of the entry points.
+// Sweep along x over the boxes sorted by their low x.
+static helios_status check_grid_boxes(const helios_voxel_desc* g, int n) {
+    if (n < 2) return HELIOS_OK;
+    std::vector<std::array<double, 6>> b((size_t)n);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            b[i][a] = (double)g[i].origin[a];
+            b[i][3 + a] = (double)g[i].origin[a] + (double)g[i].dims[a] * (double)g[i].cell;
+        }
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return b[x][0] < b[y][0]; });
+    for (int i = 0; i < n; ++i) {
+        const auto& p = b[order[i]];
+        for (int j = i + 1; j < n && b[order[j]][0] < p[3]; ++j) {
+            const auto& q = b[order[j]];
+            if (p[1] < q[4] && q[1] < p[4] && p[2] < q[5] && q[2] < p[5])
+                return set_error(HELIOS_ERR_INVALID_ARG, "grids %d and %d overlap", order[i], order[j]);
+        }
+    }
+    return HELIOS_OK;
+}
+
+// BVH over the grids' boxes (median split on the longest axis of the box
+// centres), nodes in the layout of the triangle BVH: child boxes and
+// (child0, child1) with leaf children ~grid.  Boxes are widened so that a
+// ray the FP64 march takes into a grid is never culled by the FP32 test.
+static int grid_bvh_rec(const std::vector<std::array<float, 6>>& box, std::vector<int>& idx, int lo, int hi,
+                        std::vector<float4>& nodes, std::array<float, 6>& out_box) {
+    auto merge = [](std::array<float, 6>& a, const std::array<float, 6>& c) {
+        for (int k = 0; k < 3; ++k) {
+            a[k] = std::min(a[k], c[k]);
+            a[3 + k] = std::max(a[3 + k], c[3 + k]);
+        }
+    };
+    if (hi - lo == 1) {
+        out_box = box[idx[lo]];
+        return ~idx[lo];
+    }
+    float cmin[3] = {3e38f, 3e38f, 3e38f}, cmax[3] = {-3e38f, -3e38f, -3e38f};
+    for (int i = lo; i < hi; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const float c = 0.5f * (box[idx[i]][k] + box[idx[i]][3 + k]);
+            cmin[k] = std::min(cmin[k], c);
+            cmax[k] = std::max(cmax[k], c);
+        }
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (cmax[k] - cmin[k] > cmax[ax] - cmin[ax]) ax = k;
+    const int mid = (lo + hi) / 2;
+    std::nth_element(idx.begin() + lo, idx.begin() + mid, idx.begin() + hi, [&](int x, int y) {
+        return box[x][ax] + box[x][3 + ax] < box[y][ax] + box[y][3 + ax];
+    });
+    const int node = (int)(nodes.size() / 4);
+    nodes.resize(nodes.size() + 4);
+    std::array<float, 6> b0, b1;
+    const int c0 = grid_bvh_rec(box, idx, lo, mid, nodes, b0);
+    const int c1 = grid_bvh_rec(box, idx, mid, hi, nodes, b1);
+    float4* n = &nodes[(size_t)node * 4];
+    n[0] = make_float4(b0[0], b0[1], b0[2], b0[3]);
+    n[1] = make_float4(b0[4], b0[5], b1[0], b1[1]);
+    n[2] = make_float4(b1[2], b1[3], b1[4], b1[5]);
+    int4 ch = make_int4(c0, c1, -1, ax);
+    memcpy(&n[3], &ch, sizeof(ch));
+    out_box = b0;
+    merge(out_box, b1);
+    return node;
+}
+
+// The grids' device descriptors, leaf-angle table copies and, with several
+// grids, their BVH.
+static helios_status build_grids(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st) {
+    const int n = desc->n_grids;
+    s->grids.assign((size_t)n, DevGrid{});
+    int64_t vox = 0;
+    for (int i = 0; i < n; ++i) {
+        const helios_voxel_desc& g = desc->grids[i];
+        DevGrid& d = s->grids[i];
+        d.density = g.density;
+        for (int a = 0; a < 3; ++a) {
+            d.g0[a] = g.origin[a];
+            d.dims[a] = g.dims[a];
+            d.bdims[a] = (g.dims[a] + kBrick - 1) >> kBrickLog2;
+        }
+        d.cell = g.cell;
+        d.opaque = g.opaque != 0;
+        d.G = g.G;
+        d.leaf_refl = g.leaf_reflectance;
+        d.vox_off = (int32_t)vox;
+        vox += (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+        if (g.lad_table) {
+            // leaf-angle table: read (host or device memory), checked, copied
+            const int32_t m = g.lad_n;
+            std::vector<float> h((size_t)m);
+            cudaError_t e = cudaMemcpyAsync(h.data(), g.lad_table, sizeof(float) * (size_t)m, cudaMemcpyDefault, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return set_cuda_error("reading a leaf-angle table", e);
+            for (int32_t k = 0; k < m; ++k)
+                if (!(h[k] >= 0.0f && h[k] <= 3.0e38f))
+                    return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: lad_table[%d] is negative or not finite", i, k);
+            float* dl = nullptr;
+            e = cudaMalloc(&dl, sizeof(float) * (size_t)m);
+            if (e != cudaSuccess) return set_cuda_error("leaf-angle table allocation", e);
+            s->lads.push_back(dl);
+            e = cudaMemcpy(dl, h.data(), sizeof(float) * (size_t)m, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return set_cuda_error("leaf-angle table copy", e);
+            d.lad = dl;
+            d.lad_n = m;
+            s->bytes += (int64_t)sizeof(float) * m;
+        }
+    }
+    if (n < 2) return HELIOS_OK;
+    std::vector<std::array<float, 6>> box((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const DevGrid& d = s->grids[i];
+        double m = 0.0;
+        for (int a = 0; a < 3; ++a)
+            m = std::max(m, std::max(std::fabs((double)d.g0[a]),
+                                     std::fabs((double)d.g0[a] + (double)d.dims[a] * d.cell)));
+        const double w = 1e-5 * m + 1e-3 * (double)d.cell;
+        for (int a = 0; a < 3; ++a) {
+            box[i][a] = (float)((double)d.g0[a] - w);
+            box[i][3 + a] = (float)((double)d.g0[a] + (double)d.dims[a] * d.cell + w);
+        }
+    }
+    std::vector<int> idx((size_t)n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::vector<float4> nodes;
+    nodes.reserve((size_t)4 * (n - 1));
+    std::array<float, 6> root;
+    grid_bvh_rec(box, idx, 0, n, nodes, root);
+    cudaError_t e = cudaMalloc(&s->gnodes, sizeof(float4) * nodes.size());
+    if (e == cudaSuccess) e = cudaMemcpy(s->gnodes, nodes.data(), sizeof(float4) * nodes.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&s->grids_d, sizeof(DevGrid) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->grids_d, s->grids.data(), sizeof(DevGrid) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_cuda_error("grid BVH", e);
+    s->bytes += (int64_t)(sizeof(float4) * nodes.size() + sizeof(DevGrid) * (size_t)n);
+    return HELIOS_OK;
 }
 
 struct LegPlan {
@@ -259,8 +410,9 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         return set_error(HELIOS_ERR_UNSUPPORTED, "n_meshes must be in 0..%d", kMaxMesh);
     if (desc->n_meshes > 0 && !desc->meshes) return set_error(HELIOS_ERR_INVALID_ARG, "meshes is NULL");
     if (desc->n_grids < 0) return set_error(HELIOS_ERR_INVALID_ARG, "n_grids < 0");
-    if (desc->n_grids > 1) return set_error(HELIOS_ERR_UNSUPPORTED, "at most one voxel grid per scene");
-    if (desc->n_grids == 1 && !desc->grids) return set_error(HELIOS_ERR_INVALID_ARG, "grids is NULL");
+    if (desc->n_grids > kMaxGrids)
+        return set_error(HELIOS_ERR_UNSUPPORTED, "at most %d voxel grids per scene", kMaxGrids);
+    if (desc->n_grids > 0 && !desc->grids) return set_error(HELIOS_ERR_INVALID_ARG, "grids is NULL");
     int64_t n_tri = 0;
     for (int m = 0; m < desc->n_meshes; ++m) {
         const helios_mesh_desc& M = desc->meshes[m];
@@ -270,20 +422,23 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         n_tri += M.n_faces;
     }
     int64_t n_vox = 0;
-    if (desc->n_grids == 1) {
-        const helios_voxel_desc& g = desc->grids[0];
-        if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1) return set_error(HELIOS_ERR_INVALID_ARG, "grid dims must be >= 1");
-        if (!(g.cell > 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid cell must be > 0");
-        if (!(g.G >= 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid G must be >= 0");
-        if (!g.density) return set_error(HELIOS_ERR_INVALID_ARG, "grid density is NULL");
+    for (int i = 0; i < desc->n_grids; ++i) {
+        const helios_voxel_desc& g = desc->grids[i];
+        if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1)
+            return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: dims must be >= 1", i);
+        if (!(g.cell > 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: cell must be > 0", i);
+        if (!(g.G >= 0.0f)) return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: G must be >= 0", i);
+        if (!g.density) return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: density is NULL", i);
         if (g.lad_table && (g.lad_n < 2 || g.lad_n > 65536))
-            return set_error(HELIOS_ERR_INVALID_ARG, "grid lad_n must be in 2..65536");
-        n_vox = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+            return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: lad_n must be in 2..65536", i);
+        n_vox += (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+        if (n_tri + n_vox >= (int64_t)INT32_MAX) break;
     }
     if (n_tri + n_vox >= (int64_t)INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many primitives for 32-bit ids");
+    helios_status r = check_grid_boxes(desc->grids, desc->n_grids);
+    if (r != HELIOS_OK) return r;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     helios_scene* s = new helios_scene();
-    memset(s, 0, sizeof(*s));
     cudaGetDevice(&s->device);
     s->n_tri = n_tri;
     s->n_int = n_tri > 1 ? n_tri - 1 : 0;
@@ -297,57 +452,27 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         off += desc->meshes[m].n_faces;
     }
     s->mesh_first[desc->n_meshes] = (int32_t)off;
-    if (desc->n_grids == 1) s->grid = desc->grids[0];
-    cudaError_t e = cudaSuccess;
-    if (desc->n_grids == 1 && s->grid.lad_table) {
-        // leaf-angle table: read (host or device memory), checked, copied
-        const int32_t n = s->grid.lad_n;
-        std::vector<float> h((size_t)n);
-        e = cudaMemcpyAsync(h.data(), s->grid.lad_table, sizeof(float) * (size_t)n, cudaMemcpyDefault, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            delete s;
-            return set_cuda_error("reading the leaf-angle table", e);
-        }
-        for (int32_t i = 0; i < n; ++i)
-            if (!(h[i] >= 0.0f && h[i] <= 3.0e38f)) {
-                delete s;
-                return set_error(HELIOS_ERR_INVALID_ARG, "lad_table[%d] is negative or not finite", i);
-            }
-        e = cudaMalloc(&s->lad, sizeof(float) * (size_t)n);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->lad, h.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            cudaFree(s->lad);
-            delete s;
-            return set_cuda_error("leaf-angle table copy", e);
-        }
-        s->lad_n = n;
-        s->grid.lad_table = nullptr;     // the caller's pointer is not kept
+    r = build_grids(s, desc, st);
+    if (r != HELIOS_OK) {
+        free_scene_buffers(s);
+        delete s;
+        return r;
     }
+    cudaError_t e = cudaSuccess;
     if (s->n_int > 0) e = cudaMalloc(&s->nodes, sizeof(float4) * 4 * (size_t)s->n_int);
     if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tris, sizeof(float4) * 3 * (size_t)n_tri);
     if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tri_index, sizeof(int32_t) * (size_t)n_tri);
     if (e != cudaSuccess) {
-        helios_status r = set_cuda_error("scene allocation", e);
-        cudaFree(s->lad);
-        cudaFree(s->nodes);
-        cudaFree(s->tris);
-        cudaFree(s->tri_index);
+        r = set_cuda_error("scene allocation", e);
+        free_scene_buffers(s);
         delete s;
         return r;
     }
-    s->bytes = (int64_t)sizeof(float4) * (4 * s->n_int + 3 * n_tri) + (int64_t)sizeof(int32_t) * n_tri +
-               (int64_t)sizeof(float) * s->lad_n;
-    helios_status r = build_bvh(s, desc, st);
+    s->bytes += (int64_t)sizeof(float4) * (4 * s->n_int + 3 * n_tri) + (int64_t)sizeof(int32_t) * n_tri;
+    r = build_bvh(s, desc, st);
     if (r != HELIOS_OK) {
         cudaStreamSynchronize(st);
-        cudaFree(s->lad);
-        cudaFree(s->nodes4);
-        cudaFree(s->nodes);
-        cudaFree(s->tris);
-        cudaFree(s->tri_index);
+        free_scene_buffers(s);
         delete s;
         return r;
     }
@@ -361,11 +486,7 @@ helios_status helios_free_scene(helios_scene* scene) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != scene->device) cudaSetDevice(scene->device);
-    cudaFree(scene->nodes);
-    cudaFree(scene->nodes4);
-    cudaFree(scene->tris);
-    cudaFree(scene->tri_index);
-    cudaFree(scene->lad);
+    free_scene_buffers(scene);
     if (cur != scene->device) cudaSetDevice(cur);
     delete scene;
     return HELIOS_OK;
@@ -461,7 +582,7 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     L.blocks_per_sm = opts->blocks_per_sm;
     if (P.total_pulses == 0) return HELIOS_OK;
     OccupancyMasks masks;
-    st = build_occupancy(L.scenes, (cudaStream_t)cuda_stream, masks);
+    st = build_occupancy(L.scenes, scenes, (cudaStream_t)cuda_stream, masks);
     if (st != HELIOS_OK) return st;
     return launch_scan(L, (cudaStream_t)cuda_stream);
 }
@@ -480,8 +601,9 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     if (opts->mode != HELIOS_MODE_EXPECTED)
         return set_error(HELIOS_ERR_INVALID_ARG, "the adjoint is defined for mode EXPECTED only");
     for (int i = 0; i < n_scenes; ++i)
-        if (scenes[i]->n_grid && scenes[i]->grid.opaque)
-            return set_error(HELIOS_ERR_UNSUPPORTED, "opaque voxels have no density gradient; the adjoint needs transmissive grids");
+        for (const DevGrid& g : scenes[i]->grids)
+            if (g.opaque)
+                return set_error(HELIOS_ERR_UNSUPPORTED, "opaque voxels have no density gradient; the adjoint needs transmissive grids");
     int threads = opts->block_threads > 0 ? opts->block_threads : 256;
     if (threads % 32 != 0 || threads < 64 || threads > 256)
         return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
@@ -495,7 +617,10 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
         for (int m = 0; m < scenes[i]->n_mesh; ++m)
             dr[m] = grads[i].d_reflectance ? grads[i].d_reflectance[m] : nullptr;
         L.d_refl.push_back(dr);
-        L.d_density.push_back(scenes[i]->n_grid && grads[i].d_density ? grads[i].d_density[0] : nullptr);
+        int32_t want = 0;
+        if (grads[i].d_density)
+            for (int g = 0; g < scenes[i]->n_grid; ++g) want |= grads[i].d_density[g] != nullptr;
+        L.want_dens.push_back(want);
     }
     for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
     L.legs = P.legs;
@@ -506,7 +631,7 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     L.threads = threads;
     if (P.total_pulses == 0) return HELIOS_OK;
     OccupancyMasks masks;
-    st = build_occupancy(L.scenes, (cudaStream_t)cuda_stream, masks);
+    st = build_occupancy(L.scenes, scenes, (cudaStream_t)cuda_stream, masks, grads);
     if (st != HELIOS_OK) return st;
     return launch_adjoint(L, (cudaStream_t)cuda_stream);
 }
@@ -773,7 +898,7 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
     for (int i = 0; i < n_scenes; ++i) L.scenes.push_back(dev_scene(scenes[i]));
     for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
     OccupancyMasks masks;
-    st = build_occupancy(L.scenes, hs.s0, masks);
+    st = build_occupancy(L.scenes, scenes, hs.s0, masks);
     if (st != HELIOS_OK) return st;
     L.seed = opts->seed;
     L.mode = opts->mode;

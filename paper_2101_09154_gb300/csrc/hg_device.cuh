@@ -15,6 +15,7 @@ constexpr int kMaxMesh = 16;
 constexpr int kMaxScenes = 16;
 constexpr int kMaxScanners = 4;
 constexpr int kMaxLegs = 128;
+constexpr int kMaxGrids = 4096;        // voxel grids per scene
 constexpr double kC = 299792458.0;        // speed of light (Sec. 3.4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kDelayPerMetre = 2.0e9 / kC;  // round-trip delay in ns per metre of range
@@ -41,36 +42,50 @@ constexpr int kConeExt = 112;         // more in global scratch (non-static scan
 constexpr int kBrickLog2 = 2;   // 4^3-voxel bricks for empty-space skipping
 constexpr int kBrick = 1 << kBrickLog2;
 
+// One voxel grid (Sec. 3.5.4).  Voxel (x,y,z) spans g0 + [x, x+1) cell etc.;
+// its id in outputs is n_tri + vox_off + (z ny + y) nx + x, and its
+// transmission draw is keyed by vox_off + (z ny + y) nx + x.
+struct DevGrid {
+    const float* density;       // [nz][ny][nx]
+    const uint32_t* occ;        // brick occupancy bits (x fastest), NULL: not used
+    const float* lad;           // leaf-angle table G(mu_i), mu_i = i/(lad_n-1)
+    float* ddens;               // adjoint: dL/ddensity of this grid, NULL: not wanted
+    float g0[3];
+    float cell;
+    int32_t dims[3];
+    int32_t opaque;             // non-transmissive voxels
+    int32_t bdims[3];           // bricks of kBrick^3 voxels per axis
+    int32_t lad_n;              // 0: constant G
+    float G, leaf_refl;
+    int32_t vox_off;            // voxels of the scene's earlier grids
+    int32_t pad;
+};
+
 struct DevScene {
     const float4* nodes;
     const float4* nodes4;       // 4-wide collapse of the same tree (8 float4 per node)
     const float4* tris;
     const int32_t* tri_index;   // global triangle id -> packed (sorted) position
     const float* refl[kMaxMesh];
-    const float* density;
     int32_t mesh_first[kMaxMesh + 1];
     int32_t n_tri, n_int, n_mesh, has_grid;
     int32_t n_node4;
-    int32_t opaque;             // the grid's voxels are non-transmissive
-    int32_t dims[3];
-    float G, leaf_refl, cell;
-    float g0[3];
-    int32_t bdims[3];           // bricks of kBrick^3 voxels per axis
-    const uint32_t* occ;        // brick occupancy bits (x fastest), NULL: not used
-    const float* lad;           // leaf-angle table G(mu_i), mu_i = i/(lad_n-1)
-    int32_t lad_n;              // 0: constant G
+    int32_t n_grid;
+    DevGrid grid;               // the grid of a one-grid scene
+    const DevGrid* grids;       // all grids of a scene with several (device)
+    const float4* gnodes;       // BVH over their boxes: 4 float4 per node, leaf ~grid
 };
 
 // sigma = G density (Eq. extinction).  With a leaf-angle table (Table ladlut)
 // G depends on the subray direction: linear interpolation at mu = |d_z| of the
 // unit direction between entries at mu_i = i/(n-1); without one, the grid's
-// constant G.  Evaluated once per subray, before its march.
-__device__ __forceinline__ float proj_factor(const DevScene& sc, float dz) {
-    if (sc.lad_n < 2) return sc.G;
-    const float t = fminf(fabsf(dz), 1.0f) * (float)(sc.lad_n - 1);   // NaN -> the last entry
-    const int i = min((int)t, sc.lad_n - 2);
+// constant G.  Evaluated once per subray and grid, before its march.
+__device__ __forceinline__ float proj_factor(const DevGrid& g, float dz) {
+    if (g.lad_n < 2) return g.G;
+    const float t = fminf(fabsf(dz), 1.0f) * (float)(g.lad_n - 1);   // NaN -> the last entry
+    const int i = min((int)t, g.lad_n - 2);
     const float f = t - (float)i;
-    const float g0 = __ldg(sc.lad + i), g1 = __ldg(sc.lad + i + 1);
+    const float g0 = __ldg(g.lad + i), g1 = __ldg(g.lad + i + 1);
     return fmaf(f, g1 - g0, g0);
 }
 
@@ -792,7 +807,7 @@ __device__ __forceinline__ float cross32(int p, int p0, int s, float f0, float i
 }
 
 // set up the march along o + t d for t in [t_enter, min(t_exit, t_hi)); false: no voxel
-__device__ __forceinline__ bool march_init(const DevScene& S, const double o[3],
+__device__ __forceinline__ bool march_init(const DevGrid& S, const double o[3],
                                            const double d[3], double t_hi, March& m) {
     double g0[3] = {(double)S.g0[0], (double)S.g0[1], (double)S.g0[2]};
     double cell = (double)S.cell;
@@ -881,7 +896,7 @@ struct VoxSeg {
     float t_out32;
 };
 
-__device__ __forceinline__ bool march_current(const DevScene& S, const March& m, VoxSeg& v) {
+__device__ __forceinline__ bool march_current(const DevGrid& S, const March& m, VoxSeg& v) {
     if (m.ix < 0 || m.iy < 0 || m.iz < 0 || m.ix >= S.dims[0] || m.iy >= S.dims[1] ||
         m.iz >= S.dims[2])
         return false;
@@ -900,7 +915,7 @@ __device__ __forceinline__ bool march_current(const DevScene& S, const March& m,
 // not read there; 0 is returned, or with MARK_EMPTY -1, which a march may
 // answer with march_skip_brick.  Every caller treats either as empty.
 template <bool MARK_EMPTY = false>
-__device__ __forceinline__ float voxel_density(const DevScene& S, const March& m, const VoxSeg& v) {
+__device__ __forceinline__ float voxel_density(const DevGrid& S, const March& m, const VoxSeg& v) {
     if (S.occ != nullptr) {
         int b = ((m.iz >> kBrickLog2) * S.bdims[1] + (m.iy >> kBrickLog2)) * S.bdims[0] +
                 (m.ix >> kBrickLog2);
@@ -979,7 +994,7 @@ __device__ __forceinline__ FF plane_ff_at(const March& m, int a, int plane) {
 // every other axis, exactly the inner planes ordered before that event.
 // Taking those crossings here gives the voxel, next-crossing times and entry
 // axis the one-voxel march would reach.  false: the march ends in the brick.
-__device__ __forceinline__ bool march_skip_brick(const DevScene& S, March& m, uint32_t& flags) {
+__device__ __forceinline__ bool march_skip_brick(const DevGrid& S, March& m, uint32_t& flags) {
     const int bx0 = m.ix & ~(kBrick - 1), by0 = m.iy & ~(kBrick - 1), bz0 = m.iz & ~(kBrick - 1);
     const int bx1 = min(bx0 + kBrick - 1, S.dims[0] - 1);
     const int by1 = min(by0 + kBrick - 1, S.dims[1] - 1);
@@ -1037,6 +1052,122 @@ __device__ __forceinline__ bool march_skip_brick(const DevScene& S, March& m, ui
     m.steps_left -= abs(m.ix - ox) + abs(m.iy - oy) + abs(m.iz - oz);
     if (m.steps_left <= 0) { flags |= kPfMarchCap; return false; }
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// scenes with several grids: their boxes have disjoint interiors, so the
+// segments of a ray in them follow one another in the order of the boxes'
+// entry points.  A grid's key is (t_enter, index), t_enter = max(0, entry of
+// an FP32 slab test against its box as stored in the grid BVH, widened at
+// build time so that no box the FP64 march would enter is culled).
+// next_grid returns the grid of least key above the cursor with
+// t_enter < t_hi; each call is one bounded walk of the grid BVH.
+// ---------------------------------------------------------------------------
+constexpr int kGridStack = 32;
+
+struct GridCursor {
+    float te;       // key of the last grid returned
+    int gi;
+};
+
+__device__ __forceinline__ void box_span(const float o[3], const float iv[3], const float lo[3],
+                                         const float hi[3], float& tn, float& tf) {
+    tn = 0.0f;
+    tf = 3.0e38f;
+    for (int a = 0; a < 3; ++a) {
+        const float t0 = (lo[a] - o[a]) * iv[a], t1 = (hi[a] - o[a]) * iv[a];
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+}
+
+__device__ __forceinline__ int next_grid(const DevScene& sc, const float o[3], const float iv[3],
+                                         float t_hi, GridCursor& c) {
+    if (sc.n_grid == 1) {
+        if (c.gi >= 0) return -1;
+        c.gi = 0;
+        return 0;
+    }
+    float best_t = t_hi;
+    int best = -1;
+    int stack[kGridStack];
+    int sp = 0, node = 0;
+    for (int guard = 0; guard < 2 * sc.n_grid + 4; ++guard) {
+        const float4* n = sc.gnodes + 4 * (size_t)node;
+        const float4 a = __ldg(n), b = __ldg(n + 1), e = __ldg(n + 2);
+        const int4 ch = __ldg(reinterpret_cast<const int4*>(n + 3));
+        const float lo0[3] = {a.x, a.y, a.z}, hi0[3] = {a.w, b.x, b.y};
+        const float lo1[3] = {b.z, b.w, e.x}, hi1[3] = {e.y, e.z, e.w};
+        for (int k = 0; k < 2; ++k) {
+            float tn, tf;
+            box_span(o, iv, k ? lo1 : lo0, k ? hi1 : hi0, tn, tf);
+            if (!(tn <= tf) || tf < c.te || tn > best_t || !(tn < t_hi)) continue;
+            const int child = k ? ch.y : ch.x;
+            if (child < 0) {
+                const int gi = ~child;
+                const bool after = tn > c.te || (tn == c.te && gi > c.gi);
+                const bool before = best < 0 || tn < best_t || (tn == best_t && gi < best);
+                if (after && before) {
+                    best_t = tn;
+                    best = gi;
+                }
+            } else if (sp < kGridStack) {
+                stack[sp++] = child;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    if (best >= 0) {
+        c.te = best_t;
+        c.gi = best;
+    }
+    return best;
+}
+
+__device__ __forceinline__ void grid_ray(const double o[3], const double d[3], float of[3], float iv[3]) {
+    for (int a = 0; a < 3; ++a) {
+        of[a] = (float)o[a];
+        const float df = (float)d[a];
+        iv[a] = df != 0.0f ? 1.0f / df : 1.0e30f;
+    }
+}
+
+// the grid's march set up on the next grid (in entry order) whose box the
+// FP64 march enters before t_hi; NULL when none is left
+__device__ __forceinline__ const DevGrid* next_march(const DevScene& sc, const float of[3],
+                                                     const float iv[3], const double o[3],
+                                                     const double d[3], double t_hi, GridCursor& c,
+                                                     March& m) {
+    const float th = (float)t_hi * 1.0001f + 1.0e-3f;
+    for (int guard = 0; guard < sc.n_grid; ++guard) {
+        const int gi = next_grid(sc, of, iv, th, c);
+        if (gi < 0) return nullptr;
+        const DevGrid* G = sc.n_grid == 1 ? &sc.grid : sc.grids + gi;
+        if (march_init(*G, o, d, t_hi, m)) return G;
+    }
+    return nullptr;
+}
+
+// body(G, m) on each grid the ray crosses before t_hi, in entry order, with
+// m set up on it; body returns false to end the walk.  GK 1: the scene has
+// at most one grid (sc.grid); GK 2: any number.
+template <int GK, class F>
+__device__ __forceinline__ void walk_grids(const DevScene& sc, const double o[3], const double d[3],
+                                           double t_hi, F&& body) {
+    if (GK == 1) {
+        March m;
+        if (march_init(sc.grid, o, d, t_hi, m)) body(sc.grid, m);
+        return;
+    }
+    float of[3], iv[3];
+    grid_ray(o, d, of, iv);
+    GridCursor c = {-1.0f, -1};
+    March m;
+    for (int guard = 0; guard < sc.n_grid; ++guard) {
+        const DevGrid* G = next_march(sc, of, iv, o, d, t_hi, c, m);
+        if (!G || !body(*G, m)) return;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -23,9 +23,10 @@ struct helios_scene {
     const float* refl[hg::kMaxMesh];
     int32_t mesh_first[hg::kMaxMesh + 1];
     int64_t mesh_faces[hg::kMaxMesh];
-    helios_voxel_desc grid;
-    float* lad;               // [lad_n] copy of the grid's leaf-angle table, or NULL
-    int32_t lad_n;
+    std::vector<hg::DevGrid> grids;   // per grid (occupancy masks and gradients unset)
+    std::vector<float*> lads;         // device copies of the grids' leaf-angle tables
+    hg::DevGrid* grids_d;             // device copy of `grids` (scenes with several grids)
+    float4* gnodes;                   // BVH over the grid boxes (scenes with several grids)
     int64_t bytes;
 };
 
@@ -61,7 +62,7 @@ struct AdjointLaunch {
     std::vector<DevLeg> legs;
     // gradients per scene
     std::vector<std::vector<float*>> d_refl;
-    std::vector<float*> d_density;
+    std::vector<int32_t> want_dens;       // some grid of the scene takes a density gradient
     const float* g;
     const int32_t* window;
     const int32_t* subray_hit;
@@ -74,13 +75,16 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st);
 helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st);
 
 // Brick occupancy masks of the scenes' voxel grids, formed in stream order from
-// the densities as they are when the stream reaches them; sets DevScene::occ
-// and frees the masks (stream-ordered) when destroyed.
+// the densities as they are when the stream reaches them.  Sets each grid's
+// occ (and, given gradients, its ddens): in DevScene::grid for a one-grid
+// scene, else in a per-call device copy of the scene's grid array.  Frees
+// what it allocated (stream-ordered) when destroyed.
 struct OccupancyMasks {
     std::vector<void*> bufs;
     cudaStream_t st = nullptr;
     ~OccupancyMasks();
 };
-helios_status build_occupancy(std::vector<DevScene>& scenes, cudaStream_t st, OccupancyMasks& keep);
+helios_status build_occupancy(std::vector<DevScene>& scenes, helios_scene* const* hs, cudaStream_t st,
+                              OccupancyMasks& keep, const helios_scene_grads* grads = nullptr);
 
 }  // namespace hg

@@ -74,14 +74,15 @@ __device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* 
 }
 
 // Expected-mode returns of one subray in summation order: the voxels along
-// the march (weight T_k (1 - e^{-sigma l}) at the segment midpoint), then the
-// triangle (weight T).  emit(R, weighted power, primitive id).
-template <bool GRID, class F>
+// the march, grid after grid in entry order (weight T_k (1 - e^{-sigma l}) at
+// the segment midpoint), then the triangle (weight T).  emit(R, weighted
+// power, primitive id).
+template <int GK, class F>
 __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevScanner& sn,
                                                  const PulseFF& f, const SubrayConst& c,
                                                  const RayRes& rr, uint32_t& fl, F&& emit) {
     float T = 1.0f;
-    if (GRID && sc.has_grid) {
+    if (GK > 0 && sc.has_grid) {
         float dh[3], dl[3];
         subray_dir_ff(f, c, dh, dl);
         double o[3], d[3];
@@ -89,44 +90,46 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
             o[a] = ff2d(f.oh[a], f.ol[a]);
             d[a] = ff2d(dh[a], dl[a]);
         }
-        const float Gs = proj_factor(sc, dh[2]);
         double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
-        March m;
-        if (march_init(sc, o, d, t_hi, m)) {
+        bool stopped = false;
+        walk_grids<GK>(sc, o, d, t_hi, [&](const DevGrid& G, March& m) -> bool {
+            const float Gs = proj_factor(G, dh[2]);
             for (;;) {
                 VoxSeg v;
-                if (!march_current(sc, m, v)) break;
-                float dens = voxel_density(sc, m, v);
+                if (!march_current(G, m, v)) return true;
+                float dens = voxel_density(G, m, v);
                 if (dens > 0.0f) {
                     FF t_in, t_out;
                     march_segment_ff(m, v, t_in, t_out);
                     float len = ff_diff(t_out, t_in);
-                    if (len > 0.0f && sc.opaque) {
+                    if (len > 0.0f && G.opaque) {
                         // an opaque voxel returns all that reaches it and passes
                         // nothing: Lambertian on the face entered
                         const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
-                        emit(t_in, T * return_power(sn, t_in.hi + t_in.lo, c.tan_a, sc.leaf_refl,
+                        emit(t_in, T * return_power(sn, t_in.hi + t_in.lo, c.tan_a, G.leaf_refl,
                                                     ax >= 0 ? fabsf(dh[ax]) : 1.0f),
-                             sc.n_tri + (int32_t)v.vid);
-                        return;
+                             sc.n_tri + G.vox_off + (int32_t)v.vid);
+                        stopped = true;
+                        return false;
                     }
                     if (len > 0.0f) {
                         float xs = Gs * dens * len;
                         float w = -T * expm1f(-xs);
                         T *= expf(-xs);
                         FF R = ff_add_f(t_in, 0.5f * len);
-                        emit(R, w * return_power(sn, R.hi + R.lo, c.tan_a, sc.leaf_refl, 1.0f),
-                             sc.n_tri + (int32_t)v.vid);
+                        emit(R, w * return_power(sn, R.hi + R.lo, c.tan_a, G.leaf_refl, 1.0f),
+                             sc.n_tri + G.vox_off + (int32_t)v.vid);
                     }
                 }
-                if (!march_step(m, v, fl)) break;
+                if (!march_step(m, v, fl)) return true;
             }
-        }
+        });
+        if (stopped) return;
     }
     if (rr.id >= 0) emit(ff_norm(rr.Rh, rr.Rl), T * rr.P, rr.id);
 }
 
-template <int MODE, bool GRID, int NL>
+template <int MODE, int GK, int NL>
 __global__ void __launch_bounds__(256)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -308,7 +311,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     float rho = 0.0f;
                     if (hit >= 0) {
                         dt_hit = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
-                        t_tri = GRID ? (double)tb + (double)dt_hit : 0.0;
+                        t_tri = GK > 0 ? (double)tb + (double)dt_hit : 0.0;
                         const float4* tp = sc.tris + 3 * (size_t)hit;
                         gid = __float_as_int(__ldg(&tp[0].w));
                         int mesh = __float_as_int(__ldg(&tp[1].w));
@@ -317,40 +320,40 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
                     }
                     bool voxel_event = false;
-                    if (GRID && sc.has_grid) {
+                    if (GK > 0 && sc.has_grid) {
                         double o[3], d[3];
                         for (int a = 0; a < 3; ++a) {
                             o[a] = ff2d(f.oh[a], f.ol[a]);
                             d[a] = ff2d(dh[a], dl[a]);
                         }
-                        const float Gs = proj_factor(sc, dh[2]);
-                        March m;
-                        if (march_init(sc, o, d, t_tri, m)) {
-                            const int64_t k = p0 + pl;
+                        const int64_t k = p0 + pl;
+                        // the first event along the path: grids in entry order
+                        walk_grids<GK>(sc, o, d, t_tri, [&](const DevGrid& G, March& m) -> bool {
+                            const float Gs = proj_factor(G, dh[2]);
                             for (;;) {
                                 VoxSeg v;
-                                if (!march_current(sc, m, v)) break;
-                                float dens = voxel_density(sc, m, v);
+                                if (!march_current(G, m, v)) return true;
+                                float dens = voxel_density(G, m, v);
                                 if (dens > 0.0f) {
                                     FF t_in, t_out;
                                     march_segment_ff(m, v, t_in, t_out);
                                     float len = ff_diff(t_out, t_in);
-                                    if (len > 0.0f && sc.opaque) {
+                                    if (len > 0.0f && G.opaque) {
                                         // non-transmissive voxel (Sec. 3.5.4): stop where
                                         // the subray enters it, Lambertian on that face
                                         if (MODE == 0) {
                                             const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
                                             rr.Rh = t_in.hi;
                                             rr.Rl = t_in.lo;
-                                            rr.id = sc.n_tri + (int32_t)v.vid;
-                                            rr.P = return_power(sn, t_in.hi + t_in.lo, tan_a, sc.leaf_refl,
+                                            rr.id = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                            rr.P = return_power(sn, t_in.hi + t_in.lo, tan_a, G.leaf_refl,
                                                                 ax >= 0 ? fabsf(dh[ax]) : 1.0f);
                                             voxel_event = true;
                                         } else {
                                             r2h = t_in.hi;
                                             r2l = t_in.lo;
                                         }
-                                        break;
+                                        return false;
                                     }
                                     if (len > 0.0f) {
                                         float sigma = Gs * dens;
@@ -358,29 +361,29 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                             // Eq. intersection_dist: s = -ln(u)/sigma
                                             uint64_t w[4];
                                             philox4x64((uint64_t)k, (uint64_t)(uint32_t)s,
-                                                       (uint64_t)v.vid, (uint64_t)lg.leg_id,
+                                                       (uint64_t)(G.vox_off + v.vid), (uint64_t)lg.leg_id,
                                                        P.seed, 0ull, w);
                                             float sdist = -logf(uniform23(w[0])) / sigma;
                                             if (sdist < len) {
                                                 FF R = ff_add_f(t_in, sdist);
                                                 rr.Rh = R.hi;
                                                 rr.Rl = R.lo;
-                                                rr.id = sc.n_tri + (int32_t)v.vid;
-                                                rr.P = return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
+                                                rr.id = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                                rr.P = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f);
                                                 voxel_event = true;
-                                                break;
+                                                return false;
                                             }
                                         } else {
                                             FF R2 = ff_add_f(t_in, 0.5f * len);
                                             r2h = R2.hi;
                                             r2l = R2.lo;
-                                            break;
+                                            return false;
                                         }
                                     }
                                 }
-                                if (!march_step(m, v, fl)) break;
+                                if (!march_step(m, v, fl)) return true;
                             }
-                        }
+                        });
                     }
                     if (!voxel_event && gid >= 0) {
                         rr.Rh = tb;
@@ -600,7 +603,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + (size_t)n_rl * 32 + lane, -1);
                             ++n_rl;
                         }
-                        expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl,
+                        expected_returns<GK>(sc, sn, f, s_sc[s], rrp[s], fl,
                                                [&](const FF& R, float Pw, int32_t id) {
                             float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                             float jf = rintf(tau * sn.inv_bin);
@@ -693,39 +696,51 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         March mch;
                         uint32_t fl = 0;
                         float dabs[3] = {1.0f, 1.0f, 1.0f};
-                        float Gs = sc.G;
-                        if (GRID && sc.has_grid && lane_on) {
-                            double o[3], d[3];
+                        float dz = 1.0f, Gs = 0.0f;
+                        // the walk over several grids (GK 2) stays live between returns
+                        const DevGrid* Gp = &sc.grid;
+                        double o[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 1.0}, t_hi = 0.0;
+                        float of[3] = {0.0f, 0.0f, 0.0f}, iv[3] = {0.0f, 0.0f, 0.0f};
+                        GridCursor gcur = {-1.0f, -1};
+                        if (GK > 0 && sc.has_grid && lane_on) {
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
                             for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
-                            Gs = proj_factor(sc, dh[2]);
+                            dz = dh[2];
                             for (int a = 0; a < 3; ++a) {
                                 o[a] = ff2d(f.oh[a], f.ol[a]);
                                 d[a] = ff2d(dh[a], dl[a]);
                             }
-                            double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
-                            on = march_init(sc, o, d, t_hi, mch);
+                            t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+                            if (GK == 1) {
+                                on = march_init(sc.grid, o, d, t_hi, mch);
+                            } else {
+                                grid_ray(o, d, of, iv);
+                                Gp = next_march(sc, of, iv, o, d, t_hi, gcur, mch);
+                                on = Gp != nullptr;
+                            }
+                            if (on) Gs = proj_factor(GK == 1 ? sc.grid : *Gp, dz);
                         }
                         while (__any_sync(full, on)) {
                             bool has = false;
                             float tau = 0.0f, pv = 0.0f;
                             int32_t vid = 0;
                             while (on) {
+                                const DevGrid& G = GK == 1 ? sc.grid : *Gp;
                                 VoxSeg v;
-                                if (!march_current(sc, mch, v)) { on = false; break; }
-                                float dens = voxel_density(sc, mch, v);
-                                if (dens > 0.0f) {
+                                bool more = march_current(G, mch, v);
+                                float dens = more ? voxel_density(G, mch, v) : 0.0f;
+                                if (more && dens > 0.0f) {
                                     FF t_in, t_out;
                                     march_segment_ff(mch, v, t_in, t_out);
                                     float len = ff_diff(t_out, t_in);
-                                    if (len > 0.0f && sc.opaque) {
+                                    if (len > 0.0f && G.opaque) {
                                         // opaque: all of T returns here, nothing passes
                                         const int ax = mch.entry_axis >= 0 ? mch.entry_axis : mch.face0;
-                                        pv = T * return_power(sn, t_in.hi + t_in.lo, tan_a, sc.leaf_refl,
+                                        pv = T * return_power(sn, t_in.hi + t_in.lo, tan_a, G.leaf_refl,
                                                               ax >= 0 ? dabs[ax] : 1.0f);
                                         tau = ff_mul_sub(t_in, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                        vid = sc.n_tri + (int32_t)v.vid;
+                                        vid = sc.n_tri + G.vox_off + (int32_t)v.vid;
                                         has = true;
                                         T = 0.0f;
                                         on = false;
@@ -736,13 +751,19 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         float w = -T * expm1f(-xs);
                                         T *= expf(-xs);
                                         FF R = ff_add_f(t_in, 0.5f * len);
-                                        pv = w * return_power(sn, R.hi + R.lo, tan_a, sc.leaf_refl, 1.0f);
+                                        pv = w * return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f);
                                         tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                        vid = sc.n_tri + (int32_t)v.vid;
+                                        vid = sc.n_tri + G.vox_off + (int32_t)v.vid;
                                         has = true;
                                     }
                                 }
-                                if (!march_step(mch, v, fl)) on = false;
+                                if (!more || !march_step(mch, v, fl)) {
+                                    // this grid is done: the next one along the ray, if any
+                                    if (GK == 2 && (Gp = next_march(sc, of, iv, o, d, t_hi, gcur, mch)) != nullptr)
+                                        Gs = proj_factor(*Gp, dz);
+                                    else
+                                        on = false;
+                                }
                                 if (has) break;
                             }
                             unsigned hm = __ballot_sync(full, has);
@@ -890,7 +911,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 const int s = s0 + lane;
                                 if (s >= S) continue;
                                 uint32_t fl2 = 0;
-                                expected_returns<GRID>(sc, sn, f, s_sc[s], rrp[s], fl2,
+                                expected_returns<GK>(sc, sn, f, s_sc[s], rrp[s], fl2,
                                                        [&](const FF& R, float Pw, int32_t id) {
                                     const float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                                     if (!(rintf(tau * sn.inv_bin) >= (float)(-P.mom_cb - 1) &&
@@ -1048,10 +1069,10 @@ static helios_status launch_echo_widths(const DevLeg* legs, int n_legs, const De
 // ---------------------------------------------------------------------------
 // host launcher
 // ---------------------------------------------------------------------------
-template <int MODE, bool GRID, int NL>
+template <int MODE, int GK, int NL>
 static helios_status launch_one(const ScanParams<NL>& p, int threads, int blocks_per_sm,
                                 size_t smem, cudaStream_t st, int grid_cap) {
-    auto kern = scan_kernel<MODE, GRID, NL>;
+    auto kern = scan_kernel<MODE, GK, NL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return set_cuda_error("cudaFuncSetAttribute(scan)", e);
@@ -1071,15 +1092,21 @@ static helios_status launch_one(const ScanParams<NL>& p, int threads, int blocks
     return HELIOS_OK;
 }
 
+// the kernel variant for a launch: GK 0 no grid in any leg's scene, 1 at most
+// one grid per scene, 2 some scene with several grids
+static int grid_kind(const DevScene& sc) { return sc.n_grid > 1 ? 2 : (sc.n_grid > 0 ? 1 : 0); }
+
 template <int NL>
-static helios_status dispatch(const ScanParams<NL>& p, int mode, bool grid, int threads,
+static helios_status dispatch(const ScanParams<NL>& p, int mode, int gk, int threads,
                               int blocks_per_sm, size_t smem, cudaStream_t st, int grid_cap) {
     if (mode == 0) {
-        return grid ? launch_one<0, true, NL>(p, threads, blocks_per_sm, smem, st, grid_cap)
-                    : launch_one<0, false, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+        if (gk == 2) return launch_one<0, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+        if (gk == 1) return launch_one<0, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+        return launch_one<0, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
     }
-    return grid ? launch_one<1, true, NL>(p, threads, blocks_per_sm, smem, st, grid_cap)
-                : launch_one<1, false, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    if (gk == 2) return launch_one<1, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    if (gk == 1) return launch_one<1, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    return launch_one<1, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
 }
 
 // floats of per-warp shared waveform scratch: W, plus (expected mode) either
@@ -1102,9 +1129,9 @@ static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_c
     return b;
 }
 
-template <int MODE, bool GRID, int NL>
+template <int MODE, int GK, int NL>
 static int max_grid(int threads, int blocks_per_sm, size_t smem) {
-    auto kern = scan_kernel<MODE, GRID, NL>;
+    auto kern = scan_kernel<MODE, GK, NL>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
@@ -1126,8 +1153,8 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         nb_cap = max(nb_cap, L.scanners[lg.scanner].n_bins);
     }
     nb_cap = (nb_cap + 3) & ~3;
-    bool any_grid = false;
-    for (const DevLeg& lg : L.legs) any_grid |= L.scenes[lg.scene].has_grid != 0;
+    int gk = 0;
+    for (const DevLeg& lg : L.legs) gk = max(gk, grid_kind(L.scenes[lg.scene]));
     // expected mode with a Gaussian pulse: moment bins in stream-ordered scratch
     int cb = 0;
     bool direct = L.mode == 1;   // some leg sums its waveform directly
@@ -1162,15 +1189,19 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
     // the most blocks any launch below can have: per-block and per-warp scratch
     int grid = 0;
     if (L.mode == 0)
-        grid = L.persistent ? (any_grid ? max_grid<0, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
-                                        : max_grid<0, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
-                            : (any_grid ? max_grid<0, true, 1>(threads, L.blocks_per_sm, smem)
-                                        : max_grid<0, false, 1>(threads, L.blocks_per_sm, smem));
+        grid = L.persistent ? (gk == 2 ? max_grid<0, 2, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<0, 1, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<0, 0, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                            : (gk == 2 ? max_grid<0, 2, 1>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<0, 1, 1>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<0, 0, 1>(threads, L.blocks_per_sm, smem));
     else
-        grid = L.persistent ? (any_grid ? max_grid<1, true, kMaxLegs>(threads, L.blocks_per_sm, smem)
-                                        : max_grid<1, false, kMaxLegs>(threads, L.blocks_per_sm, smem))
-                            : (any_grid ? max_grid<1, true, 1>(threads, L.blocks_per_sm, smem)
-                                        : max_grid<1, false, 1>(threads, L.blocks_per_sm, smem));
+        grid = L.persistent ? (gk == 2 ? max_grid<1, 2, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<1, 1, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<1, 0, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                            : (gk == 2 ? max_grid<1, 2, 1>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<1, 1, 1>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<1, 0, 1>(threads, L.blocks_per_sm, smem));
     // candidate lists longer than kConeCap continue in global scratch
     int32_t* cext = nullptr;
     const int cext_cap = kConeExt;
@@ -1234,7 +1265,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             p.rlist = rlist; p.rl_cap = rl_cap; p.ht_cb = ht_cb;
             p.cext = cext; p.cext_cap = cext_cap;
             p.queue = nullptr;
-            bool g = L.scenes[L.legs[l].scene].has_grid != 0;
+            const int g = grid_kind(L.scenes[L.legs[l].scene]);
             helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
             if (s != HELIOS_OK) return s;
         }
@@ -1269,7 +1300,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         e = cudaMemsetAsync(q, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) { cudaFreeAsync(q, st); delete p; return set_cuda_error("cudaMemsetAsync(queue)", e); }
         p->queue = q;
-        helios_status s = dispatch<kMaxLegs>(*p, L.mode, any_grid, threads, L.blocks_per_sm, smem, st, 0);
+        helios_status s = dispatch<kMaxLegs>(*p, L.mode, gk, threads, L.blocks_per_sm, smem, st, 0);
         cudaFreeAsync(q, st);
         delete p;
         if (s != HELIOS_OK) return s;
@@ -1329,13 +1360,13 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs_static takes at most %d legs, got %d",
                          kStaticQueues * kMaxLegs, n_legs);
     int s_cap = 1, pc_cap = 1, rays_cap = 32, nb_cap = 4;
-    bool any_grid = false;
+    int gk = 0;
     for (int l = 0; l < n_legs; ++l) {
         s_cap = max(s_cap, legs[l].S);
         pc_cap = max(pc_cap, legs[l].pulses_per_item);
         rays_cap = max(rays_cap, legs[l].S * legs[l].pulses_per_sub);
         nb_cap = max(nb_cap, scanners[legs[l].scanner].n_bins);
-        any_grid |= scenes[legs[l].scene].has_grid != 0;
+        gk = max(gk, grid_kind(scenes[legs[l].scene]));
     }
     nb_cap = (nb_cap + 3) & ~3;
     size_t smem = smem_bytes(mode, pc_cap, s_cap, rays_cap, nb_cap, threads);
@@ -1364,7 +1395,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
         p.w_stride = warp_stride(mode, nb_cap, 0, true);
         p.queue = g_static_ptr[dev] + g;
-        helios_status s = dispatch<kMaxLegs>(p, mode, any_grid, threads, blocks_per_sm, smem, st, 0);
+        helios_status s = dispatch<kMaxLegs>(p, mode, gk, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;
     }
     // echo widths from the stored rows and bins (the caller provides echo_bin)

@@ -406,6 +406,67 @@ def uls_voxels(seed: int = 2, n: int = 256, n_pulses: int = 1_000_000, n_bins: i
                          f"PRF {prf/1e3:.0f} kHz, q=2, N_b={n_bins}")
 
 
+def tree_density(rng, n=128, max_density=2.0):
+    """A voxel tree in an n^3 box (x, y centred; z from the ground): a trunk
+    column of dense voxels and an ellipsoidal crown whose leaf-area density is
+    smooth noise cut to zero over about half of the crown."""
+    z, y, x = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    c = n / 2.0
+    r_tr = max(1.0, n * rng.uniform(0.02, 0.04))
+    trunk = ((x - c) ** 2 + (y - c) ** 2 <= r_tr ** 2) & (z < n * rng.uniform(0.35, 0.5))
+    zc, rz = n * rng.uniform(0.6, 0.7), n * rng.uniform(0.25, 0.33)
+    rxy = n * rng.uniform(0.3, 0.48)
+    crown = ((x - c) / rxy) ** 2 + ((y - c) / rxy) ** 2 + ((z - zc) / rz) ** 2 <= 1.0
+    f = smooth_noise_3d(rng, n, max(2.0, n / 16.0))
+    thr = np.quantile(f[crown], 0.5) if crown.any() else 0.0
+    leaf = np.clip((f - thr) / max(f.max() - thr, 1e-30), 0.0, 1.0) * max_density
+    d = np.where(crown, leaf, 0.0)
+    d = np.where(trunk, 4.0 * max_density, d)
+    return np.ascontiguousarray(d.astype(np.float32))
+
+
+def tree_grids(rng, slots, n=128, cell=0.045, n_templates=16, G=0.5):
+    """Voxel trees at the given box corners (boxes n*cell wide, disjoint by
+    construction of the slots).  Trees share ``n_templates`` seeded density
+    arrays, so a scene with thousands of trees holds a few of them."""
+    templates = [tree_density(rng, n) for _ in range(min(n_templates, len(slots)) or 1)]
+    pick = rng.integers(0, len(templates), size=len(slots))
+    grids = []
+    for i, (x0, y0, z0) in enumerate(slots):
+        grids.append(VoxelGrid(origin=(float(x0), float(y0), float(z0)), cell=cell, dims=(n, n, n),
+                               density=templates[pick[i]], G=G, leaf_reflectance=0.5,
+                               object_id=5))
+    return grids
+
+
+def voxel_forest(seed: int = 7, n_trees: int = 9, n: int = 24, cell: float = 0.25,
+                 n_pulses: int = 4000, n_bins: int = 512, agl: float = 25.0, speed: float = 12.0,
+                 prf: float = 2000.0) -> Workload:
+    """ULS over separate voxel trees (one grid each, boxes on a 3 x 3 lattice,
+    neighbours touching along x) above a 2-triangle ground."""
+    rng = np.random.default_rng(seed)
+    L = n * cell
+    slots = []
+    for k in range(n_trees):
+        i, j = k % 3, k // 3
+        slots.append((i * L, j * (L + 1.5), 0.0))
+    grids = tree_grids(rng, slots, n=n, cell=cell, n_templates=n_trees)
+    W = 3 * L
+    H = (n_trees + 2) // 3 * (L + 1.5)
+    gv = np.array([[-20, -20, 0], [W + 20, -20, 0], [W + 20, H + 20, 0], [-20, H + 20, 0]], dtype=np.float64)
+    gf = np.array([[0, 1, 2], [0, 2, 3]])
+    scene = Scene(meshes=[_mesh(gv, gf, np.full(2, 0.3), 1)], grids=grids)
+    sc = Scanner(prf_hz=prf, divergence_rad=0.3e-3, beam_sample_quality=2,
+                 pulse_shape=PULSE_GAUSSIAN, pulse_fwhm_ns=4.0, bin_ns=0.25, n_bins=n_bins,
+                 max_echoes=8, echo_threshold_rel=0.05, range_noise_sigma_m=0.01,
+                 deflector=DEFL_POLYGON, scan_freq_hz=50.0, scan_angle_max_rad=math.radians(30.0))
+    track = speed * n_pulses / prf
+    leg = Leg(scene_index=0, platform=PLATFORM_LINEAR, start=(W / 2 - track / 2, H / 2, agl),
+              end=(W / 2 + track / 2, H / 2, agl), speed_mps=speed, n_pulses=n_pulses, t0=0.0, leg_id=6)
+    return Workload(f"voxel_forest_{n_trees}x{n}cube_{n_pulses}p", [scene], [sc], [leg],
+                    note=f"{n_trees} voxel trees of {n}^3 at {cell} m (one grid each) over a ground")
+
+
 def _rect_mesh(p0, e1, e2, cell):
     """Planar rectangle p0 + u e1 + v e2 (u, v in [0, 1]) in square-ish cells of
     about ``cell`` metres, two triangles per cell."""
@@ -458,13 +519,33 @@ def urban_scene(rng, length=2000.0, facade_cell=0.17, ground_cell=1.0, half_widt
     return Scene(meshes=[street, buildings])
 
 
+def urban_trees(rng, length=2000.0, n_trees=2000, n=128, cell=0.045):
+    """Slots for street trees: boxes n*cell wide packed end to end along x in
+    six rows, one on each sidewalk (|y| in [0.8, 0.8 + n cell]) and two behind
+    each side's buildings (from |y| = 34.2); ``n_trees`` of them, chosen at
+    random, get a voxel tree."""
+    L = n * cell
+    per_row = int(length // L)
+    rows = [(0.8, 1.0), (34.2, 1.0), (34.2 + L, 1.0), (0.8, -1.0), (34.2, -1.0), (34.2 + L, -1.0)]
+    slots = []
+    for y_in, side in rows:
+        y0 = y_in if side > 0 else -y_in - L
+        for i in range(per_row):
+            slots.append((i * L, y0, 0.0))
+    pick = np.sort(rng.choice(len(slots), size=min(n_trees, len(slots)), replace=False))
+    return tree_grids(rng, [slots[i] for i in pick], n=n, cell=cell)
+
+
 def urban_mls(seed: int = 4, length: float = 2000.0, speed: float = 10.0, prf: float = 100_000.0,
-              facade_cell: float = 0.17, n_bins: int = 512, q: int = 3) -> Workload:
+              facade_cell: float = 0.17, n_bins: int = 512, q: int = 3, n_trees: int = 2000) -> Workload:
     """Mobile laser scanning along an urban street: a profile scanner (head
     rotating 100 rev/s, its spin plane across the street) on a vehicle at
-    2.5 m driving ``length`` metres at ``speed``."""
+    2.5 m driving ``length`` metres at ``speed``; ``n_trees`` voxel trees
+    (128^3 at 0.045 m, one grid each) line the street."""
     rng = np.random.default_rng(seed)
     scene = urban_scene(rng, length=length, facade_cell=facade_cell)
+    if n_trees > 0:
+        scene.grids = urban_trees(rng, length=length, n_trees=n_trees)
     sc = Scanner(prf_hz=prf, divergence_rad=0.3e-3, beam_sample_quality=q,
                  pulse_shape=PULSE_GAUSSIAN, pulse_fwhm_ns=4.0, bin_ns=0.25, n_bins=n_bins,
                  max_echoes=8, echo_threshold_rel=0.05, range_noise_sigma_m=0.01,
@@ -474,10 +555,11 @@ def urban_mls(seed: int = 4, length: float = 2000.0, speed: float = 10.0, prf: f
     leg = Leg(scene_index=0, platform=PLATFORM_LINEAR, start=(0.0, 0.0, 2.5), end=(length, 0.0, 2.5),
               speed_mps=speed, attitude_rpy=(0.0, math.pi / 2, 0.0), n_pulses=n_pulses, t0=0.0,
               leg_id=4)
-    return Workload(f"urban_mls_{scene.n_triangles}tri_{n_pulses}p", [scene], [sc], [leg],
+    nt = len(scene.grids)
+    return Workload(f"urban_mls_{scene.n_triangles}tri_{nt}trees_{n_pulses}p", [scene], [sc], [leg],
                     note=f"street + extruded buildings ({scene.n_triangles} triangles, facade cell "
-                         f"{facade_cell} m), {length:.0f} m at {speed} m/s, profile head 100 rev/s, "
-                         f"PRF {prf/1e3:.0f} kHz, q={q}, N_b={n_bins}")
+                         f"{facade_cell} m), {nt} voxel trees (128^3 at 0.045 m), {length:.0f} m at "
+                         f"{speed} m/s, profile head 100 rev/s, PRF {prf/1e3:.0f} kHz, q={q}, N_b={n_bins}")
 
 
 def perturbed_density(density: np.ndarray, seed: int = 1, rel: float = 0.1) -> np.ndarray:

@@ -113,3 +113,37 @@ def test_struct_layouts_match_the_header(tmp_path):
         py = structs[cname]
         got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
         assert got == int(val), (cname, field, got, int(val))
+
+
+def test_scene_build_rejects_overlapping_grids_before_any_device_call(lib):
+    """Grid boxes must have disjoint interiors (touching is fine); the check
+    runs on the host before anything touches a device (the density pointers
+    here are never dereferenced)."""
+    import paper_2101_09154_gb300 as hg
+
+    def grid(x0, n=4, cell=0.5):
+        g = hg.VoxelDesc()
+        g.origin = (ctypes.c_float * 3)(x0, 0.0, 0.0)
+        g.cell = cell
+        g.dims = (ctypes.c_int32 * 3)(n, n, n)
+        g.G = 0.5
+        g.leaf_reflectance = 0.5
+        g.density = 16
+        return g
+
+    for xs, ok in (((0.0, 1.5), False), ((0.0, 2.0, 4.0, 1.9), False)):
+        gd = (hg.VoxelDesc * len(xs))(*[grid(x) for x in xs])
+        desc = hg.SceneDesc()
+        desc.n_meshes = 0
+        desc.n_grids = len(xs)
+        desc.grids = ctypes.cast(gd, ctypes.POINTER(hg.VoxelDesc))
+        h = ctypes.c_void_p()
+        code = lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h))
+        assert code == -1 and b"overlap" in lib.helios_last_error()
+    # too many grids
+    desc = hg.SceneDesc()
+    desc.n_grids = 4097
+    gd = (hg.VoxelDesc * 1)()
+    desc.grids = ctypes.cast(gd, ctypes.POINTER(hg.VoxelDesc))
+    h = ctypes.c_void_p()
+    assert lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h)) == -6

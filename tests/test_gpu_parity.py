@@ -437,3 +437,60 @@ def test_uls_voxels_with_leaf_angle_table(hg, mode):
         b, _ = hg.scan([hg.Scene(w.scenes[0])], w.scanners, w.legs, mode=1)
         A, B = to_np(a["waveform"]), to_np(b["waveform"])
         assert np.abs(A - B).max() <= 1e-5 * np.abs(A).max()
+
+
+def _forest(lad_tables=False, opaque=False, **kw):
+    w = scenes.voxel_forest(**kw)
+    grids = w.scenes[0].grids
+    if lad_tables:
+        for g, kind in zip(grids, ["erectophile", "planophile", None, "spherical", "uniform", None,
+                                   "plagiophile", "extremophile", None]):
+            if kind:
+                g.lad = lad.table(kind, 19).astype(np.float32)
+    if opaque:
+        grids[4].opaque = 1
+    return w
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("variant", ["plain", "lad_opaque"])
+def test_several_voxel_grids(hg, mode, variant):
+    """Nine voxel trees, one grid each (neighbours touching along x), walked
+    in entry order through the grid BVH; per-grid leaf-angle tables and one
+    opaque tree in the second variant."""
+    w = _forest(lad_tables=variant != "plain", opaque=variant != "plain", n_pulses=3001)
+    _, _, res = run_both(hg, w, mode=mode, seed=5)
+    stats = compare(*res[0], expected_mode=(mode == 1))
+    assert stats["echoes"] > 1500
+    if mode == 0:
+        hits = res[0][1]["subray_hit"]
+        n_tri = w.scenes[0].n_triangles
+        vox = hits[hits >= n_tri] - n_tri
+        offs = np.cumsum([0] + [int(np.prod(g.dims)) for g in w.scenes[0].grids])
+        assert len(set(np.searchsorted(offs, vox, side="right") - 1)) >= 6   # returns from most trees
+
+
+def test_adjoint_with_several_grids(hg):
+    """Per-grid density gradients (and reflectance) against the oracle's, with
+    leaf-angle tables on some of the trees."""
+    w = _forest(lad_tables=True, n_pulses=1200, n_bins=384)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    out, _ = hg.scan([gs], [sc], [leg], mode=1)
+    gW = 0.5 * torch.sin(torch.arange(out["waveform"].numel(), device=out["waveform"].device,
+                                      dtype=torch.float32)) * out["waveform"].abs().max()
+    grads = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"])
+    torch.cuda.synchronize()
+    osc = oracle.OracleScene(w.scenes[0])
+    rows = np.arange(leg.n_pulses)
+    d_refl, d_dens = oracle.adjoint(osc, sc, leg, rows, to_np(gW).reshape(-1, sc.n_bins).astype(np.float64),
+                                    to_np(out["window_bin"]))
+    gd = np.concatenate([to_np(t).ravel() for t in grads[0]["density"]])
+    scale = np.abs(d_dens).max()
+    assert scale > 0 and len(gd) == len(d_dens)
+    err = np.abs(gd - d_dens) - (1e-3 * np.abs(d_dens) + 1e-6 * scale)
+    assert (err <= 0).all(), f"density gradient: {int((err > 0).sum())} entries outside tolerance"
+    touched = [int((np.abs(to_np(t)) > 0).sum()) for t in grads[0]["density"]]
+    assert sum(t > 0 for t in touched) >= 6
+    gr = to_np(grads[0]["reflectance"][0])
+    assert np.allclose(gr, d_refl, rtol=1e-3, atol=1e-6 * np.abs(d_refl).max())

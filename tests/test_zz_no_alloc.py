@@ -64,3 +64,18 @@ def test_static_scan_rejects_too_many_legs(hg):
     with pytest.raises(hg.HeliosError) as e:
         hg.scan_static(gsc, w.scanners, legs)
     assert e.value.code == -1 and "2048" in str(e.value)
+
+
+def test_static_scan_with_several_grids(hg):
+    """A scene with nine voxel trees (one grid each): the static entry reads
+    the scene's own grid descriptors, without occupancy masks."""
+    w = scenes.voxel_forest(seed=8, n_pulses=1500, n_bins=256)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    ref, _ = hg.scan(gsc, w.scanners, w.legs, seed=4, persistent=True)
+    torch.cuda.synchronize()
+    got, _ = hg.scan_static(gsc, w.scanners, w.legs, seed=4)
+    torch.cuda.synchronize()
+    for k in INT_KEYS:
+        assert torch.equal(got[k], ref[k]), k
+    assert _close(got["waveform"], ref["waveform"], nb=256)
+    assert (ref["subray_hit"] >= gsc[0].n_triangles).float().mean() > 0.05
