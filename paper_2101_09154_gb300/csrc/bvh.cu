@@ -489,35 +489,50 @@ helios_status build_occupancy(std::vector<DevScene>& scenes, helios_scene* const
             continue;
         }
         if (d.n_grid < 2) continue;
-        // several grids: one mask buffer, one descriptor array for this call
+        // several grids: one mask buffer, one descriptor array for this call.
+        // Grids that share a density array (and its dims) share one mask.
         std::vector<DevGrid> G = hs[i]->grids;
+        std::vector<DevGrid> uniq;                   // one per distinct density array
+        std::vector<int64_t> uoff;
+        std::vector<int> which(G.size());
         int64_t words = 0, max_nb = 0;
-        std::vector<int64_t> woff(G.size());
         for (size_t k = 0; k < G.size(); ++k) {
-            const int64_t nb = (int64_t)G[k].bdims[0] * G[k].bdims[1] * G[k].bdims[2];
-            woff[k] = words;
-            words += (nb + 31) >> 5;
-            max_nb = std::max(max_nb, nb);
+            int u = -1;
+            for (size_t j = 0; j < uniq.size() && u < 0; ++j)
+                if (uniq[j].density == G[k].density && uniq[j].dims[0] == G[k].dims[0] &&
+                    uniq[j].dims[1] == G[k].dims[1] && uniq[j].dims[2] == G[k].dims[2])
+                    u = (int)j;
+            if (u < 0) {
+                const int64_t nb = (int64_t)G[k].bdims[0] * G[k].bdims[1] * G[k].bdims[2];
+                u = (int)uniq.size();
+                uniq.push_back(G[k]);
+                uoff.push_back(words);
+                words += (nb + 31) >> 5;
+                max_nb = std::max(max_nb, nb);
+            }
+            which[k] = u;
         }
+        if (max_nb >= ((int64_t)1 << 31)) return set_error(HELIOS_ERR_UNSUPPORTED, "grid too large for masks");
         uint32_t* occ = nullptr;
         DevGrid* dg = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&occ), words * sizeof(uint32_t), st);
         if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(occupancy)", e);
         keep.bufs.push_back(occ);
-        e = cudaMallocAsync(reinterpret_cast<void**>(&dg), sizeof(DevGrid) * G.size(), st);
+        e = cudaMallocAsync(reinterpret_cast<void**>(&dg), sizeof(DevGrid) * (G.size() + uniq.size()), st);
         if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(grid descriptors)", e);
         keep.bufs.push_back(dg);
+        for (size_t j = 0; j < uniq.size(); ++j) uniq[j].occ = occ + uoff[j];
         for (size_t k = 0; k < G.size(); ++k) {
-            G[k].occ = occ + woff[k];
+            G[k].occ = occ + uoff[which[k]];
             G[k].ddens = dd ? dd[k] : nullptr;
         }
+        G.insert(G.end(), uniq.begin(), uniq.end());   // [grids..., distinct arrays...]
         // pageable source: the call returns once the bytes are staged
         e = cudaMemcpyAsync(dg, G.data(), sizeof(DevGrid) * G.size(), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return set_cuda_error("grid descriptors copy", e);
         const int threads = 256;
-        if (max_nb >= ((int64_t)1 << 31)) return set_error(HELIOS_ERR_UNSUPPORTED, "grid too large for masks");
-        dim3 grid((unsigned)((max_nb + threads - 1) / threads), (unsigned)G.size());
-        k_occupancy_grids<<<grid, threads, 0, st>>>(dg);
+        dim3 grid((unsigned)((max_nb + threads - 1) / threads), (unsigned)uniq.size());
+        k_occupancy_grids<<<grid, threads, 0, st>>>(dg + (G.size() - uniq.size()));
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_cuda_error("occupancy kernel launch", e);
         d.grids = dg;

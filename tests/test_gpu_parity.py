@@ -477,8 +477,12 @@ def test_adjoint_with_several_grids(hg):
     sc, leg = w.scanners[0], w.legs[0]
     gs = hg.Scene(w.scenes[0])
     out, _ = hg.scan([gs], [sc], [leg], mode=1)
-    gW = 0.5 * torch.sin(torch.arange(out["waveform"].numel(), device=out["waveform"].device,
-                                      dtype=torch.float32)) * out["waveform"].abs().max()
+    # dL/dW of a squared misfit to a scan of perturbed densities (every grid)
+    ref_grids = [scenes.VoxelGrid(**{**g.__dict__, "density": scenes.perturbed_density(g.density, seed=1 + i)})
+                 for i, g in enumerate(w.scenes[0].grids)]
+    gref = hg.Scene(scenes.Scene(meshes=w.scenes[0].meshes, grids=ref_grids))
+    out_ref, _ = hg.scan([gref], [sc], [leg], mode=1)
+    gW = 2.0 * (out["waveform"] - out_ref["waveform"])
     grads = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"])
     torch.cuda.synchronize()
     osc = oracle.OracleScene(w.scenes[0])
