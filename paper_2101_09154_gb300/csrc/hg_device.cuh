@@ -1057,16 +1057,22 @@ __device__ __forceinline__ bool march_skip_brick(const DevGrid& S, March& m, uin
 // ---------------------------------------------------------------------------
 // scenes with several grids: their boxes have disjoint interiors, so the
 // segments of a ray in them follow one another in the order of the boxes'
-// entry points.  A grid's key is (t_enter, index), t_enter = max(0, entry of
-// an FP32 slab test against its box as stored in the grid BVH, widened at
-// build time so that no box the FP64 march would enter is culled).
-// next_grid returns the grid of least key above the cursor with
-// t_enter < t_hi; each call is one bounded walk of the grid BVH.
+// entry points.  A grid's key is (t_enter, index), t_enter = max(0, entry)
+// in FP64 exactly as march_init forms it.  The grid BVH holds the boxes
+// widened at build time; its FP32 slab tests only cull (conservatively: a
+// box the FP64 march enters is never dropped).  next_grid returns the grid of
+// least key above the cursor that the ray enters before t_hi; each call is
+// one bounded walk of the grid BVH.
 // ---------------------------------------------------------------------------
 constexpr int kGridStack = 32;
 
+struct GridRay {
+    float of[3], ivf[3];        // FP32 culling
+    double iv[3];               // 1/d (0 where d = 0)
+};
+
 struct GridCursor {
-    float te;       // key of the last grid returned
+    double te;      // key of the last grid returned
     int gi;
 };
 
@@ -1081,14 +1087,35 @@ __device__ __forceinline__ void box_span(const float o[3], const float iv[3], co
     }
 }
 
-__device__ __forceinline__ int next_grid(const DevScene& sc, const float o[3], const float iv[3],
-                                         float t_hi, GridCursor& c) {
+// FP64 entry of o + t d (t >= 0) into grid g's box, the planes formed as in
+// march_init; false: the ray does not enter it before t_hi
+__device__ __forceinline__ bool grid_entry64(const DevGrid& g, const double o[3], const double d[3],
+                                             const double iv[3], double t_hi, double& te) {
+    double tn = 0.0, tf = t_hi;
+    for (int a = 0; a < 3; ++a) {
+        const double lo = (double)g.g0[a], hi = lo + (double)g.dims[a] * (double)g.cell;
+        if (d[a] == 0.0) {
+            if (o[a] < lo || o[a] >= hi) return false;
+            continue;
+        }
+        const double t0 = (lo - o[a]) * iv[a], t1 = (hi - o[a]) * iv[a];
+        tn = fmax(tn, fmin(t0, t1));
+        tf = fmin(tf, fmax(t0, t1));
+    }
+    te = tn;
+    return tn < tf;
+}
+
+__device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, const double o[3],
+                                         const double d[3], double t_hi, GridCursor& c) {
     if (sc.n_grid == 1) {
         if (c.gi >= 0) return -1;
         c.gi = 0;
         return 0;
     }
-    float best_t = t_hi;
+    const float th = (float)t_hi * 1.0001f + 1.0e-3f;
+    const float cte = (float)c.te * 0.9999f - 1.0e-3f;      // below the cursor, for culling
+    double best_t = t_hi;
     int best = -1;
     int stack[kGridStack];
     int sp = 0, node = 0;
@@ -1098,17 +1125,20 @@ __device__ __forceinline__ int next_grid(const DevScene& sc, const float o[3], c
         const int4 ch = __ldg(reinterpret_cast<const int4*>(n + 3));
         const float lo0[3] = {a.x, a.y, a.z}, hi0[3] = {a.w, b.x, b.y};
         const float lo1[3] = {b.z, b.w, e.x}, hi1[3] = {e.y, e.z, e.w};
+        const float bt = (float)best_t * 1.0001f + 1.0e-3f;
         for (int k = 0; k < 2; ++k) {
             float tn, tf;
-            box_span(o, iv, k ? lo1 : lo0, k ? hi1 : hi0, tn, tf);
-            if (!(tn <= tf) || tf < c.te || tn > best_t || !(tn < t_hi)) continue;
+            box_span(r.of, r.ivf, k ? lo1 : lo0, k ? hi1 : hi0, tn, tf);
+            if (!(tn <= tf) || tf < cte || tn > bt || !(tn < th)) continue;
             const int child = k ? ch.y : ch.x;
             if (child < 0) {
                 const int gi = ~child;
-                const bool after = tn > c.te || (tn == c.te && gi > c.gi);
-                const bool before = best < 0 || tn < best_t || (tn == best_t && gi < best);
+                double te;
+                if (!grid_entry64(sc.grids[gi], o, d, r.iv, t_hi, te)) continue;
+                const bool after = te > c.te || (te == c.te && gi > c.gi);
+                const bool before = best < 0 || te < best_t || (te == best_t && gi < best);
                 if (after && before) {
-                    best_t = tn;
+                    best_t = te;
                     best = gi;
                 }
             } else if (sp < kGridStack) {
@@ -1125,23 +1155,22 @@ __device__ __forceinline__ int next_grid(const DevScene& sc, const float o[3], c
     return best;
 }
 
-__device__ __forceinline__ void grid_ray(const double o[3], const double d[3], float of[3], float iv[3]) {
+__device__ __forceinline__ void grid_ray(const double o[3], const double d[3], GridRay& r) {
     for (int a = 0; a < 3; ++a) {
-        of[a] = (float)o[a];
+        r.of[a] = (float)o[a];
         const float df = (float)d[a];
-        iv[a] = df != 0.0f ? 1.0f / df : 1.0e30f;
+        r.ivf[a] = df != 0.0f ? 1.0f / df : 1.0e30f;
+        r.iv[a] = d[a] != 0.0 ? 1.0 / d[a] : 0.0;
     }
 }
 
-// the grid's march set up on the next grid (in entry order) whose box the
-// FP64 march enters before t_hi; NULL when none is left
-__device__ __forceinline__ const DevGrid* next_march(const DevScene& sc, const float of[3],
-                                                     const float iv[3], const double o[3],
-                                                     const double d[3], double t_hi, GridCursor& c,
-                                                     March& m) {
-    const float th = (float)t_hi * 1.0001f + 1.0e-3f;
+// the march set up on the next grid (in entry order) that the FP64 march
+// enters before t_hi; NULL when none is left
+__device__ __forceinline__ const DevGrid* next_march(const DevScene& sc, const GridRay& r,
+                                                     const double o[3], const double d[3], double t_hi,
+                                                     GridCursor& c, March& m) {
     for (int guard = 0; guard < sc.n_grid; ++guard) {
-        const int gi = next_grid(sc, of, iv, th, c);
+        const int gi = next_grid(sc, r, o, d, t_hi, c);
         if (gi < 0) return nullptr;
         const DevGrid* G = sc.n_grid == 1 ? &sc.grid : sc.grids + gi;
         if (march_init(*G, o, d, t_hi, m)) return G;
@@ -1160,12 +1189,12 @@ __device__ __forceinline__ void walk_grids(const DevScene& sc, const double o[3]
         if (march_init(sc.grid, o, d, t_hi, m)) body(sc.grid, m);
         return;
     }
-    float of[3], iv[3];
-    grid_ray(o, d, of, iv);
-    GridCursor c = {-1.0f, -1};
+    GridRay r;
+    grid_ray(o, d, r);
+    GridCursor c = {-1.0, -1};
     March m;
     for (int guard = 0; guard < sc.n_grid; ++guard) {
-        const DevGrid* G = next_march(sc, of, iv, o, d, t_hi, c, m);
+        const DevGrid* G = next_march(sc, r, o, d, t_hi, c, m);
         if (!G || !body(*G, m)) return;
     }
 }

@@ -700,8 +700,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         // the walk over several grids (GK 2) stays live between returns
                         const DevGrid* Gp = &sc.grid;
                         double o[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 1.0}, t_hi = 0.0;
-                        float of[3] = {0.0f, 0.0f, 0.0f}, iv[3] = {0.0f, 0.0f, 0.0f};
-                        GridCursor gcur = {-1.0f, -1};
+                        GridRay gray;
+                        GridCursor gcur = {-1.0, -1};
                         if (GK > 0 && sc.has_grid && lane_on) {
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
@@ -715,8 +715,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (GK == 1) {
                                 on = march_init(sc.grid, o, d, t_hi, mch);
                             } else {
-                                grid_ray(o, d, of, iv);
-                                Gp = next_march(sc, of, iv, o, d, t_hi, gcur, mch);
+                                grid_ray(o, d, gray);
+                                Gp = next_march(sc, gray, o, d, t_hi, gcur, mch);
                                 on = Gp != nullptr;
                             }
                             if (on) Gs = proj_factor(GK == 1 ? sc.grid : *Gp, dz);
@@ -759,7 +759,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 }
                                 if (!more || !march_step(mch, v, fl)) {
                                     // this grid is done: the next one along the ray, if any
-                                    if (GK == 2 && (Gp = next_march(sc, of, iv, o, d, t_hi, gcur, mch)) != nullptr)
+                                    if (GK == 2 && (Gp = next_march(sc, gray, o, d, t_hi, gcur, mch)) != nullptr)
                                         Gs = proj_factor(*Gp, dz);
                                     else
                                         on = false;
