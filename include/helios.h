@@ -127,7 +127,8 @@ typedef struct {
 /* A scene: meshes are concatenated in order; triangle id = offset of its mesh
  * + face index.  At most 16 meshes and 4096 voxel grids per scene
  * (HELIOS_ERR_UNSUPPORTED otherwise).  The grids' boxes must have disjoint
- * interiors (touching faces are allowed; INVALID_ARG otherwise): a ray's
+ * interiors (touching faces are allowed, and so are overlaps thinner than
+ * 1e-6 of the largest box edge; INVALID_ARG otherwise): a ray's
  * segments in them then follow the order of its entry points, which is the
  * order its transmission is applied in.  Voxel primitive ids are n_triangles +
  * (voxels of the earlier grids) + (z*ny + y)*nx + x; the stochastic

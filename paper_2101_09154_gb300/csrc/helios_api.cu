@@ -171,11 +171,17 @@ static helios_status check_grid_boxes(const helios_voxel_desc* g, int n) {
     std::vector<int> order((size_t)n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int x, int y) { return b[x][0] < b[y][0]; });
+    // overlaps thinner than 1e-6 of the boxes' size are rounding of the
+    // corners (e.g. FP32 origins i * width): taken as touching
+    double ext = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) ext = std::max(ext, b[i][3 + a] - b[i][a]);
+    const double eps = 1e-6 * ext;
     for (int i = 0; i < n; ++i) {
         const auto& p = b[order[i]];
-        for (int j = i + 1; j < n && b[order[j]][0] < p[3]; ++j) {
+        for (int j = i + 1; j < n && b[order[j]][0] < p[3] - eps; ++j) {
             const auto& q = b[order[j]];
-            if (p[1] < q[4] && q[1] < p[4] && p[2] < q[5] && q[2] < p[5])
+            if (p[1] < q[4] - eps && q[1] < p[4] - eps && p[2] < q[5] - eps && q[2] < p[5] - eps)
                 return set_error(HELIOS_ERR_INVALID_ARG, "grids %d and %d overlap", order[i], order[j]);
         }
     }

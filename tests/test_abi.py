@@ -147,3 +147,26 @@ def test_scene_build_rejects_overlapping_grids_before_any_device_call(lib):
     desc.grids = ctypes.cast(gd, ctypes.POINTER(hg.VoxelDesc))
     h = ctypes.c_void_p()
     assert lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h)) == -6
+
+
+def test_scene_build_takes_rounding_thin_overlaps_as_touching(lib):
+    """Boxes whose FP32 corners overlap by rounding (1e-7 of their size) pass
+    the host check; what happens next needs a device (no-device builds stop
+    with a CUDA error)."""
+    import paper_2101_09154_gb300 as hg
+    gd = (hg.VoxelDesc * 2)()
+    for i, x0 in enumerate((0.0, 1.9999998)):
+        gd[i].origin = (ctypes.c_float * 3)(x0, 0.0, 0.0)
+        gd[i].cell = 0.5
+        gd[i].dims = (ctypes.c_int32 * 3)(4, 4, 4)
+        gd[i].G = 0.5
+        gd[i].density = 16
+    desc = hg.SceneDesc()
+    desc.n_grids = 2
+    desc.grids = ctypes.cast(gd, ctypes.POINTER(hg.VoxelDesc))
+    h = ctypes.c_void_p()
+    code = lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h))
+    assert b"overlap" not in lib.helios_last_error()
+    assert code in (0, -3)
+    if code == 0:
+        lib.helios_free_scene(h)
