@@ -97,7 +97,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
             for (;;) {
                 VoxSeg v;
                 if (!march_current(G, m, v)) return true;
-                float dens = voxel_density(G, m, v);
+                float dens = voxel_density<GK == 2>(G, m, v);
                 if (dens > 0.0f) {
                     FF t_in, t_out;
                     march_segment_ff(m, v, t_in, t_out);
@@ -121,7 +121,8 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
                              sc.n_tri + G.vox_off + (int32_t)v.vid);
                     }
                 }
-                if (!march_step(m, v, fl)) return true;
+                // several grids (sparse trees): an empty brick is crossed in one jump
+                if (!(GK == 2 && dens < 0.0f ? march_skip_brick(G, m, fl) : march_step(m, v, fl))) return true;
             }
         });
         if (stopped) return;
@@ -333,7 +334,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             for (;;) {
                                 VoxSeg v;
                                 if (!march_current(G, m, v)) return true;
-                                float dens = voxel_density(G, m, v);
+                                float dens = voxel_density<GK == 2>(G, m, v);
                                 if (dens > 0.0f) {
                                     FF t_in, t_out;
                                     march_segment_ff(m, v, t_in, t_out);
@@ -381,7 +382,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         }
                                     }
                                 }
-                                if (!march_step(m, v, fl)) return true;
+                                if (!(GK == 2 && dens < 0.0f ? march_skip_brick(G, m, fl) : march_step(m, v, fl)))
+                                    return true;
                             }
                         });
                     }
@@ -696,30 +698,37 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         March mch;
                         uint32_t fl = 0;
                         float dabs[3] = {1.0f, 1.0f, 1.0f};
-                        float dz = 1.0f, Gs = 0.0f;
-                        // the walk over several grids (GK 2) stays live between returns
+                        float Gs = 0.0f;
+                        // the walk over several grids (GK 2): its cursor stays live between
+                        // returns; the ray is formed again at each change of grid
                         const DevGrid* Gp = &sc.grid;
-                        double o[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 1.0}, t_hi = 0.0;
-                        GridRay gray;
+                        double t_hi = 0.0;
                         GridCursor gcur = {-1.0, -1};
-                        if (GK > 0 && sc.has_grid && lane_on) {
+                        auto next_g = [&]() -> bool {
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
-                            for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
-                            dz = dh[2];
+                            double o[3], d[3];
                             for (int a = 0; a < 3; ++a) {
                                 o[a] = ff2d(f.oh[a], f.ol[a]);
                                 d[a] = ff2d(dh[a], dl[a]);
                             }
-                            t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
                             if (GK == 1) {
-                                on = march_init(sc.grid, o, d, t_hi, mch);
+                                if (!march_init(sc.grid, o, d, t_hi, mch)) return false;
                             } else {
+                                GridRay gray;
                                 grid_ray(o, d, gray);
                                 Gp = next_march(sc, gray, o, d, t_hi, gcur, mch);
-                                on = Gp != nullptr;
+                                if (Gp == nullptr) return false;
                             }
-                            if (on) Gs = proj_factor(GK == 1 ? sc.grid : *Gp, dz);
+                            Gs = proj_factor(GK == 1 ? sc.grid : *Gp, dh[2]);
+                            return true;
+                        };
+                        if (GK > 0 && sc.has_grid && lane_on) {
+                            float dh[3], dl[3];
+                            subray_dir_ff(f, s_sc[s], dh, dl);
+                            for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
+                            t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+                            on = next_g();
                         }
                         while (__any_sync(full, on)) {
                             bool has = false;
@@ -729,7 +738,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 const DevGrid& G = GK == 1 ? sc.grid : *Gp;
                                 VoxSeg v;
                                 bool more = march_current(G, mch, v);
-                                float dens = more ? voxel_density(G, mch, v) : 0.0f;
+                                float dens = more ? voxel_density<GK == 2>(G, mch, v) : 0.0f;
                                 if (more && dens > 0.0f) {
                                     FF t_in, t_out;
                                     march_segment_ff(mch, v, t_in, t_out);
@@ -757,12 +766,10 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         has = true;
                                     }
                                 }
-                                if (!more || !march_step(mch, v, fl)) {
+                                if (!more || !(GK == 2 && dens < 0.0f ? march_skip_brick(G, mch, fl)
+                                                                      : march_step(mch, v, fl))) {
                                     // this grid is done: the next one along the ray, if any
-                                    if (GK == 2 && (Gp = next_march(sc, gray, o, d, t_hi, gcur, mch)) != nullptr)
-                                        Gs = proj_factor(*Gp, dz);
-                                    else
-                                        on = false;
+                                    if (!(GK == 2 && next_g())) on = false;
                                 }
                                 if (has) break;
                             }
