@@ -27,6 +27,13 @@
  *    through per-pulse flags and the optional device status word.
  *  - Scene geometry is FP32.  Instrument, platform and leg parameters are
  *    FP64 so that host-side and device-side geometry agree to FP64.
+ *  - Each call is one NVTX range named after it (visible under a profiler).
+ *  - Host-side fault injection for tests, read from the environment at every
+ *    call: HELIOS_FAULT=badarg makes every call except helios_last_error and
+ *    helios_version return HELIOS_ERR_INVALID_ARG at entry; HELIOS_FAULT=oom
+ *    makes a call that would allocate device memory return HELIOS_ERR_OOM
+ *    where it first would (nothing is launched before, everything it
+ *    allocated is released).  No fault is injected on the device.
  */
 #ifndef HELIOS_GB300_H
 #define HELIOS_GB300_H
@@ -217,7 +224,8 @@ typedef struct {
 
 /* One leg (Sec. 3.1): the platform moves from start towards end at speed_mps
  * (LINEAR) heading at the next waypoint, or stays at start (STATIC).  Pulse k
- * is emitted at t0 + k/prf.  leg_id keys the random draws of this leg. */
+ * is emitted at t0 + k/prf.  leg_id keys the random draws of this leg.  A leg
+ * interrupted after its first K pulses is resumed with first_pulse = K. */
 typedef struct {
     int32_t scene_index;
     int32_t scanner_index;
@@ -232,6 +240,10 @@ typedef struct {
     uint32_t leg_id;
     float platform_noise_m;       /* sigma of an N(0, s) offset of the platform position on each
                                      axis, drawn per pulse (Sec. 3.7 platform noise); 0: none */
+    int64_t first_pulse;          /* resume: the leg's pulses first_pulse .. first_pulse +
+                                     n_pulses - 1 are scanned into n_pulses output rows.  Every
+                                     draw is keyed by the absolute pulse index, so the rows equal
+                                     those of the whole leg (>= 0; INVALID_ARG otherwise) */
 } helios_leg_desc;
 
 typedef struct {

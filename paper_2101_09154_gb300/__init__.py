@@ -87,7 +87,8 @@ class LegDesc(C.Structure):
     _fields_ = [("scene_index", C.c_int32), ("scanner_index", C.c_int32), ("platform", C.c_int32),
                 ("beam_sample_quality", C.c_int32), ("start", C.c_double * 3), ("end", C.c_double * 3),
                 ("speed_mps", C.c_double), ("attitude_rpy", C.c_double * 3), ("t0", C.c_double),
-                ("n_pulses", C.c_int64), ("leg_id", C.c_uint32), ("platform_noise_m", C.c_float)]
+                ("n_pulses", C.c_int64), ("leg_id", C.c_uint32), ("platform_noise_m", C.c_float),
+                ("first_pulse", C.c_int64)]
 
 
 class ScanOpts(C.Structure):
@@ -226,6 +227,7 @@ def leg_desc(lg) -> LegDesc:
     d.n_pulses = int(lg.n_pulses)
     d.leg_id = int(lg.leg_id)
     d.platform_noise_m = float(lg.platform_noise_m)
+    d.first_pulse = int(getattr(lg, "first_pulse", 0))
     return d
 
 

@@ -2,10 +2,13 @@
 // validation, derived instrument constants, scene lifetime and launches.
 #include "hg_host.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -27,6 +30,40 @@ helios_status set_cuda_error(const char* what, cudaError_t e) {
     (void)cudaGetLastError();  // clear a non-sticky error
     return set_error(e == cudaErrorMemoryAllocation ? HELIOS_ERR_OOM : HELIOS_ERR_CUDA, "%s: %s",
                      what, cudaGetErrorString(e));
+}
+
+// one NVTX range per API call
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
+
+// host-side fault injection for tests (HELIOS_FAULT=badarg|oom, read per call)
+enum { kFaultNone = 0, kFaultBadArg = 1, kFaultOom = 2 };
+static int injected_fault() {
+    const char* f = std::getenv("HELIOS_FAULT");
+    if (!f) return kFaultNone;
+    if (!strcmp(f, "badarg")) return kFaultBadArg;
+    if (!strcmp(f, "oom")) return kFaultOom;
+    return kFaultNone;
+}
+
+// device allocations of the API layer: an injected oom fails the first one
+static cudaError_t dev_malloc(void** p, size_t n) {
+    if (injected_fault() == kFaultOom) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, n);
+}
+static cudaError_t dev_malloc_async(void** p, size_t n, cudaStream_t st) {
+    if (injected_fault() == kFaultOom) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, n, st);
+}
+// a scan's first device allocation is its scratch (masks, lists, queues)
+static helios_status scratch_fault() {
+    if (injected_fault() == kFaultOom)
+        return set_error(HELIOS_ERR_OOM, "scan scratch: injected fault (HELIOS_FAULT=oom)");
+    return HELIOS_OK;
 }
 
 static int32_t subray_count(int32_t q) {
@@ -266,7 +303,7 @@ static helios_status build_grids(helios_scene* s, const helios_scene_desc* desc,
                 if (!(h[k] >= 0.0f && h[k] <= 3.0e38f))
                     return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: lad_table[%d] is negative or not finite", i, k);
             float* dl = nullptr;
-            e = cudaMalloc(&dl, sizeof(float) * (size_t)m);
+            e = dev_malloc(reinterpret_cast<void**>(&dl), sizeof(float) * (size_t)m);
             if (e != cudaSuccess) return set_cuda_error("leaf-angle table allocation", e);
             s->lads.push_back(dl);
             e = cudaMemcpy(dl, h.data(), sizeof(float) * (size_t)m, cudaMemcpyHostToDevice);
@@ -296,9 +333,9 @@ static helios_status build_grids(helios_scene* s, const helios_scene_desc* desc,
     nodes.reserve((size_t)4 * (n - 1));
     std::array<float, 6> root;
     grid_bvh_rec(box, idx, 0, n, nodes, root);
-    cudaError_t e = cudaMalloc(&s->gnodes, sizeof(float4) * nodes.size());
+    cudaError_t e = dev_malloc(reinterpret_cast<void**>(&s->gnodes), sizeof(float4) * nodes.size());
     if (e == cudaSuccess) e = cudaMemcpy(s->gnodes, nodes.data(), sizeof(float4) * nodes.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&s->grids_d, sizeof(DevGrid) * (size_t)n);
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&s->grids_d), sizeof(DevGrid) * (size_t)n);
     if (e == cudaSuccess)
         e = cudaMemcpy(s->grids_d, s->grids.data(), sizeof(DevGrid) * (size_t)n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return set_cuda_error("grid BVH", e);
@@ -339,6 +376,8 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (L.first_pulse < 0 || L.first_pulse > ((int64_t)1 << 52))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse must be in 0..2^52", l);
         if (!(L.platform_noise_m >= 0.0f))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
@@ -374,6 +413,7 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         d.pulses_per_item = item_pulses(d.pulses_per_sub, mode);
         d.leg_id = L.leg_id;
         d.platform_noise = L.platform_noise_m;
+        d.k_first = L.first_pulse;
         d.pulse_off = P.total_pulses;
         d.wave_off = P.wave;
         d.sub_off = P.sub;
@@ -385,6 +425,17 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         P.legs.push_back(d);
     }
     return HELIOS_OK;
+}
+
+// The kernels index the outputs of absolute pulse k at offset + k: the plan's
+// offsets (where a leg's rows start) less first_pulse rows.
+static DevLeg kernel_leg(DevLeg d, const helios_scanner_desc* scanners) {
+    const helios_scanner_desc& sc = scanners[d.scanner];
+    d.pulse_off -= d.k_first;
+    d.wave_off -= d.k_first * sc.n_bins;
+    d.sub_off -= d.k_first * d.S;
+    d.echo_off -= d.k_first * sc.max_echoes;
+    return d;
 }
 
 static helios_status check_scenes(helios_scene* const* scenes, int32_t n_scenes) {
@@ -410,6 +461,9 @@ int32_t helios_subray_count(int32_t q) { return subray_count(q); }
 helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_stream,
                                  helios_scene** out) {
     g_err.clear();
+    CallRange range_("helios_build_scene");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_build_scene: injected fault (HELIOS_FAULT=badarg)");
     if (!desc || !out) return set_error(HELIOS_ERR_INVALID_ARG, "desc and out must not be NULL");
     *out = nullptr;
     if (desc->n_meshes < 0 || desc->n_meshes > kMaxMesh)
@@ -465,9 +519,11 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         return r;
     }
     cudaError_t e = cudaSuccess;
-    if (s->n_int > 0) e = cudaMalloc(&s->nodes, sizeof(float4) * 4 * (size_t)s->n_int);
-    if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tris, sizeof(float4) * 3 * (size_t)n_tri);
-    if (e == cudaSuccess && n_tri > 0) e = cudaMalloc(&s->tri_index, sizeof(int32_t) * (size_t)n_tri);
+    if (s->n_int > 0) e = dev_malloc(reinterpret_cast<void**>(&s->nodes), sizeof(float4) * 4 * (size_t)s->n_int);
+    if (e == cudaSuccess && n_tri > 0)
+        e = dev_malloc(reinterpret_cast<void**>(&s->tris), sizeof(float4) * 3 * (size_t)n_tri);
+    if (e == cudaSuccess && n_tri > 0)
+        e = dev_malloc(reinterpret_cast<void**>(&s->tri_index), sizeof(int32_t) * (size_t)n_tri);
     if (e != cudaSuccess) {
         r = set_cuda_error("scene allocation", e);
         free_scene_buffers(s);
@@ -488,6 +544,9 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
 
 helios_status helios_free_scene(helios_scene* scene) {
     g_err.clear();
+    CallRange range_("helios_free_scene");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_free_scene: injected fault (HELIOS_FAULT=badarg)");
     if (!scene) return HELIOS_OK;
     int cur = 0;
     cudaGetDevice(&cur);
@@ -500,6 +559,9 @@ helios_status helios_free_scene(helios_scene* scene) {
 
 helios_status helios_lad_table(int32_t distribution, int32_t n, float* table, void* cuda_stream) {
     g_err.clear();
+    CallRange range_("helios_lad_table");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_lad_table: injected fault (HELIOS_FAULT=badarg)");
     if (distribution < HELIOS_LAD_PLANOPHILE || distribution > HELIOS_LAD_SPHERICAL)
         return set_error(HELIOS_ERR_INVALID_ARG, "unknown leaf angle distribution %d", distribution);
     if (n < 2 || n > 65536) return set_error(HELIOS_ERR_INVALID_ARG, "n must be in 2..65536");
@@ -509,6 +571,9 @@ helios_status helios_lad_table(int32_t distribution, int32_t n, float* table, vo
 
 helios_status helios_scene_get_info(const helios_scene* scene, helios_scene_info* info) {
     g_err.clear();
+    CallRange range_("helios_scene_get_info");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scene_get_info: injected fault (HELIOS_FAULT=badarg)");
     if (!scene || !info) return set_error(HELIOS_ERR_INVALID_ARG, "scene and info must not be NULL");
     info->n_triangles = scene->n_tri;
     info->n_bvh_nodes = scene->n_int;
@@ -524,6 +589,9 @@ helios_status helios_output_layout(const helios_scanner_desc* scanners, int32_t 
                                    int64_t* subray_offset, int64_t* echo_offset,
                                    helios_layout* totals) {
     g_err.clear();
+    CallRange range_("helios_output_layout");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_output_layout: injected fault (HELIOS_FAULT=badarg)");
     LegPlan P;
     helios_status st = plan_legs(scanners, n_scanners, legs, n_legs, -1, 768, HELIOS_MODE_STOCHASTIC, P);
     if (st != HELIOS_OK) return st;
@@ -548,6 +616,9 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
                                const helios_scan_opts* opts, const helios_outputs* out,
                                void* cuda_stream) {
     g_err.clear();
+    CallRange range_("helios_scan_legs");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs: injected fault (HELIOS_FAULT=badarg)");
     helios_status st = check_scenes(scenes, n_scenes);
     if (st != HELIOS_OK) return st;
     if (!opts || !out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and out must not be NULL");
@@ -568,7 +639,7 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     ScanLaunch L;
     for (int i = 0; i < n_scenes; ++i) L.scenes.push_back(dev_scene(scenes[i]));
     for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
-    L.legs = P.legs;
+    for (const DevLeg& d : P.legs) L.legs.push_back(kernel_leg(d, scanners));
     L.out.waveform = out->waveform;
     L.out.window_bin = out->window_bin;
     L.out.echo_count = out->echo_count;
@@ -587,6 +658,8 @@ helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n_scenes,
     L.threads = threads;
     L.blocks_per_sm = opts->blocks_per_sm;
     if (P.total_pulses == 0) return HELIOS_OK;
+    st = scratch_fault();
+    if (st != HELIOS_OK) return st;
     OccupancyMasks masks;
     st = build_occupancy(L.scenes, scenes, (cudaStream_t)cuda_stream, masks);
     if (st != HELIOS_OK) return st;
@@ -600,6 +673,9 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
                                   const int32_t* window_bin, const int32_t* subray_hit,
                                   const helios_scene_grads* grads, void* cuda_stream) {
     g_err.clear();
+    CallRange range_("helios_scan_adjoint");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_adjoint: injected fault (HELIOS_FAULT=badarg)");
     helios_status st = check_scenes(scenes, n_scenes);
     if (st != HELIOS_OK) return st;
     if (!opts || !d_waveform || !window_bin || !grads)
@@ -629,13 +705,15 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
         L.want_dens.push_back(want);
     }
     for (int i = 0; i < n_scanners; ++i) L.scanners.push_back(derive_scanner(scanners[i]));
-    L.legs = P.legs;
+    for (const DevLeg& d : P.legs) L.legs.push_back(kernel_leg(d, scanners));
     L.g = d_waveform;
     L.window = window_bin;
     L.subray_hit = subray_hit;
     L.seed = opts->seed;
     L.threads = threads;
     if (P.total_pulses == 0) return HELIOS_OK;
+    st = scratch_fault();
+    if (st != HELIOS_OK) return st;
     OccupancyMasks masks;
     st = build_occupancy(L.scenes, scenes, (cudaStream_t)cuda_stream, masks, grads);
     if (st != HELIOS_OK) return st;
@@ -664,6 +742,9 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
                                                  int32_t n_legs, const helios_scan_opts* opts,
                                                  const helios_outputs* out, void* cuda_stream) {
     g_err.clear();
+    CallRange range_("helios_scan_legs_static");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs_static: injected fault (HELIOS_FAULT=badarg)");
     helios_status st = check_scenes(scenes, n_scenes);
     if (st != HELIOS_OK) return st;
     if (!opts || !out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and out must not be NULL");
@@ -702,6 +783,8 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
+        if (L.first_pulse < 0 || L.first_pulse > ((int64_t)1 << 52))
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse must be in 0..2^52", l);
         if (!(L.platform_noise_m >= 0.0f))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
@@ -736,10 +819,12 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         d.pulses_per_item = item_pulses(d.pulses_per_sub, opts->mode);
         d.leg_id = L.leg_id;
         d.platform_noise = L.platform_noise_m;
-        d.pulse_off = pulses;
-        d.wave_off = wave;
-        d.sub_off = sub;
-        d.echo_off = echo;
+        // outputs of absolute pulse k at offset + k (rows start at first_pulse)
+        d.k_first = L.first_pulse;
+        d.pulse_off = pulses - L.first_pulse;
+        d.wave_off = wave - L.first_pulse * sc.n_bins;
+        d.sub_off = sub - L.first_pulse * d.S;
+        d.echo_off = echo - L.first_pulse * sc.max_echoes;
         pulses += L.n_pulses;
         wave += L.n_pulses * sc.n_bins;
         sub += L.n_pulses * d.S;
@@ -827,6 +912,9 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
                                                int64_t chunk_pulses, void* cuda_stream) {
     using namespace hg;
     g_err.clear();
+    CallRange range_("helios_scan_legs_host");
+    if (injected_fault() == kFaultBadArg)
+        return set_error(HELIOS_ERR_INVALID_ARG, "helios_scan_legs_host: injected fault (HELIOS_FAULT=badarg)");
     helios_status st = check_scenes(scenes, n_scenes);
     if (st != HELIOS_OK) return st;
     if (!opts || !host_out) return set_error(HELIOS_ERR_INVALID_ARG, "opts and host_out must not be NULL");
@@ -897,7 +985,7 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
         if (e != cudaSuccess) { hs.scanned[i] = nullptr; return set_cuda_error("cudaEventCreate", e); }
         e = cudaEventCreateWithFlags(&hs.copied[i], cudaEventDisableTiming);
         if (e != cudaSuccess) { hs.copied[i] = nullptr; return set_cuda_error("cudaEventCreate", e); }
-        e = cudaMallocAsync(&hs.buf[i], bytes, hs.s0);
+        e = dev_malloc_async(&hs.buf[i], bytes, hs.s0);
         if (e != cudaSuccess) { hs.buf[i] = nullptr; return set_cuda_error("cudaMallocAsync(staging)", e); }
     }
     ScanLaunch L;
@@ -931,8 +1019,9 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
         // the chunk's legs, their outputs indexed from the slot's start
         L.legs.clear();
         for (const Piece& pc : chunks[c]) {
-            DevLeg d = P.legs[pc.leg];
-            d.k_first = pc.k0;
+            // rows pc.k0 .. of the leg: absolute pulses first_pulse + pc.k0 ..
+            DevLeg d = kernel_leg(P.legs[pc.leg], scanners);
+            d.k_first += pc.k0;
             d.n_pulses = pc.n;
             d.pulse_off -= lo.p;
             d.wave_off -= lo.w;

@@ -91,6 +91,7 @@ class Leg:
     beam_sample_quality: int = -1         # -1: use the scanner's
     leg_id: int = 0
     platform_noise_m: float = 0.0         # sigma of the per-pulse platform position noise
+    first_pulse: int = 0                  # resume: scan pulses first_pulse .. first_pulse + n_pulses - 1
 
 
 @dataclass

@@ -170,3 +170,50 @@ def test_scene_build_takes_rounding_thin_overlaps_as_touching(lib):
     assert code in (0, -3)
     if code == 0:
         lib.helios_free_scene(h)
+
+
+def test_host_side_fault_injection(lib, monkeypatch):
+    """HELIOS_FAULT=badarg fails every call at entry; HELIOS_FAULT=oom fails a
+    call where it would first allocate device memory (the scene build's first
+    buffer here: no device is touched before it)."""
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    sc, leg = scenes.Scanner(), scenes.Leg(n_pulses=10)
+    monkeypatch.setenv("HELIOS_FAULT", "badarg")
+    with pytest.raises(hg.HeliosError) as e:
+        hg.output_layout([sc], [leg])
+    assert e.value.code == -1 and "injected" in str(e.value)
+    monkeypatch.setenv("HELIOS_FAULT", "oom")
+    assert hg.output_layout([sc], [leg])["total_pulses"] == 10     # allocates nothing
+    verts = (ctypes.c_float * 9)(0, 0, 0, 1, 0, 0, 0, 1, 0)
+    m = hg.MeshDesc()
+    m.verts = ctypes.cast(verts, ctypes.c_void_p)     # never read before the failing allocation
+    m.n_verts = 3
+    m.faces = 16
+    m.n_faces = 2
+    m.reflectance = 16
+    md = (hg.MeshDesc * 1)(m)
+    desc = hg.SceneDesc()
+    desc.meshes = ctypes.cast(md, ctypes.POINTER(hg.MeshDesc))
+    desc.n_meshes = 1
+    h = ctypes.c_void_p()
+    assert lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h)) == -2
+    assert b"memory" in lib.helios_last_error().lower()
+    monkeypatch.delenv("HELIOS_FAULT")
+
+
+def test_first_pulse_resume_layout_and_validation(lib):
+    """A resumed leg (first_pulse = K) has n_pulses rows like any other; a
+    negative first_pulse is refused."""
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    sc = scenes.Scanner(n_bins=64)
+    a = hg.output_layout([sc], [scenes.Leg(n_pulses=100), scenes.Leg(n_pulses=50, leg_id=1)])
+    b = hg.output_layout([sc], [scenes.Leg(n_pulses=100, first_pulse=12345),
+                                scenes.Leg(n_pulses=50, leg_id=1, first_pulse=7)])
+    for k in ("pulse_offset", "wave_offset", "subray_offset", "echo_offset"):
+        assert list(a[k]) == list(b[k])
+    assert a["total_pulses"] == b["total_pulses"] == 150
+    with pytest.raises(hg.HeliosError) as e:
+        hg.output_layout([sc], [scenes.Leg(n_pulses=5, first_pulse=-1)])
+    assert e.value.code == -1 and "first_pulse" in str(e.value)

@@ -50,3 +50,17 @@ def test_host_scan_rejects_bad_chunk(hg):
     with pytest.raises(hg.HeliosError) as e:
         hg.scan_to_host(gsc, w.scanners, w.legs, chunk_pulses=0)
     assert e.value.code == -1 and "chunk_pulses" in str(e.value)
+
+
+def test_host_scan_of_a_resumed_leg(hg):
+    """The host-memory scan honours first_pulse in every chunk."""
+    import dataclasses
+    w = scenes.als_terrain(seed=5, size=96, n_trees=6, n_pulses=5000, n_bins=256, agl=120.0,
+                           speed=30.0, prf=50_000.0)
+    leg = dataclasses.replace(w.legs[0], first_pulse=1900, n_pulses=3100)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    dev, lay = hg.scan(gsc, w.scanners, [leg], seed=3, subrays=False)
+    host, lay2 = hg.scan_to_host(gsc, w.scanners, [leg], seed=3, chunk_pulses=1000)
+    torch.cuda.synchronize()
+    for k in ("waveform", "window_bin", "echo_count", "echo_range", "echo_bin"):
+        assert np.array_equal(dev[k].cpu().numpy(), host[k].numpy()), k

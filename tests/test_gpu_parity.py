@@ -503,3 +503,32 @@ def test_adjoint_with_several_grids(hg):
     assert sum(t > 0 for t in touched) >= 6
     gr = to_np(grads[0]["reflectance"][0])
     assert np.allclose(gr, d_refl, rtol=1e-3, atol=1e-6 * np.abs(d_refl).max())
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_resumed_leg_matches_the_oracle_and_the_whole_leg(hg, mode):
+    """first_pulse = K scans pulses K.. into rows 0..: against the oracle on
+    those pulses, and against the same rows of the whole leg's scan (every
+    draw is keyed by the absolute pulse index)."""
+    import dataclasses
+    w = scenes.uls_voxels(seed=6, n=48, n_pulses=3001, n_bins=512, agl=12.0, speed=1.0, prf=2000.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    K = 1237
+    rleg = dataclasses.replace(leg, first_pulse=K, n_pulses=leg.n_pulses - K)
+    gs = hg.Scene(w.scenes[0])
+    full, lay_f = hg.scan([gs], [sc], [leg], mode=mode, seed=11)
+    part, lay_p = hg.scan([gs], [sc], [rleg], mode=mode, seed=11)
+    torch.cuda.synchronize()
+    S = hg.subray_count(sc.beam_sample_quality)
+    osc = oracle.OracleScene(w.scenes[0])
+    rows = np.arange(rleg.n_pulses)
+    ref = oracle.scan(osc, sc, leg, K + rows, mode=mode, seed=11)
+    stats = compare(leg_view(part, lay_p, 0, sc, S, rows), ref, expected_mode=(mode == 1))
+    assert stats["echoes"] > 500
+    a = leg_view(part, lay_p, 0, sc, S, rows)
+    b = leg_view(full, lay_f, 0, sc, S, K + rows)
+    ok = (ref["flags"] & oracle.F_DECISION) == 0      # no near-tie decision on these pulses
+    assert np.array_equal(a["window_bin"][ok], b["window_bin"][ok])
+    scale = np.abs(b["waveform"]).max(axis=1, keepdims=True)
+    assert (np.abs(a["waveform"] - b["waveform"]) <= 1e-5 * scale + 1e-30)[ok].all()
+    assert np.array_equal(a["echo_count"][ok], b["echo_count"][ok])
