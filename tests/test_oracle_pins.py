@@ -964,3 +964,41 @@ def test_opaque_grid_behind_a_transmissive_one():
             assert abs(R[0] - 5.0) < 1e-9                   # the opaque grid's top face at z = 1
     p = math.exp(-0.5 * _f32(0.6) * 1.0)
     assert abs(through / 400 - p) < 4.5 * math.sqrt(p * (1 - p) / 400)
+
+
+def test_march_over_several_grids_matches_per_voxel_brute_force():
+    """The march over three grids (two touching along x, one apart, different
+    cells) lists exactly the voxels a per-voxel slab test finds, in range
+    order, with ids running over the grids' voxels in their listed order."""
+    rng = np.random.default_rng(5)
+    specs = [((-1.0, -1.0, -1.0), 0.5, (3, 4, 2)),      # x in [-1, 0.5)
+             ((0.5, -1.0, -1.0), 0.5, (2, 4, 2)),       # touches the first at x = 0.5
+             ((-0.5, 1.5, -2.0), 0.25, (4, 3, 5))]      # apart
+    grids = [scenes.VoxelGrid(origin=o, cell=c, dims=dm, density=np.ones(dm[::-1], np.float32))
+             for o, c, dm in specs]
+    osc = oracle.OracleScene(scenes.Scene(meshes=[], grids=grids))
+    offs = np.cumsum([0] + [int(np.prod(dm)) for _, _, dm in specs])
+    for _ in range(300):
+        o = rng.uniform(-4, 4, 3)
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        vid, ti, to = osc.march(o, d)
+        ref = []
+        for gi, (org, c, (nx, ny, nz)) in enumerate(specs):
+            for z in range(nz):
+                for y in range(ny):
+                    for x in range(nx):
+                        a = np.array(org) + c * np.array([x, y, z])
+                        b = a + c
+                        with np.errstate(divide="ignore", invalid="ignore"):
+                            t1 = (a - o) / d
+                            t2 = (b - o) / d
+                        tin = max(0.0, np.max(np.minimum(t1, t2)))
+                        tout = np.min(np.maximum(t1, t2))
+                        if tout - tin > 1e-9:
+                            ref.append((tin, int(offs[gi] + (z * ny + y) * nx + x), tout))
+        ref.sort()
+        got = [(a, int(v), b) for a, v, b in zip(ti, vid, to) if b - a > 1e-9]
+        assert [r[1] for r in ref] == [g[1] for g in got]
+        for r, g in zip(ref, got):
+            assert abs(r[0] - g[0]) < 1e-12 and abs(r[2] - g[2]) < 1e-12
