@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     const int c0 = (cb + 3) >> 1;     // table cell of bin 0
     const float dt = (float)sn.bin_ns;
     float* const* drefl = P.d_refl[lg.scene];
+    float* const ddens1 = sc.grid.ddens;     // the one grid's gradient (GK 1)
     for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
     if (tab) {
         // h_k = p(k bin) (1, u/sigma, (u^2-1)/sigma^2, (u^3-3u)/sigma^3), u = k bin/sigma
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                     if (listing && n < P.rl_cap) {
                                         // the voxel's index over all of the scene's grids
                                         const size_t e = (size_t)n * 32 + lane;
-                                        __stcg(reinterpret_cast<int32_t*>(RL) + e, G.vox_off + (int32_t)v.vid);
+                                        __stcg(reinterpret_cast<int32_t*>(RL) + e,
+                                               (GK == 1 ? 0 : G.vox_off) + (int32_t)v.vid);
                                         __stcg(RL + RLs + e, Gs * A * T * len * a);
                                         __stcg(RL + 2 * RLs + e, Gs * len);
                                         __stcg(RL + 3 * RLs + e, A * w);
@@ -281,9 +283,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                         const float t1 = __ldcg(RL + RLs + o2);
                         const float gl = __ldcg(RL + 2 * RLs + o2);
                         const float aw = __ldcg(RL + 3 * RLs + o2);
-                        float* dd;
-                        int32_t vid;
-                        grid_of_voxel<GK>(sc, vx, dd, vid);
+                        float* dd = ddens1;
+                        int32_t vid = vx;
+                        if (GK == 2) grid_of_voxel<GK>(sc, vx, dd, vid);
                         if (dd) atomicAdd(&dd[vid], fmaf(-gl, suffix, t1));
                         suffix += aw;
                     }
