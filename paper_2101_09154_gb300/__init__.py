@@ -7,10 +7,17 @@ no CPU fallback: if the library is missing or no CUDA device is present the
 calls raise.
 
 Main entry points:
-    Scene(scene)                      build the BVH on the current CUDA device
+    Scene(scene)                      build the BVH (and, with several voxel grids,
+                                      the BVH over their boxes) on the current device
     scan(scenes, scanners, legs, ...) simulate legs -> waveforms, echoes, ...
-    scan_adjoint(...)                 gradients of a waveform loss
+    scan_to_host(...)                 the same with outputs in page-locked host memory
+    scan_static(...)                  the same without any device allocation
+    scan_adjoint(...)                 gradients of a waveform loss (per mesh, per grid)
     WaveformFunction                  torch.autograd.Function around both
+    lad_table(kind, n)                leaf-angle table G(|cos zenith|) for a voxel grid
+    fit.fit_reflectance(...)          adjoint-driven per-triangle reflectance fit
+
+A leg with ``first_pulse = K`` resumes an interrupted scan at pulse K.
 """
 from __future__ import annotations
 
@@ -236,6 +243,9 @@ class Scene:
 
     Reflectance and density tensors are referenced by the library (not
     copied), so in-place updates are seen by later scans without a rebuild.
+    Grids given the same density array share one device tensor (and so see
+    each other's updates); a grid's ``lad`` table (host values or a device
+    tensor from ``lad_table``) is copied by the build.
     """
 
     def __init__(self, scene, device=None, stream=None):
