@@ -249,6 +249,15 @@ class Scene:
     """
 
     def __init__(self, scene, device=None, stream=None):
+        # the library reads nx*ny*nz densities per grid: check the arrays first
+        for i, g in enumerate(scene.grids):
+            n = int(np.prod([int(x) for x in g.dims]))
+            if np.asarray(g.density).size != n:
+                raise ValueError(f"grid {i}: density has {np.asarray(g.density).size} values, dims "
+                                 f"{tuple(g.dims)} need {n}")
+            lad = getattr(g, "lad", None)
+            if lad is not None and not (2 <= int(np.prod(getattr(lad, "shape", (len(lad),)))) <= 65536):
+                raise ValueError(f"grid {i}: a leaf-angle table needs 2..65536 entries")
         torch = _torch()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev

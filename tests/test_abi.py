@@ -217,3 +217,16 @@ def test_first_pulse_resume_layout_and_validation(lib):
     with pytest.raises(hg.HeliosError) as e:
         hg.output_layout([sc], [scenes.Leg(n_pulses=5, first_pulse=-1)])
     assert e.value.code == -1 and "first_pulse" in str(e.value)
+
+
+def test_scene_wrapper_checks_density_sizes_before_any_upload():
+    import numpy as np
+    import paper_2101_09154_gb300 as hg
+    import scenes
+    g = scenes.VoxelGrid(origin=(0, 0, 0), cell=1.0, dims=(4, 4, 4), density=np.zeros((4, 4, 3), np.float32))
+    with pytest.raises(ValueError, match="need 64"):
+        hg.Scene(scenes.Scene(meshes=[], grids=[g]))
+    g = scenes.VoxelGrid(origin=(0, 0, 0), cell=1.0, dims=(2, 2, 2), density=np.zeros((2, 2, 2), np.float32),
+                         lad=np.ones(1, np.float32))
+    with pytest.raises(ValueError, match="2..65536"):
+        hg.Scene(scenes.Scene(meshes=[], grids=[g]))
