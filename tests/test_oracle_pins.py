@@ -517,9 +517,9 @@ def test_adjoint_matches_central_differences():
         return float(((W - W_ref) ** 2).sum())
 
     touched = np.nonzero(d_dens)[0]
-    assert len(touched) > 20
+    assert len(touched) > 64
     rng = np.random.default_rng(2)
-    for v in rng.choice(touched, 12, replace=False):
+    for v in rng.choice(touched, 64, replace=False):      # 64 traversed voxels
         x = float(base.ravel()[v])
         h = 1e-4 * max(abs(x), 1e-2)
         dp = base.copy().ravel(); dp[v] = np.float32(x + h)
