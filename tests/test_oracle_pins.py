@@ -228,8 +228,8 @@ def test_pulse_shapes():
 
 def test_bvh_matches_brute_force_on_random_soups():
     rng = np.random.default_rng(11)
-    for seed in range(40):
-        n = int(rng.integers(1, 400))
+    for seed in range(100):
+        n = int(rng.integers(1, 501))
         osc = oracle.OracleScene(scenes.triangle_soup(seed, n))
         for _ in range(50):
             o = rng.uniform(-15, 15, 3)
