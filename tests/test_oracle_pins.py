@@ -1002,3 +1002,29 @@ def test_march_over_several_grids_matches_per_voxel_brute_force():
         assert [r[1] for r in ref] == [g[1] for g in got]
         for r, g in zip(ref, got):
             assert abs(r[0] - g[0]) < 1e-12 and abs(r[2] - g[2]) < 1e-12
+
+
+def test_two_grids_stochastic_stop_frequencies():
+    """Eq. intersection_dist along one ray through two separate grids (listed
+    in the opposite order): it stops in the first with 1 - e^-t1, in the
+    second with e^-t1 (1 - e^-t2), reaches the ground with e^-(t1 + t2)."""
+    sc = scenes.Scanner()
+    top = scenes.VoxelGrid(origin=(-1.0, -1.0, 2.0), cell=0.5, dims=(4, 4, 2),
+                           density=np.full((2, 4, 4), 0.9, np.float32), G=0.5)
+    low = scenes.VoxelGrid(origin=(-1.0, -1.0, -1.0), cell=0.5, dims=(4, 4, 4),
+                           density=np.full((4, 4, 4), 0.4, np.float32), G=0.7)
+    ground = _grid_scene(np.zeros((1, 1, 1), np.float32), origin=(-900.0, -900.0, -900.0), cell=0.5,
+                         ground_z=-3.0).meshes
+    osc = oracle.OracleScene(scenes.Scene(meshes=ground, grids=[low, top]))
+    n_low = 4 * 4 * 4
+    n = 8000
+    counts = np.zeros(3)
+    for k in range(n):
+        R, P, ids, _ = oracle.trace_returns(osc, sc, [0.1, 0.1, 6.0], [0.0, 0.0, -1.0], mode=0, seed=21,
+                                            pulse=k)
+        vid = ids[0] - osc.n_tri
+        counts[0 if vid >= n_low else (1 if vid >= 0 else 2)] += 1   # top grid, low grid, ground
+    t1, t2 = 0.5 * _f32(0.9) * 1.0, 0.7 * _f32(0.4) * 2.0
+    p = np.array([1 - math.exp(-t1), math.exp(-t1) * (1 - math.exp(-t2)), math.exp(-t1 - t2)])
+    sd = np.sqrt(n * p * (1 - p))
+    assert np.all(np.abs(counts - n * p) < 5 * sd), (counts, n * p)
