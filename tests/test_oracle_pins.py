@@ -1028,3 +1028,40 @@ def test_two_grids_stochastic_stop_frequencies():
     p = np.array([1 - math.exp(-t1), math.exp(-t1) * (1 - math.exp(-t2)), math.exp(-t1 - t2)])
     sd = np.sqrt(n * p * (1 - p))
     assert np.all(np.abs(counts - n * p) < 5 * sd), (counts, n * p)
+
+
+def test_rotating_head_turns_at_the_head_rate_with_the_polygon_in_elevation():
+    """Rotating head (the MLS/TLS head): with a flat elevation the pulse
+    directions stay in the spin plane, consecutive pulses turn by
+    head_rate/PRF about the spin axis and a full turn comes back; with a
+    polygon mirror the elevation sweeps [-max, max] once per mirror line."""
+    prf, rate = 1000.0, 2 * math.pi * 5.0          # 5 rev/s: 200 pulses per turn
+    sc = scenes.Scanner(prf_hz=prf, deflector=scenes.DEFL_ROTATING_HEAD, head_rate_rad_s=rate,
+                        scan_freq_hz=1.0, scan_angle_max_rad=0.0)
+    leg = scenes.Leg(platform=scenes.PLATFORM_STATIC, n_pulses=400)
+    ds = np.array([oracle.pulse_ray(sc, leg, k)[1] for k in range(401)])
+    assert np.allclose(np.linalg.norm(ds, axis=1), 1.0, atol=1e-14)
+    axis = np.cross(ds[0], ds[1])
+    axis /= np.linalg.norm(axis)
+    assert np.abs(ds @ axis).max() < 1e-12                         # one plane
+    step = np.arccos(np.clip(np.sum(ds[1:] * ds[:-1], axis=1), -1, 1))
+    assert np.allclose(step, rate / prf, atol=1e-9)
+    assert np.allclose(ds[200], ds[0], atol=1e-12) and np.allclose(ds[400], ds[0], atol=1e-12)
+    # polygon mirror in elevation: angle to the spin plane in [-max, max], sweeping it per line
+    amax = math.radians(20.0)
+    sc2 = scenes.replace(sc, scan_freq_hz=50.0, scan_angle_max_rad=amax)
+    ds2 = np.array([oracle.pulse_ray(sc2, leg, k)[1] for k in range(400)])
+    el = np.arcsin(np.clip(ds2 @ axis, -1, 1))
+    assert np.abs(el).max() <= amax + 1e-12
+    # a linear sweep sampled 20 times per line: constant steps of 2 max/20 inside a
+    # line, then a jump back; the samples reach -max and max - 2 max/20
+    d_el = np.diff(el)
+    inside = d_el > 0
+    assert np.allclose(d_el[inside], 2 * amax / 20, atol=1e-9)
+    assert np.sum(~inside) == 400 // 20 - 1
+    assert abs(el.min() + amax) < 1e-9 and abs(el.max() - (amax - 2 * amax / 20)) < 1e-9
+    # azimuth in the spin plane still advances at the head rate
+    flat = ds2 - np.outer(ds2 @ axis, axis)
+    flat /= np.linalg.norm(flat, axis=1, keepdims=True)
+    stepf = np.arccos(np.clip(np.sum(flat[1:] * flat[:-1], axis=1), -1, 1))
+    assert np.allclose(stepf, rate / prf, atol=1e-9)
