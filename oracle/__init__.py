@@ -105,6 +105,12 @@ def lib():
             l.or_subray_intensity.argtypes = [C.POINTER(Scanner), C.c_double, C.c_double]
             l.or_echo_width.argtypes = [d3, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]
             l.or_echo_width.restype = C.c_double
+            l.or_echo_peaks.argtypes = [d3, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            l.or_echo_peaks.restype = C.c_int
+            l.or_echo_object.argtypes = [C.POINTER(Scanner), C.c_int64, d3, d3,
+                                         C.POINTER(C.c_int64), C.c_double, C.POINTER(C.c_int)]
+            l.or_echo_object.restype = C.c_int64
             l.or_subray_intensity.restype = C.c_double
             l.or_pulse_shape.argtypes = [C.POINTER(Scanner), C.c_double]
             l.or_pulse_shape.restype = C.c_double
@@ -358,6 +364,31 @@ def echo_width(W, p, sigma_b):
     return s, bool(tie.value)
 
 
+def echo_peaks(W, thr_rel=0.05, K=8):
+    """Echo bins of waveform W (Sec. 3.4): returns (bins, overflow, near)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    bins = np.zeros(max(int(K), 1), np.int32)
+    ov, near = C.c_int(0), C.c_int(0)
+    n = lib().or_echo_peaks(W.ctypes.data_as(C.POINTER(C.c_double)), int(W.shape[0]),
+                            float(thr_rel), int(K), bins.ctypes.data_as(C.POINTER(C.c_int32)),
+                            C.byref(ov), C.byref(near))
+    return bins[:n].copy(), bool(ov.value), bool(near.value)
+
+
+def echo_object(scanner, P, R, ids, tb_ns):
+    """Primitive with the largest contribution at time tb_ns among returns
+    (P, R, id) in summation order; returns (id, near_tie)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    near = C.c_int(0)
+    sc = scanner_struct(scanner)
+    b = lib().or_echo_object(C.byref(sc), int(P.shape[0]), P.ctypes.data_as(C.POINTER(C.c_double)),
+                             R.ctypes.data_as(C.POINTER(C.c_double)),
+                             ids.ctypes.data_as(C.POINTER(C.c_int64)), float(tb_ns), C.byref(near))
+    return int(b), bool(near.value)
+
+
 def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_window=None,
          threads=0, echo_width=False):
     """Simulate the given pulse indices of one leg; returns a dict of numpy arrays
@@ -382,8 +413,10 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
     if fixed_window is not None:
         fw = np.ascontiguousarray(fixed_window, dtype=np.int32)
     s, l = scanner_struct(scanner), leg_struct(leg)
-    lib().or_scan(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), n, int(mode),
-                  int(seed) & (2 ** 64 - 1), _ptr(fw), C.byref(out), int(threads))
+    rc = lib().or_scan(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), n, int(mode),
+                       int(seed) & (2 ** 64 - 1), _ptr(fw), C.byref(out), int(threads))
+    if rc != 0:
+        raise ValueError("oracle scan rejected the scanner (max_echoes outside 1..64)")
     r["pulses"] = pulses
     r["S"] = S
     return r

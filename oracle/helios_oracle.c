@@ -967,6 +967,66 @@ static void adjoint_subray(job_t* J, const double* g, int32_t m,
     free(A); free(T); free(wk);
 }
 
+/* Echoes (Sec. 3.4: local maxima of the waveform above a threshold; the
+ * threshold as a fraction of the pulse's own maximum bin).  A bin is an echo
+ * when it rises strictly above its left neighbour, does not fall below its
+ * right neighbour (so a plateau gives its leftmost bin), is positive and is at
+ * or above thr_rel * max W; outside the window W counts as 0.  Bins are taken
+ * in order and the first K kept. */
+int or_echo_peaks(const double* W, int nb, double thr_rel, int K, int32_t* bins, int* overflow,
+                  int* near) {
+    double wmax = 0.0;
+    for (int b = 0; b < nb; ++b)
+        if (W[b] > wmax) wmax = W[b];
+    double thr = thr_rel * wmax;
+    double tol = 1e-4 * wmax;
+    int ne = 0;
+    *overflow = 0;
+    *near = 0;
+    for (int b = 0; b < nb; ++b) {
+        double c = W[b];
+        double l = b > 0 ? W[b - 1] : 0.0;
+        double r = b + 1 < nb ? W[b + 1] : 0.0;
+        if (c >= thr - tol && (fabs(c - l) <= tol || fabs(c - r) <= tol)) *near = 1;
+        int is_max = c > l && c >= r && c >= thr && c > 0.0;
+        if (is_max && fabs(c - thr) <= tol) *near = 1;
+        if (!is_max) continue;
+        if (ne >= K) { *overflow = 1; continue; }
+        bins[ne++] = b;
+    }
+    return ne;
+}
+
+/* Echo object: the primitive whose return contributes most to the waveform at
+ * time tb; on equal contributions the first in summation order (subray order,
+ * then along the subray).  *near: the two largest within 1e-4 relative. */
+static int64_t echo_object_list(const or_scanner* sn, const ret_t* r, int64_t n, double tb,
+                                int* near) {
+    double best = -1.0, second = -1.0;
+    int64_t bid = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double v = r[i].P * or_pulse_shape(sn, tb - delay_ns(r[i].R));
+        if (v > best) { second = best; best = v; bid = r[i].id; }
+        else if (v > second) second = v;
+    }
+    *near = second >= 0.0 && best - second <= 1e-4 * best;
+    return bid;
+}
+
+int64_t or_echo_object(const or_scanner* sn, int64_t n, const double* P, const double* R,
+                       const int64_t* id, double tb_ns, int* near) {
+    ret_t* r = (ret_t*)malloc(sizeof(ret_t) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        r[i].R = R[i];
+        r[i].P = P[i];
+        r[i].id = id[i];
+        r[i].s = 0;
+    }
+    int64_t b = echo_object_list(sn, r, n, tb_ns, near);
+    free(r);
+    return b;
+}
+
 static void simulate_pulse(job_t* J, int64_t row) {
     const or_scanner* sn = J->sn;
     const or_leg* lg = J->lg;
@@ -1040,50 +1100,35 @@ static void simulate_pulse(job_t* J, int64_t row) {
         for (int b = 0; b < nb; ++b)
             W[b] += RL->r[i].P * or_pulse_shape(sn, (double)(m + b) * dt - tau);
     }
-    /* 6. echoes: 3-bin local maximum at or above threshold * max(W) */
-    double wmax = 0.0;
-    for (int b = 0; b < nb; ++b)
-        if (W[b] > wmax) wmax = W[b];
-    double thr = sn->echo_threshold_rel * wmax;
-    double tol = 1e-4 * wmax;
-    int ne = 0;
-    for (int b = 0; b < nb; ++b) {
-        double c = W[b];
-        double l = b > 0 ? W[b - 1] : 0.0;
-        double r = b + 1 < nb ? W[b + 1] : 0.0;
-        if (c >= thr - tol && (fabs(c - l) <= tol || fabs(c - r) <= tol)) flags |= OR_F_ECHO;
-        int is_max = c > l && c >= r && c >= thr && c > 0.0;
-        if (is_max && fabs(c - thr) <= tol) flags |= OR_F_ECHO;
-        if (!is_max) continue;
-        if (ne >= K) { flags |= OR_F_OVERFLOW; continue; }
+    /* 6. echoes: 3-bin local maxima at or above threshold * max(W), first K by bin */
+    int32_t eb[OR_MAX_ECHOES];
+    int overflow = 0, near = 0;
+    int ne = or_echo_peaks(W, nb, sn->echo_threshold_rel, K, eb, &overflow, &near);
+    if (near) flags |= OR_F_ECHO;
+    if (overflow) flags |= OR_F_OVERFLOW;
+    for (int e = 0; e < ne; ++e) {
+        int b = eb[e];
         double tb = (double)(m + b) * dt;
         double Rc = sn->pulse_shape == 0 ? 0.5 * OR_C * tb * 1e-9
                                          : 0.5 * OR_C * (tb - 2.0 * sn->pulse_length_ns / 1.75) * 1e-9;
         uint64_t w[4];
-        draw(J->seed, lg->leg_id, k, 1, (uint32_t)ne, 0, w);
+        draw(J->seed, lg->leg_id, k, 1, (uint32_t)e, 0, w);
         double u1 = or_uniform24(w[0]), u2 = or_uniform24(w[1]);
         double z = sqrt(-2.0 * log(u1)) * cos(2.0 * OR_PI * u2);
-        /* object: the return with the largest contribution at b (first on ties) */
-        double best = -1.0, second = -1.0;
-        int64_t bid = -1;
-        for (int64_t i = 0; i < RL->n; ++i) {
-            double v = RL->r[i].P * or_pulse_shape(sn, tb - delay_ns(RL->r[i].R));
-            if (v > best) { second = best; best = v; bid = RL->r[i].id; }
-            else if (v > second) second = v;
-        }
-        if (second >= 0.0 && best - second <= 1e-4 * best) flags |= OR_F_OBJ;
-        out->echo_bin[row * K + ne] = b;
-        out->echo_amp[row * K + ne] = c;
-        out->echo_range_clean[row * K + ne] = Rc;
-        out->echo_range[row * K + ne] = Rc + sn->range_noise_sigma_m * z;
-        out->echo_object[row * K + ne] = (int32_t)bid;
+        int tie = 0;
+        int64_t bid = echo_object_list(sn, RL->r, RL->n, tb, &tie);
+        if (tie) flags |= OR_F_OBJ;
+        out->echo_bin[row * K + e] = b;
+        out->echo_amp[row * K + e] = W[b];
+        out->echo_range_clean[row * K + e] = Rc;
+        out->echo_range[row * K + e] = Rc + sn->range_noise_sigma_m * z;
+        out->echo_object[row * K + e] = (int32_t)bid;
         if (out->echo_width && sn->pulse_shape == 0) {
-            int tie = 0;
+            int ftie = 0;
             double sig_b = sn->pulse_fwhm_ns / (2.0 * sqrt(2.0 * log(2.0))) / dt;
-            out->echo_width[row * K + ne] = or_echo_width(W, nb, b, sig_b, &tie) * dt;
-            if (tie) flags |= OR_F_FIT;
+            out->echo_width[row * K + e] = or_echo_width(W, nb, b, sig_b, &ftie) * dt;
+            if (ftie) flags |= OR_F_FIT;
         }
-        ne++;
     }
     out->echo_count[row] = ne;
     out->flags[row] = flags;
@@ -1232,6 +1277,7 @@ int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
             const int32_t* fixed_window, const or_out* out, int n_threads) {
     if (n <= 0) return 0;
+    if (sn->max_echoes < 1 || sn->max_echoes > OR_MAX_ECHOES) return -1;
     job_t proto;
     memset(&proto, 0, sizeof(proto));
     proto.sc = sc; proto.sn = sn; proto.lg = lg; proto.pulses = pulses; proto.n = n;

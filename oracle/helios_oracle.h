@@ -90,6 +90,7 @@ typedef struct {
 } or_out;
 
 #define OR_NO_WINDOW   INT32_MIN
+#define OR_MAX_ECHOES  64         /* largest max_echoes or_scan accepts */
 
 /* parity flags: conditions under which an FP32 result may legitimately differ */
 #define OR_F_EDGE      (1u << 0)  /* a candidate triangle within eps of an edge */
@@ -121,6 +122,18 @@ double or_pulse_shape(const or_scanner* sn, double t_ns);
  * energy (sum of W^2). */
 double or_echo_width(const double* W, int nb, int p, double sigma_b, int* near_tie);
 double or_triangle_power(const or_scanner* sn, double Is, double R, double refl, double cos_inc);
+/* Echoes of one waveform W[0..nb) (Sec. 3.4, local maxima above a threshold):
+ * bin b is an echo when W[b] > W[b-1], W[b] >= W[b+1] (W is 0 outside the
+ * window), W[b] > 0 and W[b] >= thr_rel * max W.  The first K in bin order go
+ * to bins[0..K); *overflow = 1 when there were more; *near = 1 when such a
+ * decision was within 1e-4 max W.  Returns the number written. */
+int or_echo_peaks(const double* W, int nb, double thr_rel, int K, int32_t* bins, int* overflow,
+                  int* near);
+/* Echo object: of n returns (power P, range R, primitive id) in summation
+ * order, the id with the largest contribution P p(tb - 2R/c) at time tb_ns,
+ * the first on equal values; *near = 1 when the two largest are within 1e-4. */
+int64_t or_echo_object(const or_scanner* sn, int64_t n, const double* P, const double* R,
+                       const int64_t* id, double tb_ns, int* near);
 
 or_scene* or_scene_build(const or_scene_in* in);
 void or_scene_free(or_scene* sc);
@@ -142,7 +155,8 @@ int64_t or_trace_returns(const or_scene* sc, const or_scanner* sn, const double 
                          uint32_t* flags);
 
 /* mode 0 stochastic, 1 expected.  fixed_window (nullable) holds the window
- * start per pulse.  n_threads <= 0: all online cores. */
+ * start per pulse.  n_threads <= 0: all online cores.  Returns -1 (nothing
+ * written) when max_echoes is outside 1..OR_MAX_ECHOES. */
 int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
             const int32_t* fixed_window, const or_out* out, int n_threads);

@@ -1065,3 +1065,186 @@ def test_rotating_head_turns_at_the_head_rate_with_the_polygon_in_elevation():
     flat /= np.linalg.norm(flat, axis=1, keepdims=True)
     stepf = np.arccos(np.clip(np.sum(flat[1:] * flat[:-1], axis=1), -1, 1))
     assert np.allclose(stepf, rate / prf, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# echo detection (Sec. 3.4: local maxima of the waveform above a threshold,
+# the threshold 5% of the pulse's largest bin; first K echoes by bin; the
+# echo's object is the return contributing most at the echo bin)
+# --------------------------------------------------------------------------
+
+def _two_peaks(a1, b1, a2, b2, nb=200, sig=6.79):
+    b = np.arange(nb, dtype=np.float64)
+    return a1 * np.exp(-(b - b1) ** 2 / (2 * sig * sig)) + a2 * np.exp(-(b - b2) ** 2 / (2 * sig * sig))
+
+
+def test_echo_threshold_is_five_percent_of_the_waveform_maximum():
+    """A second peak at 4.9% of the largest bin is not an echo, at 5.1% it is;
+    exactly 5% counts (at or above).  Fails a threshold taken against the sum of
+    the bins (about 17x the peak here), the first bin, the first echo, or 50%."""
+    for a2, n in ((0.049, 1), (0.051, 2), (0.05, 2)):
+        bins, ov, _ = oracle.echo_peaks(_two_peaks(1.0, 40, a2, 120))
+        assert list(bins) == [40, 120][:n] and not ov, (a2, bins)
+    # the weak peak first: the threshold is still the maximum's, not the first peak's
+    for a1, n in ((0.049, 1), (0.051, 2)):
+        bins, _, _ = oracle.echo_peaks(_two_peaks(a1, 40, 1.0, 120))
+        assert list(bins) == ([120] if n == 1 else [40, 120]), (a1, bins)
+    # a lower or higher threshold fraction moves the cut
+    bins, _, _ = oracle.echo_peaks(_two_peaks(1.0, 40, 0.3, 120), thr_rel=0.5)
+    assert list(bins) == [40]
+    bins, _, _ = oracle.echo_peaks(_two_peaks(1.0, 40, 0.3, 120), thr_rel=0.29)
+    assert list(bins) == [40, 120]
+
+
+def test_echo_plateau_and_window_edges():
+    """A plateau of equal bins gives one echo, on its leftmost bin (strictly
+    above the left neighbour, not below the right one); outside the window the
+    waveform counts as zero, so a falling first bin or a rising last bin is an
+    echo."""
+    W = np.zeros(20)
+    W[5:11] = [0.2, 0.7, 0.7, 0.7, 0.2, 0.0]
+    bins, _, near = oracle.echo_peaks(W)
+    assert list(bins) == [6] and near
+    W = np.zeros(20)
+    W[:3] = [1.0, 0.5, 0.1]
+    W[17:] = [0.1, 0.5, 0.9]
+    assert list(oracle.echo_peaks(W)[0]) == [0, 19]
+    W = np.zeros(20)
+    W[17:] = [0.1, 0.9, 0.9]
+    assert list(oracle.echo_peaks(W)[0]) == [18]
+    # a constant waveform has one echo, at bin 0; an all-zero one has none
+    assert list(oracle.echo_peaks(np.full(20, 0.3))[0]) == [0]
+    assert len(oracle.echo_peaks(np.zeros(20))[0]) == 0
+
+
+def test_echo_list_keeps_the_first_k_by_bin_and_flags_overflow():
+    """Nine separated peaks with K = 8: the first eight by bin are kept even when
+    the ninth is the largest, and the overflow is reported; eight peaks fit."""
+    b = np.arange(200, dtype=np.float64)
+    amps = [0.3, 0.5, 0.4, 0.6, 0.35, 0.45, 0.55, 0.25, 1.0]
+    centres = [10 + 20 * i for i in range(9)]
+    W = sum(a * np.exp(-(b - c) ** 2 / (2 * 3.0 ** 2)) for a, c in zip(amps, centres))
+    bins, ov, _ = oracle.echo_peaks(W, K=8)
+    assert list(bins) == centres[:8] and ov
+    bins, ov, _ = oracle.echo_peaks(W, K=9)
+    assert list(bins) == centres and not ov
+    W8 = sum(a * np.exp(-(b - c) ** 2 / (2 * 3.0 ** 2)) for a, c in zip(amps[:8], centres[:8]))
+    bins, ov, _ = oracle.echo_peaks(W8, K=8)
+    assert list(bins) == centres[:8] and not ov
+
+
+def test_echo_object_is_the_largest_contribution_first_on_ties():
+    """The object of an echo at time tb is the return with the largest
+    P p(tb - 2R/c), not the largest P, the nearest or the last; on exactly
+    equal contributions the first in summation order."""
+    sc = scenes.Scanner()
+    sig = 4.0 / (2 * math.sqrt(2 * math.log(2)))
+    R0 = 30.0
+    tb = 2 * R0 / C_LIGHT * 1e9
+    R_far = R0 + 2 * sig * 1e-9 * C_LIGHT / 2      # two sigma later: p = e^-2
+    # a weaker return on the echo's time beats a stronger one two sigma away
+    bid, near = oracle.echo_object(sc, [1.0, 1.5], [R0, R_far], [11, 22], tb)
+    assert bid == 11 and not near
+    bid, _ = oracle.echo_object(sc, [1.0, 1.5], [R_far, R0], [11, 22], tb)
+    assert bid == 22
+    # equal contributions: the first wins (and the near-tie is reported)
+    bid, near = oracle.echo_object(sc, [1.0, 2.0, 2.0], [R0, R0, R0], [5, 7, 9], tb)
+    assert bid == 7 and near
+    bid, near = oracle.echo_object(sc, [2.0, 2.0, 1.0], [R0, R0, R0], [9, 7, 5], tb)
+    assert bid == 9 and near
+
+
+def _column_scene(dens_top_down, z_top, plate_z=None, plate_refl=0.5, G=0.5):
+    """A 1 x 1 m voxel column under a nadir ray from the origin: voxel j (0 =
+    nearest) spans depths [-z_top + j, -z_top + j + 1), densities given from the
+    top down; optionally a plate at z = plate_z, whose diagonal misses the ray."""
+    d = np.asarray(dens_top_down, np.float32)[::-1].reshape(-1, 1, 1)   # [z][y][x], z up
+    nz = d.shape[0]
+    grid = scenes.VoxelGrid(origin=(-0.5, -0.5, -z_top - nz), cell=1.0, dims=(1, 1, nz),
+                            density=np.ascontiguousarray(d), G=G, leaf_reflectance=0.5)
+    meshes = []
+    if plate_z is not None:
+        # the ray at x = y = 0 lies inside face 0 = (v0, v1, v2), 0.9 m from the diagonal
+        pv = np.array([[-50, -40, plate_z], [60, -40, plate_z], [60, 50, plate_z],
+                       [-50, 50, plate_z]], np.float32)
+        meshes.append(scenes.Mesh(pv, np.array([[0, 1, 2], [0, 2, 3]], np.int32),
+                                  np.full(2, plate_refl, np.float32)))
+    return scenes.Scene(meshes=meshes, grids=[grid])
+
+
+def _nadir_expected(scene, n_bins):
+    sc, leg = _nadir_leg()
+    sc.n_bins = n_bins
+    osc = oracle.OracleScene(scene)
+    return sc, oracle.scan(osc, sc, leg, mode=1, seed=1), osc
+
+
+def test_scene_threshold_voxel_layer_and_plate():
+    """Expected mode, one subray (I_s = I0): a voxel layer (depth 20-21 m,
+    return T(1 - e^{-sigma l}) at its midpoint) and a plate 30 m down (return
+    rho T).  With the radar equation's 1/R^2 the plate's peak is set to 4.9% or
+    5.1% of the layer's, and then the layer's to 4.9% or 5.1% of the plate's."""
+    C0 = 1.0 * 0.1 ** 2 * 0.9 * 1.0 / 4.0          # I0 Dr^2 eta_sys eta_atm / 4
+    Rv, Rp = 20.5, 30.0
+    for ratio, n in ((0.049, 1), (0.051, 2)):
+        # strong layer (T = 1/2), weak plate
+        dens = np.float32(2.0 * math.log(2.0))
+        T = math.exp(-0.5 * float(dens))
+        Pv = C0 * 0.5 * (1 - T) / Rv ** 2
+        rho = ratio * Pv * Rp ** 2 / (C0 * T)
+        sc, r, osc = _nadir_expected(_column_scene([dens], 20.0, plate_z=-30.0, plate_refl=rho), 400)
+        assert r["echo_count"][0] == n, (ratio, r["echo_count"][0])
+        assert r["echo_object"][0, 0] == osc.n_tri + 0          # the layer's voxel
+        if n == 2:
+            assert r["echo_object"][0, 1] == 0                  # the plate's face 0
+        # weak layer, strong plate (rho = 0.5): solve (1-T)/T for the ratio
+        x = ratio * 0.5 * Rv ** 2 / (0.5 * Rp ** 2)
+        dens = np.float32(-2.0 * math.log(1.0 / (1.0 + x)))
+        sc, r, osc = _nadir_expected(_column_scene([dens], 20.0, plate_z=-30.0, plate_refl=0.5), 400)
+        assert r["echo_count"][0] == n, (ratio, r["echo_count"][0])
+        assert r["echo_object"][0, n - 1] == 0
+        dt = sc.bin_ns
+        tb = (r["window_bin"][0] + r["echo_bin"][0, n - 1]) * dt
+        assert abs(tb - 2 * Rp / C_LIGHT * 1e9) <= 0.5 * dt + 1e-9
+
+
+def test_scene_nine_layers_keep_the_nearest_eight():
+    """Nine voxel layers 4 m apart, every one an echo; the nearest is the
+    weakest and the farthest among the strongest.  K = 8 keeps the eight
+    nearest (by bin, not by strength) and flags the overflow."""
+    dens = np.zeros(33, np.float32)
+    dens[0::4] = [0.01, 0.2, 0.2, 0.2, 0.2, 0.2, 0.2, 0.2, 3.0]
+    C0 = 1.0 * 0.1 ** 2 * 0.9 / 4.0
+    T, P, R = 1.0, [], []
+    for j in range(33):
+        a = math.exp(-0.5 * float(dens[j]))
+        if dens[j] > 0:
+            R.append(20.0 + j + 0.5)
+            P.append(C0 * 0.5 * T * (1 - a) / R[-1] ** 2)
+        T *= a
+    P = np.array(P)
+    assert P.min() >= 0.06 * P.max() and np.argmin(P) == 0      # all echoes; the first weakest
+    sc, r, osc = _nadir_expected(_column_scene(dens, 20.0), 1024)
+    assert r["echo_count"][0] == 8 and (r["flags"][0] & oracle.F_OVERFLOW)
+    dt = sc.bin_ns
+    for e in range(8):
+        tb = (r["window_bin"][0] + r["echo_bin"][0, e]) * dt
+        assert abs(tb - 2 * R[e] / C_LIGHT * 1e9) <= 0.5 * dt + 1e-9
+        assert r["echo_object"][0, e] == osc.n_tri + (32 - 4 * e)   # voxel z index from the bottom
+    # eight layers: no overflow
+    dens8 = dens.copy()
+    dens8[32] = 0.0
+    sc, r, _ = _nadir_expected(_column_scene(dens8, 20.0), 1024)
+    assert r["echo_count"][0] == 8 and not (r["flags"][0] & oracle.F_OVERFLOW)
+
+
+def test_scene_echo_object_stronger_of_two_merged_returns():
+    """A voxel layer (20-20.9 m, clipped by a plate at 20.9 m) and the plate
+    form one echo.  With a bright plate behind a thin layer the object is the
+    plate (not the nearest, not the first return); with a dense layer in front
+    of a dark plate it is the voxel (not the last return)."""
+    for dens, refl, want_voxel in ((0.2, 0.9, False), (6.0, 0.1, True)):
+        sc, r, osc = _nadir_expected(
+            _column_scene([np.float32(dens)], 20.0, plate_z=-20.9, plate_refl=refl), 200)
+        assert r["echo_count"][0] == 1
+        assert r["echo_object"][0, 0] == (osc.n_tri + 0 if want_voxel else 0)
