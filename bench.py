@@ -106,18 +106,19 @@ def workload(name, small=False):
     return scenes.batched_legs()
 
 
-def workload_config(w, name):
+def workload_config(w, name, subray_count, world=1):
+    """The workload's description, the same for both arms (each passes its own
+    subray-count function: the library's, or the oracle's for the reference arm)."""
     sc = w.scanners[0]
-    import paper_2101_09154_gb300 as hg
-    S = [hg.subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
-                         else w.scanners[l.scanner_index].beam_sample_quality) for l in w.legs]
+    S = [subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
+                      else w.scanners[l.scanner_index].beam_sample_quality) for l in w.legs]
     return {"workload": w.name, "description": w.note, "pulses": w.n_pulses,
             "subrays_per_pulse": S[0] if len(set(S)) == 1 else "mixed",
             "triangles": int(sum(s.n_triangles for s in w.scenes)),
             "voxels": int(sum(int(np.prod(g.dims)) for s in w.scenes for g in s.grids)),
             "n_bins": sc.n_bins, "legs": len(w.legs),
             "l2": "inputs larger than L2 (BVH + triangles > 129 MB, outputs > 1 GB); no flush",
-            "precision": "fp32 traversal/waveform, fp64 pose and hit range"}
+            "parallelism": f"replicas x{world}"}
 
 
 # --------------------------------------------------------------------------
@@ -276,7 +277,7 @@ def run_ours(args, D):
     ms_max = D.max(ms)
     P = w.n_pulses
     n_launch = len(w.legs) if not persistent else math.ceil(len(w.legs) / 128)
-    S = workload_config(w, args.workload)["subrays_per_pulse"]
+    S = workload_config(w, args.workload, hg.subray_count)["subrays_per_pulse"]
     subrays_total = sum(l.n_pulses * hg.subray_count(l.beam_sample_quality if l.beam_sample_quality >= 0
                                                      else w.scanners[l.scanner_index].beam_sample_quality)
                         for l in w.legs)
@@ -286,8 +287,9 @@ def run_ours(args, D):
            "n_gpus": D.world, "steps": args.steps, "warmup": max(args.warmup, 3),
            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {**workload_config(w, args.workload), "parallelism": f"replicas x{D.world}",
-                      "bvh_build_s": round(build_s, 3)},
+           "config": workload_config(w, args.workload, hg.subray_count, D.world),
+           "bvh_build_s": round(build_s, 3),
+           "precision": "fp32 traversal/waveform, fp64 pose and hit range",
            "subrays_per_s": D.world * subrays_total / (ms_max / 1e3),
            "gpu_launches": n_launch * args.steps,
            "device_status": st,
@@ -301,7 +303,12 @@ def run_ours(args, D):
     kern = "hg::scan_kernel<0,%d,%d>" % (gk, 128 if persistent else 1)
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                       "algorithmic_bytes_per_launch": alg, "peak_source": kind, "kernel": kern}
+                       "algorithmic_bytes_per_launch": alg, "peak_source": kind, "kernel": kern,
+                       "bytes_model": "compulsory: every output byte written once (waveform 4*N_b, "
+                                      "window, count, flags, K echoes x 16 B per pulse) plus every "
+                                      "scene byte read once (64 B per BVH node, 52 B per triangle, "
+                                      "4 B per voxel); per-subray node/triangle/voxel visit counts "
+                                      "are not counted (no counting kernel variant)"}
     res["clocks"] = clocks
     if not args.no_extras:
         res["e2e"] = e2e(w, gsc, layout, out, args, stream, D)
@@ -542,6 +549,7 @@ def oracle_rate(w, target_s, pulses_cap=None, one_core=False):
     dt = time.time() - t0
     q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else sc.beam_sample_quality
     res = {"value": len(rows) / dt, "unit": "pulses/s", "cores": cores, "kind": "oracle",
+           "elapsed_s": dt, "sample_pulses": int(len(rows)),
            "sample": f"{len(rows)} evenly spaced pulses of the {leg.n_pulses}-pulse leg "
                      f"({oracle.subray_count(q)} subrays each), {dt:.1f} s of FP64 CPU work "
                      f"on {cores} threads"}
@@ -561,21 +569,27 @@ def run_reference(args, D):
     w = workload(args.workload, args.small)
     import oracle
     oracle.build()
-    rates = []
+    # each step: one bounded, evenly strided sample of the leg's pulses (about
+    # cpu_sample_s / steps seconds of FP64 work), timed on the wall clock
+    n_done, t_done, step_ms = 0, 0.0, []
     per_step_target = max(1.0, args.cpu_sample_s / max(args.steps, 1))
     info = None
     for i in range(args.warmup + args.steps):
         r = oracle_rate(w, per_step_target)
         if i >= args.warmup:
-            rates.append(r["value"])
+            n_done += r["sample_pulses"]
+            t_done += r["elapsed_s"]
+            step_ms.append(1e3 * r["elapsed_s"])
             info = r
-    value = float(np.mean(rates))
+    value = n_done / t_done
     return {"impl": "reference", "metric": "pulses/s (19 subrays, waveform on)", "value": value,
             "unit": "pulses/s", "n_gpus": D.world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w.n_pulses / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args.workload),
-            "cpu_baseline": {**info, "value": value},
+            "config": workload_config(w, args.workload, oracle.subray_count, D.world),
+            "step_pulses": n_done // max(args.steps, 1),
+            "cpu_baseline": {**info, "value": value,
+                             "sample": f"per step: {info['sample']}"},
             "e2e": {"value": value, "unit": "pulses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
 
