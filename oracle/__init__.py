@@ -26,7 +26,9 @@ _lib = None
 
 NO_WINDOW = -(2 ** 31)
 F_EDGE, F_TIE, F_VOX, F_WIN, F_ECHO, F_OBJ = 1, 2, 4, 8, 16, 32
-F_OVERFLOW, F_NOHIT, F_FIT = 256, 512, 1024
+F_OVERFLOW, F_NOHIT, F_FIT, F_FORCED_BAD = 256, 512, 1024, 2048
+F_SUBRAY = F_EDGE | F_TIE | F_VOX                  # a subray's hit id / range may differ
+FREE_HIT = -2                                       # force_hit entry: the oracle decides
 F_GEOMETRY = F_EDGE | F_TIE | F_VOX | F_WIN        # waveform may differ
 F_DECISION = F_GEOMETRY | F_ECHO | F_OBJ           # echo lists may differ
 
@@ -82,7 +84,7 @@ class Out(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("window_bin", "waveform", "echo_count", "echo_bin",
                                             "echo_amp", "echo_range", "echo_range_clean",
                                             "echo_object", "echo_width", "subray_hit", "subray_range",
-                                            "flags")]
+                                            "flags", "subray_flags", "echo_object_alt")]
 
 
 def lib():
@@ -134,7 +136,8 @@ def lib():
                                            C.POINTER(C.c_uint32)]
             l.or_trace_returns.restype = C.c_int64
             l.or_scan.argtypes = [C.c_void_p, C.POINTER(Scanner), C.POINTER(Leg), C.c_void_p,
-                                  C.c_int64, C.c_int, C.c_uint64, C.c_void_p, C.POINTER(Out), C.c_int]
+                                  C.c_int64, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p,
+                                  C.POINTER(Out), C.c_int]
             l.or_adjoint.argtypes = [C.c_void_p, C.POINTER(Scanner), C.POINTER(Leg), C.c_void_p,
                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
             _lib = l
@@ -390,9 +393,15 @@ def echo_object(scanner, P, R, ids, tb_ns):
 
 
 def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_window=None,
-         threads=0, echo_width=False):
+         threads=0, echo_width=False, force_hit=None):
     """Simulate the given pulse indices of one leg; returns a dict of numpy arrays
-    (with ``echo_width``, the fitted echo widths in ns, Gaussian pulses only)."""
+    (with ``echo_width``, the fitted echo widths in ns, Gaussian pulses only).
+
+    ``force_hit`` ([n, S] int32, FREE_HIT where the oracle decides) gives
+    subray events chosen elsewhere (an FP32 path's choices on flagged subrays);
+    ``subray_flags`` in the result holds the flags each subray raised, and
+    ``rerun(rows, force_hit, fixed_window)`` repeats the scan for a subset of
+    the rows with the same scene, scanner, leg, mode and seed."""
     if pulses is None:
         pulses = np.arange(leg.n_pulses, dtype=np.int64)
     pulses = np.ascontiguousarray(pulses, dtype=np.int64)
@@ -405,20 +414,32 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
              echo_amp=np.zeros((n, K)), echo_range=np.zeros((n, K)),
              echo_range_clean=np.zeros((n, K)), echo_object=np.zeros((n, K), np.int32),
              subray_hit=np.zeros((n, S), np.int32), subray_range=np.zeros((n, S)),
-             flags=np.zeros(n, np.uint32))
+             flags=np.zeros(n, np.uint32), subray_flags=np.zeros((n, S), np.uint32),
+             echo_object_alt=np.zeros((n, K), np.int32))
     if echo_width:
         r["echo_width"] = np.zeros((n, K))
     out = Out(**{k: _ptr(v) for k, v in r.items()})
-    fw = None
+    fw = fh = None
     if fixed_window is not None:
         fw = np.ascontiguousarray(fixed_window, dtype=np.int32)
+        assert fw.shape == (n,)
+    if force_hit is not None:
+        fh = np.ascontiguousarray(force_hit, dtype=np.int32)
+        assert fh.shape == (n, S)
     s, l = scanner_struct(scanner), leg_struct(leg)
     rc = lib().or_scan(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), n, int(mode),
-                       int(seed) & (2 ** 64 - 1), _ptr(fw), C.byref(out), int(threads))
+                       int(seed) & (2 ** 64 - 1), _ptr(fw), _ptr(fh), C.byref(out), int(threads))
     if rc != 0:
         raise ValueError("oracle scan rejected the scanner (max_echoes outside 1..64)")
     r["pulses"] = pulses
     r["S"] = S
+    r["thr_rel"] = float(scanner.echo_threshold_rel)
+
+    def rerun(rows, force_hit=None, fixed_window=None):
+        return scan(oscene, scanner, leg, pulses[np.asarray(rows, np.int64)], mode=mode, seed=seed,
+                    fixed_window=fixed_window, threads=threads, echo_width=echo_width,
+                    force_hit=force_hit)
+    r["rerun"] = rerun
     return r
 
 

@@ -487,8 +487,11 @@ static int box_enter(const double lo[3], const double hi[3], double eps, const d
 
 typedef struct { double t, smin; int64_t id; } cand_t;
 
-int64_t or_intersect(const or_scene* sc, const double o[3], const double d[3],
-                     double* t_hit, double* cos_hit, uint32_t* flags) {
+/* clear_only = 0: the closest hit (edge points count as inside) with parity
+ * flags; clear_only = 1: the closest hit whose point is at least eps inside
+ * its triangle (no FP32 evaluation could miss it). */
+static int64_t intersect_impl(const or_scene* sc, const double o[3], const double d[3],
+                              int clear_only, double* t_hit, double* cos_hit, uint32_t* flags) {
     *t_hit = INFINITY;
     *cos_hit = 0.0;
     if (sc->n_tri == 0) return -1;
@@ -514,7 +517,7 @@ int64_t or_intersect(const or_scene* sc, const double o[3], const double d[3],
                 if (smin < -e) continue;
                 if (nc < 64) cands[nc++] = (cand_t){t, smin, id};
                 else overflow = 1;
-                if (smin >= 0.0 && (t < best_t || (t == best_t && id < best))) {
+                if (smin >= (clear_only ? e : 0.0) && (t < best_t || (t == best_t && id < best))) {
                     best_t = t; best = id; best_cos = c; best_s = smin;
                 }
             }
@@ -539,6 +542,11 @@ int64_t or_intersect(const or_scene* sc, const double o[3], const double d[3],
     *t_hit = best_t;
     *cos_hit = best_cos;
     return best;
+}
+
+int64_t or_intersect(const or_scene* sc, const double o[3], const double d[3],
+                     double* t_hit, double* cos_hit, uint32_t* flags) {
+    return intersect_impl(sc, o, d, 0, t_hit, cos_hit, flags);
 }
 
 int64_t or_intersect_brute(const or_scene* sc, const double o[3], const double d[3],
@@ -569,6 +577,7 @@ typedef struct {
     int64_t alt_vid; /* the voxel an FP32 march could visit instead at that corner */
     int axis;        /* axis of the face the ray entered through, -1: started inside */
     int gi;          /* grid */
+    int alt_axis;    /* corner: the axis whose plane is crossed within eps of the exit */
 } vseg;
 
 typedef struct { vseg* v; int64_t n, cap; } vlist;
@@ -668,7 +677,7 @@ static void march_grid(const or_scene* sc, int gi, const double o[3], const doub
         double t_out = tn[a] < t_end ? tn[a] : t_end;
         int64_t vid = (idx[2] * ny + idx[1]) * nx + idx[0];
         if (t_out > t_in) {
-            vseg s = {vid, t_in, t_out, G * (double)g->dens[vid], 0, -1, entry, gi};
+            vseg s = {vid, t_in, t_out, G * (double)g->dens[vid], 0, -1, entry, gi, -1};
             /* second-smallest crossing near the exit: order ambiguous in FP32 */
             for (int b = 0; b < 3; ++b) {
                 if (b == a || step[b] == 0) continue;
@@ -678,6 +687,7 @@ static void march_grid(const or_scene* sc, int gi, const double o[3], const doub
                     if (j[b] >= 0 && j[b] < g->gd[b]) {
                         s.corner = 1;
                         s.alt_vid = (j[2] * ny + j[1]) * nx + j[0];
+                        s.alt_axis = b;
                     }
                 }
             }
@@ -792,12 +802,57 @@ typedef struct {
     int mode;
     uint64_t seed;
     const int32_t* fixed_window;
+    const int32_t* force_hit; /* [n][S] or NULL: events given per subray (OR_FREE_HIT: none) */
     const or_out* out;
     const double* g;      /* adjoint only */
     int adjoint;
     int64_t begin, end;
     scratch_t S;
 } job_t;
+
+/* expected (differentiable) mode, over the voxels marched into J->S.vl: voxel
+ * k returns w_k = T_k (1 - e^{-sigma_k l_k}) at its segment midpoint, the
+ * triangle tri (if any) returns the transmitted T. */
+static void expected_returns(job_t* J, int s, const double ds[3], double alpha, int64_t tri,
+                             double t_tri, double cos_tri, int64_t* ev_id, double* ev_R) {
+    const or_scene* sc = J->sc;
+    const or_scanner* sn = J->sn;
+    vlist* L = &J->S.vl;
+    double T = 1.0;
+    for (int64_t i = 0; i < L->n; ++i) {
+        vseg* v = &L->v[i];
+        const struct or_grid* g = &sc->grid[v->gi];
+        if (v->sigma <= 0.0) continue;
+        if (g->opaque) {
+            /* an opaque voxel returns all that reaches it and passes nothing;
+             * the subray record keeps the triangle hit, as in every expected-mode
+             * scan (it is the adjoint's checkpoint) */
+            double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
+            double Is = or_subray_intensity(sn, R, alpha);
+            ret_t r = {R, T * or_triangle_power(sn, Is, R, g->leaf_refl, c), vox_id(sc, v, v->vid), s};
+            rpush(&J->S.rl, r);
+            if (tri >= 0) {
+                *ev_id = tri;
+                *ev_R = t_tri;
+            }
+            return;
+        }
+        double len = v->t_out - v->t_in;
+        double a = exp(-v->sigma * len);
+        double R = 0.5 * (v->t_in + v->t_out);
+        double Is = or_subray_intensity(sn, R, alpha);
+        ret_t r = {R, T * (1.0 - a) * voxel_power(sn, g, Is, R), vox_id(sc, v, v->vid), s};
+        rpush(&J->S.rl, r);
+        T *= a;
+    }
+    if (tri >= 0) {
+        double Is = or_subray_intensity(sn, t_tri, alpha);
+        ret_t r = {t_tri, T * or_triangle_power(sn, Is, t_tri, (double)sc->refl[tri], cos_tri), tri, s};
+        rpush(&J->S.rl, r);
+        *ev_id = tri;
+        *ev_R = t_tri;
+    }
+}
 
 /* one subray: fill the return list (stochastic: <= 1 return; expected: voxels
  * then triangle).  Returns the primitive of the event and its range. */
@@ -870,38 +925,189 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
         }
         return;
     }
-    /* expected (differentiable) mode: voxel k returns w_k = T_k (1 - e^{-sigma_k l_k})
-     * at its segment midpoint, the triangle returns the transmitted T. */
-    double T = 1.0;
+    expected_returns(J, s, ds, alpha, tri, t_tri, cos_tri, ev_id, ev_R);
+}
+
+/* 1 when the ray meets, at some 0 < t <= t_max, an edge shared by two
+ * triangles (the same two vertex positions) within eps of that edge in both:
+ * a watertight triangle test hits one of the two there, so no FP32 path may
+ * pass between them. */
+static int closed_edge_before(const or_scene* sc, const double o[3], const double d[3],
+                              double t_max) {
+    if (sc->n_tri == 0 || !(t_max > 0.0)) return 0;
+    int64_t stack[256];
+    int sp = 0;
+    int64_t near_id[64];
+    int near_k[64];
+    int nn = 0;
+    stack[sp++] = 0;
+    while (sp > 0 && nn < 64) {
+        const bnode* nd = &sc->nodes[stack[--sp]];
+        double te;
+        double bound = isinf(t_max) ? INFINITY : t_max + eps_rel(t_max) + sc->eps_box;
+        if (!box_enter(nd->lo, nd->hi, sc->eps_box, o, d, bound, &te)) continue;
+        if (nd->left < 0) {
+            for (int64_t i = nd->start; i < nd->start + nd->count && nn < 64; ++i) {
+                int64_t id = sc->order[i];
+                const double* v = &sc->tv[9 * id];
+                double t, smin, c;
+                if (!tri_eval(v, o, d, &t, &smin, &c) || t > t_max) continue;
+                if (fabs(smin) >= eps_rel(t)) continue;
+                /* the edge the point is nearest to */
+                double e1[3], e2[3], n[3], p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                sub3(&v[3], &v[0], e1);
+                sub3(&v[6], &v[0], e2);
+                cross3(e1, e2, n);
+                double nrm = norm3(n), best = DBL_MAX;
+                int kb = 0;
+                for (int k = 0; k < 3; ++k) {
+                    const double* a = &v[3 * k];
+                    const double* b = &v[3 * ((k + 1) % 3)];
+                    double ab[3], ap[3], cr[3];
+                    sub3(b, a, ab);
+                    sub3(p, a, ap);
+                    cross3(ab, ap, cr);
+                    double sk = dot3(cr, n) / (nrm * norm3(ab));
+                    if (sk < best) { best = sk; kb = k; }
+                }
+                near_id[nn] = id;
+                near_k[nn] = kb;
+                nn++;
+            }
+        } else if (sp + 2 <= 256) {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+    for (int i = 0; i < nn; ++i) {
+        const double* a0 = &sc->tv[9 * near_id[i] + 3 * near_k[i]];
+        const double* a1 = &sc->tv[9 * near_id[i] + 3 * ((near_k[i] + 1) % 3)];
+        for (int j = i + 1; j < nn; ++j) {
+            const double* b0 = &sc->tv[9 * near_id[j] + 3 * near_k[j]];
+            const double* b1 = &sc->tv[9 * near_id[j] + 3 * ((near_k[j] + 1) % 3)];
+            int same = (memcmp(a0, b0, 24) == 0 && memcmp(a1, b1, 24) == 0) ||
+                       (memcmp(a0, b1, 24) == 0 && memcmp(a1, b0, 24) == 0);
+            if (same) return 1;
+        }
+    }
+    return 0;
+}
+
+/* Parity support: one subray re-run with its event given.  An FP32 path may
+ * legitimately decide differently where the oracle raised a flag (a hit within
+ * eps of an edge, near-equal hits, a transmission draw within rounding of the
+ * segment length, a voxel corner).  `forced` is the event it reported: a
+ * triangle id, n_tri + voxel (stochastic mode: the voxel it stopped in), or -1
+ * (no event).  The subray's returns are formed from that event with the
+ * oracle's arithmetic.  OR_F_FORCED_BAD is raised when no flagged decision
+ * allows the event: a triangle the ray misses by more than eps, an event
+ * behind a hit no FP32 evaluation could miss or behind an edge shared by two
+ * triangles (a watertight test hits one of them), or a voxel passed although
+ * its draw stops the subray clearly inside it. */
+static void trace_subray_forced(job_t* J, int64_t k, int s, const double o[3], const double ds[3],
+                                double alpha, int64_t forced, uint32_t* flags, int64_t* ev_id,
+                                double* ev_R) {
+    const or_scene* sc = J->sc;
+    const or_scanner* sn = J->sn;
+    double t_clear, cos_clear;
+    intersect_impl(sc, o, ds, 1, &t_clear, &cos_clear, NULL);
+    const double lim = isinf(t_clear) ? INFINITY : t_clear + eps_rel(t_clear);
+    int64_t tri = -1, fvox = -1;
+    double t_tri = INFINITY, cos_tri = 0.0;
+    *ev_id = -1;
+    *ev_R = 0.0;
+    if (forced >= 0 && forced < sc->n_tri) {
+        double smin;
+        tri = forced;
+        if (!tri_eval(&sc->tv[9 * forced], o, ds, &t_tri, &smin, &cos_tri) ||
+            smin < -eps_rel(t_tri) || t_tri > lim ||
+            closed_edge_before(sc, o, ds, t_tri - eps_rel(t_tri))) {
+            *flags |= OR_F_FORCED_BAD;
+            return;
+        }
+    } else if (forced >= sc->n_tri) {
+        fvox = forced - sc->n_tri;
+        if (J->mode != 0) { *flags |= OR_F_FORCED_BAD; return; }
+    } else if (!isinf(t_clear) || closed_edge_before(sc, o, ds, INFINITY)) {
+        *flags |= OR_F_FORCED_BAD;
+        return;
+    }
+    march(sc, o, ds, tri >= 0 ? t_tri : t_clear, &J->S.vl);
+    vlist* L = &J->S.vl;
+    if (J->mode != 0) {
+        expected_returns(J, s, ds, alpha, tri, t_tri, cos_tri, ev_id, ev_R);
+        return;
+    }
     for (int64_t i = 0; i < L->n; ++i) {
         vseg* v = &L->v[i];
         const struct or_grid* g = &sc->grid[v->gi];
-        if (v->sigma <= 0.0) continue;
+        int alt = v->corner && v->alt_vid >= 0;
+        int hit_main = fvox >= 0 && vox_draw(sc, v, v->vid) == fvox;
+        int hit_alt = fvox >= 0 && alt && vox_draw(sc, v, v->alt_vid) == fvox;
         if (g->opaque) {
-            /* an opaque voxel returns all that reaches it and passes nothing;
-             * the subray record keeps the triangle hit, as in every expected-mode
-             * scan (it is the adjoint's checkpoint) */
-            double R = v->t_in, c = v->axis >= 0 ? fabs(ds[v->axis]) : 1.0;
-            double Is = or_subray_intensity(sn, R, alpha);
-            ret_t r = {R, T * or_triangle_power(sn, Is, R, g->leaf_refl, c), vox_id(sc, v, v->vid), s};
-            rpush(&J->S.rl, r);
-            if (tri >= 0) {
-                *ev_id = tri;
-                *ev_R = t_tri;
+            if (hit_main || hit_alt) {
+                double R = hit_main ? v->t_in : v->t_out;
+                /* the corner voxel is entered through the face crossed within eps of this exit */
+                double c = hit_main ? (v->axis >= 0 ? fabs(ds[v->axis]) : 1.0) : fabs(ds[v->alt_axis]);
+                double Is = or_subray_intensity(sn, R, alpha);
+                ret_t r = {R, or_triangle_power(sn, Is, R, g->leaf_refl, c), sc->n_tri + fvox, s};
+                if (hit_main && v->sigma <= 0.0) *flags |= OR_F_FORCED_BAD;
+                if (closed_edge_before(sc, o, ds, R - eps_rel(R))) *flags |= OR_F_FORCED_BAD;
+                rpush(&J->S.rl, r);
+                *ev_id = r.id;
+                *ev_R = R;
+                return;
             }
+            if (v->sigma > 0.0 && !(alt && g->dens[v->alt_vid] <= 0.0f)) {
+                *flags |= OR_F_FORCED_BAD;
+                return;
+            }
+            continue;
+        }
+        if (hit_main || hit_alt) {
+            int64_t vv = hit_main ? v->vid : v->alt_vid;
+            double sg = proj_factor(g, ds) * (double)g->dens[vv];
+            uint64_t w[4];
+            draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, vv), w);
+            double sdist = sg > 0.0 ? -log(or_uniform24(w[0])) / sg : INFINITY;
+            double len = v->t_out - v->t_in;
+            double R;
+            if (hit_main) {
+                if (!(sdist <= len + 1e-6 * sdist + 1e-12 ||
+                      (len < eps_rel(v->t_in) && sdist <= len + eps_rel(v->t_in))))
+                    *flags |= OR_F_FORCED_BAD;
+                R = v->t_in + (sdist < len ? sdist : len);
+            } else {
+                if (!(sdist <= 2.0 * eps_rel(v->t_out))) *flags |= OR_F_FORCED_BAD;
+                R = v->t_out;
+            }
+            if (closed_edge_before(sc, o, ds, R - eps_rel(R))) *flags |= OR_F_FORCED_BAD;
+            double Is = or_subray_intensity(sn, R, alpha);
+            ret_t r = {R, voxel_power(sn, g, Is, R), sc->n_tri + fvox, s};
+            rpush(&J->S.rl, r);
+            *ev_id = r.id;
+            *ev_R = R;
             return;
         }
+        if (v->sigma <= 0.0) continue;
+        uint64_t w[4];
+        draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->vid), w);
+        double sdist = -log(or_uniform24(w[0])) / v->sigma;
         double len = v->t_out - v->t_in;
-        double a = exp(-v->sigma * len);
-        double R = 0.5 * (v->t_in + v->t_out);
-        double Is = or_subray_intensity(sn, R, alpha);
-        ret_t r = {R, T * (1.0 - a) * voxel_power(sn, g, Is, R), vox_id(sc, v, v->vid), s};
-        rpush(&J->S.rl, r);
-        T *= a;
+        int near = fabs(sdist - len) <= 1e-6 * sdist + 1e-12 ||
+                   (len < eps_rel(v->t_in) && sdist <= len + eps_rel(v->t_in));
+        if (sdist < len && !near) {
+            *flags |= OR_F_FORCED_BAD;
+            return;
+        }
+    }
+    if (fvox >= 0) {
+        *flags |= OR_F_FORCED_BAD;
+        return;
     }
     if (tri >= 0) {
         double Is = or_subray_intensity(sn, t_tri, alpha);
-        ret_t r = {t_tri, T * or_triangle_power(sn, Is, t_tri, (double)sc->refl[tri], cos_tri), tri, s};
+        ret_t r = {t_tri, or_triangle_power(sn, Is, t_tri, (double)sc->refl[tri], cos_tri), tri, s};
         rpush(&J->S.rl, r);
         *ev_id = tri;
         *ev_R = t_tri;
@@ -1001,15 +1207,16 @@ int or_echo_peaks(const double* W, int nb, double thr_rel, int K, int32_t* bins,
  * time tb; on equal contributions the first in summation order (subray order,
  * then along the subray).  *near: the two largest within 1e-4 relative. */
 static int64_t echo_object_list(const or_scanner* sn, const ret_t* r, int64_t n, double tb,
-                                int* near) {
+                                int* near, int64_t* second_id) {
     double best = -1.0, second = -1.0;
-    int64_t bid = -1;
+    int64_t bid = -1, sid = -1;
     for (int64_t i = 0; i < n; ++i) {
         double v = r[i].P * or_pulse_shape(sn, tb - delay_ns(r[i].R));
-        if (v > best) { second = best; best = v; bid = r[i].id; }
-        else if (v > second) second = v;
+        if (v > best) { second = best; sid = bid; best = v; bid = r[i].id; }
+        else if (v > second) { second = v; sid = r[i].id; }
     }
     *near = second >= 0.0 && best - second <= 1e-4 * best;
+    if (second_id) *second_id = *near ? sid : -1;
     return bid;
 }
 
@@ -1022,7 +1229,7 @@ int64_t or_echo_object(const or_scanner* sn, int64_t n, const double* P, const d
         r[i].id = id[i];
         r[i].s = 0;
     }
-    int64_t b = echo_object_list(sn, r, n, tb_ns, near);
+    int64_t b = echo_object_list(sn, r, n, tb_ns, near, NULL);
     free(r);
     return b;
 }
@@ -1057,7 +1264,12 @@ static void simulate_pulse(job_t* J, int64_t row) {
         or_subray_dir(sn, q, s, d, ds);
         int64_t ev;
         double R;
-        trace_subray(J, k, s, o, ds, alpha, &flags, &ev, &R);
+        uint32_t sf = 0;
+        int32_t fh = J->force_hit ? J->force_hit[row * S + s] : OR_FREE_HIT;
+        if (fh != OR_FREE_HIT) trace_subray_forced(J, k, s, o, ds, alpha, fh, &sf, &ev, &R);
+        else trace_subray(J, k, s, o, ds, alpha, &sf, &ev, &R);
+        flags |= sf;
+        if (out->subray_flags) out->subray_flags[row * S + s] = sf;
         if (out->subray_hit) out->subray_hit[row * S + s] = (int32_t)ev;
         if (out->subray_range) out->subray_range[row * S + s] = R;
     }
@@ -1071,6 +1283,7 @@ static void simulate_pulse(job_t* J, int64_t row) {
         out->echo_range[row * K + e] = 0.0;
         out->echo_range_clean[row * K + e] = 0.0;
         out->echo_object[row * K + e] = -1;
+        if (out->echo_object_alt) out->echo_object_alt[row * K + e] = -1;
         if (out->echo_width) out->echo_width[row * K + e] = 0.0;
     }
     if (RL->n == 0) {
@@ -1116,8 +1329,10 @@ static void simulate_pulse(job_t* J, int64_t row) {
         double u1 = or_uniform24(w[0]), u2 = or_uniform24(w[1]);
         double z = sqrt(-2.0 * log(u1)) * cos(2.0 * OR_PI * u2);
         int tie = 0;
-        int64_t bid = echo_object_list(sn, RL->r, RL->n, tb, &tie);
+        int64_t sid = -1;
+        int64_t bid = echo_object_list(sn, RL->r, RL->n, tb, &tie, &sid);
         if (tie) flags |= OR_F_OBJ;
+        if (out->echo_object_alt) out->echo_object_alt[row * K + e] = (int32_t)sid;
         out->echo_bin[row * K + e] = b;
         out->echo_amp[row * K + e] = W[b];
         out->echo_range_clean[row * K + e] = Rc;
@@ -1275,13 +1490,15 @@ static void free_jobs(job_t* jobs, int nt) {
 
 int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
-            const int32_t* fixed_window, const or_out* out, int n_threads) {
+            const int32_t* fixed_window, const int32_t* force_hit, const or_out* out,
+            int n_threads) {
     if (n <= 0) return 0;
     if (sn->max_echoes < 1 || sn->max_echoes > OR_MAX_ECHOES) return -1;
     job_t proto;
     memset(&proto, 0, sizeof(proto));
     proto.sc = sc; proto.sn = sn; proto.lg = lg; proto.pulses = pulses; proto.n = n;
     proto.mode = mode; proto.seed = seed; proto.fixed_window = fixed_window; proto.out = out;
+    proto.force_hit = force_hit;
     job_t* jobs;
     int nt;
     run_jobs(&proto, n, n_threads, &jobs, &nt);

@@ -87,6 +87,9 @@ typedef struct {
     int32_t* subray_hit;         /* [n][S]     event primitive, -1 none */
     double* subray_range;        /* [n][S] */
     uint32_t* flags;             /* [n]        OR_F_* */
+    uint32_t* subray_flags;      /* [n][S]     OR_F_* raised by each subray, or NULL */
+    int32_t* echo_object_alt;    /* [n][K]     the runner-up object when within 1e-4 of the
+                                    echo object's contribution (OR_F_OBJ), else -1; or NULL */
 } or_out;
 
 #define OR_NO_WINDOW   INT32_MIN
@@ -102,6 +105,9 @@ typedef struct {
 #define OR_F_OVERFLOW  (1u << 8)  /* more echoes than max_echoes */
 #define OR_F_NOHIT     (1u << 9)  /* no subray returned */
 #define OR_F_FIT       (1u << 10) /* an echo-width fit step decided within tolerance */
+#define OR_F_FORCED_BAD (1u << 11) /* a given subray event that no flagged decision allows */
+
+#define OR_FREE_HIT    (-2)       /* force_hit entry: the oracle decides the event */
 
 void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 double or_uniform24(uint64_t w);
@@ -155,11 +161,17 @@ int64_t or_trace_returns(const or_scene* sc, const or_scanner* sn, const double 
                          uint32_t* flags);
 
 /* mode 0 stochastic, 1 expected.  fixed_window (nullable) holds the window
- * start per pulse.  n_threads <= 0: all online cores.  Returns -1 (nothing
+ * start per pulse.  force_hit (nullable, [n][S]) gives a subray's event in
+ * place of the oracle's search where it is not OR_FREE_HIT: a triangle id,
+ * n_tri + voxel (stochastic mode: the voxel the subray stopped in) or -1 (no
+ * event); this re-runs a pulse with the choices an FP32 path made on subrays
+ * the oracle flagged, and OR_F_FORCED_BAD marks a choice that no flagged
+ * decision allows.  n_threads <= 0: all online cores.  Returns -1 (nothing
  * written) when max_echoes is outside 1..OR_MAX_ECHOES. */
 int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
-            const int32_t* fixed_window, const or_out* out, int n_threads);
+            const int32_t* fixed_window, const int32_t* force_hit, const or_out* out,
+            int n_threads);
 
 /* adjoint of the expected-mode waveform: g = dL/dW [n][n_bins], window held
  * fixed.  Accumulates into d_refl [n_tri] and d_density [nz*ny*nx]. */

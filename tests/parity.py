@@ -1,11 +1,15 @@
 """Comparison helpers: CUDA outputs vs the FP64 oracle on the same seeded inputs.
 
 Tolerances (stated once, used by every GPU parity test):
-  * integers (window start, hit / echo / object ids, echo counts): exact, on
-    pulses the oracle does not flag (flags mark rays within 1e-6 R of a triangle
-    edge, near-equal hits, transmission draws within rounding of the segment
-    length, window starts within 1e-6 of a bin boundary, echo decisions within
-    the waveform tolerance);
+  * integers (window start, hit / echo / object ids, echo counts): exact.  A
+    subray the oracle flags (within 1e-6 R of a triangle edge, near-equal hits,
+    a transmission draw within rounding of the segment length, a voxel corner)
+    is left out of the hit-id and range comparison alone; its pulse is re-run
+    in the oracle with the GPU's event on that subray (which the oracle checks
+    is one a flagged decision allows) and then compared in full.  A window
+    start within 1e-6 of a bin boundary takes the GPU's value.  Echo decisions
+    within the waveform tolerance are checked on the GPU's own waveform with
+    the oracle's detector;
   * ranges: |dR| <= 1e-4 m;
   * waveform samples: |dW| <= 1e-4 |W| + 1e-7 max_b |W| per pulse (FP32 samples
     underflow or are cut where the pulse shape is below 2^-30 of its peak,
@@ -25,47 +29,109 @@ def to_np(t):
 
 
 def leg_view(out, lay, l, scanner, S, rows):
-    """Slice the concatenated outputs of leg l at the given pulse rows."""
+    """Slice the concatenated outputs of leg l at the given pulse rows (gathered
+    on the device, so only the sampled rows are copied to the host)."""
+    import torch
     po = int(lay["pulse_offset"][l])
     wo = int(lay["wave_offset"][l])
     so = int(lay["subray_offset"][l])
     eo = int(lay["echo_offset"][l])
     nb, K = scanner.n_bins, scanner.max_echoes
     rows = np.asarray(rows, np.int64)
-    v = {}
-    v["window_bin"] = to_np(out["window_bin"])[po + rows]
-    v["echo_count"] = to_np(out["echo_count"])[po + rows]
-    W = to_np(out["waveform"])
-    v["waveform"] = W[wo + rows[:, None] * nb + np.arange(nb)[None, :]]
+
+    def take(t, base, width):
+        dev = t.device
+        r = torch.as_tensor(rows, device=dev)
+        if width is None:
+            return to_np(t[base + r])
+        idx = base + r[:, None] * width + torch.arange(width, device=dev)[None, :]
+        return to_np(t[idx])
+
+    v = {"window_bin": take(out["window_bin"], po, None),
+         "echo_count": take(out["echo_count"], po, None),
+         "waveform": take(out["waveform"], wo, nb)}
     for k in ("echo_range", "echo_amp", "echo_bin", "echo_object"):
-        a = to_np(out[k])
-        v[k] = a[eo + rows[:, None] * K + np.arange(K)[None, :]]
+        v[k] = take(out[k], eo, K)
     if "subray_hit" in out:
         for k in ("subray_hit", "subray_range"):
-            a = to_np(out[k])
-            v[k] = a[so + rows[:, None] * S + np.arange(S)[None, :]]
-    v["pulse_flags"] = to_np(out["pulse_flags"])[po + rows]
+            v[k] = take(out[k], so, S)
+    v["pulse_flags"] = take(out["pulse_flags"], po, None)
     return v
 
 
-def compare(g, ref, max_flag_frac=0.2, check_subrays=True, expected_mode=False):
-    """Assert parity of one leg's GPU view `g` against oracle result `ref`."""
+def _rerun_flagged(g, ref):
+    """Re-run, in the oracle, every pulse on which a subray is flagged (or whose
+    window start is within 1e-6 of a bin boundary) with the GPU's event on each
+    flagged subray; returns the oracle result with those rows replaced and the
+    number of rows re-run.  Without the GPU's subray events (or a re-run
+    helper) the result is returned unchanged."""
     f = ref["flags"]
-    geo = (f & oracle.F_GEOMETRY) == 0
-    dec = (f & (oracle.F_DECISION | oracle.F_OVERFLOW)) == 0
+    sf = ref["subray_flags"] & oracle.F_SUBRAY
+    if "subray_hit" not in g or "rerun" not in ref:
+        return ref, 0
+    rows = np.nonzero((sf != 0).any(axis=1) | ((f & oracle.F_WIN) != 0))[0]
+    if rows.size == 0:
+        return ref, 0
+    force = np.where(sf[rows] != 0, g["subray_hit"][rows], oracle.FREE_HIT).astype(np.int32)
+    a = ref["rerun"](rows, force_hit=force)
+    bad = np.nonzero(a["flags"] & oracle.F_FORCED_BAD)[0]
+    assert bad.size == 0, (f"GPU subray events that no flagged decision allows on pulse rows "
+                           f"{rows[bad][:5]}: gpu {g['subray_hit'][rows[bad][:5]]} "
+                           f"oracle {ref['subray_hit'][rows[bad][:5]]}")
+    # a window start within 1e-6 of a bin boundary may round either way: take
+    # the GPU's window there and compare the rest as usual
+    win = (a["flags"] & oracle.F_WIN) != 0
+    if win.any():
+        fw = np.where(win, g["window_bin"][rows], a["window_bin"]).astype(np.int32)
+        b = ref["rerun"](rows, force_hit=force, fixed_window=fw)
+        b["flags"] = b["flags"] | (a["flags"] & oracle.F_WIN)
+        a = b
+    out = dict(ref)
+    for k, v in a.items():
+        if isinstance(v, np.ndarray) and k in ref and isinstance(ref[k], np.ndarray) \
+                and ref[k].shape[:1] == (len(f),) and k not in ("pulses", "subray_flags"):
+            arr = ref[k].copy()
+            arr[rows] = v
+            out[k] = arr
+    return out, int(rows.size)
+
+
+def compare(g, ref, max_flag_frac=0.05, check_subrays=True, expected_mode=False):
+    """Assert parity of one leg's GPU view `g` against oracle result `ref`.
+
+    * A subray the oracle flags (hit within 1e-6 R of an edge, near-equal hits,
+      a transmission draw within rounding of the segment, a voxel corner) is
+      left out of the hit-id / range comparison, alone; its pulse is re-run in
+      the oracle with the GPU's event on that subray, and the pulse's window,
+      waveform and echoes are compared with the re-run.
+    * Echo decisions: the GPU's echo bins must be those the oracle's detector
+      finds on the GPU's own waveform, on every pulse; on pulses without a
+      near-tie decision (a bin within the waveform tolerance of a neighbour or
+      of the threshold, two contributions within 1e-4 at an echo) they must
+      also be the oracle's own, with the same objects.
+    Returns counts, including the fraction of subrays left out."""
+    ref, n_rerun = _rerun_flagged(g, ref)
+    f = ref["flags"]
     n = len(f)
-    assert (~geo).mean() <= max_flag_frac, f"too many flagged pulses: {(~geo).mean():.3f}"
+    sub_ok = (ref["subray_flags"] & oracle.F_SUBRAY) == 0
+    assert (~sub_ok).mean() <= max_flag_frac, f"too many flagged subrays: {(~sub_ok).mean():.4f}"
+    # with the GPU's subray events every pulse is compared (flagged ones after
+    # the re-run); without them a pulse with a flagged subray is left out
+    if "subray_hit" in g and "rerun" in ref:
+        geo = np.ones(n, bool)
+    else:
+        geo = (f & oracle.F_GEOMETRY) == 0
     # window start
-    bad = np.nonzero(geo & (g["window_bin"] != ref["window_bin"]))[0]
-    assert bad.size == 0, f"window_bin differs on {bad.size} unflagged pulses, e.g. {bad[:5]}"
+    bad = np.nonzero(geo & ((f & oracle.F_WIN) == 0) & (g["window_bin"] != ref["window_bin"]))[0]
+    assert bad.size == 0, f"window_bin differs on {bad.size} pulses, e.g. {bad[:5]}"
     # subray events
     if check_subrays and "subray_hit" in g:
         hit_ok = g["subray_hit"] == ref["subray_hit"]
-        bad = np.nonzero(geo[:, None] & ~hit_ok)
+        bad = np.nonzero(sub_ok & ~hit_ok)
         assert bad[0].size == 0, (f"subray hit ids differ on {bad[0].size} unflagged subrays, "
                                   f"e.g. pulse rows {bad[0][:5]}: gpu {g['subray_hit'][bad][:5]} "
                                   f"oracle {ref['subray_hit'][bad][:5]}")
-        m = geo[:, None] & (ref["subray_hit"] >= 0)
+        m = sub_ok & (ref["subray_hit"] >= 0)
         dr = np.abs(g["subray_range"] - ref["subray_range"])[m]
         assert dr.size == 0 or dr.max() <= RANGE_TOL, f"subray range error {dr.max():.3e} m"
     # waveform
@@ -73,20 +139,46 @@ def compare(g, ref, max_flag_frac=0.2, check_subrays=True, expected_mode=False):
     peak = np.abs(R).max(axis=1, keepdims=True)
     excess = np.abs(W - R) - (W_REL * np.abs(R) + W_FLOOR * peak)
     rows = np.nonzero(geo & (excess > 0).any(axis=1))[0]
-    assert rows.size == 0, (f"waveform outside tolerance on {rows.size} unflagged pulses, e.g. row "
+    assert rows.size == 0, (f"waveform outside tolerance on {rows.size} pulses, e.g. row "
                             f"{rows[0]}: max rel err "
                             f"{(np.abs(W - R) / np.maximum(np.abs(R), 1e-300))[rows[0]].max():.3e}")
-    # echoes
+    # echo decisions on the GPU's own waveform
+    K = ref["echo_bin"].shape[1]
+    thr_rel = float(ref["thr_rel"])
+    for i in np.nonzero(geo)[0]:
+        bins, ov, _ = oracle.echo_peaks(W[i], thr_rel=thr_rel, K=K)
+        c = int(g["echo_count"][i])
+        if c != len(bins) or not np.array_equal(g["echo_bin"][i, :c], bins):
+            # FP32 forms the threshold as 0.05f * max: only a bin within
+            # rounding of the threshold may decide differently
+            wm = W[i].max()
+            assert (np.abs(W[i] - thr_rel * wm) <= 1e-6 * wm).any(), (
+                f"row {i}: GPU echo bins {g['echo_bin'][i, :c]} differ from the detector on "
+                f"its own waveform {bins}")
+    # echoes against the oracle's own decisions: counts and bins where no bin
+    # was within the waveform tolerance of a neighbour or the threshold;
+    # objects where the two largest contributions differ by more than 1e-4,
+    # else the GPU's object must be one of those two
+    dec = geo & ((f & oracle.F_ECHO) == 0)
     bad = np.nonzero(dec & (g["echo_count"] != ref["echo_count"]))[0]
     assert bad.size == 0, (f"echo counts differ on {bad.size} unflagged pulses, e.g. {bad[:5]}: "
                            f"gpu {g['echo_count'][bad[:5]]} oracle {ref['echo_count'][bad[:5]]}")
-    K = ref["echo_bin"].shape[1]
     valid = dec[:, None] & (np.arange(K)[None, :] < ref["echo_count"][:, None])
     assert np.array_equal(g["echo_bin"][valid], ref["echo_bin"][valid]), "echo bins differ"
-    assert np.array_equal(g["echo_object"][valid], ref["echo_object"][valid]), "echo objects differ"
-    de = np.abs(g["echo_range"] - ref["echo_range"])[valid]
+    same = (geo[:, None] & (np.arange(K)[None, :] < np.minimum(ref["echo_count"], g["echo_count"])[:, None])
+            & (g["echo_bin"] == ref["echo_bin"]))
+    obj_tie = ((f & oracle.F_OBJ) != 0)[:, None]
+    exact = same & ~obj_tie
+    assert np.array_equal(g["echo_object"][exact], ref["echo_object"][exact]), "echo objects differ"
+    tie = same & obj_tie
+    ok = (g["echo_object"] == ref["echo_object"]) | (g["echo_object"] == ref["echo_object_alt"])
+    assert ok[tie].all(), "echo objects on near ties are neither of the two largest contributions"
+    # ranges and amplitudes wherever the GPU's echo sits on the oracle's bin
+    de = np.abs(g["echo_range"] - ref["echo_range"])[same]
     assert de.size == 0 or de.max() <= RANGE_TOL, f"echo range error {de.max():.3e} m"
     amp_tol = W_REL * np.abs(ref["echo_amp"]) + W_FLOOR * peak
-    assert (np.abs(g["echo_amp"] - ref["echo_amp"]) <= amp_tol)[valid].all(), "echo amplitudes differ"
-    return {"pulses": n, "flagged_geometry": float((~geo).mean()),
-            "flagged_decision": float((~dec).mean()), "echoes": int(ref["echo_count"][dec].sum())}
+    assert (np.abs(g["echo_amp"] - ref["echo_amp"]) <= amp_tol)[same].all(), "echo amplitudes differ"
+    return {"pulses": n, "flagged_subrays": float((~sub_ok).mean()), "rerun_pulses": n_rerun,
+            "excluded_pulses": float((~geo).mean()),
+            "flagged_decision": float((~dec).mean()), "object_ties": int(tie.sum()),
+            "echoes": int(ref["echo_count"][dec].sum())}

@@ -1248,3 +1248,84 @@ def test_scene_echo_object_stronger_of_two_merged_returns():
             _column_scene([np.float32(dens)], 20.0, plate_z=-20.9, plate_refl=refl), 200)
         assert r["echo_count"][0] == 1
         assert r["echo_object"][0, 0] == (osc.n_tri + 0 if want_voxel else 0)
+
+
+# --------------------------------------------------------------------------
+# re-running a pulse with given subray events (parity support): forcing the
+# oracle's own choices changes nothing; a choice an FP32 path may make on a
+# flagged subray is accepted; a choice no flagged decision allows is marked
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["tls0", "tls1", "als0"])
+def test_forcing_the_oracles_own_events_reproduces_the_scan(kind):
+    mode = int(kind[-1])
+    if kind.startswith("tls"):
+        w = scenes.tls_tiny(n_az=40, n_el=40)
+    else:
+        w = scenes.als_terrain(seed=5, size=96, n_trees=6, n_pulses=3000, n_bins=256, agl=80.0)
+    osc = oracle.OracleScene(w.scenes[0])
+    r = oracle.scan(osc, w.scanners[0], w.legs[0], mode=mode, seed=3)
+    flagged = (r["subray_flags"] & oracle.F_SUBRAY) != 0
+    assert flagged.any()
+    # every pulse's subray flags together are the pulse's subray flags
+    assert np.array_equal(np.bitwise_or.reduce(r["subray_flags"], axis=1) & oracle.F_SUBRAY,
+                          r["flags"] & oracle.F_SUBRAY)
+    rows = np.nonzero(flagged.any(axis=1))[0]
+    fh = np.where(flagged[rows], r["subray_hit"][rows], oracle.FREE_HIT).astype(np.int32)
+    r2 = r["rerun"](rows, force_hit=fh)
+    assert not (r2["flags"] & oracle.F_FORCED_BAD).any()
+    for k in ("window_bin", "echo_count", "echo_bin", "echo_object", "subray_hit"):
+        assert np.array_equal(r2[k], r[k][rows]), k
+    for k in ("waveform", "echo_range", "subray_range"):
+        assert np.allclose(r2[k], r[k][rows], rtol=1e-12, atol=0), k
+
+
+def test_forced_events_at_an_edge_and_implausible_ones():
+    """A ray through the shared diagonal may be given either triangle; a ray
+    clearly inside one triangle may not be given the other, nor a miss."""
+    osc = oracle.OracleScene(scenes.flat_target(10.0, 0.0, half=5.0))
+    sc, leg = _nadir_leg()
+    sc.n_bins = 200
+    # the plate's diagonal runs through (0, 0): the nadir ray is on the edge
+    r = oracle.scan(osc, sc, leg, mode=0, seed=1)
+    assert r["subray_flags"][0, 0] & oracle.F_EDGE
+    mine = r["subray_hit"][0, 0]
+    other = 1 - mine
+    r2 = r["rerun"]([0], force_hit=np.array([[other]], np.int32))
+    assert not (r2["flags"][0] & oracle.F_FORCED_BAD)
+    assert r2["subray_hit"][0, 0] == other
+    assert abs(r2["subray_range"][0, 0] - r["subray_range"][0, 0]) < 1e-9
+    assert np.allclose(r2["waveform"], r["waveform"], rtol=1e-9)
+    # off the diagonal the other triangle, a miss or a voxel are not allowed
+    leg2 = scenes.replace(leg, start=(0.5, -0.5, 0.0))
+    r = oracle.scan(osc, sc, leg2, mode=0, seed=1)
+    assert r["subray_flags"][0, 0] == 0
+    for bad in (1 - r["subray_hit"][0, 0], -1, osc.n_tri + 3):
+        r3 = r["rerun"]([0], force_hit=np.array([[bad]], np.int32))
+        assert r3["flags"][0] & oracle.F_FORCED_BAD, bad
+
+
+def test_forced_voxel_stop_and_pass():
+    """Stochastic mode: a voxel the subray clearly passes may not be given as its
+    stop, and a voxel it clearly stops in may not be passed (a triangle behind)."""
+    dens = np.full((8, 4, 4), 0.8, np.float32)
+    scene = _grid_scene(dens, origin=(-1.0, -1.0, -4.0), cell=0.5, ground_z=-10.0)
+    osc = oracle.OracleScene(scene)
+    sc, leg = _nadir_leg(64, -math.radians(89.5), -math.radians(88.5))
+    leg = scenes.replace(leg, start=(-0.3, 0.2, 0.0))
+    r = oracle.scan(osc, sc, leg, mode=0, seed=4)
+    ids = r["subray_hit"][:, 0]
+    stop = ids >= osc.n_tri
+    assert stop.any() and (~stop).any()
+    clean = (r["subray_flags"][:, 0] == 0)
+    # a pulse that stopped in a voxel, forced to the ground instead
+    i = np.nonzero(stop & clean)[0][0]
+    r3 = r["rerun"]([i], force_hit=np.array([[0]], np.int32))
+    r4 = r["rerun"]([i], force_hit=np.array([[1]], np.int32))
+    assert (r3["flags"][0] | r4["flags"][0]) & oracle.F_FORCED_BAD
+    # a pulse that reached the ground, forced to stop in the first voxel it crossed
+    j = np.nonzero(~stop & clean)[0][0]
+    o, d = oracle.pulse_ray(sc, leg, j, seed=4)
+    vid, _, _ = osc.march(o, d)
+    r5 = r["rerun"]([j], force_hit=np.array([[osc.n_tri + vid[0]]], np.int32))
+    assert r5["flags"][0] & oracle.F_FORCED_BAD
