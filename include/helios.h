@@ -325,8 +325,16 @@ HELIOS_API helios_status helios_scan_legs(helios_scene* const* scenes, int32_t n
  * static device array of 16 int32 (64 bytes, held by every GPU that loads the
  * library until exit), so it takes at most 16 x 128 = 2048 legs per call and
  * returns HELIOS_ERR_INVALID_ARG beyond that.  Host-side staging is static too
- * (no heap use).  The first call on each device looks the array's address up
- * with cudaGetSymbolAddress; make that first call before any stream capture.
+ * (no heap use).  Each call made outside a stream capture looks the array's
+ * address up with cudaGetSymbolAddress (so a device reset between calls is
+ * harmless); a call inside a capture reuses the address of the last call
+ * outside one, so make the first call on each device before any stream
+ * capture (HELIOS_ERR_UNSUPPORTED otherwise).  Stochastic mode keeps the
+ * Hermite table of merged returns (it lives in shared memory), so its
+ * results are those of helios_scan_legs; expected mode sums each waveform
+ * directly instead of through moment bins (device scratch) and finds echo
+ * objects from its own return list, which agrees with helios_scan_legs within
+ * the waveform tolerance.
  * All calls share the array: each call zeroes the counters it uses on its
  * stream, and calls whose work overlaps on the GPU (e.g. on two streams) race
  * on them.  opts->persistent is ignored (always one launch per 128 legs).

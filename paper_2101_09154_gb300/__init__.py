@@ -448,19 +448,20 @@ def scan_to_host(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, persisten
 
 
 def scan_static(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, out=None, subrays=True,
-                stream=None, block_threads=0, rays_per_block=0, blocks_per_sm=0):
+                stream=None, block_threads=0, rays_per_block=0, blocks_per_sm=0, echo_width=False):
     """helios_scan_legs_static: the persistent scan with no device allocation.
 
     For callers that cannot allocate device memory mid-scan (another
     allocator owns the budget, a graph capture into a pool they do not
     control, real-time loops).  The work-queue counters live in a static
     device array shared by all calls, so calls must not overlap on the GPU;
-    at most 2048 legs per call.  Outputs are those of ``scan``.
+    at most 2048 legs per call.  Outputs are those of ``scan``; ``echo_width``
+    adds the fitted echo widths (read back from the stored echo bins).
     """
     scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
     layout = output_layout(scanners, legs)
     if out is None:
-        out = alloc_outputs(layout, scenes[0].device, subrays=subrays)
+        out = alloc_outputs(layout, scenes[0].device, subrays=subrays, echo_width=echo_width)
     sh = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     sd = (ScannerDesc * len(scanners))(*[scanner_desc(s) for s in scanners])
     ld = (LegDesc * max(len(legs), 1))(*[leg_desc(l) for l in legs])

@@ -1356,7 +1356,17 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_cuda_error("cudaGetDevice", e);
     if (dev < 0 || dev >= kMaxDevices) return set_error(HELIOS_ERR_UNSUPPORTED, "device index %d", dev);
-    if (!g_static_ptr[dev]) {
+    // look the address up on every call made outside a stream capture (a
+    // device reset reloads the module and moves the array); inside a capture
+    // use the address of the last call outside one
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return set_cuda_error("cudaStreamIsCapturing", e);
+    if (cap == cudaStreamCaptureStatusNone || !g_static_ptr[dev]) {
+        if (cap != cudaStreamCaptureStatusNone)
+            return set_error(HELIOS_ERR_UNSUPPORTED,
+                             "the first helios_scan_legs_static call on a device must come before "
+                             "any stream capture");
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_queue);
         if (e != cudaSuccess) return set_cuda_error("cudaGetSymbolAddress(static work queue)", e);
@@ -1376,9 +1386,26 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         gk = max(gk, grid_kind(scenes[legs[l].scene]));
     }
     nb_cap = (nb_cap + 3) & ~3;
-    size_t smem = smem_bytes(mode, pc_cap, s_cap, rays_cap, nb_cap, threads);
+    // stochastic mode with a Gaussian pulse: the Hermite table for merged
+    // returns lives in shared memory, so it is kept (as in helios_scan_legs);
+    // expected mode sums its waveforms directly (its moment bins would be
+    // device scratch)
+    int ht_cb = 0;
+    if (mode == 0) {
+        for (int l = 0; l < n_legs; ++l) {
+            const DevScanner& sn = scanners[legs[l].scanner];
+            if (sn.pulse_shape == 0) ht_cb = max(ht_cb, (int)ceilf(sn.cut_hi * sn.inv_bin) + 1);
+        }
+        if (ht_cb > 256) ht_cb = 0;
+    }
+    const int pk_cap = ht_cb > 0 ? 4 * (2 * ht_cb + 1) + 4 : 0;
+    const bool direct = mode == 1;
+    size_t smem = smem_bytes(mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, 0, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     if (n_groups == 0) return HELIOS_OK;
+    // the echo-width fit runs after the scan, from the stored rows and bins
+    Outputs kout = out;
+    kout.echo_width = nullptr;
     e = cudaMemsetAsync(g_static_ptr[dev], 0, sizeof(int32_t) * n_groups, st);
     if (e != cudaSuccess) return set_cuda_error("cudaMemsetAsync(static work queue)", e);
     for (int g = 0; g < n_groups; ++g) {
@@ -1395,12 +1422,13 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         }
         if (items >= INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many work items");
         if (items == 0) continue;
-        p.out = out;
+        p.out = kout;
         p.seed = seed;
         p.n_legs = nl;
         p.n_items = (int32_t)items;
         p.s_cap = s_cap; p.pc_cap = pc_cap; p.rays_cap = rays_cap; p.nb_cap = nb_cap;
-        p.w_stride = warp_stride(mode, nb_cap, 0, true);
+        p.w_stride = warp_stride(mode, nb_cap, 0, direct);
+        p.pk_cap = pk_cap; p.ht_cb = ht_cb;
         p.queue = g_static_ptr[dev] + g;
         helios_status s = dispatch<kMaxLegs>(p, mode, gk, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;

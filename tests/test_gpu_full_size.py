@@ -48,6 +48,7 @@ def test_uls_full_size_sampled(hg, uls, mode):
     torch.cuda.empty_cache()
     ref = oracle.scan(oracle.OracleScene(w.scenes[0]), sc, leg, rows, mode=mode, seed=0)
     st = compare(g, ref, expected_mode=(mode == 1))
+    print(f"uls mode {mode}: {st}")
     assert st["pulses"] == len(rows) and st["echoes"] > 1500, st
 
 
@@ -97,7 +98,7 @@ def test_batched_legs_full_size_sampled(hg):
                        rays_per_block=1536)
     torch.cuda.synchronize()
     osc = {}
-    total = 0
+    total = flagged = subrays = reruns = 0
     for l, leg in enumerate(w.legs):
         sc = w.scanners[leg.scanner_index]
         q = leg.beam_sample_quality if leg.beam_sample_quality >= 0 else sc.beam_sample_quality
@@ -109,4 +110,8 @@ def test_batched_legs_full_size_sampled(hg):
         ref = oracle.scan(osc[leg.scene_index], sc, leg, rows, seed=3)
         st = compare(g, ref)
         total += st["pulses"]
+        flagged += st["flagged_subrays"] * st["pulses"] * S
+        subrays += st["pulses"] * S
+        reruns += st["rerun_pulses"]
+    print(f"batched: {total} pulses, flagged subrays {flagged / subrays:.5f}, re-run pulses {reruns}")
     assert total >= 128 * 39

@@ -293,6 +293,7 @@ def test_als_full_size_sampled(hg):
     rows = np.arange(0, w.legs[0].n_pulses, 997)
     out, lay, res = run_both(hg, w, seed=0, rows=rows, subrays=True)
     stats = compare(*res[0])
+    print(f"als full size: {stats}")
     assert stats["pulses"] == len(rows)
 
 

@@ -15,7 +15,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import scenes
+from parity import compare, leg_view
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -79,3 +81,66 @@ def test_static_scan_with_several_grids(hg):
         assert torch.equal(got[k], ref[k]), k
     assert _close(got["waveform"], ref["waveform"], nb=256)
     assert (ref["subray_hit"] >= gsc[0].n_triangles).float().mean() > 0.05
+
+
+def _expected_pair(hg, w, seed):
+    gsc = [hg.Scene(s) for s in w.scenes]
+    ref, lay = hg.scan(gsc, w.scanners, w.legs, mode=hg.MODE_EXPECTED, seed=seed, persistent=True)
+    torch.cuda.synchronize()
+    return gsc, ref, lay
+
+
+@pytest.mark.parametrize("kind", ["voxels", "mesh"])
+def test_static_expected_mode_matches_allocating_scan_and_oracle(hg, kind):
+    """Expected mode with a Gaussian pulse and echo objects: the static entry
+    sums each waveform directly and picks echo objects from its own return
+    list, the allocating one uses moment bins and a second march.  Both are
+    checked against the oracle (integers exact away from flagged near-ties)
+    and against each other within the waveform and range tolerances, on two
+    calls in a row."""
+    if kind == "voxels":
+        w = scenes.uls_voxels(seed=6, n=48, n_pulses=2001, n_bins=512, agl=12.0, speed=1.0,
+                              prf=2000.0)
+    else:
+        w = scenes.als_terrain(seed=5, size=96, n_trees=6, n_pulses=3000, n_bins=256, agl=80.0)
+    sc, leg = w.scanners[0], w.legs[0]
+    nb = sc.n_bins
+    gsc, ref, lay = _expected_pair(hg, w, seed=2)
+    S = hg.subray_count(sc.beam_sample_quality)
+    rows = np.arange(leg.n_pulses)
+    oref = oracle.scan(oracle.OracleScene(w.scenes[0]), sc, leg, rows, mode=1, seed=2)
+    compare(leg_view(ref, lay, 0, sc, S, rows), oref, expected_mode=True)
+    ok = (oref["flags"] & (oracle.F_DECISION | oracle.F_OVERFLOW)) == 0
+    for _call in range(2):
+        got, _ = hg.scan_static(gsc, w.scanners, w.legs, mode=hg.MODE_EXPECTED, seed=2)
+        torch.cuda.synchronize()
+        compare(leg_view(got, lay, 0, sc, S, rows), oref, expected_mode=True)
+        assert _close(got["waveform"], ref["waveform"], nb=nb)
+        assert torch.equal(got["window_bin"], ref["window_bin"])
+        assert torch.equal(got["subray_hit"], ref["subray_hit"])
+        assert _close(got["subray_range"], ref["subray_range"])
+        K = sc.max_echoes
+        for k in ("echo_count",):
+            a, b = got[k].cpu().numpy(), ref[k].cpu().numpy()
+            assert np.array_equal(a[ok], b[ok]), k
+        for k in ("echo_bin", "echo_object"):
+            a = got[k].cpu().numpy().reshape(-1, K)
+            b = ref[k].cpu().numpy().reshape(-1, K)
+            assert np.array_equal(a[ok], b[ok]), k
+
+
+def test_static_scan_echo_widths_match_allocating_scan(hg):
+    """The optional echo-width fit requested from the static entry (with the
+    echo bins it reads back) gives the allocating scan's widths, twice."""
+    w = scenes.als_terrain(seed=5, size=96, n_trees=6, n_pulses=3000, n_bins=256, agl=80.0)
+    gsc = [hg.Scene(s) for s in w.scenes]
+    ref, _ = hg.scan(gsc, w.scanners, w.legs, seed=5, persistent=True, echo_width=True)
+    torch.cuda.synchronize()
+    for _call in range(2):
+        got, _ = hg.scan_static(gsc, w.scanners, w.legs, seed=5, echo_width=True)
+        torch.cuda.synchronize()
+        assert torch.equal(got["echo_bin"], ref["echo_bin"])
+        a = got["echo_width"].double().cpu().numpy()
+        b = ref["echo_width"].double().cpu().numpy()
+        assert np.all(np.abs(a - b) <= 1e-3 * np.abs(b) + 1e-6)
+        assert (b > 0).sum() > 1000
