@@ -8,12 +8,14 @@
 //   dL/ddensity_j = G(d) dL/dsigma_j,    dL/drho = A_tri T_{K+1}.
 // The hit set and the window start are held fixed.  One warp per pulse,
 // lanes = subrays.  For a Gaussian pulse A comes from per-pulse Hermite
-// correlation tables (see corr_tab).  Pass A marches once and lists each
+// correlation tables of orders 0-5 (see corr_tab).  Pass A marches once and lists each
 // voxel's terms; pass B walks the list back to front, so the suffix sum is
 // built term by term.  A lane whose list overflows marches a second time and
 // takes the suffix as total - prefix in FP64.
 #include "hg_device.cuh"
 #include "hg_host.h"
+
+#include <cuda_bf16.h>
 
 namespace hg {
 
@@ -45,18 +47,26 @@ __device__ __forceinline__ float corr(const float* g, int nb, const DevScanner& 
 
 // A(tau) = sum_b g_b p(b bin - tau).  With tau = j bin + delta, j even and
 // |delta| <= bin, and the Gaussian's Taylor series in Hermite form,
-//   A = sum_{n<=3} delta^n/n! C_n[j],  C_n[j] = sigma^-n sum_k g_{j+k} p(k bin) He_n(k bin/sigma),
+//   A = sum_{n<=5} delta^n/n! C_n[j],  C_n[j] = sigma^-n sum_k g_{j+k} p(k bin) He_n(k bin/sigma),
 // so one table per pulse (every second bin) replaces a (2 cb + 1)-bin dot
-// product per return.  The first dropped term is below 6e-5 of the peak
-// for bin/sigma <= 0.15.
-__device__ __forceinline__ float corr_tab(const float4* C, int c0, int ncell, float dt2,
-                                          float inv_bin2, float tau) {
+// product per return.  The first dropped term, (delta/sigma)^6/6! He_6 p, is
+// below 2.2e-7 of the pulse peak (times sum |g|) for bin/sigma <= 0.148
+// (max |He_6(u) e^{-u^2/2}| = 15).  Orders 4 and 5 are kept in bf16: their
+// terms are at most 5.9e-5 and 3.3e-6 of that scale, so the 2^-9 rounding adds
+// below 1.2e-7.
+__device__ __forceinline__ float corr_tab(const float4* C4, const __nv_bfloat162* C2, int c0,
+                                          int ncell, float dt2, float inv_bin2, float tau) {
     const float jf = rintf(tau * inv_bin2);          // j / 2
     const int c = (int)fmaxf(fminf(jf, 1.0e9f), -1.0e9f) + c0;
     if (c < 0 || c >= ncell) return 0.0f;
-    const float4 t = C[c];
+    const float4 t = C4[c];
+    const float2 h = __bfloat1622float2(C2[c]);
     const float d = fmaf(-jf, dt2, tau);
-    return fmaf(d, fmaf(d * 0.5f, fmaf(d * (1.0f / 3.0f), t.w, t.z), t.y), t.x);
+    float a = fmaf(d * 0.2f, h.y, h.x);
+    a = fmaf(d * 0.25f, a, t.w);
+    a = fmaf(d * (1.0f / 3.0f), a, t.z);
+    a = fmaf(d * 0.5f, a, t.y);
+    return fmaf(d, a, t.x);
 }
 
 // the grid holding voxel vx of the scene's concatenated voxels: its gradient
@@ -82,7 +92,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     extern __shared__ __align__(16) unsigned char smem[];
     const int tab = P.cb > 0;
     float4* s_h = reinterpret_cast<float4*>(smem);                      // [2 cb + 1] (tab)
-    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_h + (tab ? 2 * P.cb + 1 : 0));
+    float2* s_h2 = reinterpret_cast<float2*>(s_h + (tab ? 2 * P.cb + 1 : 0));   // [2 cb + 1] (tab)
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_h2 + (tab ? 2 * P.cb + 1 : 0));
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_w = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(s_sc + P.s_cap) + 15u) & ~uintptr_t(15));
@@ -98,13 +109,16 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     float* const ddens1 = sc.grid.ddens;     // the one grid's gradient (GK 1)
     for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
     if (tab) {
-        // h_k = p(k bin) (1, u/sigma, (u^2-1)/sigma^2, (u^3-3u)/sigma^3), u = k bin/sigma
+        // h_k = p(k bin) sigma^-n He_n(u), n = 0..5, u = k bin/sigma:
+        // He = 1, u, u^2 - 1, u^3 - 3u, u^4 - 6u^2 + 3, u^5 - 10u^3 + 15u
         const float is = sqrtf(sn.inv_s2);
         for (int k = tid; k < 2 * cb + 1; k += blockDim.x) {
-            const float x = (float)(k - cb) * dt, u = x * is;
+            const float x = (float)(k - cb) * dt, u = x * is, u2 = u * u;
             const float p = exp2f(-x * x * sn.gk2);
-            s_h[k] = make_float4(p, p * u * is, p * (u * u - 1.0f) * is * is,
-                                 p * (u * u * u - 3.0f * u) * is * is * is);
+            const float i2 = is * is, i3 = i2 * is;
+            s_h[k] = make_float4(p, p * u * is, p * (u2 - 1.0f) * i2, p * u * (u2 - 3.0f) * i3);
+            s_h2[k] = make_float2(p * fmaf(u2, u2 - 6.0f, 3.0f) * i2 * i2,
+                                  p * u * fmaf(u2, u2 - 10.0f, 15.0f) * i3 * i2);
         }
     }
     if (tid == 0) {
@@ -113,11 +127,13 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
         sincos(lg.rpy[2], &s_rot[4], &s_rot[5]);
     }
     __syncthreads();
-    // per warp: the correlation table and a g tile (tab), else the g row
-    const int wstride = tab ? 4 * P.ncell + 2 * (128 + cb + 1) : P.nb_cap;
+    // per warp: the correlation tables (orders 0-3 in FP32, 4-5 in bf16) and a
+    // g tile (tab), else the g row
+    const int wstride = tab ? 5 * P.ncell + 2 * (128 + cb + 1) : P.nb_cap;
     float* wbuf = s_w + (size_t)warp * ((wstride + 3) & ~3);
     float4* C = reinterpret_cast<float4*>(wbuf);
-    float* g = tab ? wbuf + 4 * P.ncell : wbuf;
+    __nv_bfloat162* C2 = reinterpret_cast<__nv_bfloat162*>(wbuf + 4 * P.ncell);
+    float* g = tab ? wbuf + 5 * P.ncell : wbuf;
     const size_t RLs = (size_t)P.rl_cap * 32;
     float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 4 * RLs : nullptr;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
@@ -153,15 +169,20 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     __syncwarp();
                     for (int i = lane; i < 128 && t0 + i < P.ncell; i += 32) {
                         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float2 a2 = make_float2(0.f, 0.f);
                         for (int kk = 0; kk <= 2 * cb; ++kk) {
                             const float gv = (kk & 1) ? go[i + (kk >> 1)] : ge[i + (kk >> 1)];
                             const float4 h = s_h[kk];
+                            const float2 h2 = s_h2[kk];
                             a.x = fmaf(gv, h.x, a.x);
                             a.y = fmaf(gv, h.y, a.y);
                             a.z = fmaf(gv, h.z, a.z);
                             a.w = fmaf(gv, h.w, a.w);
+                            a2.x = fmaf(gv, h2.x, a2.x);
+                            a2.y = fmaf(gv, h2.y, a2.y);
                         }
                         C[t0 + i] = a;
+                        C2[t0 + i] = __float22bfloat162_rn(a2);
                     }
                     __syncwarp();
                 }
@@ -170,7 +191,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 __syncwarp();
             }
             auto amp = [&](float tau) {
-                return tab ? corr_tab(C, c0, P.ncell, 2.0f * dt, 0.5f * sn.inv_bin, tau)
+                return tab ? corr_tab(C, C2, c0, P.ncell, 2.0f * dt, 0.5f * sn.inv_bin, tau)
                            : corr(g, nb, sn, dt, tau);
             };
             const PulseFF& f = s_pf[pl];
@@ -361,9 +382,9 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         p->cb = cb;
         // even bins -cb-2 .. nb+cb+1 (cells 0 .. ncell-1, bin 0 at cell (cb+3)/2)
         p->ncell = cb > 0 ? (cb + 3) / 2 + (sn.n_bins + cb + 2) / 2 + 1 : 0;
-        const int wstride = cb > 0 ? 4 * p->ncell + 2 * (128 + cb + 1) : p->nb_cap;
-        size_t smem = (cb > 0 ? sizeof(float4) * (2 * cb + 1) : 0) + sizeof(PulseFF) * p->pc_cap +
-                      sizeof(SubrayConst) * p->s_cap;
+        const int wstride = cb > 0 ? 5 * p->ncell + 2 * (128 + cb + 1) : p->nb_cap;
+        size_t smem = (cb > 0 ? (sizeof(float4) + sizeof(float2)) * (2 * cb + 1) : 0) +
+                      sizeof(PulseFF) * p->pc_cap + sizeof(SubrayConst) * p->s_cap;
         smem = ((smem + 15) & ~size_t(15)) + sizeof(float) * (size_t)(L.threads / 32) * ((wstride + 3) & ~3);
         if (smem > 227 * 1024) {
             delete p;

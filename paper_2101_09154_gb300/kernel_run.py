@@ -46,6 +46,7 @@ def main(argv=None):
     ap.add_argument("--kernel", default="stochastic", choices=["stochastic", "expected", "adjoint"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--block-threads", type=int, default=0, help="0: the library's default")
     a = ap.parse_args(argv)
 
     import torch
@@ -62,7 +63,7 @@ def main(argv=None):
     out = hg.alloc_outputs(lay, dev, subrays=True)
 
     def scan():
-        hg.scan(gsc, w.scanners, w.legs, mode=mode, out=out)
+        hg.scan(gsc, w.scanners, w.legs, mode=mode, out=out, block_threads=a.block_threads)
 
     fn = scan
     if a.kernel == "adjoint":
@@ -81,7 +82,7 @@ def main(argv=None):
 
         def fn():
             hg.scan_adjoint(gsc, w.scanners, w.legs, gW, out["window_bin"], out["subray_hit"],
-                            grads=grads)
+                            grads=grads, block_threads=a.block_threads)
     for _ in range(a.warmup):
         fn()
     torch.cuda.synchronize()
@@ -94,6 +95,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.repeat, 1)
     print(json.dumps({"workload": w.name, "kernel": a.kernel, "pulses": int(w.n_pulses),
+                      "block_threads": a.block_threads,
                       "repeat": a.repeat, "ms_per_call": ms,
                       "pulses_per_s": w.n_pulses / (ms / 1e3)}), flush=True)
 

@@ -493,10 +493,7 @@ def test_adjoint_with_several_grids(hg):
     gd = np.concatenate([to_np(t).ravel() for t in grads[0]["density"]])
     scale = np.abs(d_dens).max()
     assert scale > 0 and len(gd) == len(d_dens)
-    # the correlation tables give each return's A to 6e-5 of its pulse-scale
-    # magnitude (truncated Hermite series); a density gradient is a difference
-    # of such terms, so small entries carry an absolute error of that order
-    err = np.abs(gd - d_dens) - (1e-3 * np.abs(d_dens) + 6e-5 * scale)
+    err = np.abs(gd - d_dens) - (1e-3 * np.abs(d_dens) + 1e-6 * scale)
     big = np.abs(d_dens) >= 1e-2 * scale
     assert np.median(np.abs(gd - d_dens)[big] / np.abs(d_dens)[big]) < 1e-4
     assert (err <= 0).all(), f"density gradient: {int((err > 0).sum())} entries outside tolerance"
