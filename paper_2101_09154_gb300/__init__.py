@@ -316,6 +316,16 @@ class Scene:
         del lads
         self.handle = h
 
+    def parameters(self) -> list:
+        """The differentiable tensors: every mesh's reflectance, then every
+        distinct density tensor (grids sharing an array appear once)."""
+        seen, dens = set(), []
+        for d in self.density:
+            if id(d) not in seen:
+                seen.add(id(d))
+                dens.append(d)
+        return list(self.reflectance) + dens
+
     def info(self) -> dict:
         i = SceneInfo()
         _check(lib().helios_scene_get_info(self.handle, C.byref(i)))
@@ -507,29 +517,51 @@ def scan_adjoint(scenes, scanners, legs, d_waveform, window_bin, subray_hit=None
 
 
 class WaveformFunction:
-    """Differentiable expected-mode waveform: W = scan(reflectance, density).
+    """Differentiable expected-mode waveform: W = scan(reflectances, densities).
 
-    ``apply(scene, scanner, leg, reflectance, density)`` returns the flat
-    waveform tensor; reflectance/density must be the tensors the scene
-    references (their values are read by the kernels, gradients flow back
-    through the hand-written adjoint kernel).
+    ``apply(scene, scanners, legs, *tensors)`` returns the flat waveform tensor
+    of the legs (one scene).  ``tensors`` are tensors the scene references:
+    any of ``scene.reflectance`` (one per mesh) and ``scene.density`` (one per
+    distinct density array; grids built from the same array share it); by
+    default all of them (``scene.parameters()``).  The kernels read their
+    current values, and the gradient of every one of them comes back from the
+    hand-written adjoint kernel: a density tensor shared by several grids
+    receives the sum of their gradients.  ``scanners`` and ``legs`` may be
+    single objects or lists.
     """
 
     @staticmethod
-    def apply(scene, scanner, leg, reflectance, density):
+    def apply(scene, scanners, legs, *tensors):
         torch = _torch()
+        scanners, legs = _as_list(scanners), _as_list(legs)
+        if not tensors:
+            tensors = tuple(scene.parameters())
+        routes = []
+        for t in tensors:
+            r_idx = [i for i, r in enumerate(scene.reflectance) if r is t]
+            d_idx = [j for j, d in enumerate(scene.density) if d is t]
+            if not r_idx and not d_idx:
+                raise ValueError("WaveformFunction: a tensor that the scene does not reference")
+            routes.append((r_idx, d_idx))
 
         class _Fn(torch.autograd.Function):
             @staticmethod
-            def forward(ctx, refl, dens):
-                out, _ = scan([scene], [scanner], [leg], mode=MODE_EXPECTED, subrays=True)
+            def forward(ctx, *ts):
+                out, _ = scan([scene], scanners, legs, mode=MODE_EXPECTED, subrays=True)
                 ctx.save_for_backward(out["window_bin"], out["subray_hit"])
                 return out["waveform"]
 
             @staticmethod
             def backward(ctx, gW):
                 window, hits = ctx.saved_tensors
-                g = scan_adjoint([scene], [scanner], [leg], gW.contiguous(), window, hits)
-                return g[0]["reflectance"][0], (g[0]["density"][0] if g[0]["density"] else None)
+                g = scan_adjoint([scene], scanners, legs, gW.contiguous(), window, hits)[0]
+                res = []
+                for r_idx, d_idx in routes:
+                    parts = [g["reflectance"][i] for i in r_idx] + [g["density"][j] for j in d_idx]
+                    acc = parts[0]
+                    for q in parts[1:]:
+                        acc = acc + q
+                    res.append(acc)
+                return tuple(res)
 
-        return _Fn.apply(reflectance, density)
+        return _Fn.apply(*tensors)

@@ -43,7 +43,7 @@ struct ScanParams {
     int32_t cext_cap;
     int32_t mom_cells, mom_cb;
     long long* mom;          // per-warp moment bins (expected mode), NULL: direct sums
-    float* rlist;            // per-warp return lists (expected mode): tau, power, id
+    float4* rlist;           // per-warp return lists (expected mode): (tau, power, id bits, 0)
     int32_t rl_cap;          // entries per lane
     int32_t* queue;
 };
@@ -593,16 +593,16 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     const float scale = ldexpf(rm * rm / sn.pconst, 40);
                     int clo = INT_MAX, chi = -1;
                     uint32_t fl = 0;
-                    // return list [3][rl_cap][32]: what the echo-object pass reads
-                    // instead of marching again (a chunk of 32 subrays ends with id -1)
-                    const size_t RLs = (size_t)P.rl_cap * 32;
-                    float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
+                    // return list [rl_cap][32] of 16-byte entries: what the echo-object
+                    // pass reads instead of marching again (a chunk of 32 subrays ends
+                    // with id -1)
+                    float4* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * (size_t)P.rl_cap * 32;
                     for (int s0 = 0; s0 < S; s0 += 32) {
                         const int s = s0 + lane;
                         if (s >= S) continue;
                         if (s0 > 0) {
                             if (n_rl < P.rl_cap)
-                                __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + (size_t)n_rl * 32 + lane, -1);
+                                __stcg(RL + (size_t)n_rl * 32 + lane, make_float4(0.f, 0.f, __int_as_float(-1), 0.f));
                             ++n_rl;
                         }
                         expected_returns<GK>(sc, sn, f, s_sc[s], rrp[s], fl,
@@ -613,12 +613,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             float dl = fmaf(-jf, dt, tau);
                             float a = Pw * scale;
                             int c = (int)jf + cb + 1;
-                            if (n_rl < P.rl_cap) {
-                                const size_t e = (size_t)n_rl * 32 + lane;
-                                __stcg(RL + e, tau);
-                                __stcg(RL + RLs + e, Pw);
-                                __stcg(reinterpret_cast<int32_t*>(RL + 2 * RLs) + e, id);
-                            }
+                            if (n_rl < P.rl_cap)
+                                __stcg(RL + (size_t)n_rl * 32 + lane, make_float4(tau, Pw, __int_as_float(id), 0.f));
                             ++n_rl;
                             atomicAdd(Mu + c, (unsigned long long)llrintf(a));
                             atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
@@ -904,14 +900,18 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             }
                         };
                         if (rl_ok) {
-                            const size_t RLs = (size_t)P.rl_cap * 32;
-                            const float* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * 3 * RLs;
+                            const float4* RL = P.rlist + ((size_t)blockIdx.x * nwarps + warp) * (size_t)P.rl_cap * 32;
                             int s = lane;
+                            // entries are read two ahead of their use
+                            float4 q0 = n_rl > 0 ? __ldcg(RL + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            float4 q1 = n_rl > 1 ? __ldcg(RL + 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
                             for (int e = 0; e < n_rl; ++e) {
-                                const size_t o = (size_t)e * 32 + lane;
-                                const int32_t id = __ldcg(reinterpret_cast<const int32_t*>(RL + 2 * RLs) + o);
+                                const float4 q = q0;
+                                q0 = q1;
+                                if (e + 2 < n_rl) q1 = __ldcg(RL + (size_t)(e + 2) * 32 + lane);
+                                const int32_t id = __float_as_int(q.z);
                                 if (id < 0) { s += 32; continue; }
-                                consider(__ldcg(RL + o), __ldcg(RL + RLs + o), id, s);
+                                consider(q.x, q.y, id, s);
                             }
                         } else {
                             for (int s0 = 0; s0 < S; s0 += 32) {
@@ -1187,7 +1187,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
     size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     long long* mom = nullptr;
-    float* rlist = nullptr;
+    float4* rlist = nullptr;
     int mom_cells = 0, rl_cap = 0;
     struct Free {
         void* p; cudaStream_t s;
@@ -1228,7 +1228,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         if (L.out.echo_object) {
             // longer lists (more than kReturnListCap returns of one lane) march again
             rl_cap = kReturnListCap;
-            e = cudaMallocAsync(reinterpret_cast<void**>(&rlist), slots * 3 * rl_cap * 32 * sizeof(float), st);
+            e = cudaMallocAsync(reinterpret_cast<void**>(&rlist), slots * rl_cap * 32 * sizeof(float4), st);
             if (e != cudaSuccess) return set_cuda_error("cudaMallocAsync(return lists)", e);
             free_rl.p = rlist;
         }

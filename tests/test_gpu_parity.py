@@ -285,6 +285,47 @@ def test_autograd_function(hg):
     assert refl.grad is not None and (refl.grad != 0).any()
 
 
+def test_autograd_function_every_mesh_and_grid(hg):
+    """WaveformFunction on a scene of two meshes and nine voxel grids, three of
+    which are made to share one density array: autograd returns every mesh's reflectance
+    gradient and every distinct density tensor's gradient (the shared one the
+    sum over its grids), equal to the adjoint called directly."""
+    w = scenes.voxel_forest(seed=9, n_pulses=800, n_bins=256)
+    sc, leg = w.scanners[0], w.legs[0]
+    s0 = w.scenes[0]
+    # the leg flies over the middle column of trees (grids 1, 4, 7)
+    s0.grids[4].density = s0.grids[1].density
+    s0.grids[7].density = s0.grids[1].density
+    pv = np.array([[2, 2, 0.1], [16, 2, 0.1], [16, 20, 0.1], [2, 20, 0.1]], np.float32)
+    s0.meshes.append(scenes.Mesh(pv, np.array([[0, 1, 2], [0, 2, 3]], np.int32),
+                                 np.array([0.6, 0.4], np.float32), object_id=2))
+    gs = hg.Scene(s0)
+    params = gs.parameters()
+    assert len(params) == 2 + len({id(g.density) for g in s0.grids})
+    for t in params:
+        t.requires_grad_(True)
+    W = hg.WaveformFunction.apply(gs, sc, leg, *params)
+    gen = torch.Generator(device=W.device).manual_seed(5)
+    gW = torch.randn(W.shape, generator=gen, device=W.device)
+    (W * gW).sum().backward()
+    out, _ = hg.scan([gs], [sc], [leg], mode=1)
+    ref = hg.scan_adjoint([gs], [sc], [leg], gW, out["window_bin"], out["subray_hit"])[0]
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert (ref["reflectance"][i] != 0).any()
+        assert torch.allclose(params[i].grad, ref["reflectance"][i], rtol=1e-5,
+                              atol=1e-7 * float(ref["reflectance"][i].abs().max()))
+    for t in params[2:]:
+        want = sum(ref["density"][j] for j, d in enumerate(gs.density) if d is t)
+        assert torch.allclose(t.grad, want, rtol=1e-5, atol=1e-7 * float(want.abs().max()) + 1e-30)
+    shared = gs.density[1]
+    assert gs.density[4] is shared and gs.density[7] is shared
+    parts = [ref["density"][j] for j in (1, 4, 7)]
+    assert sum(int((p != 0).sum()) > 0 for p in parts) >= 2
+    for t in params:
+        t.requires_grad_(False)
+
+
 @pytest.mark.slow
 def test_als_full_size_sampled(hg):
     """The 3M-triangle ALS workload with 4M pulses in the benchmark's launch
