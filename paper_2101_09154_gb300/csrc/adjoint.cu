@@ -11,7 +11,7 @@
 // correlation tables of orders 0-5 (see corr_tab).  Pass A marches once and lists each
 // voxel's terms; pass B walks the list back to front, so the suffix sum is
 // built term by term.  A lane whose list overflows marches a second time and
-// takes the suffix as total - prefix in FP64.
+// takes the suffix as total - prefix, both summed in float-float.
 #include "hg_device.cuh"
 #include "hg_host.h"
 
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 // ---- pass A: march once, grid after grid in entry order; total
                 // of A_k w_k, and each voxel's terms in the lane's list
                 // [voxel, G A T l e^{-sigma l}, G l, A w] ----
-                double total = 0.0;
+                FF total = {0.0f, 0.0f};     // float-float: suffixes are differences of it
                 float T = 1.0f;
                 uint32_t fl = 0;
                 int n = 0;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                     FF R = ff_add_f(t_in, 0.5f * len);
                                     float A = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f) *
                                               amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
-                                    total += (double)A * (double)w;
+                                    ff_acc(total, A * w);
                                     if (listing && n < P.rl_cap) {
                                         // the voxel's index over all of the scene's grids
                                         const size_t e = (size_t)n * 32 + lane;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 if (hit >= 0) {
                     A_tri = return_power(sn, t32 + dt32, tan_a, 1.0f, cosi) *
                             amp(ff_mul_sub(ff_norm(t32, dt32), kDelayHi, kDelayLo, mdt_h, mdt_l));
-                    total += (double)A_tri * (double)rho * (double)T;
+                    ff_acc(total, A_tri * rho * T);
                     if (drefl[mesh]) atomicAdd(&drefl[mesh][face], A_tri * T);
                 }
                 if (!grid || !want || n == 0) continue;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     continue;
                 }
                 // ---- pass B by a second march (list too long): suffix = total - prefix ----
-                double prefix = 0.0;
+                FF prefix = {0.0f, 0.0f};
                 float Tb = 1.0f;
                 walk_grids<GK>(sc, o, d, t_tri, [&](const DevGrid& G, March& mch) -> bool {
                     const float Gs = proj_factor(G, dh[2]);
@@ -332,10 +332,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                 FF R = ff_add_f(t_in, 0.5f * len);
                                 float A = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f) *
                                           amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
-                                prefix += (double)A * (double)w;
-                                double suffix = total - prefix;
-                                double dsig = (double)A * Tb * len * a - len * suffix;
-                                if (G.ddens) atomicAdd(&G.ddens[v.vid], (float)((double)Gs * dsig));
+                                // the same FP32 products as pass A: their sum cancels
+                                ff_acc(prefix, A * w);
+                                const float suffix = (total.hi - prefix.hi) + (total.lo - prefix.lo);
+                                const float dsig = A * Tb * len * a - len * suffix;
+                                if (G.ddens) atomicAdd(&G.ddens[v.vid], Gs * dsig);
                                 Tb *= a;
                             }
                         }

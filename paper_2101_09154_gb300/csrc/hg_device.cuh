@@ -59,6 +59,7 @@ struct DevGrid {
     float G, leaf_refl;
     int32_t vox_off;            // voxels of the scene's earlier grids
     int32_t pad;
+    double inv_cell;            // 1 / cell, formed in FP64 on the host
 };
 
 struct DevScene {
@@ -387,6 +388,13 @@ __device__ __forceinline__ FF ff_norm(float hi, float lo) {
     FF r;
     two_sum(hi, lo, r.hi, r.lo);
     return r;
+}
+
+// s += x with the rounding error of the addition kept in s.lo
+__device__ __forceinline__ void ff_acc(FF& s, float x) {
+    float h, e;
+    two_sum(s.hi, x, h, e);
+    s = ff_norm(h, e + s.lo);
 }
 __device__ __forceinline__ bool ff_less(const FF& a, const FF& b) {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
@@ -807,6 +815,19 @@ __device__ __forceinline__ float cross32(int p, int p0, int s, float f0, float i
 }
 
 // set up the march along o + t d for t in [t_enter, min(t_exit, t_hi)); false: no voxel
+// 1/x in FP64 without a division: an FP32 estimate and two Newton steps
+// (the relative error squares each step, 2^-23 -> 2^-46 -> below FP64
+// rounding: within 1 ulp of 1/x).  Outside the FP32 range, the division.
+__device__ __forceinline__ double rcp64(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1.0e-30 && ax < 1.0e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 __device__ __forceinline__ bool march_init(const DevGrid& S, const double o[3],
                                            const double d[3], double t_hi, March& m) {
     double g0[3] = {(double)S.g0[0], (double)S.g0[1], (double)S.g0[2]};
@@ -814,13 +835,15 @@ __device__ __forceinline__ bool march_init(const DevGrid& S, const double o[3],
     double tlo[3], thi[3];
     double te = 0.0, tx = 1e300;
     int dims[3] = {S.dims[0], S.dims[1], S.dims[2]};
+    double ivd[3];
     for (int a = 0; a < 3; ++a) {
         double lo = g0[a], hi = g0[a] + (double)dims[a] * cell;
+        ivd[a] = d[a] != 0.0 ? rcp64(d[a]) : 0.0;
         if (d[a] == 0.0) {
             if (o[a] < lo || o[a] >= hi) return false;
             tlo[a] = -1e300; thi[a] = 1e300;
         } else {
-            double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+            double ta = (lo - o[a]) * ivd[a], tb = (hi - o[a]) * ivd[a];
             tlo[a] = fmin(ta, tb);
             thi[a] = fmax(ta, tb);
         }
@@ -837,13 +860,13 @@ __device__ __forceinline__ bool march_init(const DevGrid& S, const double o[3],
             idx[a] = d[a] > 0.0 ? 0 : dims[a] - 1;
         } else {
             double p = o[a] + te * d[a];
-            double f = floor((p - g0[a]) / cell);
+            double f = floor((p - g0[a]) * S.inv_cell);
             f = fmin(fmax(f, 0.0), (double)(dims[a] - 1));
             idx[a] = (int)f;
         }
         p0[a] = stp[a] > 0 ? idx[a] + 1 : idx[a];
         f0[a] = ff_split(stp[a] != 0 ? fma((double)p0[a], cell, g0[a]) - o[a] : 0.0);
-        iv[a] = ff_split(stp[a] != 0 ? 1.0 / d[a] : 0.0);
+        iv[a] = ff_split(ivd[a]);
     }
     m.ix = idx[0]; m.iy = idx[1]; m.iz = idx[2];
     m.sx = stp[0]; m.sy = stp[1]; m.sz = stp[2];
@@ -1160,7 +1183,7 @@ __device__ __forceinline__ void grid_ray(const double o[3], const double d[3], G
         r.of[a] = (float)o[a];
         const float df = (float)d[a];
         r.ivf[a] = df != 0.0f ? 1.0f / df : 1.0e30f;
-        r.iv[a] = d[a] != 0.0 ? 1.0 / d[a] : 0.0;
+        r.iv[a] = d[a] != 0.0 ? rcp64(d[a]) : 0.0;
     }
 }
 
