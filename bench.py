@@ -213,9 +213,9 @@ def algorithmic_bytes(w, layout, subray_outputs=False):
     """Compulsory traffic of one scan launch: every output byte written once,
     every scene byte (BVH nodes, packed triangles, reflectance, voxels) read once."""
     P = layout["total_pulses"]
-    out = layout["waveform_floats"] * 4 + P * (4 + 4 + 1) + layout["echo_elems"] * (4 + 4 + 4 + 4)
+    out = layout["waveform_floats"] * 4 + P * (4 + 4 + 1) + layout["echo_elems"] * (4 + 4 + 4 + 8)
     if subray_outputs:
-        out += layout["subray_elems"] * 8
+        out += layout["subray_elems"] * 12
     scene = 0
     for s in w.scenes:
         n = s.n_triangles
@@ -305,7 +305,7 @@ def run_ours(args, D):
                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                        "algorithmic_bytes_per_launch": alg, "peak_source": kind, "kernel": kern,
                        "bytes_model": "compulsory: every output byte written once (waveform 4*N_b, "
-                                      "window, count, flags, K echoes x 16 B per pulse) plus every "
+                                      "window, count, flags, K echoes x 20 B per pulse) plus every "
                                       "scene byte read once (64 B per BVH node, 52 B per triangle, "
                                       "4 B per voxel); per-subray node/triangle/voxel visit counts "
                                       "are not counted (no counting kernel variant)"}

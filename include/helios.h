@@ -271,9 +271,12 @@ typedef struct {
     float* echo_range;            /* required: metres, range noise included */
     float* echo_amp;              /* optional */
     int32_t* echo_bin;            /* optional: b within the window */
-    int32_t* echo_object;         /* optional: primitive id of the strongest contributor */
+    int64_t* echo_object;         /* optional: primitive id of the strongest contributor
+                                     (triangle id, or n_triangles + voxel id: voxels are
+                                     numbered over the scene's grids in order, so ids can
+                                     exceed 2^31), -1 in unused slots */
     uint8_t* pulse_flags;         /* optional: HELIOS_PF_* */
-    int32_t* subray_hit;          /* optional: event primitive or -1 */
+    int64_t* subray_hit;          /* optional: event primitive (as echo_object) or -1 */
     float* subray_range;          /* optional */
     uint32_t* status;             /* optional: one word, OR-ed HELIOS_ST_* */
     float* echo_width;            /* optional [total_pulses][K]: echo width (Sec. 3.4), the sigma
@@ -387,7 +390,7 @@ HELIOS_API helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_
                                   const helios_scanner_desc* scanners, int32_t n_scanners,
                                   const helios_leg_desc* legs, int32_t n_legs,
                                   const helios_scan_opts* opts, const float* d_waveform,
-                                  const int32_t* window_bin, const int32_t* subray_hit,
+                                  const int32_t* window_bin, const int64_t* subray_hit,
                                   const helios_scene_grads* grads, void* cuda_stream);
 
 /* Number of subrays for beam sample quality q (Sec. 3.4), or -1 if q < 0. */

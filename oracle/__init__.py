@@ -397,7 +397,7 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
     """Simulate the given pulse indices of one leg; returns a dict of numpy arrays
     (with ``echo_width``, the fitted echo widths in ns, Gaussian pulses only).
 
-    ``force_hit`` ([n, S] int32, FREE_HIT where the oracle decides) gives
+    ``force_hit`` ([n, S] int64, FREE_HIT where the oracle decides) gives
     subray events chosen elsewhere (an FP32 path's choices on flagged subrays);
     ``subray_flags`` in the result holds the flags each subray raised, and
     ``rerun(rows, force_hit, fixed_window)`` repeats the scan for a subset of
@@ -412,10 +412,10 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
     r = dict(window_bin=np.zeros(n, np.int32), waveform=np.zeros((n, nb)),
              echo_count=np.zeros(n, np.int32), echo_bin=np.zeros((n, K), np.int32),
              echo_amp=np.zeros((n, K)), echo_range=np.zeros((n, K)),
-             echo_range_clean=np.zeros((n, K)), echo_object=np.zeros((n, K), np.int32),
-             subray_hit=np.zeros((n, S), np.int32), subray_range=np.zeros((n, S)),
+             echo_range_clean=np.zeros((n, K)), echo_object=np.zeros((n, K), np.int64),
+             subray_hit=np.zeros((n, S), np.int64), subray_range=np.zeros((n, S)),
              flags=np.zeros(n, np.uint32), subray_flags=np.zeros((n, S), np.uint32),
-             echo_object_alt=np.zeros((n, K), np.int32))
+             echo_object_alt=np.zeros((n, K), np.int64))
     if echo_width:
         r["echo_width"] = np.zeros((n, K))
     out = Out(**{k: _ptr(v) for k, v in r.items()})
@@ -424,7 +424,7 @@ def scan(oscene: OracleScene, scanner, leg, pulses=None, mode=0, seed=0, fixed_w
         fw = np.ascontiguousarray(fixed_window, dtype=np.int32)
         assert fw.shape == (n,)
     if force_hit is not None:
-        fh = np.ascontiguousarray(force_hit, dtype=np.int32)
+        fh = np.ascontiguousarray(force_hit, dtype=np.int64)
         assert fh.shape == (n, S)
     s, l = scanner_struct(scanner), leg_struct(leg)
     rc = lib().or_scan(oscene.handle, C.byref(s), C.byref(l), _ptr(pulses), n, int(mode),

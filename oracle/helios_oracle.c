@@ -802,7 +802,7 @@ typedef struct {
     int mode;
     uint64_t seed;
     const int32_t* fixed_window;
-    const int32_t* force_hit; /* [n][S] or NULL: events given per subray (OR_FREE_HIT: none) */
+    const int64_t* force_hit; /* [n][S] or NULL: events given per subray (OR_FREE_HIT: none) */
     const or_out* out;
     const double* g;      /* adjoint only */
     int adjoint;
@@ -1265,12 +1265,12 @@ static void simulate_pulse(job_t* J, int64_t row) {
         int64_t ev;
         double R;
         uint32_t sf = 0;
-        int32_t fh = J->force_hit ? J->force_hit[row * S + s] : OR_FREE_HIT;
+        int64_t fh = J->force_hit ? J->force_hit[row * S + s] : OR_FREE_HIT;
         if (fh != OR_FREE_HIT) trace_subray_forced(J, k, s, o, ds, alpha, fh, &sf, &ev, &R);
         else trace_subray(J, k, s, o, ds, alpha, &sf, &ev, &R);
         flags |= sf;
         if (out->subray_flags) out->subray_flags[row * S + s] = sf;
-        if (out->subray_hit) out->subray_hit[row * S + s] = (int32_t)ev;
+        if (out->subray_hit) out->subray_hit[row * S + s] = ev;
         if (out->subray_range) out->subray_range[row * S + s] = R;
     }
     rlist* RL = &J->S.rl;
@@ -1332,12 +1332,12 @@ static void simulate_pulse(job_t* J, int64_t row) {
         int64_t sid = -1;
         int64_t bid = echo_object_list(sn, RL->r, RL->n, tb, &tie, &sid);
         if (tie) flags |= OR_F_OBJ;
-        if (out->echo_object_alt) out->echo_object_alt[row * K + e] = (int32_t)sid;
+        if (out->echo_object_alt) out->echo_object_alt[row * K + e] = sid;
         out->echo_bin[row * K + e] = b;
         out->echo_amp[row * K + e] = W[b];
         out->echo_range_clean[row * K + e] = Rc;
         out->echo_range[row * K + e] = Rc + sn->range_noise_sigma_m * z;
-        out->echo_object[row * K + e] = (int32_t)bid;
+        out->echo_object[row * K + e] = bid;
         if (out->echo_width && sn->pulse_shape == 0) {
             int ftie = 0;
             double sig_b = sn->pulse_fwhm_ns / (2.0 * sqrt(2.0 * log(2.0))) / dt;
@@ -1490,7 +1490,7 @@ static void free_jobs(job_t* jobs, int nt) {
 
 int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
-            const int32_t* fixed_window, const int32_t* force_hit, const or_out* out,
+            const int32_t* fixed_window, const int64_t* force_hit, const or_out* out,
             int n_threads) {
     if (n <= 0) return 0;
     if (sn->max_echoes < 1 || sn->max_echoes > OR_MAX_ECHOES) return -1;

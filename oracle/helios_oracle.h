@@ -82,13 +82,13 @@ typedef struct {
     double* echo_amp;            /* [n][K] */
     double* echo_range;          /* [n][K]     with range noise */
     double* echo_range_clean;    /* [n][K]     without noise */
-    int32_t* echo_object;        /* [n][K]     primitive id (tri, or n_tri + voxel) */
+    int64_t* echo_object;        /* [n][K]     primitive id (tri, or n_tri + voxel) */
     double* echo_width;          /* [n][K]     fitted Gaussian sigma (ns); NULL: no fit */
-    int32_t* subray_hit;         /* [n][S]     event primitive, -1 none */
+    int64_t* subray_hit;         /* [n][S]     event primitive, -1 none */
     double* subray_range;        /* [n][S] */
     uint32_t* flags;             /* [n]        OR_F_* */
     uint32_t* subray_flags;      /* [n][S]     OR_F_* raised by each subray, or NULL */
-    int32_t* echo_object_alt;    /* [n][K]     the runner-up object when within 1e-4 of the
+    int64_t* echo_object_alt;    /* [n][K]     the runner-up object when within 1e-4 of the
                                     echo object's contribution (OR_F_OBJ), else -1; or NULL */
 } or_out;
 
@@ -170,7 +170,7 @@ int64_t or_trace_returns(const or_scene* sc, const or_scanner* sn, const double 
  * written) when max_echoes is outside 1..OR_MAX_ECHOES. */
 int or_scan(const or_scene* sc, const or_scanner* sn, const or_leg* lg,
             const int64_t* pulses, int64_t n, int mode, uint64_t seed,
-            const int32_t* fixed_window, const int32_t* force_hit, const or_out* out,
+            const int32_t* fixed_window, const int64_t* force_hit, const or_out* out,
             int n_threads);
 
 /* adjoint of the expected-mode waveform: g = dL/dW [n][n_bins], window held

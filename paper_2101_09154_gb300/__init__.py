@@ -367,11 +367,11 @@ def alloc_outputs(layout, device, subrays=True, status=True, echo_width=False):
         "echo_range": torch.empty(int(layout["echo_elems"]), dtype=torch.float32, device=device),
         "echo_amp": torch.empty(int(layout["echo_elems"]), dtype=torch.float32, device=device),
         "echo_bin": torch.empty(int(layout["echo_elems"]), dtype=torch.int32, device=device),
-        "echo_object": torch.empty(int(layout["echo_elems"]), dtype=torch.int32, device=device),
+        "echo_object": torch.empty(int(layout["echo_elems"]), dtype=torch.int64, device=device),
         "pulse_flags": torch.empty(P, dtype=torch.uint8, device=device),
     }
     if subrays:
-        out["subray_hit"] = torch.empty(int(layout["subray_elems"]), dtype=torch.int32, device=device)
+        out["subray_hit"] = torch.empty(int(layout["subray_elems"]), dtype=torch.int64, device=device)
         out["subray_range"] = torch.empty(int(layout["subray_elems"]), dtype=torch.float32, device=device)
     if status:
         out["status"] = torch.zeros(1, dtype=torch.int32, device=device)
@@ -491,6 +491,8 @@ def scan_adjoint(scenes, scanners, legs, d_waveform, window_bin, subray_hit=None
     Returns a list (one per scene) of dicts {"reflectance": [...], "density": [...]}.
     """
     torch = _torch()
+    if subray_hit is not None and subray_hit.dtype != torch.int64:
+        raise TypeError("subray_hit must be the forward's int64 primitive ids")
     scenes, scanners, legs = _as_list(scenes), _as_list(scanners), _as_list(legs)
     if grads is None:
         grads = [{"reflectance": [torch.zeros_like(r) for r in s.reflectance],

@@ -27,11 +27,11 @@ struct AdjParams {
     int32_t want_dens[kMaxScenes];   // some grid of the scene takes a density gradient
     const float* g;
     const int32_t* window;
-    const int32_t* subray_hit;
+    const int64_t* subray_hit;
     int32_t n_items, s_cap, pc_cap, nb_cap;
     int32_t cb;              // Gaussian: halo bins of the correlation tables, 0: direct sums
     int32_t ncell;           // table cells per warp (bins -cb-1 .. nb+cb)
-    float* list;             // per-warp voxel return lists [4][rl_cap][32], NULL: none
+    float* list;             // per-warp voxel return lists [5][rl_cap][32], NULL: none
     int32_t rl_cap;
     uint64_t seed;           // the forward's seed (platform noise moves the poses)
 };
@@ -67,24 +67,6 @@ __device__ __forceinline__ float corr_tab(const float4* C4, const __nv_bfloat162
     a = fmaf(d * (1.0f / 3.0f), a, t.z);
     a = fmaf(d * 0.5f, a, t.y);
     return fmaf(d, a, t.x);
-}
-
-// the grid holding voxel vx of the scene's concatenated voxels: its gradient
-// array (NULL: none wanted) and the voxel's index in it
-template <int GK>
-__device__ __forceinline__ void grid_of_voxel(const DevScene& sc, int32_t vx, float*& dd, int32_t& vid) {
-    if (GK == 1 || sc.n_grid == 1) {
-        dd = sc.grid.ddens;
-        vid = vx;
-        return;
-    }
-    int lo = 0, hi = sc.n_grid - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&sc.grids[mid].vox_off) <= vx) lo = mid; else hi = mid - 1;
-    }
-    dd = sc.grids[lo].ddens;
-    vid = vx - __ldg(&sc.grids[lo].vox_off);
 }
 
 template <int GK>
@@ -135,7 +117,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     __nv_bfloat162* C2 = reinterpret_cast<__nv_bfloat162*>(wbuf + 4 * P.ncell);
     float* g = tab ? wbuf + 5 * P.ncell : wbuf;
     const size_t RLs = (size_t)P.rl_cap * 32;
-    float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 4 * RLs : nullptr;
+    float* RL = P.list ? P.list + ((size_t)blockIdx.x * nwarps + warp) * 5 * RLs : nullptr;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t p0 = lg.k_first + (int64_t)item * lg.pulses_per_sub;
         const int pc = (int)min((int64_t)lg.pulses_per_sub, lg.k_first + lg.n_pulses - p0);
@@ -213,8 +195,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 float t32 = 0.0f;
                 if (P.subray_hit) {
                     if (on) {
-                        int32_t gid = P.subray_hit[lg.sub_off + k * S + s];
-                        hit = (gid >= 0 && gid < sc.n_tri) ? __ldg(&sc.tri_index[gid]) : -1;
+                        const int64_t gid = P.subray_hit[lg.sub_off + k * S + s];
+                        hit = (gid >= 0 && gid < sc.n_tri) ? __ldg(&sc.tri_index[(int32_t)gid]) : -1;
                     }
                     if (hit >= 0) t32 = plane_t32(sc, hit, f.oh, dh);
                 } else {
@@ -241,7 +223,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 const bool grid = GK > 0 && sc.has_grid != 0;
                 // ---- pass A: march once, grid after grid in entry order; total
                 // of A_k w_k, and each voxel's terms in the lane's list
-                // [voxel, G A T l e^{-sigma l}, G l, A w] ----
+                // [voxel, G A T l e^{-sigma l}, G l, A w, grid] ----
                 FF total = {0.0f, 0.0f};     // float-float: suffixes are differences of it
                 float T = 1.0f;
                 uint32_t fl = 0;
@@ -268,10 +250,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                                               amp(ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l));
                                     ff_acc(total, A * w);
                                     if (listing && n < P.rl_cap) {
-                                        // the voxel's index over all of the scene's grids
+                                        // the voxel's index in its grid (and, with several
+                                        // grids, the grid's index in the scene)
                                         const size_t e = (size_t)n * 32 + lane;
-                                        __stcg(reinterpret_cast<int32_t*>(RL) + e,
-                                               (GK == 1 ? 0 : G.vox_off) + (int32_t)v.vid);
+                                        __stcg(reinterpret_cast<int32_t*>(RL) + e, (int32_t)v.vid);
+                                        if (GK == 2)
+                                            __stcg(reinterpret_cast<int32_t*>(RL + 4 * RLs) + e, (int32_t)(&G - sc.grids));
                                         __stcg(RL + RLs + e, Gs * A * T * len * a);
                                         __stcg(RL + 2 * RLs + e, Gs * len);
                                         __stcg(RL + 3 * RLs + e, A * w);
@@ -305,9 +289,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                         const float gl = __ldcg(RL + 2 * RLs + o2);
                         const float aw = __ldcg(RL + 3 * RLs + o2);
                         float* dd = ddens1;
-                        int32_t vid = vx;
-                        if (GK == 2) grid_of_voxel<GK>(sc, vx, dd, vid);
-                        if (dd) atomicAdd(&dd[vid], fmaf(-gl, suffix, t1));
+                        if (GK == 2)
+                            dd = sc.grids[__ldcg(reinterpret_cast<const int32_t*>(RL + 4 * RLs) + o2)].ddens;
+                        if (dd) atomicAdd(&dd[vx], fmaf(-gl, suffix, t1));
                         suffix += aw;
                     }
                     continue;
@@ -405,7 +389,7 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st) {
         if (sc.n_grid > 0 && L.want_dens[lg.scene]) {
             p->rl_cap = kReturnListCap;
             e = cudaMallocAsync(reinterpret_cast<void**>(&list),
-                                (size_t)grid * (L.threads / 32) * 4 * p->rl_cap * 32 * sizeof(float), st);
+                                (size_t)grid * (L.threads / 32) * 5 * p->rl_cap * 32 * sizeof(float), st);
             if (e != cudaSuccess) { delete p; return set_cuda_error("cudaMallocAsync(adjoint lists)", e); }
             p->list = list;
         }

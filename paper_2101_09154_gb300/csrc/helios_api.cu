@@ -291,7 +291,7 @@ static helios_status build_grids(helios_scene* s, const helios_scene_desc* desc,
         d.opaque = g.opaque != 0;
         d.G = g.G;
         d.leaf_refl = g.leaf_reflectance;
-        d.vox_off = (int32_t)vox;
+        d.vox_off = vox;
         vox += (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
         if (g.lad_table) {
             // leaf-angle table: read (host or device memory), checked, copied
@@ -492,10 +492,12 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
         if (!g.density) return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: density is NULL", i);
         if (g.lad_table && (g.lad_n < 2 || g.lad_n > 65536))
             return set_error(HELIOS_ERR_INVALID_ARG, "grid %d: lad_n must be in 2..65536", i);
-        n_vox += (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
-        if (n_tri + n_vox >= (int64_t)INT32_MAX) break;
+        const int64_t nv = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+        // within a grid the kernels index voxels (after the triangles) in 32 bits
+        if (n_tri + nv >= (int64_t)INT32_MAX)
+            return set_error(HELIOS_ERR_UNSUPPORTED, "grid %d: triangles + its voxels exceed 2^31 - 1", i);
+        n_vox += nv;
     }
-    if (n_tri + n_vox >= (int64_t)INT32_MAX) return set_error(HELIOS_ERR_UNSUPPORTED, "too many primitives for 32-bit ids");
     helios_status r = check_grid_boxes(desc->grids, desc->n_grids);
     if (r != HELIOS_OK) return r;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -671,7 +673,7 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
                                   const helios_scanner_desc* scanners, int32_t n_scanners,
                                   const helios_leg_desc* legs, int32_t n_legs,
                                   const helios_scan_opts* opts, const float* d_waveform,
-                                  const int32_t* window_bin, const int32_t* subray_hit,
+                                  const int32_t* window_bin, const int64_t* subray_hit,
                                   const helios_scene_grads* grads, void* cuda_stream) {
     g_err.clear();
     CallRange range_("helios_scan_adjoint");
@@ -971,8 +973,8 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
     size_t off[11], bytes = 0;
     const size_t sz[11] = {sizeof(float) * mx_w, sizeof(int32_t) * mx_p, sizeof(int32_t) * mx_p,
                            sizeof(float) * mx_e, H.echo_amp ? sizeof(float) * mx_e : 0,
-                           H.echo_bin ? sizeof(int32_t) * mx_e : 0, H.echo_object ? sizeof(int32_t) * mx_e : 0,
-                           H.pulse_flags ? sizeof(uint8_t) * mx_p : 0, sub ? sizeof(int32_t) * mx_s : 0,
+                           H.echo_bin ? sizeof(int32_t) * mx_e : 0, H.echo_object ? sizeof(int64_t) * mx_e : 0,
+                           H.pulse_flags ? sizeof(uint8_t) * mx_p : 0, sub ? sizeof(int64_t) * mx_s : 0,
                            H.subray_range ? sizeof(float) * mx_s : 0,
                            H.echo_width ? sizeof(float) * mx_e : 0};
     for (int i = 0; i < 11; ++i) { off[i] = bytes; bytes += align256(sz[i]); }
@@ -1011,9 +1013,9 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
         L.out.echo_range = reinterpret_cast<float*>(base + off[3]);
         L.out.echo_amp = H.echo_amp ? reinterpret_cast<float*>(base + off[4]) : nullptr;
         L.out.echo_bin = H.echo_bin ? reinterpret_cast<int32_t*>(base + off[5]) : nullptr;
-        L.out.echo_object = H.echo_object ? reinterpret_cast<int32_t*>(base + off[6]) : nullptr;
+        L.out.echo_object = H.echo_object ? reinterpret_cast<int64_t*>(base + off[6]) : nullptr;
         L.out.pulse_flags = H.pulse_flags ? reinterpret_cast<uint8_t*>(base + off[7]) : nullptr;
-        L.out.subray_hit = sub ? reinterpret_cast<int32_t*>(base + off[8]) : nullptr;
+        L.out.subray_hit = sub ? reinterpret_cast<int64_t*>(base + off[8]) : nullptr;
         L.out.subray_range = H.subray_range ? reinterpret_cast<float*>(base + off[9]) : nullptr;
         L.out.status = H.status;
         L.out.echo_width = H.echo_width ? reinterpret_cast<float*>(base + off[10]) : nullptr;
@@ -1043,9 +1045,9 @@ extern "C" helios_status helios_scan_legs_host(helios_scene* const* scenes, int3
             {H.echo_range + lo.e, L.out.echo_range, sizeof(float) * (hi.e - lo.e)},
             {H.echo_amp ? H.echo_amp + lo.e : nullptr, L.out.echo_amp, sizeof(float) * (hi.e - lo.e)},
             {H.echo_bin ? H.echo_bin + lo.e : nullptr, L.out.echo_bin, sizeof(int32_t) * (hi.e - lo.e)},
-            {H.echo_object ? H.echo_object + lo.e : nullptr, L.out.echo_object, sizeof(int32_t) * (hi.e - lo.e)},
+            {H.echo_object ? H.echo_object + lo.e : nullptr, L.out.echo_object, sizeof(int64_t) * (hi.e - lo.e)},
             {H.pulse_flags ? H.pulse_flags + lo.p : nullptr, L.out.pulse_flags, sizeof(uint8_t) * (hi.p - lo.p)},
-            {sub ? H.subray_hit + lo.s : nullptr, L.out.subray_hit, sizeof(int32_t) * (hi.s - lo.s)},
+            {sub ? H.subray_hit + lo.s : nullptr, L.out.subray_hit, sizeof(int64_t) * (hi.s - lo.s)},
             {H.subray_range ? H.subray_range + lo.s : nullptr, L.out.subray_range, sizeof(float) * (hi.s - lo.s)},
             {H.echo_width ? H.echo_width + lo.e : nullptr, L.out.echo_width, sizeof(float) * (hi.e - lo.e)}};
         for (const Copy& x : cp) {

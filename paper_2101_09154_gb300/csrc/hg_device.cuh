@@ -57,8 +57,7 @@ struct DevGrid {
     int32_t bdims[3];           // bricks of kBrick^3 voxels per axis
     int32_t lad_n;              // 0: constant G
     float G, leaf_refl;
-    int32_t vox_off;            // voxels of the scene's earlier grids
-    int32_t pad;
+    int64_t vox_off;            // voxels of the scene's earlier grids
     double inv_cell;            // 1 / cell, formed in FP64 on the host
 };
 
@@ -141,9 +140,9 @@ struct Outputs {
     float* echo_range;
     float* echo_amp;
     int32_t* echo_bin;
-    int32_t* echo_object;
+    int64_t* echo_object;
     uint8_t* pulse_flags;
-    int32_t* subray_hit;
+    int64_t* subray_hit;
     float* subray_range;
     uint32_t* status;
     float* echo_width;           // optional: fitted echo sigma (ns), Gaussian pulses

@@ -65,7 +65,7 @@ struct AdjointLaunch {
     std::vector<int32_t> want_dens;       // some grid of the scene takes a density gradient
     const float* g;
     const int32_t* window;
-    const int32_t* subray_hit;
+    const int64_t* subray_hit;
     uint64_t seed;
     int threads;
 };

@@ -24,7 +24,8 @@ namespace hg {
 struct RayRes {
     float Rh, Rl;    // event range (stochastic) / triangle range (expected), hi + lo
     float P;         // return power (expected mode: triangle power at unit weight)
-    int32_t id;      // event primitive / triangle id; -1: none
+    int32_t id;      // event primitive: triangle id, or n_tri + the voxel's index within its
+                     // grid (several grids: the grid's index in a per-ray array); -1: none
 };
 
 template <int NL>
@@ -61,9 +62,9 @@ __device__ __forceinline__ void accumulate(float* W, int nb, const DevScanner& s
     for (int b = blo + lane; b <= bhi; b += 32) W[b] += P * pulse_shape(sn, (float)b * dt - tau);
 }
 
-__device__ __forceinline__ void accumulate_best(float* W, float* best, int32_t* bid, int nb,
+__device__ __forceinline__ void accumulate_best(float* W, float* best, int64_t* bid, int nb,
                                                 const DevScanner& sn, float dt, float tau,
-                                                float P, int32_t id, int lane) {
+                                                float P, int64_t id, int lane) {
     int blo = max(0, __float2int_rd((tau - sn.cut_lo) * sn.inv_bin));
     int bhi = min(nb - 1, __float2int_ru((tau + sn.cut_hi) * sn.inv_bin));
     for (int b = blo + lane; b <= bhi; b += 32) {
@@ -108,7 +109,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
                         const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
                         emit(t_in, T * return_power(sn, t_in.hi + t_in.lo, c.tan_a, G.leaf_refl,
                                                     ax >= 0 ? fabsf(dh[ax]) : 1.0f),
-                             sc.n_tri + G.vox_off + (int32_t)v.vid);
+                             (int64_t)sc.n_tri + G.vox_off + v.vid);
                         stopped = true;
                         return false;
                     }
@@ -118,7 +119,7 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
                         T *= expf(-xs);
                         FF R = ff_add_f(t_in, 0.5f * len);
                         emit(R, w * return_power(sn, R.hi + R.lo, c.tan_a, G.leaf_refl, 1.0f),
-                             sc.n_tri + G.vox_off + (int32_t)v.vid);
+                             (int64_t)sc.n_tri + G.vox_off + v.vid);
                     }
                 }
                 // several grids (sparse trees): an empty brick is crossed in one jump
@@ -139,7 +140,9 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_r2 + (MODE == 1 ? P.rays_cap : 0));
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
-    uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_tau + P.rays_cap);
+    // several grids, stochastic mode: the grid of each ray's voxel event
+    int32_t* s_rg = reinterpret_cast<int32_t*>(s_tau + P.rays_cap);
+    uint32_t* s_pflag = reinterpret_cast<uint32_t*>(s_rg + (MODE == 0 && GK == 2 ? P.rays_cap : 0));
     float* s_noise = reinterpret_cast<float*>(s_pflag + P.pc_cap);   // [pc_cap][2]
     float* s_pk = s_noise + 2 * P.pc_cap;                              // [pk_cap]
     // stochastic mode: p(k bin) (1, He_1, He_2, He_3 of k bin/sigma, over sigma^n), |k| <= ht_cb
@@ -181,6 +184,11 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         const DevScanner& sn = P.scanners[lg.scanner];
         const DevScene& sc = P.scenes[lg.scene];
         const int S = lg.S;
+        // 64-bit id of ray r's event (rays of the batch in order)
+        auto ray_id64 = [&](int r, int32_t id32) -> int64_t {
+            if (GK == 2 && MODE == 0 && id32 >= sc.n_tri) return (int64_t)id32 + __ldg(&sc.grids[s_rg[r]].vox_off);
+            return id32;
+        };
         const int64_t p0 = lg.k_first + (int64_t)(item - lg.item_begin) * lg.pulses_per_item;
         const int pc = (int)min((int64_t)lg.pulses_per_item, lg.k_first + lg.n_pulses - p0);
         const int nb = sn.n_bins;
@@ -321,6 +329,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
                     }
                     bool voxel_event = false;
+                    int64_t id_off = 0;      // voxel event: the grid's first voxel id
                     if (GK > 0 && sc.has_grid) {
                         double o[3], d[3];
                         for (int a = 0; a < 3; ++a) {
@@ -346,7 +355,9 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                             const int ax = m.entry_axis >= 0 ? m.entry_axis : m.face0;
                                             rr.Rh = t_in.hi;
                                             rr.Rl = t_in.lo;
-                                            rr.id = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                            rr.id = sc.n_tri + (int32_t)v.vid;
+                                            id_off = G.vox_off;
+                                            if (GK == 2) s_rg[r] = (int32_t)(&G - sc.grids);
                                             rr.P = return_power(sn, t_in.hi + t_in.lo, tan_a, G.leaf_refl,
                                                                 ax >= 0 ? fabsf(dh[ax]) : 1.0f);
                                             voxel_event = true;
@@ -369,7 +380,9 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                                 FF R = ff_add_f(t_in, sdist);
                                                 rr.Rh = R.hi;
                                                 rr.Rl = R.lo;
-                                                rr.id = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                                rr.id = sc.n_tri + (int32_t)v.vid;
+                                                id_off = G.vox_off;
+                                                if (GK == 2) s_rg[r] = (int32_t)(&G - sc.grids);
                                                 rr.P = return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f);
                                                 voxel_event = true;
                                                 return false;
@@ -398,7 +411,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     if (fl) atomicOr(&s_pflag[pl], fl);
                     if (P.out.subray_hit) {
                         int64_t so = lg.sub_off + (p0 + pl) * S + s;
-                        P.out.subray_hit[so] = rr.id;
+                        P.out.subray_hit[so] = rr.id >= 0 ? (voxel_event ? (int64_t)rr.id + id_off : rr.id) : -1;
                         if (P.out.subray_range) P.out.subray_range[so] = rr.id >= 0 ? rr.Rh + rr.Rl : 0.0f;
                     }
                 }
@@ -410,7 +423,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             float* W = s_w + (size_t)warp * P.w_stride;
             const bool mom_path = MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0;
             float* best = W + nbw;
-            int32_t* bid = reinterpret_cast<int32_t*>(W + 2 * nbw);
+            int64_t* bid = reinterpret_cast<int64_t*>(W + 2 * nbw);
             for (int pl = sb + warp; pl < pe; pl += nwarps) {
                 const int64_t k = p0 + pl;
                 const int64_t gp = lg.pulse_off + k;
@@ -602,11 +615,12 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (s >= S) continue;
                         if (s0 > 0) {
                             if (n_rl < P.rl_cap)
-                                __stcg(RL + (size_t)n_rl * 32 + lane, make_float4(0.f, 0.f, __int_as_float(-1), 0.f));
+                                __stcg(RL + (size_t)n_rl * 32 + lane,
+                                       make_float4(0.f, 0.f, __int_as_float(-1), __int_as_float(-1)));
                             ++n_rl;
                         }
                         expected_returns<GK>(sc, sn, f, s_sc[s], rrp[s], fl,
-                                               [&](const FF& R, float Pw, int32_t id) {
+                                               [&](const FF& R, float Pw, int64_t id) {
                             float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                             float jf = rintf(tau * sn.inv_bin);
                             if (!(jf >= (float)(-cb - 1) && jf <= (float)(nb + cb))) return;
@@ -614,7 +628,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             float a = Pw * scale;
                             int c = (int)jf + cb + 1;
                             if (n_rl < P.rl_cap)
-                                __stcg(RL + (size_t)n_rl * 32 + lane, make_float4(tau, Pw, __int_as_float(id), 0.f));
+                                __stcg(RL + (size_t)n_rl * 32 + lane,
+                                       make_float4(tau, Pw, __int_as_float((int32_t)id), __int_as_float((int32_t)(id >> 32))));
                             ++n_rl;
                             atomicAdd(Mu + c, (unsigned long long)llrintf(a));
                             atomicAdd(Mu + ncell + c, (unsigned long long)llrintf(a * dl));
@@ -729,7 +744,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         while (__any_sync(full, on)) {
                             bool has = false;
                             float tau = 0.0f, pv = 0.0f;
-                            int32_t vid = 0;
+                            int64_t vid = 0;
                             while (on) {
                                 const DevGrid& G = GK == 1 ? sc.grid : *Gp;
                                 VoxSeg v;
@@ -745,7 +760,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         pv = T * return_power(sn, t_in.hi + t_in.lo, tan_a, G.leaf_refl,
                                                               ax >= 0 ? dabs[ax] : 1.0f);
                                         tau = ff_mul_sub(t_in, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                        vid = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                        vid = (int64_t)sc.n_tri + G.vox_off + v.vid;
                                         has = true;
                                         T = 0.0f;
                                         on = false;
@@ -758,7 +773,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         FF R = ff_add_f(t_in, 0.5f * len);
                                         pv = w * return_power(sn, R.hi + R.lo, tan_a, G.leaf_refl, 1.0f);
                                         tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
-                                        vid = sc.n_tri + G.vox_off + (int32_t)v.vid;
+                                        vid = (int64_t)sc.n_tri + G.vox_off + v.vid;
                                         has = true;
                                     }
                                 }
@@ -775,7 +790,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 hm &= hm - 1;
                                 float tb = __shfl_sync(full, tau, src);
                                 float pb = __shfl_sync(full, pv, src);
-                                int32_t ib = __shfl_sync(full, vid, src);
+                                int64_t ib = __shfl_sync(full, vid, src);
                                 accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
                             }
                         }
@@ -789,7 +804,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             hm &= hm - 1;
                             float tb = __shfl_sync(full, ttau, src);
                             float pb = __shfl_sync(full, tp, src);
-                            int32_t ib = __shfl_sync(full, rr.id, src);
+                            int64_t ib = __shfl_sync(full, (int64_t)rr.id, src);
                             accumulate_best(W, best, bid, nb, sn, dt, tb, pb, ib, lane);
                         }
                     }
@@ -811,7 +826,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     bool ismax = in && c > l && c >= rgt && c >= thr && c > 0.0f;
                     unsigned mk = __ballot_sync(full, ismax);
                     int pos = count + __popc(mk & lanemask_lt());
-                    int32_t obj = -1;
+                    int64_t obj = -1;
                     if (MODE == 0 && S <= 32 && P.out.echo_object) {
                         // each echo's object: the subray with the largest contribution
                         // at the echo bin (ties to the lower subray), one lane per subray
@@ -822,12 +837,12 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             if (count + __popc(mk & ((1u << src) - 1u)) >= K) break;
                             const float tbin = (float)(base + src) * dt;
                             unsigned key = 0u;       // 0: no return; else order of the value
-                            int32_t id = -1;
+                            int64_t id = -1;
                             if (lane < S) {
                                 const RayRes rr = rrp[lane];
                                 if (rr.id >= 0) {
                                     key = __float_as_uint(rr.P * pulse_shape(sn, tbin - taup[lane])) + 1u;
-                                    id = rr.id;
+                                    id = ray_id64((pl - sb) * S + lane, rr.id);
                                 }
                             }
                             const unsigned kmax = __reduce_max_sync(full, key);
@@ -847,7 +862,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 RayRes rr = rrp[s];
                                 if (rr.id < 0) continue;
                                 float v = rr.P * pulse_shape(sn, tbin - taup[s]);
-                                if (v > bv) { bv = v; obj = rr.id; }
+                                if (v > bv) { bv = v; obj = ray_id64((pl - sb) * S + s, rr.id); }
                             }
                         }
                         // echo range in FP32: (m + b) bin - offset is exact or within 1 ulp,
@@ -881,7 +896,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     const PulseFF& f = s_pf[pl];
                     for (int e0 = 0; e0 < ne; e0 += 4) {
                         float tbin[4], bv[4];
-                        int bs[4], bo[4];
+                        int bs[4];
+                        int64_t bo[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             tbin[i] = e0 + i < ne ? (float)ebin[e0 + i] * dt : 1.0e30f;
@@ -889,7 +905,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             bs[i] = INT_MAX;
                             bo[i] = -1;
                         }
-                        auto consider = [&](float tau, float Pw, int32_t id, int s) {
+                        auto consider = [&](float tau, float Pw, int64_t id, int s) {
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 float x = tbin[i] - tau;
@@ -909,7 +925,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 const float4 q = q0;
                                 q0 = q1;
                                 if (e + 2 < n_rl) q1 = __ldcg(RL + (size_t)(e + 2) * 32 + lane);
-                                const int32_t id = __float_as_int(q.z);
+                                const int64_t id = (int64_t)(uint32_t)__float_as_int(q.z) |
+                                                   ((int64_t)__float_as_int(q.w) << 32);
                                 if (id < 0) { s += 32; continue; }
                                 consider(q.x, q.y, id, s);
                             }
@@ -919,7 +936,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 if (s >= S) continue;
                                 uint32_t fl2 = 0;
                                 expected_returns<GK>(sc, sn, f, s_sc[s], rrp[s], fl2,
-                                                       [&](const FF& R, float Pw, int32_t id) {
+                                                       [&](const FF& R, float Pw, int64_t id) {
                                     const float tau = ff_mul_sub(R, kDelayHi, kDelayLo, mdt_h, mdt_l);
                                     if (!(rintf(tau * sn.inv_bin) >= (float)(-P.mom_cb - 1) &&
                                           rintf(tau * sn.inv_bin) <= (float)(nb + P.mom_cb)))
@@ -933,7 +950,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             for (int o = 16; o > 0; o >>= 1) {
                                 float ov = __shfl_xor_sync(full, bv[i], o);
                                 int os = __shfl_xor_sync(full, bs[i], o);
-                                int oo = __shfl_xor_sync(full, bo[i], o);
+                                int64_t oo = __shfl_xor_sync(full, bo[i], o);
                                 if (ov > bv[i] || (ov == bv[i] && os < bs[i])) { bv[i] = ov; bs[i] = os; bo[i] = oo; }
                             }
                         }
@@ -1120,16 +1137,17 @@ static helios_status dispatch(const ScanParams<NL>& p, int mode, int gk, int thr
 // the best-contributor arrays of the direct path or the moment tile
 static int warp_stride(int mode, int nb_cap, int cb, bool direct) {
     if (mode != 1) return nb_cap;
-    int extra = direct ? 2 * nb_cap : 0;
+    int extra = direct ? 3 * nb_cap : 0;        // best contribution (float) + its id (int64)
     if (cb > 0) extra = max(extra, 4 * (128 + 2 * cb));
     return nb_cap + extra;
 }
 
-static size_t smem_bytes(int mode, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads,
+static size_t smem_bytes(int mode, int gk, int pc_cap, int s_cap, int rays_cap, int nb_cap, int threads,
                          int pk_cap = 0, int cb = 0, bool direct = true) {
     size_t b = (sizeof(RayRes) + (mode == 1 ? sizeof(float2) : 0)) * rays_cap +
                sizeof(PulseFF) * pc_cap + sizeof(SubrayConst) * s_cap +
-               sizeof(float) * rays_cap + sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
+               sizeof(float) * rays_cap + (mode == 0 && gk == 2 ? sizeof(int32_t) * rays_cap : 0) +
+               sizeof(uint32_t) * pc_cap + 2 * sizeof(float) * pc_cap +
                sizeof(float) * pk_cap + sizeof(int32_t) * (size_t)pc_cap * (kConeCap + 1);
     b = (b + 15) & ~size_t(15);
     b += (size_t)(threads / 32) * warp_stride(mode, nb_cap, cb, direct) * sizeof(float);
@@ -1184,7 +1202,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         if (ht_cb > 256) ht_cb = 0;
     }
     const int pk_cap = cb > 0 ? 2 * cb + 1 : (ht_cb > 0 ? 4 * (2 * ht_cb + 1) + 4 : 0);
-    size_t smem = smem_bytes(L.mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb, direct);
+    size_t smem = smem_bytes(L.mode, gk, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, cb, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     long long* mom = nullptr;
     float4* rlist = nullptr;
@@ -1400,7 +1418,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
     }
     const int pk_cap = ht_cb > 0 ? 4 * (2 * ht_cb + 1) + 4 : 0;
     const bool direct = mode == 1;
-    size_t smem = smem_bytes(mode, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, 0, direct);
+    size_t smem = smem_bytes(mode, gk, pc_cap, s_cap, rays_cap, nb_cap, threads, pk_cap, 0, direct);
     if (smem > 227 * 1024) return set_error(HELIOS_ERR_UNSUPPORTED, "work item needs %zu bytes of shared memory", smem);
     if (n_groups == 0) return HELIOS_OK;
     // the echo-width fit runs after the scan, from the stored rows and bins

@@ -520,14 +520,14 @@ def urban_scene(rng, length=2000.0, facade_cell=0.17, ground_cell=1.0, half_widt
     return Scene(meshes=[street, buildings])
 
 
-def urban_trees(rng, length=2000.0, n_trees=2000, n=96, cell=60.0 / 1024.0):
+def urban_trees(rng, length=2000.0, n_trees=2000, n=128, cell=45.0 / 1024.0):
     """Slots for street trees: boxes n*cell wide packed end to end along x in
     six rows, one on each sidewalk (|y| in [0.75, 0.75 + n cell]) and two
     behind each side's buildings (from |y| = 34.25); ``n_trees`` of them,
-    chosen at random, get a voxel tree.  The cell (60/1024 m: 96 voxels make
+    chosen at random, get a voxel tree.  The cell (45/1024 m: 128 voxels make
     a 5.625 m box) and the slot corners are exact in FP32, so neighbouring
-    boxes touch without overlapping.  2000 trees of 96^3 are 1.77e9 voxels,
-    within the 32-bit primitive ids (2000 of 128^3 would not be)."""
+    boxes touch without overlapping.  2000 trees of 128^3 are 4.19e9 voxels
+    (primitive ids are 64-bit)."""
     L = n * cell
     per_row = int(length // L)
     rows = [(0.75, 1.0), (34.25, 1.0), (34.25 + L, 1.0), (0.75, -1.0), (34.25, -1.0), (34.25 + L, -1.0)]
@@ -545,7 +545,7 @@ def urban_mls(seed: int = 4, length: float = 2000.0, speed: float = 10.0, prf: f
     """Mobile laser scanning along an urban street: a profile scanner (head
     rotating 100 rev/s, its spin plane across the street) on a vehicle at
     2.5 m driving ``length`` metres at ``speed``; ``n_trees`` voxel trees
-    (96^3 at 60/1024 m, one grid each) line the street."""
+    (128^3 at 45/1024 m, one grid each) line the street."""
     rng = np.random.default_rng(seed)
     scene = urban_scene(rng, length=length, facade_cell=facade_cell)
     if n_trees > 0:
@@ -562,7 +562,7 @@ def urban_mls(seed: int = 4, length: float = 2000.0, speed: float = 10.0, prf: f
     nt = len(scene.grids)
     return Workload(f"urban_mls_{scene.n_triangles}tri_{nt}trees_{n_pulses}p", [scene], [sc], [leg],
                     note=f"street + extruded buildings ({scene.n_triangles} triangles, facade cell "
-                         f"{facade_cell} m), {nt} voxel trees (96^3 at 0.059 m), {length:.0f} m at "
+                         f"{facade_cell} m), {nt} voxel trees (128^3 at 0.044 m), {length:.0f} m at "
                          f"{speed} m/s, profile head 100 rev/s, PRF {prf/1e3:.0f} kHz, q={q}, N_b={n_bins}")
 
 

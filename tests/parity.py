@@ -72,7 +72,7 @@ def _rerun_flagged(g, ref):
     rows = np.nonzero((sf != 0).any(axis=1) | ((f & oracle.F_WIN) != 0))[0]
     if rows.size == 0:
         return ref, 0
-    force = np.where(sf[rows] != 0, g["subray_hit"][rows], oracle.FREE_HIT).astype(np.int32)
+    force = np.where(sf[rows] != 0, g["subray_hit"][rows], oracle.FREE_HIT).astype(np.int64)
     a = ref["rerun"](rows, force_hit=force)
     bad = np.nonzero(a["flags"] & oracle.F_FORCED_BAD)[0]
     assert bad.size == 0, (f"GPU subray events that no flagged decision allows on pulse rows "

@@ -326,6 +326,35 @@ def test_autograd_function_every_mesh_and_grid(hg):
         t.requires_grad_(False)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_voxel_ids_beyond_32_bits(hg, mode):
+    """1030 voxel trees of 128^3 in a row (one shared density template), so
+    the last trees' voxel ids exceed 2^31: a TLS scan of the last three trees
+    against the oracle, ids compared as 64-bit integers."""
+    rng = np.random.default_rng(11)
+    n, cell, n_trees = 128, 45.0 / 1024.0, 1030
+    L = n * cell
+    dens = scenes.tree_density(rng, n)
+    grids = [scenes.VoxelGrid(origin=(i * L, 0.0, 0.0), cell=cell, dims=(n, n, n), density=dens)
+             for i in range(n_trees)]
+    x_end = n_trees * L
+    pv = np.array([[x_end - 40, -20, 0], [x_end + 20, -20, 0], [x_end + 20, 26, 0], [x_end - 40, 26, 0]],
+                  np.float32)
+    ground = scenes.Mesh(pv, np.array([[0, 1, 2], [0, 2, 3]], np.int32), np.array([0.3, 0.35], np.float32))
+    scene = scenes.Scene(meshes=[ground], grids=grids)
+    sc = scenes.Scanner(deflector=scenes.DEFL_TLS_GRID, grid_n_az=40, grid_n_el=30,
+                        el_min_rad=-1.45, el_max_rad=-0.5, n_bins=512, beam_sample_quality=1)
+    leg = scenes.Leg(n_pulses=1200, leg_id=9, start=(x_end - 1.5 * L, L / 2, 9.0))
+    w = scenes.Workload("ids64", [scene], [sc], [leg])
+    _, _, res = run_both(hg, w, mode=mode, seed=5)
+    g, ref = res[0]
+    stats = compare(g, ref, expected_mode=(mode == 1))
+    first_last = 1 + (n_trees - 3) * n ** 3       # n_tri + voxels before the third-last tree
+    hit = ref["subray_hit"] if mode == 0 else ref["echo_object"]
+    assert (hit >= first_last).sum() > 100 and hit.max() > 2 ** 31
+    assert stats["echoes"] > 500
+
+
 @pytest.mark.slow
 def test_als_full_size_sampled(hg):
     """The 3M-triangle ALS workload with 4M pulses in the benchmark's launch

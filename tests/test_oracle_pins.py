@@ -1271,7 +1271,7 @@ def test_forcing_the_oracles_own_events_reproduces_the_scan(kind):
     assert np.array_equal(np.bitwise_or.reduce(r["subray_flags"], axis=1) & oracle.F_SUBRAY,
                           r["flags"] & oracle.F_SUBRAY)
     rows = np.nonzero(flagged.any(axis=1))[0]
-    fh = np.where(flagged[rows], r["subray_hit"][rows], oracle.FREE_HIT).astype(np.int32)
+    fh = np.where(flagged[rows], r["subray_hit"][rows], oracle.FREE_HIT).astype(np.int64)
     r2 = r["rerun"](rows, force_hit=fh)
     assert not (r2["flags"] & oracle.F_FORCED_BAD).any()
     for k in ("window_bin", "echo_count", "echo_bin", "echo_object", "subray_hit"):
@@ -1291,7 +1291,7 @@ def test_forced_events_at_an_edge_and_implausible_ones():
     assert r["subray_flags"][0, 0] & oracle.F_EDGE
     mine = r["subray_hit"][0, 0]
     other = 1 - mine
-    r2 = r["rerun"]([0], force_hit=np.array([[other]], np.int32))
+    r2 = r["rerun"]([0], force_hit=np.array([[other]], np.int64))
     assert not (r2["flags"][0] & oracle.F_FORCED_BAD)
     assert r2["subray_hit"][0, 0] == other
     assert abs(r2["subray_range"][0, 0] - r["subray_range"][0, 0]) < 1e-9
@@ -1301,7 +1301,7 @@ def test_forced_events_at_an_edge_and_implausible_ones():
     r = oracle.scan(osc, sc, leg2, mode=0, seed=1)
     assert r["subray_flags"][0, 0] == 0
     for bad in (1 - r["subray_hit"][0, 0], -1, osc.n_tri + 3):
-        r3 = r["rerun"]([0], force_hit=np.array([[bad]], np.int32))
+        r3 = r["rerun"]([0], force_hit=np.array([[bad]], np.int64))
         assert r3["flags"][0] & oracle.F_FORCED_BAD, bad
 
 
@@ -1320,12 +1320,12 @@ def test_forced_voxel_stop_and_pass():
     clean = (r["subray_flags"][:, 0] == 0)
     # a pulse that stopped in a voxel, forced to the ground instead
     i = np.nonzero(stop & clean)[0][0]
-    r3 = r["rerun"]([i], force_hit=np.array([[0]], np.int32))
-    r4 = r["rerun"]([i], force_hit=np.array([[1]], np.int32))
+    r3 = r["rerun"]([i], force_hit=np.array([[0]], np.int64))
+    r4 = r["rerun"]([i], force_hit=np.array([[1]], np.int64))
     assert (r3["flags"][0] | r4["flags"][0]) & oracle.F_FORCED_BAD
     # a pulse that reached the ground, forced to stop in the first voxel it crossed
     j = np.nonzero(~stop & clean)[0][0]
     o, d = oracle.pulse_ray(sc, leg, j, seed=4)
     vid, _, _ = osc.march(o, d)
-    r5 = r["rerun"]([j], force_hit=np.array([[osc.n_tri + vid[0]]], np.int32))
+    r5 = r["rerun"]([j], force_hit=np.array([[osc.n_tri + vid[0]]], np.int64))
     assert r5["flags"][0] & oracle.F_FORCED_BAD

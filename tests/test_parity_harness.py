@@ -45,7 +45,7 @@ def test_other_choice_on_flagged_subrays_is_accepted():
     flagged = (r["subray_flags"] & oracle.F_SUBRAY) != 0
     assert flagged.sum() >= 3
     # the GPU stand-in took the other triangle of the diagonal on flagged subrays
-    other = np.where(flagged, 1 - r["subray_hit"], oracle.FREE_HIT).astype(np.int32)
+    other = np.where(flagged, 1 - r["subray_hit"], oracle.FREE_HIT).astype(np.int64)
     rows = np.nonzero(flagged.any(axis=1))[0]
     alt = r["rerun"](rows, force_hit=other[rows])
     assert not (alt["flags"] & oracle.F_FORCED_BAD).any()
