@@ -131,8 +131,11 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
     if (rr.id >= 0) emit(ff_norm(rr.Rh, rr.Rl), T * rr.P, rr.id);
 }
 
+// The expected-mode several-grid variant would take 245 registers (one block
+// per SM); capped at two blocks per SM it spills a little but runs 8% faster
+// (urban MLS).  Every other variant keeps the compiler's own choice.
 template <int MODE, int GK, int NL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (MODE == 1 && GK == 2) ? 2 : 0)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     RayRes* s_rr = reinterpret_cast<RayRes*>(smem);
