@@ -318,9 +318,38 @@ def run_ours(args, D):
             if args.workload == "als":
                 res["batched"] = batched_compare(args)
                 res["echo_width_fit"] = echo_width_cost(w, gsc, layout, args)
+                res["mls"] = mls_step(args)
             if args.workload == "mls":
                 res["reflectance_fit"] = reflectance_fit(args)
     return res, w
+
+
+def mls_step(args):
+    """The urban MLS workload at full size (2 km street of extruded buildings,
+    20.7 M triangles, 2000 voxel trees of 128^3, rotating profile head, 20 M
+    pulses, 37 subrays, 512 bins): device time of one stochastic scan step
+    (2 warm-up steps, mean of 2)."""
+    import torch
+    import paper_2101_09154_gb300 as hg
+    w = workload("mls", args.small)
+    t0 = time.time()
+    gsc = [hg.Scene(s) for s in w.scenes]
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    lay = hg.output_layout(w.scanners, w.legs)
+    out = hg.alloc_outputs(lay, gsc[0].device, subrays=False)
+    ms = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, seed=12345, out=out, subrays=False), 2, 2)
+    P = w.n_pulses
+    S = hg.subray_count(w.scanners[0].beam_sample_quality)
+    res = {"workload": w.name, "description": w.note, "pulses": P, "subrays_per_pulse": S,
+           "triangles": int(sum(s.n_triangles for s in w.scenes)),
+           "voxel_trees": int(sum(len(s.grids) for s in w.scenes)),
+           "voxels": int(sum(int(np.prod(g.dims)) for s in w.scenes for g in s.grids)),
+           "scene_build_s": round(build_s, 3), "ms_per_step": ms,
+           "pulses_per_s": P / (ms / 1e3), "subrays_per_s": P * S / (ms / 1e3)}
+    del out, gsc
+    torch.cuda.empty_cache()
+    return res
 
 
 def echo_width_cost(w, gsc, layout, args):
@@ -338,26 +367,34 @@ def echo_width_cost(w, gsc, layout, args):
 
 
 def reflectance_fit(args):
-    """50 adjoint-driven SIRT iterations of per-triangle reflectance on a 200 m
-    stretch of the urban street (2 M pulses, 37 subrays): time, loss drop and
-    RMSE against the seeded ground truth over the triangles the scan sees."""
+    """50 adjoint-driven SIRT iterations of per-triangle reflectance over the
+    whole urban MLS leg (2 km, 20 M pulses, 37 subrays, 2000 trees of 128^3;
+    pieces of 4 M pulses): time, loss drop and RMSE against the seeded ground
+    truth over the triangles the scan sees."""
     import torch
     import scenes
     import paper_2101_09154_gb300 as hg
     from paper_2101_09154_gb300.fit import fit_reflectance
-    w = scenes.urban_mls(length=30.0, facade_cell=0.5) if args.small else \
-        scenes.urban_mls(length=200.0, facade_cell=0.25)
+    w = scenes.urban_mls(length=30.0, facade_cell=0.5) if args.small else scenes.urban_mls()
     sc, leg = w.scanners[0], w.legs[0]
+    chunk = 0 if args.small else 4_000_000
     gs = hg.Scene(w.scenes[0])
     truth = [r.clone() for r in gs.reflectance]
-    target = hg.scan([gs], [sc], [leg], mode=1)[0]["waveform"].clone()
-    fit_reflectance(gs, sc, leg, target, iters=2)          # warm-up
+    # the target: the expected-mode scan of the seeded reflectances, piece by piece
+    nb = sc.n_bins
+    target = torch.empty(leg.n_pulses * nb, dtype=torch.float32, device=gs.device)
+    from paper_2101_09154_gb300.fit import _chunks
+    for k0, piece in _chunks(leg, chunk):
+        o, _ = hg.scan([gs], [sc], [piece], mode=1, subrays=False)
+        target[k0 * nb:(k0 + piece.n_pulses) * nb] = o["waveform"]
+        del o
+    fit_reflectance(gs, sc, leg, target, iters=1, chunk_pulses=chunk)          # warm-up
     for r, t in zip(gs.reflectance, truth):
         r.copy_(t)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    res = fit_reflectance(gs, sc, leg, target, iters=50)
+    res = fit_reflectance(gs, sc, leg, target, iters=50, chunk_pulses=chunk)
     e1.record()
     torch.cuda.synchronize()
     sq, n, sq_w, n_w = 0.0, 0, 0.0, 0
@@ -369,7 +406,7 @@ def reflectance_fit(args):
         sq, n = sq + float((err[seen] ** 2).sum()), n + int(seen.sum())
         sq_w, n_w = sq_w + float((err[well] ** 2).sum()), n_w + int(well.sum())
     return {"workload": w.name, "pulses": w.n_pulses, "triangles": w.scenes[0].n_triangles,
-            "iterations": 50, "fit_ms": e0.elapsed_time(e1),
+            "iterations": 50, "fit_ms": e0.elapsed_time(e1), "chunk_pulses": chunk,
             "loss_first": res["loss"][0], "loss_last": res["loss"][-1],
             "triangles_seen": n, "rmse_seen": (sq / max(n, 1)) ** 0.5,
             "rmse_well_observed": (sq_w / max(n_w, 1)) ** 0.5}

@@ -45,3 +45,26 @@ def test_reflectance_fit_recovers_ground_truth(hg):
         assert np.sqrt(np.mean(err[well] ** 2)) < 1e-3
         # triangles no pulse sees keep the starting value
         assert np.all(gs.reflectance[m].cpu().numpy()[~seen] == np.float32(0.5))
+
+
+def test_chunked_fit_matches_whole_leg(hg):
+    """The fit over pieces of 70 000 pulses (the last one ragged) gives the
+    whole leg's losses and reflectances.  The adjoint's atomics sum in another
+    order: reflectances agree to 1e-4 relative; a loss after a step is a
+    difference of terms of the first loss's size, so losses agree to 1e-8 of
+    the first one."""
+    from paper_2101_09154_gb300.fit import fit_reflectance
+    w = scenes.urban_mls(length=30.0, facade_cell=0.5)
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    truth = [r.clone() for r in gs.reflectance]
+    target = hg.scan([gs], [sc], [leg], mode=1)[0]["waveform"].clone()
+    a = fit_reflectance(gs, sc, leg, target, iters=5)
+    ra = [r.clone() for r in gs.reflectance]
+    for r, t in zip(gs.reflectance, truth):
+        r.copy_(t)
+    b = fit_reflectance(gs, sc, leg, target, iters=5, chunk_pulses=70_000)
+    torch.cuda.synchronize()
+    assert np.allclose(a["loss"], b["loss"], rtol=1e-4, atol=1e-8 * a["loss"][0])
+    for x, y in zip(ra, gs.reflectance):
+        assert torch.allclose(x, y, rtol=1e-4, atol=1e-6)
