@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 const SubrayConst& c = s_sc[ss];
                 float dh[3], dl[3];
                 subray_dir_ff(f, c, dh, dl);
-                double o[3], d[3];
+                FF o[3], d[3];
                 for (int a = 0; a < 3; ++a) {
-                    o[a] = ff2d(f.oh[a], f.ol[a]);
-                    d[a] = ff2d(dh[a], dl[a]);
+                    o[a] = ff_norm(f.oh[a], f.ol[a]);
+                    d[a] = ff_norm(dh[a], dl[a]);
                 }
                 const float tan_a = c.tan_a;
                 // triangle hit: the forward's checkpoint, else a traversal
@@ -208,17 +208,17 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     t32 = tb;
                 }
                 if (!on) continue;
-                double t_tri = CUDART_INF;
+                FF t_tri = {CUDART_INF_F, 0.0f};
                 float cosi = 0.0f, rho = 0.0f, dt32 = 0.0f;
                 int mesh = 0, face = 0;
                 if (hit >= 0) {
                     dt32 = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, t32, cosi);
-                    t_tri = (double)t32 + (double)dt32;
+                    t_tri = ff_norm(t32, dt32);
                     const float4* tp = sc.tris + 3 * (size_t)hit;
                     mesh = __float_as_int(__ldg(&tp[1].w));
                     face = __float_as_int(__ldg(&tp[2].w));
                     rho = __ldg(&sc.refl[mesh][face]);
-                    if (!(t_tri > 0.0)) { t_tri = CUDART_INF; hit = -1; }
+                    if (!(t_tri.hi > 0.0f)) { t_tri = FF{CUDART_INF_F, 0.0f}; hit = -1; }
                 }
                 const bool grid = GK > 0 && sc.has_grid != 0;
                 // ---- pass A: march once, grid after grid in entry order; total

@@ -287,7 +287,11 @@ static helios_status build_grids(helios_scene* s, const helios_scene_desc* desc,
             d.bdims[a] = (g.dims[a] + kBrick - 1) >> kBrickLog2;
         }
         d.cell = g.cell;
-        d.inv_cell = 1.0 / (double)g.cell;
+        {
+            const double ic = 1.0 / (double)g.cell;
+            d.icell_h = (float)ic;
+            d.icell_l = (float)(ic - (double)d.icell_h);
+        }
         d.opaque = g.opaque != 0;
         d.G = g.G;
         d.leaf_refl = g.leaf_reflectance;

@@ -58,7 +58,7 @@ struct DevGrid {
     int32_t lad_n;              // 0: constant G
     float G, leaf_refl;
     int64_t vox_off;            // voxels of the scene's earlier grids
-    double inv_cell;            // 1 / cell, formed in FP64 on the host
+    float icell_h, icell_l;     // 1 / cell as a float pair, formed on the host
 };
 
 struct DevScene {
@@ -404,6 +404,39 @@ __device__ __forceinline__ FF ff_split(double x) {
     r.lo = (float)(x - (double)r.hi);
     return r;
 }
+// float-float arithmetic (error-free transformations; about 2^-44 relative)
+__device__ __forceinline__ FF ff_add(const FF& a, const FF& b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ff_norm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ FF ff_sub(const FF& a, const FF& b) {
+    return ff_add(a, FF{-b.hi, -b.lo});
+}
+__device__ __forceinline__ FF ff_mul(const FF& a, const FF& b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    return ff_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+// 1/b (b.hi != 0): the FP32 quotient r and one Newton step, r + r (1 - b r),
+// with 1 - b r formed from the exact product b.hi r
+__device__ __forceinline__ FF ff_rcp(const FF& b) {
+    const float r = 1.0f / b.hi;
+    float p, pe;
+    two_prod(b.hi, r, p, pe);
+    const float e = ((1.0f - p) - pe) - b.lo * r;
+    return ff_norm(r, r * e);
+}
+__device__ __forceinline__ FF ff_min(const FF& a, const FF& b) { return ff_less(b, a) ? b : a; }
+__device__ __forceinline__ FF ff_max(const FF& a, const FF& b) { return ff_less(a, b) ? b : a; }
+__device__ __forceinline__ bool ff_eq(const FF& a, const FF& b) { return a.hi == b.hi && a.lo == b.lo; }
+// the pair n * c exactly (|n| < 2^24)
+__device__ __forceinline__ FF ff_int_mul(int n, float c) {
+    float p, e;
+    two_prod((float)n, c, p, e);
+    return ff_norm(p, e);
+}
+
 // floor(a * b) for a normalised pair a and a constant pair (bh, bl)
 __device__ __forceinline__ int ff_floor_mul(const FF& a, float bh, float bl) {
     float p, e;
@@ -814,77 +847,87 @@ __device__ __forceinline__ float cross32(int p, int p0, int s, float f0, float i
 }
 
 // set up the march along o + t d for t in [t_enter, min(t_exit, t_hi)); false: no voxel
-// 1/x in FP64 without a division: an FP32 estimate and two Newton steps
-// (the relative error squares each step, 2^-23 -> 2^-46 -> below FP64
-// rounding: within 1 ulp of 1/x).  Outside the FP32 range, the division.
-__device__ __forceinline__ double rcp64(double x) {
-    const double ax = fabs(x);
-    if (!(ax > 1.0e-30 && ax < 1.0e30)) return 1.0 / x;
-    double r = (double)__frcp_rn((float)x);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+// The grid's box along o + t d (o, d as float pairs): each axis's slab
+// [tlo, thi] (an axis the ray is parallel to: the whole line, or false when
+// the origin is outside the slab), 1/d per axis, and the entry
+// te = max(0, tlo) and exit min(thi, t_hi).  Float-float throughout.
+__device__ __forceinline__ bool grid_span_ff(const DevGrid& S, const FF o[3], const FF d[3],
+                                             const FF& t_hi, FF tlo[3], FF iv[3], FF& te, FF& tend) {
+    te = FF{0.0f, 0.0f};
+    FF tx = t_hi;
+    for (int a = 0; a < 3; ++a) {
+        const FF lo = {S.g0[a], 0.0f};
+        const FF hi = ff_add(lo, ff_int_mul(S.dims[a], S.cell));
+        if (d[a].hi == 0.0f) {
+            if (ff_less(o[a], lo) || !ff_less(o[a], hi)) return false;
+            tlo[a] = FF{-CUDART_INF_F, 0.0f};
+            iv[a] = FF{0.0f, 0.0f};
+            continue;
+        }
+        iv[a] = ff_rcp(d[a]);
+        const FF ta = ff_mul(ff_sub(lo, o[a]), iv[a]), tb = ff_mul(ff_sub(hi, o[a]), iv[a]);
+        tlo[a] = ff_min(ta, tb);
+        te = ff_max(te, tlo[a]);
+        tx = ff_min(tx, ff_max(ta, tb));
+    }
+    tend = tx;
+    return ff_less(te, tend);
 }
 
-__device__ __forceinline__ bool march_init(const DevGrid& S, const double o[3],
-                                           const double d[3], double t_hi, March& m) {
-    double g0[3] = {(double)S.g0[0], (double)S.g0[1], (double)S.g0[2]};
-    double cell = (double)S.cell;
-    double tlo[3], thi[3];
-    double te = 0.0, tx = 1e300;
-    int dims[3] = {S.dims[0], S.dims[1], S.dims[2]};
-    double ivd[3];
-    for (int a = 0; a < 3; ++a) {
-        double lo = g0[a], hi = g0[a] + (double)dims[a] * cell;
-        ivd[a] = d[a] != 0.0 ? rcp64(d[a]) : 0.0;
-        if (d[a] == 0.0) {
-            if (o[a] < lo || o[a] >= hi) return false;
-            tlo[a] = -1e300; thi[a] = 1e300;
-        } else {
-            double ta = (lo - o[a]) * ivd[a], tb = (hi - o[a]) * ivd[a];
-            tlo[a] = fmin(ta, tb);
-            thi[a] = fmax(ta, tb);
-        }
-        te = fmax(te, tlo[a]);
-        tx = fmin(tx, thi[a]);
-    }
-    double tend = fmin(tx, t_hi);
-    if (!(te < tend)) return false;
+// set up the march along o + t d for t in [t_enter, min(t_exit, t_hi)); false:
+// no voxel.  Float-float throughout (no FP64 instruction): the entry, the first
+// voxel's indices and each axis's first crossing numerator f0.
+__device__ __forceinline__ bool march_init(const DevGrid& S, const FF o[3], const FF d[3],
+                                           const FF& t_hi, March& m) {
+    FF tlo[3], ivd[3], te, tend;
+    if (!grid_span_ff(S, o, d, t_hi, tlo, ivd, te, tend)) return false;
+    const int dims[3] = {S.dims[0], S.dims[1], S.dims[2]};
+    const FF icell = {S.icell_h, S.icell_l};
+    const bool te_pos = te.hi > 0.0f;
     int idx[3], stp[3], p0[3];
-    FF f0[3], iv[3];
+    FF f0[3];
     for (int a = 0; a < 3; ++a) {
-        stp[a] = d[a] > 0.0 ? 1 : (d[a] < 0.0 ? -1 : 0);
-        if (te > 0.0 && tlo[a] == te && d[a] != 0.0) {
-            idx[a] = d[a] > 0.0 ? 0 : dims[a] - 1;
+        stp[a] = d[a].hi > 0.0f ? 1 : (d[a].hi < 0.0f ? -1 : 0);
+        if (te_pos && stp[a] != 0 && ff_eq(tlo[a], te)) {
+            idx[a] = stp[a] > 0 ? 0 : dims[a] - 1;
         } else {
-            double p = o[a] + te * d[a];
-            double f = floor((p - g0[a]) * S.inv_cell);
-            f = fmin(fmax(f, 0.0), (double)(dims[a] - 1));
-            idx[a] = (int)f;
+            // floor(x / cell) for x = p - g0: the estimate x * (1/cell), then
+            // corrected against n cell and (n + 1) cell (exact pairs), so a point
+            // on a voxel boundary (a ray inside a boundary plane) takes the
+            // voxel above it, as the exact quotient does
+            const FF p = ff_add(o[a], ff_mul(te, d[a]));
+            const FF x = ff_sub(p, FF{S.g0[a], 0.0f});
+            const FF v = ff_mul(x, icell);
+            float f = floorf(v.hi);
+            if (f == v.hi && v.lo < 0.0f) f -= 1.0f;
+            f = fminf(fmaxf(f, -1.0f), (float)dims[a]);
+            int n = (int)f;
+            if (ff_less(x, ff_int_mul(n, S.cell))) --n;
+            else if (!ff_less(x, ff_int_mul(n + 1, S.cell))) ++n;
+            idx[a] = min(max(n, 0), dims[a] - 1);
         }
         p0[a] = stp[a] > 0 ? idx[a] + 1 : idx[a];
-        f0[a] = ff_split(stp[a] != 0 ? fma((double)p0[a], cell, g0[a]) - o[a] : 0.0);
-        iv[a] = ff_split(ivd[a]);
+        f0[a] = stp[a] != 0 ? ff_sub(ff_add(FF{S.g0[a], 0.0f}, ff_int_mul(p0[a], S.cell)), o[a])
+                            : FF{0.0f, 0.0f};
     }
     m.ix = idx[0]; m.iy = idx[1]; m.iz = idx[2];
     m.sx = stp[0]; m.sy = stp[1]; m.sz = stp[2];
     m.px = p0[0]; m.py = p0[1]; m.pz = p0[2];
     m.f0hx = f0[0].hi; m.f0hy = f0[1].hi; m.f0hz = f0[2].hi;
     m.f0lx = f0[0].lo; m.f0ly = f0[1].lo; m.f0lz = f0[2].lo;
-    m.ivhx = iv[0].hi; m.ivhy = iv[1].hi; m.ivhz = iv[2].hi;
-    m.ivlx = iv[0].lo; m.ivly = iv[1].lo; m.ivlz = iv[2].lo;
+    m.ivhx = ivd[0].hi; m.ivhy = ivd[1].hi; m.ivhz = ivd[2].hi;
+    m.ivlx = ivd[0].lo; m.ivly = ivd[1].lo; m.ivlz = ivd[2].lo;
     m.cell = S.cell;
     m.tnx = cross32(m.px, m.px, m.sx, m.f0hx, m.ivhx, m.cell);
     m.tny = cross32(m.py, m.py, m.sy, m.f0hy, m.ivhy, m.cell);
     m.tnz = cross32(m.pz, m.pz, m.sz, m.f0hz, m.ivhz, m.cell);
-    m.t_enter = ff_split(te);
-    m.t_end = ff_split(tend);
+    m.t_enter = te;
+    m.t_end = tend;
     m.entry_axis = -1;
     m.face0 = -1;
-    if (te > 0.0)
+    if (te_pos)
         for (int a = 2; a >= 0; --a)
-            if (d[a] != 0.0 && tlo[a] == te) m.face0 = a;
+            if (stp[a] != 0 && ff_eq(tlo[a], te)) m.face0 = a;
     m.steps_left = dims[0] + dims[1] + dims[2] + 4;
     return true;
 }
@@ -1090,12 +1133,12 @@ constexpr int kGridStack = 32;
 
 struct GridRay {
     float of[3], ivf[3];        // FP32 culling
-    double iv[3];               // 1/d (0 where d = 0)
+    FF o[3], d[3];              // the ray as float pairs
 };
 
 struct GridCursor {
-    double te;      // key of the last grid returned
-    int gi;
+    FF te;          // key of the last grid returned
+    int gi;         // -1: none yet
 };
 
 __device__ __forceinline__ void box_span(const float o[3], const float iv[3], const float lo[3],
@@ -1109,35 +1152,22 @@ __device__ __forceinline__ void box_span(const float o[3], const float iv[3], co
     }
 }
 
-// FP64 entry of o + t d (t >= 0) into grid g's box, the planes formed as in
-// march_init; false: the ray does not enter it before t_hi
-__device__ __forceinline__ bool grid_entry64(const DevGrid& g, const double o[3], const double d[3],
-                                             const double iv[3], double t_hi, double& te) {
-    double tn = 0.0, tf = t_hi;
-    for (int a = 0; a < 3; ++a) {
-        const double lo = (double)g.g0[a], hi = lo + (double)g.dims[a] * (double)g.cell;
-        if (d[a] == 0.0) {
-            if (o[a] < lo || o[a] >= hi) return false;
-            continue;
-        }
-        const double t0 = (lo - o[a]) * iv[a], t1 = (hi - o[a]) * iv[a];
-        tn = fmax(tn, fmin(t0, t1));
-        tf = fmin(tf, fmax(t0, t1));
-    }
-    te = tn;
-    return tn < tf;
+// entry of o + t d (t >= 0) into grid g's box, formed exactly as march_init
+// forms it; false: the ray does not enter it before t_hi
+__device__ __forceinline__ bool grid_entry_ff(const DevGrid& g, const GridRay& r, const FF& t_hi, FF& te) {
+    FF tlo[3], iv[3], tend;
+    return grid_span_ff(g, r.o, r.d, t_hi, tlo, iv, te, tend);
 }
 
-__device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, const double o[3],
-                                         const double d[3], double t_hi, GridCursor& c) {
+__device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, const FF& t_hi, GridCursor& c) {
     if (sc.n_grid == 1) {
         if (c.gi >= 0) return -1;
         c.gi = 0;
         return 0;
     }
-    const float th = (float)t_hi * 1.0001f + 1.0e-3f;
-    const float cte = (float)c.te * 0.9999f - 1.0e-3f;      // below the cursor, for culling
-    double best_t = t_hi;
+    const float th = t_hi.hi * 1.0001f + 1.0e-3f;
+    const float cte = c.gi >= 0 ? c.te.hi * 0.9999f - 1.0e-3f : -1.0e30f;   // below the cursor, for culling
+    FF best_t = t_hi;
     int best = -1;
     int stack[kGridStack];
     int sp = 0, node = 0;
@@ -1147,7 +1177,7 @@ __device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, c
         const int4 ch = __ldg(reinterpret_cast<const int4*>(n + 3));
         const float lo0[3] = {a.x, a.y, a.z}, hi0[3] = {a.w, b.x, b.y};
         const float lo1[3] = {b.z, b.w, e.x}, hi1[3] = {e.y, e.z, e.w};
-        const float bt = (float)best_t * 1.0001f + 1.0e-3f;
+        const float bt = best_t.hi * 1.0001f + 1.0e-3f;
         for (int k = 0; k < 2; ++k) {
             float tn, tf;
             box_span(r.of, r.ivf, k ? lo1 : lo0, k ? hi1 : hi0, tn, tf);
@@ -1155,10 +1185,10 @@ __device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, c
             const int child = k ? ch.y : ch.x;
             if (child < 0) {
                 const int gi = ~child;
-                double te;
-                if (!grid_entry64(sc.grids[gi], o, d, r.iv, t_hi, te)) continue;
-                const bool after = te > c.te || (te == c.te && gi > c.gi);
-                const bool before = best < 0 || te < best_t || (te == best_t && gi < best);
+                FF te;
+                if (!grid_entry_ff(sc.grids[gi], r, t_hi, te)) continue;
+                const bool after = c.gi < 0 || ff_less(c.te, te) || (ff_eq(te, c.te) && gi > c.gi);
+                const bool before = best < 0 || ff_less(te, best_t) || (ff_eq(te, best_t) && gi < best);
                 if (after && before) {
                     best_t = te;
                     best = gi;
@@ -1177,35 +1207,34 @@ __device__ __forceinline__ int next_grid(const DevScene& sc, const GridRay& r, c
     return best;
 }
 
-__device__ __forceinline__ void grid_ray(const double o[3], const double d[3], GridRay& r) {
+__device__ __forceinline__ void grid_ray(const FF o[3], const FF d[3], GridRay& r) {
     for (int a = 0; a < 3; ++a) {
-        r.of[a] = (float)o[a];
-        const float df = (float)d[a];
-        r.ivf[a] = df != 0.0f ? 1.0f / df : 1.0e30f;
-        r.iv[a] = d[a] != 0.0 ? rcp64(d[a]) : 0.0;
+        r.o[a] = o[a];
+        r.d[a] = d[a];
+        r.of[a] = o[a].hi;
+        r.ivf[a] = d[a].hi != 0.0f ? 1.0f / d[a].hi : 1.0e30f;
     }
 }
 
-// the march set up on the next grid (in entry order) that the FP64 march
-// enters before t_hi; NULL when none is left
-__device__ __forceinline__ const DevGrid* next_march(const DevScene& sc, const GridRay& r,
-                                                     const double o[3], const double d[3], double t_hi,
+// the march set up on the next grid (in entry order) that the march enters
+// before t_hi; NULL when none is left
+__device__ __forceinline__ const DevGrid* next_march(const DevScene& sc, const GridRay& r, const FF& t_hi,
                                                      GridCursor& c, March& m) {
     for (int guard = 0; guard < sc.n_grid; ++guard) {
-        const int gi = next_grid(sc, r, o, d, t_hi, c);
+        const int gi = next_grid(sc, r, t_hi, c);
         if (gi < 0) return nullptr;
         const DevGrid* G = sc.n_grid == 1 ? &sc.grid : sc.grids + gi;
-        if (march_init(*G, o, d, t_hi, m)) return G;
+        if (march_init(*G, r.o, r.d, t_hi, m)) return G;
     }
     return nullptr;
 }
 
 // body(G, m) on each grid the ray crosses before t_hi, in entry order, with
 // m set up on it; body returns false to end the walk.  GK 1: the scene has
-// at most one grid (sc.grid); GK 2: any number.
+// at most one grid (sc.grid); GK 2: any number.  o and d as float pairs.
 template <int GK, class F>
-__device__ __forceinline__ void walk_grids(const DevScene& sc, const double o[3], const double d[3],
-                                           double t_hi, F&& body) {
+__device__ __forceinline__ void walk_grids(const DevScene& sc, const FF o[3], const FF d[3], const FF& t_hi,
+                                           F&& body) {
     if (GK == 1) {
         March m;
         if (march_init(sc.grid, o, d, t_hi, m)) body(sc.grid, m);
@@ -1213,10 +1242,10 @@ __device__ __forceinline__ void walk_grids(const DevScene& sc, const double o[3]
     }
     GridRay r;
     grid_ray(o, d, r);
-    GridCursor c = {-1.0, -1};
+    GridCursor c = {{0.0f, 0.0f}, -1};
     March m;
     for (int guard = 0; guard < sc.n_grid; ++guard) {
-        const DevGrid* G = next_march(sc, r, o, d, t_hi, c, m);
+        const DevGrid* G = next_march(sc, r, t_hi, c, m);
         if (!G || !body(*G, m)) return;
     }
 }

@@ -86,12 +86,12 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
     if (GK > 0 && sc.has_grid) {
         float dh[3], dl[3];
         subray_dir_ff(f, c, dh, dl);
-        double o[3], d[3];
+        FF o[3], d[3];
         for (int a = 0; a < 3; ++a) {
-            o[a] = ff2d(f.oh[a], f.ol[a]);
-            d[a] = ff2d(dh[a], dl[a]);
+            o[a] = ff_norm(f.oh[a], f.ol[a]);
+            d[a] = ff_norm(dh[a], dl[a]);
         }
-        double t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+        const FF t_hi = rr.id >= 0 ? ff_norm(rr.Rh, rr.Rl) : FF{CUDART_INF_F, 0.0f};
         bool stopped = false;
         walk_grids<GK>(sc, o, d, t_hi, [&](const DevGrid& G, March& m) -> bool {
             const float Gs = proj_factor(G, dh[2]);
@@ -318,26 +318,26 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 float dt_hit = 0.0f;
                 if (active) {
                     float cosi = 0.0f;
-                    double t_tri = CUDART_INF;
+                    FF t_tri = {CUDART_INF_F, 0.0f};
                     int gid = -1;
                     float rho = 0.0f;
                     if (hit >= 0) {
                         dt_hit = refine_hit_ff(sc, hit, f.oh, f.ol, dh, dl, tb, cosi);
-                        t_tri = GK > 0 ? (double)tb + (double)dt_hit : 0.0;
+                        t_tri = ff_norm(tb, dt_hit);
                         const float4* tp = sc.tris + 3 * (size_t)hit;
                         gid = __float_as_int(__ldg(&tp[0].w));
                         int mesh = __float_as_int(__ldg(&tp[1].w));
                         int face = __float_as_int(__ldg(&tp[2].w));
                         rho = __ldg(&sc.refl[mesh][face]);
-                        if (!(tb + dt_hit > 0.0f)) { t_tri = CUDART_INF; gid = -1; }
+                        if (!(tb + dt_hit > 0.0f)) { t_tri = FF{CUDART_INF_F, 0.0f}; gid = -1; }
                     }
                     bool voxel_event = false;
                     int64_t id_off = 0;      // voxel event: the grid's first voxel id
                     if (GK > 0 && sc.has_grid) {
-                        double o[3], d[3];
+                        FF o[3], d[3];
                         for (int a = 0; a < 3; ++a) {
-                            o[a] = ff2d(f.oh[a], f.ol[a]);
-                            d[a] = ff2d(dh[a], dl[a]);
+                            o[a] = ff_norm(f.oh[a], f.ol[a]);
+                            d[a] = ff_norm(dh[a], dl[a]);
                         }
                         const int64_t k = p0 + pl;
                         // the first event along the path: grids in entry order
@@ -716,22 +716,22 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         // the walk over several grids (GK 2): its cursor stays live between
                         // returns; the ray is formed again at each change of grid
                         const DevGrid* Gp = &sc.grid;
-                        double t_hi = 0.0;
-                        GridCursor gcur = {-1.0, -1};
+                        FF t_hi = {0.0f, 0.0f};
+                        GridCursor gcur = {{0.0f, 0.0f}, -1};
                         auto next_g = [&]() -> bool {
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
-                            double o[3], d[3];
+                            FF o[3], d[3];
                             for (int a = 0; a < 3; ++a) {
-                                o[a] = ff2d(f.oh[a], f.ol[a]);
-                                d[a] = ff2d(dh[a], dl[a]);
+                                o[a] = ff_norm(f.oh[a], f.ol[a]);
+                                d[a] = ff_norm(dh[a], dl[a]);
                             }
                             if (GK == 1) {
                                 if (!march_init(sc.grid, o, d, t_hi, mch)) return false;
                             } else {
                                 GridRay gray;
                                 grid_ray(o, d, gray);
-                                Gp = next_march(sc, gray, o, d, t_hi, gcur, mch);
+                                Gp = next_march(sc, gray, t_hi, gcur, mch);
                                 if (Gp == nullptr) return false;
                             }
                             Gs = proj_factor(GK == 1 ? sc.grid : *Gp, dh[2]);
@@ -741,7 +741,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                             float dh[3], dl[3];
                             subray_dir_ff(f, s_sc[s], dh, dl);
                             for (int a = 0; a < 3; ++a) dabs[a] = fabsf(dh[a]);
-                            t_hi = rr.id >= 0 ? ff2d(rr.Rh, rr.Rl) : CUDART_INF;
+                            t_hi = rr.id >= 0 ? ff_norm(rr.Rh, rr.Rl) : FF{CUDART_INF_F, 0.0f};
                             on = next_g();
                         }
                         while (__any_sync(full, on)) {
