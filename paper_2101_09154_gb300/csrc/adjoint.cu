@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                     if (hit >= 0) t32 = plane_t32(sc, hit, f.oh, dh);
                 } else {
                     RayF ray;
-                    make_ray(f.oh, dh, ray);
+                    make_ray(f.oh, f.ol, dh, ray);
                     float tb = 3.0e38f;
                     uint32_t fl = 0;
                     traverse(sc, ray, on, tb, hit, fl);

@@ -460,7 +460,8 @@ __device__ __forceinline__ float ff_mul_sub(const FF& a, float bh, float bl, flo
 // FP32 ray for traversal
 // ---------------------------------------------------------------------------
 struct RayF {
-    float ox, oy, oz;
+    float ox, oy, oz;        // origin: high words of the float-float pair
+    float lx, ly, lz;        // origin: low words (the triangle test subtracts both)
     float idx, idy, idz;     // 1/d (tiny components replaced by +-1e-20)
     float oix, oiy, oiz;     // o * (1/d)
     float sx, sy, sz;        // watertight shear constants
@@ -477,8 +478,10 @@ __device__ __forceinline__ float sel3(int k, float x, float y, float z) {
 
 // origin and watertight-test setup (Woop, Benthin & Wald, JCGT 2013): all a
 // ray needs for tri_hit
-__device__ __forceinline__ void make_ray_tri(const float o[3], const float d[3], RayF& r) {
+__device__ __forceinline__ void make_ray_tri(const float o[3], const float ol[3], const float d[3],
+                                             RayF& r) {
     r.ox = o[0]; r.oy = o[1]; r.oz = o[2];
+    r.lx = ol[0]; r.ly = ol[1]; r.lz = ol[2];
     const float dx = d[0], dy = d[1], dz = d[2];
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
@@ -499,8 +502,8 @@ __device__ __forceinline__ void make_ray_slab(const float d[3], RayF& r) {
     r.oix = r.ox * r.idx; r.oiy = r.oy * r.idy; r.oiz = r.oz * r.idz;
 }
 
-__device__ __forceinline__ void make_ray(const float o[3], const float d[3], RayF& r) {
-    make_ray_tri(o, d, r);
+__device__ __forceinline__ void make_ray(const float o[3], const float ol[3], const float d[3], RayF& r) {
+    make_ray_tri(o, ol, d, r);
     make_ray_slab(d, r);
 }
 
@@ -518,9 +521,15 @@ __device__ __forceinline__ bool slab(const RayF& r, float lx, float ly, float lz
 // Watertight ray-triangle test; on a hit closer than t_best updates t_best.
 __device__ __forceinline__ bool tri_hit(const RayF& r, float4 a, float4 b, float4 c,
                                         float& t_best) {
-    float Ax = a.x - r.ox, Ay = a.y - r.oy, Az = a.z - r.oz;
-    float Bx = b.x - r.ox, By = b.y - r.oy, Bz = b.z - r.oz;
-    float Cx = c.x - r.ox, Cy = c.y - r.oy, Cz = c.z - r.oz;
+    // Vertices relative to the float-float origin.  The first difference is
+    // exact for a vertex within a factor of two of the origin's coordinate,
+    // so a far-from-zero origin (a street 2 km long) keeps its low word; an
+    // origin rounded to FP32 alone moves edge crossings by its rounding error
+    // (up to 6e-5 m at 1 km), more than the edge distance hits are resolved to.
+    // Each vertex maps the same way in every triangle: still watertight.
+    float Ax = (a.x - r.ox) - r.lx, Ay = (a.y - r.oy) - r.ly, Az = (a.z - r.oz) - r.lz;
+    float Bx = (b.x - r.ox) - r.lx, By = (b.y - r.oy) - r.ly, Bz = (b.z - r.oz) - r.lz;
+    float Cx = (c.x - r.ox) - r.lx, Cy = (c.y - r.oy) - r.ly, Cz = (c.z - r.oz) - r.lz;
     float akx = sel3(r.kx, Ax, Ay, Az), aky = sel3(r.ky, Ax, Ay, Az), akz = sel3(r.kz, Ax, Ay, Az);
     float bkx = sel3(r.kx, Bx, By, Bz), bky = sel3(r.ky, Bx, By, Bz), bkz = sel3(r.kz, Bx, By, Bz);
     float ckx = sel3(r.kx, Cx, Cy, Cz), cky = sel3(r.ky, Cx, Cy, Cz), ckz = sel3(r.kz, Cx, Cy, Cz);

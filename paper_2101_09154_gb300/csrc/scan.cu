@@ -261,7 +261,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 float dh[3], dl[3];
                 subray_dir_ff(f, s_sc[0], dh, dl);     // subray 0: the pulse axis
                 RayF ray;
-                make_ray(f.oh, dh, ray);
+                make_ray(f.oh, f.ol, dh, ray);
                 int32_t* ext = P.cext ? P.cext + ((size_t)blockIdx.x * P.pc_cap + (act ? pl : 0)) * P.cext_cap
                                       : nullptr;
                 int n;
@@ -287,7 +287,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 float dh[3], dl[3];
                 subray_dir_ff(f, s_sc[s], dh, dl);
                 RayF ray;
-                make_ray_tri(f.oh, dh, ray);
+                make_ray_tri(f.oh, f.ol, dh, ray);
                 float tb = 3.0e38f;
                 int hit = -1;
                 uint32_t fl = 0;

@@ -129,7 +129,7 @@ def compare(g, ref, max_flag_frac=0.05, check_subrays=True, expected_mode=False)
         hit_ok = g["subray_hit"] == ref["subray_hit"]
         bad = np.nonzero(sub_ok & ~hit_ok)
         assert bad[0].size == 0, (f"subray hit ids differ on {bad[0].size} unflagged subrays, "
-                                  f"e.g. pulse rows {bad[0][:5]}: gpu {g['subray_hit'][bad][:5]} "
+                                  f"e.g. pulse rows {bad[0][:5]} subrays {bad[1][:5]}: gpu {g['subray_hit'][bad][:5]} "
                                   f"oracle {ref['subray_hit'][bad][:5]}")
         m = sub_ok & (ref["subray_hit"] >= 0)
         dr = np.abs(g["subray_range"] - ref["subray_range"])[m]

@@ -4,7 +4,9 @@ sampled pulses against the FP64 oracle (which computes them one by one):
 * the voxel canopy (256^3 voxels at 0.1 m, 1 M pulses, 19 subrays, 1024 bins),
   stochastic and expected forward, and the expected-mode adjoint;
 * 128 scan legs of 10 k - 2 M pulses and 1/7/19/37 subrays over terrain tiles
-  and voxel blocks, in one persistent launch with the tuned block shape.
+  and voxel blocks, in one persistent launch with the tuned block shape;
+* the urban street (20.7 M triangles, 2000 voxel trees of 128^3, 20 M pulses,
+  37 subrays) in both modes.
 
 Tolerances are those of ``tests/parity.py`` (gradients: 1e-3 relative with a
 floor of 1e-6 of the largest entry).
@@ -115,3 +117,30 @@ def test_batched_legs_full_size_sampled(hg):
         reruns += st["rerun_pulses"]
     print(f"batched: {total} pulses, flagged subrays {flagged / subrays:.5f}, re-run pulses {reruns}")
     assert total >= 128 * 39
+
+
+@pytest.fixture(scope="module")
+def urban():
+    w = scenes.urban_mls()
+    return w, oracle.OracleScene(w.scenes[0])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_urban_mls_full_size_sampled(hg, urban, mode):
+    """The whole urban leg (2 km street, 20.7 M triangles, 2000 voxel trees of
+    128^3, 20 M pulses x 37 subrays, 512 bins) in one launch; every 4001st
+    pulse against the oracle."""
+    w, osc = urban
+    sc, leg = w.scanners[0], w.legs[0]
+    gs = hg.Scene(w.scenes[0])
+    out, lay = hg.scan([gs], [sc], [leg], mode=mode, seed=6)
+    torch.cuda.synchronize()
+    rows = np.arange(0, leg.n_pulses, 4001)
+    S = hg.subray_count(sc.beam_sample_quality)
+    g = leg_view(out, lay, 0, sc, S, rows)
+    del out
+    torch.cuda.empty_cache()
+    ref = oracle.scan(osc, sc, leg, rows, mode=mode, seed=6)
+    st = compare(g, ref, expected_mode=(mode == 1))
+    print(f"urban mode {mode}: {st}")
+    assert st["pulses"] == len(rows) and st["echoes"] > 3000, st
