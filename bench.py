@@ -209,20 +209,71 @@ def ncu_traffic(workload_name, pulses):
     return float(m_b.group(1)) * pulses
 
 
-def algorithmic_bytes(w, layout, subray_outputs=False):
-    """Compulsory traffic of one scan launch: every output byte written once,
-    every scene byte (BVH nodes, packed triangles, reflectance, voxels) read once."""
+def output_bytes(layout, subray_outputs=False):
+    """Bytes one scan launch writes: waveform rows, window, count, flags and K
+    echo slots (range, amplitude, bin, 8-byte object) per pulse."""
     P = layout["total_pulses"]
     out = layout["waveform_floats"] * 4 + P * (4 + 4 + 1) + layout["echo_elems"] * (4 + 4 + 4 + 8)
     if subray_outputs:
         out += layout["subray_elems"] * 12
+    return int(out)
+
+
+def scene_bytes_once(w):
+    """Every scene byte read once: BVH nodes, packed triangles, reflectance, voxels."""
     scene = 0
     for s in w.scenes:
         n = s.n_triangles
         scene += max(n - 1, 0) * 64 + n * 48 + n * 4
         # grids that share one density array read it once
         scene += sum(int(np.prod(g.dims)) * 4 for g in {id(g.density): g for g in s.grids}.values())
-    return int(out + scene)
+    return int(scene)
+
+
+def algorithmic_bytes(w, layout, subray_outputs=False):
+    """Compulsory traffic of one scan launch: every output byte written once,
+    every scene byte read once."""
+    return output_bytes(layout, subray_outputs) + scene_bytes_once(w)
+
+
+def fetch_model(hg, w, gsc, mode, seed, per_leg=65536):
+    """What the pulses need from memory (helios_fetch_counts_sample on an
+    evenly spaced sample of at most per_leg pulses of each leg): means per
+    pulse, weighted by the legs' pulse counts, of the 4-wide nodes (128 B),
+    triangles (48 B) and distinct voxels (4 B) of each pulse's subrays, and
+    the resulting scene bytes per pulse."""
+    import torch
+    keys = ("nodes", "triangles", "voxels", "voxel_visits")
+    acc = {k: 0.0 for k in keys}
+    acc["fetch_bytes"] = 0.0
+    P = sampled = flagged = 0
+    for l in w.legs:
+        if l.n_pulses == 0:
+            continue
+        stride = max(1, -(-l.n_pulses // per_leg))
+        count = -(-l.n_pulses // stride)
+        c = hg.fetch_counts(gsc[l.scene_index], w.scanners[l.scanner_index], l, mode=mode, seed=seed,
+                            first=0, stride=stride, count=count)
+        fb = hg.fetch_bytes(c)
+        for k in keys:
+            acc[k] += float(c[k].double().mean()) * l.n_pulses
+        acc["fetch_bytes"] += float(fb.double().mean()) * l.n_pulses
+        flagged += int((c["flags"] != 0).sum())
+        P += l.n_pulses
+        sampled += count
+    torch.cuda.synchronize()
+    res = {k: v / max(P, 1) for k, v in acc.items()}
+    res.update(sampled_pulses=sampled, flagged_pulses=flagged,
+               coherence=res["voxel_visits"] / res["voxels"] if res["voxels"] > 0 else None)
+    return res
+
+
+BYTES_MODEL = ("per pulse: its output row (waveform 4*N_b, window, count, flags, K echo slots of "
+               "20 B) written once, plus what it needs from the scene as a union over its subrays, "
+               "counted by helios_fetch_counts_sample on a sample of the leg: 128 B per 4-wide BVH "
+               "node the beam cone enters, 48 B per triangle whose box the cone overlaps (each read "
+               "once per pulse however many subrays test it), 4 B per distinct voxel the subrays "
+               "march through; reuse across pulses (L1/L2) is not subtracted")
 
 
 # --------------------------------------------------------------------------
@@ -296,7 +347,9 @@ def run_ours(args, D):
            "step_ms_all": [round(x, 4) for x in per]}
     # roofline of the (single) kernel per step
     peaks, kind = measured_peaks()
-    alg = algorithmic_bytes(w, layout)
+    fm = fetch_model(hg, w, gsc, mode, 12345, per_leg=4096 if persistent else 65536)
+    alg = output_bytes(layout) + int(round(fm["fetch_bytes"] * P))
+    comp = algorithmic_bytes(w, layout)
     achieved = alg / (ms / 1e3) / 1e9
     traffic = ncu_traffic(args.workload, P) if args.workload == "als" and not args.small else None
     gk = max((2 if len(s.grids) > 1 else len(s.grids)) for s in w.scenes)
@@ -304,11 +357,11 @@ def run_ours(args, D):
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                        "algorithmic_bytes_per_launch": alg, "peak_source": kind, "kernel": kern,
-                       "bytes_model": "compulsory: every output byte written once (waveform 4*N_b, "
-                                      "window, count, flags, K echoes x 20 B per pulse) plus every "
-                                      "scene byte read once (64 B per BVH node, 52 B per triangle, "
-                                      "4 B per voxel); per-subray node/triangle/voxel visit counts "
-                                      "are not counted (no counting kernel variant)"}
+                       "bytes_model": BYTES_MODEL,
+                       "fetch_counts_per_pulse": {k: (round(v, 3) if isinstance(v, float) else v)
+                                                  for k, v in fm.items()},
+                       "compulsory_bytes_per_launch": comp,
+                       "frac_compulsory": comp / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     res["clocks"] = clocks
     if not args.no_extras:
         res["e2e"] = e2e(w, gsc, layout, out, args, stream, D)
@@ -341,12 +394,19 @@ def mls_step(args):
     ms = _timed(lambda: hg.scan(gsc, w.scanners, w.legs, seed=12345, out=out, subrays=False), 2, 2)
     P = w.n_pulses
     S = hg.subray_count(w.scanners[0].beam_sample_quality)
+    fm = fetch_model(hg, w, gsc, 0, 12345, per_leg=50_000)
+    alg = output_bytes(lay) + P * fm["fetch_bytes"]
+    peaks, _ = measured_peaks()
     res = {"workload": w.name, "description": w.note, "pulses": P, "subrays_per_pulse": S,
            "triangles": int(sum(s.n_triangles for s in w.scenes)),
            "voxel_trees": int(sum(len(s.grids) for s in w.scenes)),
            "voxels": int(sum(int(np.prod(g.dims)) for s in w.scenes for g in s.grids)),
            "scene_build_s": round(build_s, 3), "ms_per_step": ms,
-           "pulses_per_s": P / (ms / 1e3), "subrays_per_s": P * S / (ms / 1e3)}
+           "pulses_per_s": P / (ms / 1e3), "subrays_per_s": P * S / (ms / 1e3),
+           "roofline": {"bytes_per_pulse": round(alg / P, 1), "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                        "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "fetch_counts_per_pulse": {k: (round(v, 3) if isinstance(v, float) else v)
+                                                   for k, v in fm.items()}}}
     del out, gsc
     torch.cuda.empty_cache()
     return res
@@ -556,11 +616,31 @@ def adjoint_ratio(args):
     f_ms = timed(fwd)
     b_ms = timed(lambda: bwd(gW))
     s_ms = timed(lambda: hg.scan([gs], [sc], [leg], mode=0, out=out))
+    # algorithmic bytes per kernel: the per-pulse fetch model of each mode
+    # (the forwards also write the subray hit/range checkpoint); the adjoint
+    # reads dL/dW, the window and the checkpoint, needs the expected mode's
+    # fetches and updates a gradient (read + write, 8 B) per distinct voxel
+    P = leg.n_pulses
+    S = hg.subray_count(sc.beam_sample_quality)
+    peaks, kind = measured_peaks()
+    fm = {m: fetch_model(hg, w, [gs], m, 12345 if m == 0 else 0) for m in (0, 1)}
+    outb = output_bytes(lay, subray_outputs=True)
+    per_kernel = {
+        "stochastic_forward": (outb + P * fm[0]["fetch_bytes"], s_ms),
+        "expected_forward": (outb + P * fm[1]["fetch_bytes"], f_ms),
+        "adjoint": (P * (4 * sc.n_bins + 4 + 8 * S + fm[1]["fetch_bytes"] + 8 * fm[1]["voxels"]), b_ms),
+    }
+    roof = {k: {"bytes_per_pulse": round(b / P, 1), "achieved_gbs": b / (t / 1e3) / 1e9,
+                "frac": b / (t / 1e3) / 1e9 / peaks["hbm_gbs"]} for k, (b, t) in per_kernel.items()}
     return {"workload": w.name, "pulses": leg.n_pulses, "expected_forward_ms": f_ms,
             "adjoint_ms": b_ms, "adjoint_forward_ratio": b_ms / f_ms,
             "stochastic_forward_ms": s_ms,
             "stochastic_pulses_per_s": leg.n_pulses / (s_ms / 1e3),
-            "expected_pulses_per_s": leg.n_pulses / (f_ms / 1e3)}
+            "expected_pulses_per_s": leg.n_pulses / (f_ms / 1e3),
+            "roofline": roof, "peak_source": kind,
+            "fetch_counts_per_pulse": {("stochastic", "expected")[m]: {k: (round(v, 3) if isinstance(v, float) else v)
+                                                                      for k, v in fm[m].items()}
+                                       for m in (0, 1)}}
 
 
 # --------------------------------------------------------------------------

@@ -153,6 +153,7 @@ typedef struct {
     int64_t device_bytes;      /* bytes owned by the scene */
     int32_t n_meshes;
     int32_t n_grids;
+    int64_t n_bvh4_nodes;      /* nodes of its 4-wide collapse (the beam-cone walk's tree) */
 } helios_scene_info;
 
 /* Build the acceleration structure on the device (Sec. 5.1's role, here an
@@ -392,6 +393,48 @@ HELIOS_API helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_
                                   const helios_scan_opts* opts, const float* d_waveform,
                                   const int32_t* window_bin, const int64_t* subray_hit,
                                   const helios_scene_grads* grads, void* cuda_stream);
+
+/* Fetch counts of one pulse: what it needs from memory, as a union over its
+ * subrays.  A measurement aid for the roofline's algorithmic bytes (the
+ * paper has no counterpart): a pulse's bytes are its output row plus
+ * 128 nodes + 48 triangles + 4 voxels. */
+typedef struct {
+    int64_t nodes;         /* 4-wide BVH nodes (128 B) the beam cone enters: the root and
+                              each internal slot whose box the cone overlaps */
+    int64_t triangles;     /* triangles (48 B) whose widened box the cone overlaps: the
+                              candidates every subray of the pulse tests */
+    int64_t voxels;        /* distinct voxels (4 B density) the subrays march through, each
+                              up to where the scan's march stops in the given mode */
+    int64_t voxel_visits;  /* voxel visits summed over the subrays */
+    int32_t flags;         /* HELIOS_FC_* */
+    int32_t reserved;
+} helios_fetch_counts;
+
+#define HELIOS_FC_STACK         0x01  /* cone walk stack full: nodes, triangles undercounted */
+#define HELIOS_FC_LIST_OVERFLOW 0x02  /* more candidates than the scan's per-pulse list holds
+                                         (128): the scan traverses per subray for this pulse */
+#define HELIOS_FC_SET_FULL      0x04  /* over 3072 distinct voxels: later visits counted as
+                                         distinct (an upper bound) */
+#define HELIOS_FC_MARCH_CAP     0x08  /* a march hit its step cap */
+
+/* Fetch counts of `count` pulses of one leg: pulse first + i * stride of the
+ * leg (0-based within the leg's n_pulses; first >= 0, stride >= 1, the last
+ * one < n_pulses), poses and draws as helios_scan_legs with the same seed
+ * and mode (Sec. 3.2-3.5).  The cone is the one the scan walks: half-angle
+ * atan of the half divergence (Sec. 3.4), from the pulse origin, unbounded
+ * in range, tested against boxes conservatively (each box grown by the
+ * cone's radius at its farthest corner); with one subray per pulse the scan
+ * traverses per ray instead, and the count is still the cone's.  Voxel marches stop at the stochastic event (Eq.
+ * intersection_dist) in mode STOCHASTIC, at the subray's triangle hit in
+ * mode EXPECTED, at the first dense voxel of an opaque grid in both.  out:
+ * device array of `count` entries, written on cuda_stream (not on the scan
+ * path; not timed with it).  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+HELIOS_API helios_status helios_fetch_counts_sample(helios_scene* scene,
+                                                    const helios_scanner_desc* scanner,
+                                                    const helios_leg_desc* leg, int32_t mode,
+                                                    uint64_t seed, int64_t first, int64_t stride,
+                                                    int64_t count, helios_fetch_counts* out,
+                                                    void* cuda_stream);
 
 /* Number of subrays for beam sample quality q (Sec. 3.4), or -1 if q < 0. */
 HELIOS_API int32_t helios_subray_count(int32_t q);

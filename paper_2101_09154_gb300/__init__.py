@@ -72,7 +72,7 @@ class SceneDesc(C.Structure):
 
 class SceneInfo(C.Structure):
     _fields_ = [("n_triangles", C.c_int64), ("n_bvh_nodes", C.c_int64), ("device_bytes", C.c_int64),
-                ("n_meshes", C.c_int32), ("n_grids", C.c_int32)]
+                ("n_meshes", C.c_int32), ("n_grids", C.c_int32), ("n_bvh4_nodes", C.c_int64)]
 
 
 class ScannerDesc(C.Structure):
@@ -113,6 +113,11 @@ class Outputs(C.Structure):
 class Layout(C.Structure):
     _fields_ = [("total_pulses", C.c_int64), ("waveform_floats", C.c_int64),
                 ("subray_elems", C.c_int64), ("echo_elems", C.c_int64)]
+
+
+class FetchCounts(C.Structure):
+    _fields_ = [("nodes", C.c_int64), ("triangles", C.c_int64), ("voxels", C.c_int64),
+                ("voxel_visits", C.c_int64), ("flags", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SceneGrads(C.Structure):
@@ -163,6 +168,10 @@ def lib():
         l.helios_scan_adjoint.restype = st
         l.helios_lad_table.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
         l.helios_lad_table.restype = st
+        l.helios_fetch_counts_sample.argtypes = [C.c_void_p, C.POINTER(ScannerDesc), C.POINTER(LegDesc),
+                                                 C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_int64,
+                                                 C.c_void_p, C.c_void_p]
+        l.helios_fetch_counts_sample.restype = st
         l.helios_subray_count.argtypes = [C.c_int32]
         l.helios_subray_count.restype = C.c_int32
         l.helios_last_error.restype = C.c_char_p
@@ -516,6 +525,39 @@ def scan_adjoint(scenes, scanners, legs, d_waveform, window_bin, subray_hit=None
                                      C.byref(opts), _ptr(d_waveform), _ptr(window_bin),
                                      _ptr(subray_hit), gs, _stream_handle(stream)))
     return grads
+
+
+# helios_fetch_counts: bytes of one fetch of each kind, and the flag bits
+NODE4_BYTES, TRIANGLE_BYTES, VOXEL_BYTES = 128, 48, 4
+FC_STACK, FC_LIST_OVERFLOW, FC_SET_FULL, FC_MARCH_CAP = 0x01, 0x02, 0x04, 0x08
+
+
+def fetch_counts(scene, scanner, leg, mode=MODE_STOCHASTIC, seed=0, first=0, stride=1, count=None,
+                 stream=None):
+    """What pulses first + i * stride of one leg need from memory, each as a
+    union over its subrays (helios_fetch_counts_sample): a dict of int64
+    tensors on the scene's device, keys nodes, triangles, voxels,
+    voxel_visits and flags (FC_* bits).  count defaults to every such pulse
+    of the leg."""
+    torch = _torch()
+    if count is None:
+        count = max(0, -(-(int(leg.n_pulses) - int(first)) // int(stride)))
+    assert C.sizeof(FetchCounts) == 5 * 8       # one row of five int64 per pulse
+    raw = torch.zeros((int(count), 5), dtype=torch.int64, device=scene.device)
+    with torch.cuda.device(scene.device):
+        _check(lib().helios_fetch_counts_sample(scene.handle, C.byref(scanner_desc(scanner)),
+                                                C.byref(leg_desc(leg)), int(mode),
+                                                int(seed) & (2 ** 64 - 1), int(first), int(stride),
+                                                int(count), _ptr(raw), _stream_handle(stream)))
+    return {"nodes": raw[:, 0], "triangles": raw[:, 1], "voxels": raw[:, 2],
+            "voxel_visits": raw[:, 3], "flags": raw[:, 4] & 0xFFFFFFFF}
+
+
+def fetch_bytes(counts):
+    """Scene bytes per pulse of fetch_counts: 128 per 4-wide node, 48 per
+    triangle, 4 per voxel (an int64 tensor)."""
+    return (NODE4_BYTES * counts["nodes"] + TRIANGLE_BYTES * counts["triangles"]
+            + VOXEL_BYTES * counts["voxels"])
 
 
 class WaveformFunction:

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhelios_gb300.so")
-SOURCES = ["helios_api.cu", "bvh.cu", "scan.cu", "adjoint.cu", "lad.cu"]
+SOURCES = ["helios_api.cu", "bvh.cu", "scan.cu", "adjoint.cu", "lad.cu", "stats.cu"]
 HEADERS = ["hg_device.cuh", "hg_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -587,6 +587,7 @@ helios_status helios_scene_get_info(const helios_scene* scene, helios_scene_info
     info->device_bytes = scene->bytes;
     info->n_meshes = scene->n_mesh;
     info->n_grids = scene->n_grid;
+    info->n_bvh4_nodes = scene->n_node4;
     return HELIOS_OK;
 }
 
@@ -725,6 +726,30 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     st = build_occupancy(L.scenes, scenes, (cudaStream_t)cuda_stream, masks, grads);
     if (st != HELIOS_OK) return st;
     return launch_adjoint(L, (cudaStream_t)cuda_stream);
+}
+
+helios_status helios_fetch_counts_sample(helios_scene* scene, const helios_scanner_desc* scanner,
+                                         const helios_leg_desc* leg, int32_t mode, uint64_t seed,
+                                         int64_t first, int64_t stride, int64_t count,
+                                         helios_fetch_counts* out, void* cuda_stream) {
+    g_err.clear();
+    if (!scene || !scanner || !leg) return set_error(HELIOS_ERR_INVALID_ARG, "scene, scanner, leg must not be NULL");
+    if (mode != HELIOS_MODE_STOCHASTIC && mode != HELIOS_MODE_EXPECTED)
+        return set_error(HELIOS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (count < 0 || first < 0 || stride < 1)
+        return set_error(HELIOS_ERR_INVALID_ARG, "need count >= 0, first >= 0, stride >= 1");
+    if (count > 0 && !out) return set_error(HELIOS_ERR_INVALID_ARG, "out must not be NULL");
+    helios_leg_desc L = *leg;
+    L.scene_index = 0;
+    L.scanner_index = 0;
+    LegPlan P;
+    helios_status st = plan_legs(scanner, 1, &L, 1, 1, 256, mode, P);
+    if (st != HELIOS_OK) return st;
+    if (count > 0 && (first >= L.n_pulses || (count - 1) > (L.n_pulses - 1 - first) / stride))
+        return set_error(HELIOS_ERR_INVALID_ARG, "sampled pulses must lie inside the leg's %lld pulses",
+                         (long long)L.n_pulses);
+    return launch_fetch_counts(dev_scene(scene), derive_scanner(*scanner), kernel_leg(P.legs[0], scanner),
+                               mode, seed, first, stride, count, out, (cudaStream_t)cuda_stream);
 }
 
 }  // extern "C"

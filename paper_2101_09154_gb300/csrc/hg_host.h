@@ -74,6 +74,10 @@ helios_status launch_adjoint(const AdjointLaunch& L, cudaStream_t st);
 
 helios_status build_bvh(helios_scene* s, const helios_scene_desc* desc, cudaStream_t st);
 
+helios_status launch_fetch_counts(const DevScene& sc, const DevScanner& sn, const DevLeg& lg,
+                                  int mode, uint64_t seed, int64_t first, int64_t stride,
+                                  int64_t count, helios_fetch_counts* out, cudaStream_t st);
+
 // Brick occupancy masks of the scenes' voxel grids, formed in stream order from
 // the densities as they are when the stream reaches them.  Sets each grid's
 // occ (and, given gradients, its ddens): in DevScene::grid for a one-grid

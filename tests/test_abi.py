@@ -77,6 +77,16 @@ def test_invalid_arguments_return_codes_without_a_gpu(lib):
                                      1024, None)
     assert code == -1
     assert b"n_scenes" in lib.helios_last_error()
+    # fetch counts: a NULL scene or a sample outside the leg is refused on the host
+    sd, ld = hg.scanner_desc(scenes.Scanner()), hg.leg_desc(scenes.Leg(n_pulses=10))
+    assert lib.helios_fetch_counts_sample(None, ctypes.byref(sd), ctypes.byref(ld), 0, 0, 0, 1, 4,
+                                          ctypes.c_void_p(16), None) == -1
+    assert b"NULL" in lib.helios_last_error()
+    assert lib.helios_fetch_counts_sample(ctypes.c_void_p(16), ctypes.byref(sd), ctypes.byref(ld), 0, 0,
+                                          4, 3, 3, ctypes.c_void_p(16), None) == -1
+    assert b"inside the leg" in lib.helios_last_error()
+    assert lib.helios_fetch_counts_sample(ctypes.c_void_p(16), ctypes.byref(sd), ctypes.byref(ld), 0, 0,
+                                          0, 0, 3, ctypes.c_void_p(16), None) == -1
     # leaf-angle tables: bad requests are refused before any launch
     assert lib.helios_lad_table(0, 91, ctypes.c_void_p(16), None) == -1
     assert lib.helios_lad_table(7, 91, ctypes.c_void_p(16), None) == -1
@@ -95,7 +105,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     import paper_2101_09154_gb300 as hg
     structs = {"helios_voxel_desc": hg.VoxelDesc, "helios_mesh_desc": hg.MeshDesc,
                "helios_scanner_desc": hg.ScannerDesc, "helios_leg_desc": hg.LegDesc,
-               "helios_outputs": hg.Outputs, "helios_scan_opts": hg.ScanOpts}
+               "helios_outputs": hg.Outputs, "helios_scan_opts": hg.ScanOpts,
+               "helios_fetch_counts": hg.FetchCounts, "helios_scene_info": hg.SceneInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "helios.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
