@@ -252,7 +252,8 @@ typedef struct {
     int32_t persistent;           /* 1: all legs in one launch over a work queue */
     uint64_t seed;                /* Philox key */
     int32_t block_threads;        /* 0: default (256) */
-    int32_t rays_per_block;       /* 0: default; target subrays per work item */
+    int32_t rays_per_block;       /* 0: default (768); target subrays per work item (scan and
+                                     adjoint), <= 4096 */
     int32_t blocks_per_sm;        /* 0: occupancy-derived */
     int32_t reserved;
 } helios_scan_opts;

@@ -494,7 +494,7 @@ def scan_static(scenes, scanners, legs, mode=MODE_STOCHASTIC, seed=0, out=None, 
 
 
 def scan_adjoint(scenes, scanners, legs, d_waveform, window_bin, subray_hit=None, grads=None,
-                 stream=None, block_threads=0):
+                 stream=None, block_threads=0, rays_per_block=0):
     """Accumulate dL/d(reflectance), dL/d(density) for dL/dW = d_waveform (expected mode).
 
     Returns a list (one per scene) of dicts {"reflectance": [...], "density": [...]}.
@@ -519,7 +519,7 @@ def scan_adjoint(scenes, scanners, legs, d_waveform, window_bin, subray_hit=None
     sh = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     sd = (ScannerDesc * len(scanners))(*[scanner_desc(s) for s in scanners])
     ld = (LegDesc * max(len(legs), 1))(*[leg_desc(l) for l in legs])
-    opts = ScanOpts(mode=MODE_EXPECTED, block_threads=int(block_threads))
+    opts = ScanOpts(mode=MODE_EXPECTED, block_threads=int(block_threads), rays_per_block=int(rays_per_block))
     d_waveform = d_waveform.contiguous()
     _check(lib().helios_scan_adjoint(sh, len(scenes), sd, len(scanners), ld, len(legs),
                                      C.byref(opts), _ptr(d_waveform), _ptr(window_bin),

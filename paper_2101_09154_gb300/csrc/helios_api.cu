@@ -697,8 +697,12 @@ helios_status helios_scan_adjoint(helios_scene* const* scenes, int32_t n_scenes,
     int threads = opts->block_threads > 0 ? opts->block_threads : 256;
     if (threads % 32 != 0 || threads < 64 || threads > 256)
         return set_error(HELIOS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 64..256");
+    // items of ~768 subrays (40 pulses at 19 subrays): with 8 warps per block a
+    // smaller item leaves warps idle at the per-item barrier
+    const int rays = opts->rays_per_block > 0 ? opts->rays_per_block : 768;
+    if (rays > 4096) return set_error(HELIOS_ERR_INVALID_ARG, "rays_per_block must be <= 4096");
     LegPlan P;
-    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, 256, HELIOS_MODE_EXPECTED, P);
+    st = plan_legs(scanners, n_scanners, legs, n_legs, n_scenes, rays, HELIOS_MODE_EXPECTED, P);
     if (st != HELIOS_OK) return st;
     AdjointLaunch L;
     for (int i = 0; i < n_scenes; ++i) {

@@ -47,6 +47,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--block-threads", type=int, default=0, help="0: the library's default")
+    ap.add_argument("--rays-per-block", type=int, default=0, help="subrays per work item, 0: the library's default")
     a = ap.parse_args(argv)
 
     import torch
@@ -63,7 +64,8 @@ def main(argv=None):
     out = hg.alloc_outputs(lay, dev, subrays=True)
 
     def scan():
-        hg.scan(gsc, w.scanners, w.legs, mode=mode, out=out, block_threads=a.block_threads)
+        hg.scan(gsc, w.scanners, w.legs, mode=mode, out=out, block_threads=a.block_threads,
+                rays_per_block=a.rays_per_block)
 
     fn = scan
     if a.kernel == "adjoint":
@@ -82,7 +84,8 @@ def main(argv=None):
 
         def fn():
             hg.scan_adjoint(gsc, w.scanners, w.legs, gW, out["window_bin"], out["subray_hit"],
-                            grads=grads, block_threads=a.block_threads)
+                            grads=grads, block_threads=a.block_threads,
+                            rays_per_block=a.rays_per_block)
     for _ in range(a.warmup):
         fn()
     torch.cuda.synchronize()
@@ -95,7 +98,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.repeat, 1)
     print(json.dumps({"workload": w.name, "kernel": a.kernel, "pulses": int(w.n_pulses),
-                      "block_threads": a.block_threads,
+                      "block_threads": a.block_threads, "rays_per_block": a.rays_per_block,
                       "repeat": a.repeat, "ms_per_call": ms,
                       "pulses_per_s": w.n_pulses / (ms / 1e3)}), flush=True)
 
