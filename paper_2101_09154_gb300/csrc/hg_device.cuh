@@ -682,7 +682,10 @@ __device__ __forceinline__ bool cone_slab(const RayF& r, float ta, const float a
     const float fx = fmaxf(fabsf(b[0] - r.ox), fabsf(b[3] - r.ox));
     const float fy = fmaxf(fabsf(b[1] - r.oy), fabsf(b[4] - r.oy));
     const float fz = fmaxf(fabsf(b[2] - r.oz), fabsf(b[5] - r.oz));
-    const float R = ta * sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
+    // q rsqrt(q) is within 2^-22 of sqrt(q): far inside the cone's 0.1% angle
+    // margin (ta), so the test stays conservative at a third of the cost
+    const float q = fmaxf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 1.0e-30f);
+    const float R = ta * (q * rsqrtf(q));
     float tx0 = fmaf(b[0], r.idx, -r.oix), tx1 = fmaf(b[3], r.idx, -r.oix);
     float ty0 = fmaf(b[1], r.idy, -r.oiy), ty1 = fmaf(b[4], r.idy, -r.oiy);
     float tz0 = fmaf(b[2], r.idz, -r.oiz), tz1 = fmaf(b[5], r.idz, -r.oiz);
