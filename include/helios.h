@@ -84,7 +84,7 @@ typedef int32_t helios_status;
 #define HELIOS_PLATFORM_LINEAR 1
 #define HELIOS_PULSE_GAUSSIAN  0
 #define HELIOS_PULSE_CARLSSON  1     /* Eq. beam_time: (t/tau)^2 exp(-t/tau) */
-#define HELIOS_MODE_STOCHASTIC 0     /* Eq. intersection_dist with Philox draws */
+#define HELIOS_MODE_STOCHASTIC 0     /* Eq. intersection_dist with Philox4x32-10 draws */
 #define HELIOS_MODE_EXPECTED   1     /* expected transmittance, differentiable */
 
 typedef struct helios_scene helios_scene; /* opaque; owns its BVH buffers */
@@ -132,8 +132,8 @@ typedef struct {
 } helios_voxel_desc;
 
 /* A scene: meshes are concatenated in order; triangle id = offset of its mesh
- * + face index.  At most 16 meshes and 4096 voxel grids per scene
- * (HELIOS_ERR_UNSUPPORTED otherwise).  The grids' boxes must have disjoint
+ * + face index.  At most 16 meshes, 4096 voxel grids and 2^40 - 1 voxels in
+ * all per scene (HELIOS_ERR_UNSUPPORTED otherwise).  The grids' boxes must have disjoint
  * interiors (touching faces are allowed, and so are overlaps thinner than
  * 1e-6 of the largest box edge; INVALID_ARG otherwise): a ray's
  * segments in them then follow the order of its entry points, which is the
@@ -244,13 +244,15 @@ typedef struct {
     int64_t first_pulse;          /* resume: the leg's pulses first_pulse .. first_pulse +
                                      n_pulses - 1 are scanned into n_pulses output rows.  Every
                                      draw is keyed by the absolute pulse index, so the rows equal
-                                     those of the whole leg (>= 0; INVALID_ARG otherwise) */
+                                     those of the whole leg (first_pulse >= 0 and
+                                     first_pulse + n_pulses <= 2^44; INVALID_ARG otherwise) */
 } helios_leg_desc;
 
 typedef struct {
     int32_t mode;                 /* HELIOS_MODE_* */
     int32_t persistent;           /* 1: all legs in one launch over a work queue */
-    uint64_t seed;                /* Philox key */
+    uint64_t seed;                /* Philox4x32-10 key (counter: pulse, stream, subray or echo,
+                                     voxel id, leg id) */
     int32_t block_threads;        /* 0: default (256) */
     int32_t rays_per_block;       /* 0: default (768); target subrays per work item (scan and
                                      adjoint), <= 4096 */

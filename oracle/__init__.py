@@ -93,8 +93,8 @@ def lib():
         if _lib is None:
             l = C.CDLL(build())
             d3 = C.POINTER(C.c_double)
-            l.or_philox4x64_10.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
-            l.or_uniform24.argtypes = [C.c_uint64]
+            l.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            l.or_uniform24.argtypes = [C.c_uint32]
             l.or_uniform24.restype = C.c_double
             l.or_subray_count.argtypes = [C.c_int]
             l.or_subray_angles.argtypes = [C.c_int, C.c_double, C.c_int, d3, d3]
@@ -313,11 +313,11 @@ def subray_angles(q, theta_r, s):
     return a.value, p.value
 
 
-def philox4x64_10(ctr, key):
-    c = (C.c_uint64 * 4)(*[int(x) & (2 ** 64 - 1) for x in ctr])
-    k = (C.c_uint64 * 2)(*[int(x) & (2 ** 64 - 1) for x in key])
-    o = (C.c_uint64 * 4)()
-    lib().or_philox4x64_10(c, k, o)
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
     return [int(x) for x in o]
 
 

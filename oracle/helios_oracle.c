@@ -31,26 +31,26 @@
 #define OR_C 299792458.0 /* speed of light, Sec. 3.4 */
 
 /* ------------------------------------------------------------------------ */
-/* Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11: "Parallel random      */
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11: "Parallel random      */
 /* numbers: as easy as 1, 2, 3").  Replaces the seeded sequential RNG of      */
 /* Sec. 3.7 with a counter-based one, so draws do not depend on thread order. */
 /* ------------------------------------------------------------------------ */
-static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
-    __uint128_t p = (__uint128_t)a * (__uint128_t)b;
-    *hi = (uint64_t)(p >> 64);
-    *lo = (uint64_t)p;
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
 }
 
-void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
-    uint64_t k0 = key[0], k1 = key[1];
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
     for (int r = 0; r < 10; ++r) {
-        uint64_t h0, l0, h1, l1;
-        mulhilo64(M0, x0, &h0, &l0);
-        mulhilo64(M1, x2, &h1, &l1);
-        uint64_t y0 = h1 ^ x1 ^ k0, y1 = l1, y2 = h0 ^ x3 ^ k1, y3 = l0;
+        uint32_t h0, l0, h1, l1;
+        mulhilo32(M0, x0, &h0, &l0);
+        mulhilo32(M1, x2, &h1, &l1);
+        uint32_t y0 = h1 ^ x1 ^ k0, y1 = l1, y2 = h0 ^ x3 ^ k1, y3 = l0;
         x0 = y0; x1 = y1; x2 = y2; x3 = y3;
         k0 += W0; k1 += W1;
     }
@@ -59,14 +59,21 @@ void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out
 
 /* a uniform in (0,1): (top 23 bits + 1/2) * 2^-23, i.e. odd multiples of 2^-24,
  * exactly representable in FP32 too (so both precisions draw the same number) */
-double or_uniform24(uint64_t w) { return ((double)(w >> 41) + 0.5) * (1.0 / 8388608.0); }
+double or_uniform24(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
-/* Counter layout: (pulse, stream<<32 | subray_or_echo, voxel_or_0, leg_id), key (seed, 0). */
+/* Counter (128 bits) of one draw: word 0 = pulse bits 0-31; word 1 = pulse bits
+ * 32-43, stream (2 bits) at bit 12, subray or echo index (9 bits) at bit 14,
+ * voxel id bits 32-39 at bit 23; word 2 = voxel id bits 0-31; word 3 = leg id.
+ * Key = the seed's low and high words.  Pulses < 2^44, voxel ids < 2^40. */
 static void draw(uint64_t seed, uint32_t leg, int64_t pulse, uint32_t stream, uint32_t idx,
-                 uint64_t sub, uint64_t out[4]) {
-    uint64_t c[4] = {(uint64_t)pulse, ((uint64_t)stream << 32) | idx, sub, (uint64_t)leg};
-    uint64_t k[2] = {seed, 0};
-    or_philox4x64_10(c, k, out);
+                 uint64_t sub, uint32_t out[4]) {
+    const uint64_t p = (uint64_t)pulse;
+    uint32_t c[4] = {(uint32_t)p,
+                     ((uint32_t)(p >> 32) & 0xFFFu) | ((stream & 3u) << 12) | ((idx & 0x1FFu) << 14) |
+                         (((uint32_t)(sub >> 32) & 0xFFu) << 23),
+                     (uint32_t)sub, leg};
+    uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox4x32_10(c, k, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -176,7 +183,7 @@ void or_pulse_ray(const or_scanner* sn, const or_leg* lg, int64_t k, uint64_t se
     /* platform noise (Sec. 3.7): N(0, sigma) on each axis, Box-Muller on the
      * Philox draw of stream 2 for this pulse */
     if (lg->platform_noise_m > 0.0) {
-        uint64_t w[4];
+        uint32_t w[4];
         draw(seed, lg->leg_id, k, 2, 0, 0, w);
         double u1 = or_uniform24(w[0]), u2 = or_uniform24(w[1]);
         double u3 = or_uniform24(w[2]), u4 = or_uniform24(w[3]);
@@ -892,14 +899,14 @@ static void trace_subray(job_t* J, int64_t k, int s, const double o[3], const do
             if (v->corner && v->alt_vid >= 0) {
                 double sa = proj_factor(g, ds) * (double)g->dens[v->alt_vid];
                 if (sa > 0.0) {
-                    uint64_t w[4];
+                    uint32_t w[4];
                     draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->alt_vid), w);
                     double sal = -log(or_uniform24(w[0])) / sa;
                     if (sal <= 2.0 * eps_rel(v->t_out)) *flags |= OR_F_VOX;
                 }
             }
             if (v->sigma <= 0.0) continue;
-            uint64_t w[4];
+            uint32_t w[4];
             draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->vid), w);
             double u = or_uniform24(w[0]);
             double sdist = -log(u) / v->sigma;
@@ -1067,7 +1074,7 @@ static void trace_subray_forced(job_t* J, int64_t k, int s, const double o[3], c
         if (hit_main || hit_alt) {
             int64_t vv = hit_main ? v->vid : v->alt_vid;
             double sg = proj_factor(g, ds) * (double)g->dens[vv];
-            uint64_t w[4];
+            uint32_t w[4];
             draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, vv), w);
             double sdist = sg > 0.0 ? -log(or_uniform24(w[0])) / sg : INFINITY;
             double len = v->t_out - v->t_in;
@@ -1090,7 +1097,7 @@ static void trace_subray_forced(job_t* J, int64_t k, int s, const double o[3], c
             return;
         }
         if (v->sigma <= 0.0) continue;
-        uint64_t w[4];
+        uint32_t w[4];
         draw(J->seed, J->lg->leg_id, k, 0, (uint32_t)s, (uint64_t)vox_draw(sc, v, v->vid), w);
         double sdist = -log(or_uniform24(w[0])) / v->sigma;
         double len = v->t_out - v->t_in;
@@ -1324,7 +1331,7 @@ static void simulate_pulse(job_t* J, int64_t row) {
         double tb = (double)(m + b) * dt;
         double Rc = sn->pulse_shape == 0 ? 0.5 * OR_C * tb * 1e-9
                                          : 0.5 * OR_C * (tb - 2.0 * sn->pulse_length_ns / 1.75) * 1e-9;
-        uint64_t w[4];
+        uint32_t w[4];
         draw(J->seed, lg->leg_id, k, 1, (uint32_t)e, 0, w);
         double u1 = or_uniform24(w[0]), u2 = or_uniform24(w[1]);
         double z = sqrt(-2.0 * log(u1)) * cos(2.0 * OR_PI * u2);

@@ -109,8 +109,8 @@ typedef struct {
 
 #define OR_FREE_HIT    (-2)       /* force_hit entry: the oracle decides the event */
 
-void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
-double or_uniform24(uint64_t w);
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform24(uint32_t w);
 int or_subray_count(int q);
 int or_subray_angles(int q, double theta_r, int s, double* alpha, double* phi);
 void or_onb(const double n[3], double u[3], double v[3]);

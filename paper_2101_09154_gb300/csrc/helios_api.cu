@@ -381,8 +381,9 @@ static helios_status plan_legs(const helios_scanner_desc* scanners, int32_t n_sc
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
-        if (L.first_pulse < 0 || L.first_pulse > ((int64_t)1 << 52))
-            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse must be in 0..2^52", l);
+        // draws are keyed by the absolute pulse index in 44 bits
+        if (L.first_pulse < 0 || L.first_pulse > kMaxPulseIndex - L.n_pulses)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse + n_pulses must be in 0..2^44", l);
         if (!(L.platform_noise_m >= 0.0f))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))
@@ -502,6 +503,10 @@ helios_status helios_build_scene(const helios_scene_desc* desc, void* cuda_strea
             return set_error(HELIOS_ERR_UNSUPPORTED, "grid %d: triangles + its voxels exceed 2^31 - 1", i);
         n_vox += nv;
     }
+    // draws are keyed by the voxel id in 40 bits
+    if (n_vox >= kMaxVoxelId)
+        return set_error(HELIOS_ERR_UNSUPPORTED, "the grids hold %lld voxels; at most 2^40 - 1 per scene",
+                         (long long)n_vox);
     helios_status r = check_grid_boxes(desc->grids, desc->n_grids);
     if (r != HELIOS_OK) return r;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -819,8 +824,9 @@ extern "C" helios_status helios_scan_legs_static(helios_scene* const* scenes, in
         if (L.platform != HELIOS_PLATFORM_STATIC && L.platform != HELIOS_PLATFORM_LINEAR)
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: unknown platform", l);
         if (L.n_pulses < 0) return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: n_pulses < 0", l);
-        if (L.first_pulse < 0 || L.first_pulse > ((int64_t)1 << 52))
-            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse must be in 0..2^52", l);
+        // draws are keyed by the absolute pulse index in 44 bits
+        if (L.first_pulse < 0 || L.first_pulse > kMaxPulseIndex - L.n_pulses)
+            return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: first_pulse + n_pulses must be in 0..2^44", l);
         if (!(L.platform_noise_m >= 0.0f))
             return set_error(HELIOS_ERR_INVALID_ARG, "leg %d: platform_noise_m must be >= 0", l);
         if (L.platform == HELIOS_PLATFORM_LINEAR && !(L.speed_mps >= 0.0))

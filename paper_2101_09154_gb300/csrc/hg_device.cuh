@@ -36,6 +36,8 @@ constexpr float kHalfCns = (float)(0.5e-9 * kC);
 // child0 is the lower child along `axis`, so the near child of a ray with
 // d[axis] >= 0 is child0.  Triangle t occupies tris[3t .. 3t+2]:
 //   (v0, global id), (v1, mesh), (v2, face).
+constexpr int64_t kMaxPulseIndex = (int64_t)1 << 44;   // pulse indices of the draws' counter
+constexpr int64_t kMaxVoxelId = (int64_t)1 << 40;      // voxel ids of the draws' counter
 constexpr int kReturnListCap = 256;   // expected-mode returns listed per lane and pulse
 constexpr int kConeCap = 16;          // candidate triangles per pulse in shared memory
 constexpr int kConeExt = 112;         // more in global scratch (non-static scans)
@@ -175,27 +177,41 @@ constexpr uint32_t kStEchoOverflow = 0x04u;
 constexpr int32_t kNoWindow = INT32_MIN;
 
 // ---------------------------------------------------------------------------
-// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11).  Counter layout:
-// (pulse, stream<<32 | subray_or_echo, voxel_or_0, leg_id), key (seed, 0).
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): its 32 x 32 -> 64-bit
+// products are single multiplies here (a 64-bit Philox multiply is several).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                           uint64_t k0, uint64_t k1, uint64_t out[4]) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+__device__ __forceinline__ void philox4x32(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t k0, uint32_t k1, uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint64_t h0 = __umul64hi(M0, c0), l0 = M0 * c0;
-        uint64_t h1 = __umul64hi(M1, c2), l1 = M1 * c2;
-        uint64_t y0 = h1 ^ c1 ^ k0, y2 = h0 ^ c3 ^ k1;
+        const uint32_t h0 = __umulhi(M0, c0), l0 = M0 * c0;
+        const uint32_t h1 = __umulhi(M1, c2), l1 = M1 * c2;
+        const uint32_t y0 = h1 ^ c1 ^ k0, y2 = h0 ^ c3 ^ k1;
         c0 = y0; c1 = l1; c2 = y2; c3 = l0;
         k0 += W0; k1 += W1;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// One draw's four words.  The 128-bit counter: pulse bits 0-31; pulse bits
+// 32-43 | stream << 12 | subray-or-echo index << 14 | voxel id bits 32-39 << 23;
+// voxel id bits 0-31; leg id.  The key is the seed.  Streams: 0 voxel
+// transmission (index = subray), 1 range noise (index = echo), 2 platform
+// noise.  The API keeps pulses below 2^44 and voxel ids below 2^40.
+__device__ __forceinline__ void draw4(uint64_t seed, uint32_t leg, int64_t pulse, uint32_t stream,
+                                      uint32_t idx, int64_t vox, uint32_t out[4]) {
+    const uint64_t p = (uint64_t)pulse, v = (uint64_t)vox;
+    philox4x32((uint32_t)p,
+               ((uint32_t)(p >> 32) & 0xFFFu) | (stream << 12) | ((idx & 0x1FFu) << 14) |
+                   (((uint32_t)(v >> 32) & 0xFFu) << 23),
+               (uint32_t)v, leg, (uint32_t)seed, (uint32_t)(seed >> 32), out);
+}
+
 // (top 23 bits + 1/2) * 2^-23: odd multiples of 2^-24, exact in FP32
-__device__ __forceinline__ float uniform23(uint64_t w) {
-    return ((float)(uint32_t)(w >> 41) + 0.5f) * (1.0f / 8388608.0f);
+__device__ __forceinline__ float uniform23(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,8 +242,8 @@ __device__ __forceinline__ void pulse_frame(const DevScanner& sn, const DevLeg& 
     if (lg.platform_noise > 0.0) {
         // platform noise (Sec. 3.7): N(0, sigma) per axis, Box-Muller on the
         // Philox draw of stream 2 for this pulse
-        uint64_t w[4];
-        philox4x64((uint64_t)k, 2ull << 32, 0ull, (uint64_t)lg.leg_id, seed, 0ull, w);
+        uint32_t w[4];
+        draw4(seed, lg.leg_id, k, 2u, 0u, 0, w);
         const double r1 = sqrt(-2.0 * log((double)uniform23(w[0])));
         const double r2 = sqrt(-2.0 * log((double)uniform23(w[2])));
         const double a1 = 2.0 * kPi * (double)uniform23(w[1]), a2 = 2.0 * kPi * (double)uniform23(w[3]);

@@ -238,9 +238,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         for (int i = tid; i < 2 * pc; i += blockDim.x) {
             const int e = i & 1;
             if (e < K) {
-                uint64_t w[4];
-                philox4x64((uint64_t)(p0 + (i >> 1)), (1ull << 32) | (uint64_t)e, 0ull,
-                           (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                uint32_t w[4];
+                draw4(P.seed, lg.leg_id, p0 + (i >> 1), 1u, (uint32_t)e, 0, w);
                 float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
                 s_noise[i] = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
             }
@@ -374,10 +373,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         float sigma = Gs * dens;
                                         if (MODE == 0) {
                                             // Eq. intersection_dist: s = -ln(u)/sigma
-                                            uint64_t w[4];
-                                            philox4x64((uint64_t)k, (uint64_t)(uint32_t)s,
-                                                       (uint64_t)(G.vox_off + v.vid), (uint64_t)lg.leg_id,
-                                                       P.seed, 0ull, w);
+                                            uint32_t w[4];
+                                            draw4(P.seed, lg.leg_id, k, 0u, (uint32_t)s, G.vox_off + v.vid, w);
                                             float sdist = -logf(uniform23(w[0])) / sigma;
                                             if (sdist < len) {
                                                 FF R = ff_add_f(t_in, sdist);
@@ -875,9 +872,8 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         if (pos < 2) {
                             z = s_noise[2 * pl + pos];
                         } else {
-                            uint64_t w[4];
-                            philox4x64((uint64_t)k, (1ull << 32) | (uint64_t)(uint32_t)pos, 0ull,
-                                       (uint64_t)lg.leg_id, P.seed, 0ull, w);
+                            uint32_t w[4];
+                            draw4(P.seed, lg.leg_id, k, 1u, (uint32_t)pos, 0, w);
                             float u1 = uniform23(w[0]), u2 = uniform23(w[1]);
                             z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
                         }

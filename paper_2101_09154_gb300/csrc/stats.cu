@@ -190,10 +190,8 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const __grid_const
                             const float len = ff_diff(t_out, t_in);
                             if (len > 0.0f && G.opaque) return false;
                             if (len > 0.0f && P.mode == HELIOS_MODE_STOCHASTIC) {
-                                uint64_t w[4];
-                                philox4x64((uint64_t)kj, (uint64_t)(uint32_t)s,
-                                           (uint64_t)(G.vox_off + v.vid), (uint64_t)lg.leg_id, P.seed,
-                                           0ull, w);
+                                uint32_t w[4];
+                                draw4(P.seed, lg.leg_id, kj, 0u, (uint32_t)s, G.vox_off + v.vid, w);
                                 const float sdist = -logf(uniform23(w[0])) / (Gs * dens);
                                 if (sdist < len) return false;
                             }

@@ -215,7 +215,7 @@ def test_host_side_fault_injection(lib, monkeypatch):
 
 def test_first_pulse_resume_layout_and_validation(lib):
     """A resumed leg (first_pulse = K) has n_pulses rows like any other; a
-    negative first_pulse is refused."""
+    negative first_pulse, or one whose last pulse reaches 2^44, is refused."""
     import paper_2101_09154_gb300 as hg
     import scenes
     sc = scenes.Scanner(n_bins=64)
@@ -228,6 +228,11 @@ def test_first_pulse_resume_layout_and_validation(lib):
     with pytest.raises(hg.HeliosError) as e:
         hg.output_layout([sc], [scenes.Leg(n_pulses=5, first_pulse=-1)])
     assert e.value.code == -1 and "first_pulse" in str(e.value)
+    # the draws' counter holds pulse indices below 2^44
+    hg.output_layout([sc], [scenes.Leg(n_pulses=5, first_pulse=2 ** 44 - 5)])
+    with pytest.raises(hg.HeliosError) as e:
+        hg.output_layout([sc], [scenes.Leg(n_pulses=5, first_pulse=2 ** 44 - 4)])
+    assert e.value.code == -1 and "2^44" in str(e.value)
 
 
 def test_scene_wrapper_checks_density_sizes_before_any_upload():
