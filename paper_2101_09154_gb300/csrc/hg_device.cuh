@@ -1029,6 +1029,25 @@ __device__ __forceinline__ void march_segment_ff(const March& m, const VoxSeg& v
     if (ff_less(m.t_end, t_out)) t_out = m.t_end;
 }
 
+// FP32 estimate of the current voxel's segment length, ending at t1 (its exit
+// crossing clipped to t_end, in FP32): the entry crossing is formed in FP32
+// like the exit ones.  Each end is within a few ulps of the float-float one
+// (no cancellation: the crossings grow away from the origin), so the length
+// is within 1e-6 of t1 of the exact one.
+__device__ __forceinline__ float segment_len32(const March& m, float t1) {
+    float t0 = m.t_enter.hi;
+    const int a = m.entry_axis;
+    if (a >= 0) {
+        const int i = a == 0 ? m.ix : (a == 1 ? m.iy : m.iz);
+        const int s = a == 0 ? m.sx : (a == 1 ? m.sy : m.sz);
+        const int p0 = a == 0 ? m.px : (a == 1 ? m.py : m.pz);
+        const float f0h = a == 0 ? m.f0hx : (a == 1 ? m.f0hy : m.f0hz);
+        const float ivh = a == 0 ? m.ivhx : (a == 1 ? m.ivhy : m.ivhz);
+        t0 = fmaxf(t0, cross32(s > 0 ? i : i + 1, p0, s, f0h, ivh, m.cell));
+    }
+    return t1 - t0;
+}
+
 // b - a for close float pairs (the hi difference is exact)
 __device__ __forceinline__ float ff_diff(const FF& b, const FF& a) {
     return (b.hi - a.hi) + (b.lo - a.lo);

@@ -346,7 +346,20 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                 VoxSeg v;
                                 if (!march_current(G, m, v)) return true;
                                 float dens = voxel_density<GK == 2>(G, m, v);
-                                if (dens > 0.0f) {
+                                // stochastic: the voxel's draw first; a draw beyond the FP32
+                                // segment by more than its rounding passes the voxel without
+                                // the float-float segment (the decision is the exact one)
+                                float sdist = 0.0f;
+                                bool clear = false;
+                                if (MODE == 0 && dens > 0.0f && !G.opaque) {
+                                    // Eq. intersection_dist: s = -ln(u)/sigma
+                                    uint32_t w[4];
+                                    draw4(P.seed, lg.leg_id, k, 0u, (uint32_t)s, G.vox_off + v.vid, w);
+                                    sdist = -logf(uniform23(w[0])) / (Gs * dens);
+                                    const float t1 = fminf(v.t_out32, m.t_end.hi);
+                                    clear = sdist > segment_len32(m, t1) + fmaf(1.0e-6f, fabsf(t1), 1.0e-6f);
+                                }
+                                if (dens > 0.0f && !clear) {
                                     FF t_in, t_out;
                                     march_segment_ff(m, v, t_in, t_out);
                                     float len = ff_diff(t_out, t_in);
@@ -370,12 +383,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                                         return false;
                                     }
                                     if (len > 0.0f) {
-                                        float sigma = Gs * dens;
                                         if (MODE == 0) {
-                                            // Eq. intersection_dist: s = -ln(u)/sigma
-                                            uint32_t w[4];
-                                            draw4(P.seed, lg.leg_id, k, 0u, (uint32_t)s, G.vox_off + v.vid, w);
-                                            float sdist = -logf(uniform23(w[0])) / sigma;
                                             if (sdist < len) {
                                                 FF R = ff_add_f(t_in, sdist);
                                                 rr.Rh = R.hi;
