@@ -505,8 +505,18 @@ def e2e(w, gsc, layout, out, args, stream, D):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = D.max(e0.elapsed_time(e1) / n)
+    # this box's device-to-host rate into the same pinned buffers (one plain
+    # copy of the waveform, after the timed steps): the bound the step meets
+    src, dst = out["waveform"], host_out["waveform"]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dst.copy_(src, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    link = src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
     return {"value": D.world * w.n_pulses / (ms / 1e3), "unit": "pulses/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n,
+            "d2h_link_gbs": link, "link_bound_ms": d2h / (link * 1e9) * 1e3}
 
 
 def _timed(fn, steps, warmup):
