@@ -127,9 +127,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 
 def test_scene_build_rejects_overlapping_grids_before_any_device_call(lib):
-    """Grid boxes must have disjoint interiors (touching is fine); the check
-    runs on the host before anything touches a device (the density pointers
-    here are never dereferenced)."""
+    """Grid boxes must have disjoint interiors (touching is fine) and hold fewer
+    than 2^40 voxels in all; the checks run on the host before anything
+    touches a device (the density pointers here are never dereferenced)."""
     import paper_2101_09154_gb300 as hg
 
     def grid(x0, n=4, cell=0.5):
@@ -151,6 +151,18 @@ def test_scene_build_rejects_overlapping_grids_before_any_device_call(lib):
         h = ctypes.c_void_p()
         code = lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h))
         assert code == -1 and b"overlap" in lib.helios_last_error()
+    # more than 2^40 - 1 voxels in all (the draws' counter holds 40 bits of voxel id):
+    # 513 grids of 1024 x 1024 x 2047 voxels, each below the per-grid 2^31 limit
+    gd = (hg.VoxelDesc * 513)(*[grid(3000.0 * i, 1024, 1.0) for i in range(513)])
+    for g in gd:
+        g.dims = (ctypes.c_int32 * 3)(1024, 1024, 2047)
+    desc = hg.SceneDesc()
+    desc.n_meshes = 0
+    desc.n_grids = 513
+    desc.grids = ctypes.cast(gd, ctypes.POINTER(hg.VoxelDesc))
+    h = ctypes.c_void_p()
+    assert lib.helios_build_scene(ctypes.byref(desc), None, ctypes.byref(h)) == -6
+    assert b"2^40" in lib.helios_last_error()
     # too many grids
     desc = hg.SceneDesc()
     desc.n_grids = 4097
