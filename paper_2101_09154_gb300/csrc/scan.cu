@@ -135,12 +135,12 @@ __device__ __forceinline__ void expected_returns(const DevScene& sc, const DevSc
 // per SM); capped at two blocks per SM it spills a little but runs 8% faster
 // (urban MLS).  Every other variant keeps the compiler's own choice.
 template <int MODE, int GK, int NL>
-__global__ void __launch_bounds__(256, (MODE == 1 && GK == 2) ? 2 : 0)
+__global__ void __launch_bounds__(256, (MODE >= 1 && GK == 2) ? 2 : 0)
 scan_kernel(const __grid_constant__ ScanParams<NL> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     RayRes* s_rr = reinterpret_cast<RayRes*>(smem);
     float2* s_r2 = reinterpret_cast<float2*>(s_rr + P.rays_cap);       // [rays_cap], expected mode
-    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_r2 + (MODE == 1 ? P.rays_cap : 0));
+    PulseFF* s_pf = reinterpret_cast<PulseFF*>(s_r2 + (MODE >= 1 ? P.rays_cap : 0));
     SubrayConst* s_sc = reinterpret_cast<SubrayConst*>(s_pf + P.pc_cap);
     float* s_tau = reinterpret_cast<float*>(s_sc + P.s_cap);
     // several grids, stochastic mode: the grid of each ray's voxel event
@@ -203,7 +203,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
         __syncthreads();
         if (new_leg) {
             for (int s = tid; s < S; s += blockDim.x) subray_const(lg.q, sn.theta_r, s, s_sc[s]);
-            if (MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0) {
+            if (MODE >= 1 && P.mom != nullptr && sn.pulse_shape == 0) {
                 for (int k = tid; k < 2 * P.mom_cb + 1; k += blockDim.x) {
                     float x = (float)(k - P.mom_cb) * dt;
                     s_pk[k] = exp2f(-x * x * sn.gk2);
@@ -415,7 +415,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         rr.P = return_power(sn, tb + dt_hit, tan_a, rho, cosi);
                     }
                     s_rr[r] = rr;
-                    if (MODE == 1) s_r2[r] = make_float2(r2h, r2l);
+                    if (MODE >= 1) s_r2[r] = make_float2(r2h, r2l);
                     if (fl) atomicOr(&s_pflag[pl], fl);
                     if (P.out.subray_hit) {
                         int64_t so = lg.sub_off + (p0 + pl) * S + s;
@@ -429,7 +429,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
             // ---------------- phase 2: waveform + echoes, one warp per pulse ----------------
             const int nbw = P.nb_cap;
             float* W = s_w + (size_t)warp * P.w_stride;
-            const bool mom_path = MODE == 1 && P.mom != nullptr && sn.pulse_shape == 0;
+            const bool mom_path = MODE == 1 || (MODE == 2 && P.mom != nullptr && sn.pulse_shape == 0);
             float* best = W + nbw;
             int64_t* bid = reinterpret_cast<int64_t*>(W + 2 * nbw);
             for (int pl = sb + warp; pl < pe; pl += nwarps) {
@@ -443,7 +443,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         FF r = ff_norm(rr.Rh, rr.Rl);
                         if (ff_less(r, rmin)) rmin = r;
                     }
-                    if (MODE == 1) {
+                    if (MODE >= 1) {
                         const float2 q = s_r2[(size_t)(pl - sb) * S + s];
                         FF r = ff_norm(q.x, q.y);
                         if (ff_less(r, rmin)) rmin = r;
@@ -508,7 +508,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                 int n_rl = 0;            // this lane's entries in the warp's return list
                 for (int b = zlo + 4 * lane; b < zhi && !in_regs; b += 128) {
                     *reinterpret_cast<float4*>(W + b) = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (MODE == 1 && !mom_path) {
+                    if (MODE >= 1 && !mom_path) {
                         *reinterpret_cast<float4*>(best + b) = make_float4(0.f, 0.f, 0.f, 0.f);
                         *reinterpret_cast<int4*>(bid + b) = make_int4(-1, -1, -1, -1);
                     }
@@ -860,7 +860,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                         }
                     }
                     if (ismax && pos < K) {
-                        if (MODE == 1) {
+                        if (MODE >= 1) {
                             if (mom_path) reinterpret_cast<int32_t*>(best)[pos] = b;
                             else obj = bid[b];
                         } else if (!(S <= 32 && P.out.echo_object)) {
@@ -892,7 +892,7 @@ scan_kernel(const __grid_constant__ ScanParams<NL> P) {
                     }
                     count += __popc(mk);
                 }
-                if (MODE == 1 && mom_path && P.out.echo_object && count > 0) {
+                if (MODE >= 1 && mom_path && P.out.echo_object && count > 0) {
                     const bool rl_ok = __all_sync(full, n_rl <= P.rl_cap);
                     // echo objects: re-march and evaluate every return at the echo
                     // bins only; the strongest contribution wins, ties to the first
@@ -1128,17 +1128,28 @@ static helios_status launch_one(const ScanParams<NL>& p, int threads, int blocks
 static int grid_kind(const DevScene& sc) { return sc.n_grid > 1 ? 2 : (sc.n_grid > 0 ? 1 : 0); }
 
 template <int NL>
-static helios_status dispatch(const ScanParams<NL>& p, int mode, int gk, int threads,
+static helios_status dispatch(const ScanParams<NL>& p, int kmode, int gk, int threads,
                               int blocks_per_sm, size_t smem, cudaStream_t st, int grid_cap) {
-    if (mode == 0) {
+    if (kmode == 0) {
         if (gk == 2) return launch_one<0, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
         if (gk == 1) return launch_one<0, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
         return launch_one<0, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
     }
-    if (gk == 2) return launch_one<1, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
-    if (gk == 1) return launch_one<1, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
-    return launch_one<1, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    if (kmode == 1) {
+        if (gk == 2) return launch_one<1, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+        if (gk == 1) return launch_one<1, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+        return launch_one<1, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    }
+    if (gk == 2) return launch_one<2, 2, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    if (gk == 1) return launch_one<2, 1, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
+    return launch_one<2, 0, NL>(p, threads, blocks_per_sm, smem, st, grid_cap);
 }
+
+// The kernel's mode: 0 stochastic; expected mode is 1 when every leg of the
+// launch sums its waveform from moment bins (Gaussian pulses, bins allocated)
+// and 2 otherwise, whose kernel also carries the direct sums (the smaller
+// kernel of 1 runs faster: 169 -> 158 ms on 2 M urban pulses)
+static int kernel_mode(int mode, bool direct) { return mode == 0 ? 0 : (direct ? 2 : 1); }
 
 // floats of per-warp shared waveform scratch: W, plus (expected mode) either
 // the best-contributor arrays of the direct path or the moment tile
@@ -1219,21 +1230,29 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         ~Free() { if (p) cudaFreeAsync(p, s); }
     } free_mom{nullptr, st}, free_rl{nullptr, st}, free_cext{nullptr, st};
     // the most blocks any launch below can have: per-block and per-warp scratch
+    const int kmode = kernel_mode(L.mode, direct || cb == 0);
     int grid = 0;
-    if (L.mode == 0)
+    if (kmode == 0)
         grid = L.persistent ? (gk == 2 ? max_grid<0, 2, kMaxLegs>(threads, L.blocks_per_sm, smem)
                                : gk == 1 ? max_grid<0, 1, kMaxLegs>(threads, L.blocks_per_sm, smem)
                                          : max_grid<0, 0, kMaxLegs>(threads, L.blocks_per_sm, smem))
                             : (gk == 2 ? max_grid<0, 2, 1>(threads, L.blocks_per_sm, smem)
                                : gk == 1 ? max_grid<0, 1, 1>(threads, L.blocks_per_sm, smem)
                                          : max_grid<0, 0, 1>(threads, L.blocks_per_sm, smem));
-    else
+    else if (kmode == 1)
         grid = L.persistent ? (gk == 2 ? max_grid<1, 2, kMaxLegs>(threads, L.blocks_per_sm, smem)
                                : gk == 1 ? max_grid<1, 1, kMaxLegs>(threads, L.blocks_per_sm, smem)
                                          : max_grid<1, 0, kMaxLegs>(threads, L.blocks_per_sm, smem))
                             : (gk == 2 ? max_grid<1, 2, 1>(threads, L.blocks_per_sm, smem)
                                : gk == 1 ? max_grid<1, 1, 1>(threads, L.blocks_per_sm, smem)
                                          : max_grid<1, 0, 1>(threads, L.blocks_per_sm, smem));
+    else
+        grid = L.persistent ? (gk == 2 ? max_grid<2, 2, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<2, 1, kMaxLegs>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<2, 0, kMaxLegs>(threads, L.blocks_per_sm, smem))
+                            : (gk == 2 ? max_grid<2, 2, 1>(threads, L.blocks_per_sm, smem)
+                               : gk == 1 ? max_grid<2, 1, 1>(threads, L.blocks_per_sm, smem)
+                                         : max_grid<2, 0, 1>(threads, L.blocks_per_sm, smem));
     // candidate lists longer than kConeCap continue in global scratch
     int32_t* cext = nullptr;
     const int cext_cap = kConeExt;
@@ -1298,7 +1317,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
             p.cext = cext; p.cext_cap = cext_cap;
             p.queue = nullptr;
             const int g = grid_kind(L.scenes[L.legs[l].scene]);
-            helios_status s = dispatch<1>(p, L.mode, g, threads, L.blocks_per_sm, smem, st, (int)items);
+            helios_status s = dispatch<1>(p, kmode, g, threads, L.blocks_per_sm, smem, st, (int)items);
             if (s != HELIOS_OK) return s;
         }
         return widths();
@@ -1332,7 +1351,7 @@ helios_status launch_scan(const ScanLaunch& L, cudaStream_t st) {
         e = cudaMemsetAsync(q, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) { cudaFreeAsync(q, st); delete p; return set_cuda_error("cudaMemsetAsync(queue)", e); }
         p->queue = q;
-        helios_status s = dispatch<kMaxLegs>(*p, L.mode, gk, threads, L.blocks_per_sm, smem, st, 0);
+        helios_status s = dispatch<kMaxLegs>(*p, kmode, gk, threads, L.blocks_per_sm, smem, st, 0);
         cudaFreeAsync(q, st);
         delete p;
         if (s != HELIOS_OK) return s;
@@ -1455,7 +1474,7 @@ helios_status launch_scan_static(const DevScene* scenes, int n_scenes, const Dev
         p.w_stride = warp_stride(mode, nb_cap, 0, direct);
         p.pk_cap = pk_cap; p.ht_cb = ht_cb;
         p.queue = g_static_ptr[dev] + g;
-        helios_status s = dispatch<kMaxLegs>(p, mode, gk, threads, blocks_per_sm, smem, st, 0);
+        helios_status s = dispatch<kMaxLegs>(p, kernel_mode(mode, true), gk, threads, blocks_per_sm, smem, st, 0);
         if (s != HELIOS_OK) return s;
     }
     // echo widths from the stored rows and bins (the caller provides echo_bin)
